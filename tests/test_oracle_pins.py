@@ -1,0 +1,409 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the mathematics and by
+textbook special cases, not against the oracle itself.
+
+Each test names what fixes the expected value: a textbook rule, an exact
+rational brute force (oracle.exact), a library routine used as an
+independent step (numpy's Gauss-Legendre rule and Legendre polynomials),
+or an invariant of linear elasticity (symmetry, rigid-body kernel, patch
+test, strain energy of a uniform strain, integration by parts).
+"""
+import math
+from fractions import Fraction as Fr
+
+import numpy as np
+import numpy.polynomial.legendre as npleg
+import pytest
+
+import oracle
+from oracle import exact
+import synthetic as syn
+
+
+# --------------------------------------------------------------------------
+# 1D rules
+# --------------------------------------------------------------------------
+def test_gauss_textbook_values():
+    # Gauss(2), Gauss(3) on [0,1]: 1/2 -+ 1/(2 sqrt 3); 1/2 -+ sqrt(3/5)/2 with 5/18, 8/18, 5/18.
+    x, w = oracle.gauss01(2)
+    np.testing.assert_allclose(x, [0.5 - 0.5 / np.sqrt(3), 0.5 + 0.5 / np.sqrt(3)], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(w, [0.5, 0.5], rtol=0, atol=1e-15)
+    x, w = oracle.gauss01(3)
+    h = 0.5 * np.sqrt(3.0 / 5.0)
+    np.testing.assert_allclose(x, [0.5 - h, 0.5, 0.5 + h], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(w, [5 / 18, 8 / 18, 5 / 18], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("q", range(1, 13))
+def test_gauss_matches_numpy_and_exactness(q):
+    x, w = oracle.gauss01(q)
+    t, v = npleg.leggauss(q)
+    np.testing.assert_allclose(x, (t + 1) / 2, rtol=0, atol=2e-15)
+    np.testing.assert_allclose(w, v / 2, rtol=0, atol=2e-15)
+    for k in range(2 * q):  # exact for degree <= 2q-1
+        assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) < 1e-14
+    # and not beyond: the textbook error of the q-point rule on [0,1] for x^(2q)
+    # is (q!)^4 / ((2q+1) ((2q)!)^2)
+    err = 1.0 / (2 * q + 1) - np.dot(w, x ** (2 * q))
+    theory = math.factorial(q) ** 4 / ((2 * q + 1) * math.factorial(2 * q) ** 2)
+    if theory > 1e-11:
+        assert abs(err - theory) <= 1e-3 * theory
+
+
+def test_gll_textbook_values():
+    np.testing.assert_allclose(oracle.gll01(1), [0, 1], atol=0)
+    np.testing.assert_allclose(oracle.gll01(2), [0, 0.5, 1], atol=1e-16)
+    s5 = np.sqrt(5) / 10
+    np.testing.assert_allclose(oracle.gll01(3), [0, 0.5 - s5, 0.5 + s5, 1], atol=1e-15)
+    s21 = np.sqrt(21) / 14
+    np.testing.assert_allclose(oracle.gll01(4), [0, 0.5 - s21, 0.5, 0.5 + s21, 1], atol=1e-15)
+
+
+@pytest.mark.parametrize("p", range(1, 11))
+def test_gll_interior_nodes_are_roots_of_dP(p):
+    x = oracle.gll01(p)
+    assert x[0] == 0.0 and x[-1] == 1.0 and np.all(np.diff(x) > 0)
+    dP = npleg.legder([0] * p + [1])
+    if p > 1:
+        assert np.max(np.abs(npleg.legval(2 * x[1:-1] - 1, dP))) < 1e-11 * p * p
+    np.testing.assert_allclose(x, 1 - x[::-1], atol=1e-15)  # symmetric
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
+def test_lagrange_basis_properties(p):
+    nodes = oracle.gll01(p)
+    val, der = oracle.lagrange(nodes, nodes)
+    np.testing.assert_allclose(val, np.eye(p + 1), atol=0)
+    rng = np.random.default_rng(p)
+    pts = rng.uniform(0, 1, 17)
+    val, der = oracle.lagrange(nodes, pts)
+    np.testing.assert_allclose(val.sum(0), 1.0, atol=1e-13)
+    np.testing.assert_allclose(der.sum(0), 0.0, atol=1e-11)
+    for deg in range(p + 1):  # reproduces polynomials and derivatives of degree <= p
+        c = rng.normal(size=deg + 1)
+        f = np.polynomial.Polynomial(c)
+        for xs in (pts, nodes):
+            v, d = oracle.lagrange(nodes, xs)
+            np.testing.assert_allclose(f(nodes) @ v, f(xs), atol=1e-12)
+            np.testing.assert_allclose(f(nodes) @ d, f.deriv()(xs), atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Reference stiffness blocks S_mn
+# --------------------------------------------------------------------------
+def _numpy_1d_integrals(p):
+    """int phi_i phi_j, int phi_i' phi_j, int phi_i' phi_j' on [0,1] with an
+    independent construction: the Lagrange basis expanded in shifted Legendre
+    polynomials (numpy.polynomial.legendre, Vandermonde solve on the GLL
+    nodes) and integrated with numpy's 30-point Gauss rule."""
+    nodes = oracle.gll01(p)
+    coef = np.linalg.inv(npleg.legvander(2 * nodes - 1, p))  # column i: l_i in Legendre basis
+    t, v = npleg.leggauss(30)
+    w = v / 2
+    P = npleg.legvander(t, p) @ coef
+    dcoef = np.stack([2 * npleg.legder(coef[:, i]) for i in range(p + 1)], axis=1)
+    dP = npleg.legvander(t, max(p - 1, 0))[:, :dcoef.shape[0]] @ dcoef
+    M = P.T @ (w[:, None] * P)
+    Dm = dP.T @ (w[:, None] * P)
+    K = dP.T @ (w[:, None] * dP)
+    return M, Dm, K
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+def test_ref_blocks_against_fubini(p):
+    S = oracle.ref(p).blocks()
+    M, Dm, K = _numpy_1d_integrals(p)
+    D = p + 1
+    mats = {(False, False): M, (True, False): Dm, (False, True): Dm.T, (True, True): K}
+    for m in range(3):
+        for n in range(3):
+            # tensor index a = ix + D*(iy + D*iz) -> kron order (z, y, x)
+            f = [mats[(k == m, k == n)] for k in range(3)]
+            ref = np.kron(f[2], np.kron(f[1], f[0]))
+            np.testing.assert_allclose(S[m, n], ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+    np.testing.assert_allclose(S.sum(axis=3), 0.0, atol=1e-12)  # grad of a constant is 0
+    for m in range(3):
+        for n in range(3):
+            np.testing.assert_allclose(S[m, n], S[n, m].T, atol=1e-14)
+
+
+def test_ref_blocks_exact_rational_p2():
+    S = oracle.ref(2).blocks()
+    R = exact.ref_gradient_integrals(2)
+    for m in range(3):
+        for n in range(3):
+            np.testing.assert_allclose(S[m, n], np.array(R[m][n], dtype=float), rtol=0, atol=2e-15)
+
+
+# --------------------------------------------------------------------------
+# Element matrix against the exact-rational brute force (p = 1, 2)
+# --------------------------------------------------------------------------
+J_RAT = [[Fr(1, 2), Fr(1, 10), Fr(0)], [Fr(-1, 8), Fr(1, 3), Fr(1, 7)], [Fr(1, 5), Fr(0), Fr(1)]]
+J_RAT2 = [[Fr(2, 3), Fr(0), Fr(-1, 9)], [Fr(1, 4), Fr(3, 4), Fr(0)], [Fr(0), Fr(1, 6), Fr(1, 2)]]
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_element_matrix_exact(p):
+    lam, mu = Fr(3, 2), Fr(2, 3)
+    Kx = np.array(exact.element_matrix(p, J_RAT, lam, mu), dtype=float)
+    Ko = oracle.ref(p).element_matrix(np.array(J_RAT, dtype=float), float(lam), float(mu))
+    assert np.max(np.abs(Ko - Kx)) <= 1e-13 * np.max(np.abs(Kx))
+    np.testing.assert_allclose(Ko, Ko.T, atol=1e-13 * np.abs(Ko).max())
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_global_two_element_exact(p):
+    lam, mu = Fr(1, 1), Fr(5, 7)
+    Ax = np.array(exact.global_matrix(p, 2, [J_RAT, J_RAT2], lam, mu), dtype=float)
+    aff = np.zeros((2, 12))
+    aff[0, :9] = np.array(J_RAT, dtype=float).reshape(9)
+    aff[1, :9] = np.array(J_RAT2, dtype=float).reshape(9)
+    Ao = oracle.assemble_dense(p, 2, 1, 1, aff, float(lam), float(mu))
+    scale = np.abs(Ax).max()
+    assert np.max(np.abs(Ao - Ax)) <= 1e-13 * scale
+    x = np.random.default_rng(0).uniform(-1, 1, Ax.shape[0])
+    y = oracle.apply(p, 2, 1, 1, aff, float(lam), float(mu), x)
+    assert np.max(np.abs(y - Ax @ x)) <= 1e-13 * scale * np.abs(x).sum() / len(x) * 10
+
+
+def test_trilinear_brick_is_textbook_p1():
+    # For p = 1 on the unit cube with lambda = 0, mu = 1/2 the x-x block of
+    # the stiffness equals the scalar Laplacian of the trilinear brick plus
+    # the d_x d_x term:  K_xx = 1/2 (Lap + Dxx).  Both are products of the
+    # 1D linear-element matrices  M = [[1/3,1/6],[1/6,1/3]],  K = [[1,-1],[-1,1]].
+    M = np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])
+    K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    Dxx = np.kron(M, np.kron(M, K1))
+    Lap = Dxx + np.kron(M, np.kron(K1, M)) + np.kron(K1, np.kron(M, M))
+    Ke = oracle.ref(1).element_matrix(np.eye(3), 0.0, 0.5)
+    np.testing.assert_allclose(Ke[:8, :8], 0.5 * (Lap + Dxx), atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Operator invariants on the global apply
+# --------------------------------------------------------------------------
+def _rand_mesh(n=2, seed=3):
+    return syn.random_affine_cube(n, seed)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_symmetry_and_positivity(p):
+    m = _rand_mesh()
+    lam, mu = syn.lame(1.0, 0.3)
+    N = m.n_dofs(p)
+    rng = np.random.default_rng(p)
+    x, y = rng.normal(size=N), rng.normal(size=N)
+    Ax = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, x)
+    Ay = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, y)
+    assert abs(y @ Ax - x @ Ay) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(Ay)
+    ess = syn.clamp_mask(m, p)
+    xc = np.where(ess, 0.0, x)
+    Axc = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, xc, ess=ess)
+    assert xc @ Axc > 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_translations_in_kernel_any_geometry(p):
+    m = _rand_mesh(seed=7)
+    lam, mu = syn.lame(1.0, 0.45)
+    Nn = m.n_nodes(p)
+    rng = np.random.default_rng(0)
+    scale = np.abs(oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, rng.uniform(-1, 1, 3 * Nn))).max()
+    for c in range(3):
+        t = np.zeros(3 * Nn)
+        t[c * Nn:(c + 1) * Nn] = 1.0
+        y = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, t)
+        assert np.abs(y).max() <= 1e-12 * scale
+
+
+M_GLOBAL = np.array([[1.3, 0.2, -0.1], [0.1, 0.9, 0.3], [-0.2, 0.15, 1.1]])
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_rotations_in_kernel_conforming(p):
+    n = 2
+    m = syn.globally_affine_mesh(n, n, n, M_GLOBAL, t=(0.3, -0.2, 0.5))
+    X = oracle.node_coords_box(n, n, n, p) @ M_GLOBAL.T + np.array([0.3, -0.2, 0.5])
+    lam, mu = syn.lame(2.0, 0.3)
+    rng = np.random.default_rng(1)
+    scale = np.abs(oracle.apply(p, n, n, n, m.affine, lam, mu, rng.uniform(-1, 1, 3 * len(X)))).max()
+    for w in np.eye(3):
+        u = np.cross(w, X)  # rigid rotation about axis w
+        y = oracle.apply(p, n, n, n, m.affine, lam, mu, u.T.reshape(-1))
+        assert np.abs(y).max() <= 1e-12 * scale
+
+
+def _interior_rows(n, p):
+    M1 = n * p + 1
+    g = np.arange(M1)
+    gz, gy, gx = np.meshgrid(g, g, g, indexing="ij")
+    inner = ((gx > 0) & (gx < M1 - 1) & (gy > 0) & (gy < M1 - 1) & (gz > 0) & (gz < M1 - 1)).reshape(-1)
+    return np.tile(inner, 3)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_patch_test_and_uniform_strain_energy(p):
+    n = 3
+    m = syn.globally_affine_mesh(n, n, n, M_GLOBAL, t=(0.1, 0.2, 0.3))
+    X = oracle.node_coords_box(n, n, n, p) @ M_GLOBAL.T + np.array([0.1, 0.2, 0.3])
+    lam, mu = syn.lame(1.0, 0.3)
+    Gd = np.array([[0.3, -0.7, 0.2], [0.5, 0.1, -0.4], [0.25, 0.6, -0.2]])
+    u = (X @ Gd.T + np.array([0.01, -0.02, 0.03])).T.reshape(-1)
+    y = oracle.apply(p, n, n, n, m.affine, lam, mu, u)
+    inner = _interior_rows(n, p)
+    assert np.abs(y[inner]).max() <= 1e-12 * np.abs(y).max()
+    eps = 0.5 * (Gd + Gd.T)
+    vol = np.linalg.det(M_GLOBAL)
+    energy = vol * (lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps))
+    assert abs(u @ y - energy) <= 1e-12 * energy
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_quadratic_field_integration_by_parts(p):
+    # u_c = 1/2 x^T H_c x  =>  div sigma is constant and for interior dofs
+    # (A u)_i = -int (div sigma) . phi_i  (no boundary term).
+    n = 3
+    m = syn.box_mesh(n, n, n, hi=(1.5, 1.0, 0.8))
+    X = oracle.node_coords_box(n, n, n, p, hi=(1.5, 1.0, 0.8))
+    lam, mu = 0.7, 0.4
+    rng = np.random.default_rng(5)
+    H = rng.normal(size=(3, 3, 3))
+    H = 0.5 * (H + H.transpose(0, 2, 1))
+    u = np.stack([0.5 * np.einsum("ni,ij,nj->n", X, H[c], X) for c in range(3)]).reshape(-1)
+    # d_j u_i = H_i[j,k] x_k ; div sigma_i = lam d_i div u + mu sum_j (d_j d_j u_i + d_i d_j u_j)
+    divsig = np.array([lam * sum(H[k][k][i] for k in range(3))
+                       + mu * (np.trace(H[i]) + sum(H[j][i][j] for j in range(3))) for i in range(3)])
+    y = oracle.apply(p, n, n, n, m.affine, lam, mu, u)
+    F = oracle.load(p, n, n, n, m.affine, f0=-divsig)
+    inner = _interior_rows(n, p)
+    assert np.abs(y[inner] - F[inner]).max() <= 1e-11 * np.abs(y).max()
+
+
+def test_linear_in_lame_and_scaling():
+    p = 2
+    m = _rand_mesh(seed=11)
+    x = np.random.default_rng(2).normal(size=m.n_dofs(p))
+    a = oracle.apply(p, 2, 2, 2, m.affine, 1.0, 0.0, x)
+    b = oracle.apply(p, 2, 2, 2, m.affine, 0.0, 1.0, x)
+    c = oracle.apply(p, 2, 2, 2, m.affine, 0.8, 0.3, x)
+    np.testing.assert_allclose(c, 0.8 * a + 0.3 * b, atol=1e-12 * np.abs(c).max())
+    # single element, J = s I: the stiffness scales like s^(d-2) = s
+    one = np.zeros((1, 12))
+    one[0, [0, 4, 8]] = 1.0
+    two = one.copy()
+    two[0, [0, 4, 8]] = 2.5
+    x1 = np.random.default_rng(3).normal(size=3 * 27)
+    y1 = oracle.apply(p, 1, 1, 1, one, 0.6, 0.9, x1)
+    y2 = oracle.apply(p, 1, 1, 1, two, 0.6, 0.9, x1)
+    np.testing.assert_allclose(y2, 2.5 * y1, atol=1e-13 * np.abs(y2).max())
+
+
+# --------------------------------------------------------------------------
+# Constraint, sampled rows, diagonal, load, transfers
+# --------------------------------------------------------------------------
+def test_constraint_semantics_and_rows():
+    p = 3
+    m = _rand_mesh(seed=4)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), 9)
+    y = oracle.apply(p, 2, 2, 2, m.affine, lam, mu, x, ess=ess)
+    e = ess.astype(bool)
+    np.testing.assert_array_equal(y[e], x[e])
+    x2 = x.copy()
+    x2[e] = 123.0
+    y2 = oracle.apply(p, 2, 2, 2, m.affine, lam, mu, x2, ess=ess)
+    np.testing.assert_array_equal(y2[~e], y[~e])
+    # matches the dense constrained matrix
+    A = oracle.constrain_dense(oracle.assemble_dense(p, 2, 2, 2, m.affine, lam, mu), ess)
+    np.testing.assert_allclose(y, A @ x, atol=1e-12 * np.abs(y).max())
+    rows = np.random.default_rng(0).choice(len(x), 200, replace=False)
+    yr = oracle.apply_rows(p, 2, 2, 2, m.affine, lam, mu, x, rows, ess=ess)
+    np.testing.assert_allclose(yr, y[rows], atol=1e-12 * np.abs(y).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_diag_equals_assembled_and_closed_form(p):
+    m = syn.random_affine_cube(2, 21)
+    lam, mu = syn.lame(3.0, 0.35)
+    ess = syn.clamp_mask(m, p)
+    d = oracle.diag(p, 2, 2, 2, m.affine, lam, mu, ess=ess)
+    A = oracle.assemble_dense(p, 2, 2, 2, m.affine, lam, mu)
+    e = ess.astype(bool)
+    np.testing.assert_allclose(d[~e], np.diag(A)[~e], rtol=1e-13)
+    assert np.all(d[e] == 1.0)
+    # closed form from 1D sums (independent numpy tables):
+    # diag_(i,c) = sum_e detJ sum_mn [(lam+mu) Ji_mc Ji_nc + mu sum_k Ji_mk Ji_nk] S^i_mn
+    Mi, Ci, Ki = (np.diag(a) for a in _numpy_1d_integrals(p))
+    D = p + 1
+    Nn = m.n_nodes(p)
+    dd = np.zeros(3 * Nn)
+    Mx = 2 * p + 1
+    for el in range(m.ne):
+        J = m.affine[el, :9].reshape(3, 3)
+        Ji, det = np.linalg.inv(J), np.linalg.det(J)
+        ex, ey, ez = el % 2, (el // 2) % 2, el // 4
+        for iz in range(D):
+            for iy in range(D):
+                for ix in range(D):
+                    i3 = (ix, iy, iz)
+                    S = np.empty((3, 3))
+                    for mm in range(3):
+                        for nn in range(3):
+                            v = 1.0
+                            for k in range(3):
+                                if k == mm and k == nn:
+                                    v *= Ki[i3[k]]
+                                elif k == mm or k == nn:
+                                    v *= Ci[i3[k]]
+                                else:
+                                    v *= Mi[i3[k]]
+                            S[mm, nn] = v
+                    g = (ex * p + ix) + Mx * ((ey * p + iy) + Mx * (ez * p + iz))
+                    G = Ji @ Ji.T
+                    for c in range(3):
+                        coef = (lam + mu) * np.outer(Ji[:, c], Ji[:, c]) + mu * G
+                        dd[c * Nn + g] += det * np.sum(coef * S)
+    np.testing.assert_allclose(d[~e], dd[~e], rtol=1e-12)
+
+
+def test_load_partition_of_unity():
+    p = 3
+    m = _rand_mesh(seed=8)
+    f0 = np.array([0.5, -1.0, 2.0])
+    F = oracle.load(p, 2, 2, 2, m.affine, f0=f0)
+    Nn = m.n_nodes(p)
+    vol = sum(np.linalg.det(m.affine[e, :9].reshape(3, 3)) for e in range(m.ne))
+    for c in range(3):
+        assert abs(F[c * Nn:(c + 1) * Nn].sum() - f0[c] * vol) <= 1e-13 * abs(f0[c] * vol)
+
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (4, 8), (1, 3)])
+def test_transfer_adjoint_and_polynomial_exactness(pc, pf):
+    n = 2
+    rng = np.random.default_rng(pc * 10 + pf)
+    u = rng.normal(size=3 * oracle.n_nodes(n, n, n, pc))
+    v = rng.normal(size=3 * oracle.n_nodes(n, n, n, pf))
+    Pu = oracle.prolong(pc, pf, n, n, n, u)
+    Rv = oracle.restrict(pc, pf, n, n, n, v)
+    assert abs(Pu @ v - u @ Rv) <= 1e-12 * np.linalg.norm(Pu) * np.linalg.norm(v)
+    # a global polynomial of degree <= pc in each variable is interpolated exactly
+    Xc = oracle.node_coords_box(n, n, n, pc)
+    Xf = oracle.node_coords_box(n, n, n, pf)
+
+    def field(X):
+        x, y, z = X.T
+        return np.stack([x ** pc * y + 0.3, (1 - z) ** pc * x, y ** pc - x * z]).reshape(-1)
+
+    np.testing.assert_allclose(oracle.prolong(pc, pf, n, n, n, field(Xc)), field(Xf), atol=1e-13)
+
+
+def test_dense_solve_residual():
+    p = 2
+    m = syn.box_mesh(2, 1, 1, hi=(2.0, 1.0, 1.0))
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    b = oracle.load(p, 2, 1, 1, m.affine, f0=(0, 0, -1), ess=ess)
+    x = oracle.solve_dense(p, 2, 1, 1, m.affine, lam, mu, b, ess)
+    r = b - oracle.apply(p, 2, 1, 1, m.affine, lam, mu, x, ess=ess)
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(b)
+    assert x[ess.astype(bool)].max() == 0.0
