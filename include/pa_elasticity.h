@@ -1,0 +1,159 @@
+/*
+ * pa_elasticity.h -- C ABI of the GB300 (sm_103a) matrix-free Partial
+ * Assembly operator for high-order linear elasticity on affine hexahedra,
+ * and of the p-multigrid preconditioned CG solver that it drives.
+ *
+ * Method: arXiv 2601.08374, "Shifting the Sweet Spot: High-Performance
+ * Matrix-Free Method for High-Order Elasticity".
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Mesh: structured nx*ny*nz grid of hexahedra, element e = ex + nx*(ey +
+ *    ny*ez).  Each element is the image of the reference cell [0,1]^3 under
+ *    its own affine map x = x0 + J xi (Sec. 4.4: J^-1 and det J are
+ *    constant per element).
+ *  - Space: H1 tensor-product Lagrange basis of degree p on the p+1
+ *    Gauss-Lobatto-Legendre nodes per direction (Eq. 6; Sec. 5.1.4),
+ *    integrated with q Gauss-Legendre points per direction (default
+ *    q = p + 2, Sec. 5.1.4).
+ *  - L-vector (all x, y, b, d arguments): component-major, 3*Nn entries with
+ *    Nn = (nx p + 1)(ny p + 1)(nz p + 1); entry (c, g) at c*Nn + g with the
+ *    global node g = gx + (nx p + 1)*(gy + (ny p + 1)*gz).
+ *  - Precision: PA_FP64 vectors are double, PA_FP32 vectors are float.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  All apply/solve calls are asynchronous on that stream
+ *    unless stated otherwise.
+ *  - Memory: device pointers are owned by the caller.  Handles own their
+ *    setup data and workspaces, allocated at create/setup time only; no
+ *    apply allocates memory.
+ *  - Errors: every function returns PA_OK (0) or a positive PA_E* code and
+ *    never aborts; pa_last_error() returns a thread-local message for the
+ *    last failure on the calling thread.
+ */
+#ifndef PA_ELASTICITY_H
+#define PA_ELASTICITY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum pa_status {
+    PA_OK = 0,
+    PA_EINVAL = 1,     /* invalid argument (sizes, degree, null handle, det J <= 0) */
+    PA_ENOMEM = 2,     /* device or host allocation failed                         */
+    PA_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error)  */
+    PA_ENOTCONV = 4,   /* solver reached its iteration cap                         */
+    PA_EBREAKDOWN = 5, /* solver breakdown: p^T A p <= 0 or a NaN/Inf reduction    */
+    PA_ETIMEOUT = 6,   /* a bounded device-side wait expired                       */
+    PA_EBUSY = 7       /* resource busy (e.g. server admission refused)            */
+};
+
+enum pa_precision { PA_FP64 = 0, PA_FP32 = 1 };
+
+typedef struct pa_mesh pa_mesh;
+typedef struct pa_op pa_op;
+typedef struct pa_solver pa_solver;
+
+/* Message describing the last error on this thread ("" if none). */
+const char *pa_last_error(void);
+
+/* ABI version (major*10000 + minor*100 + patch). */
+int pa_version(void);
+
+/* Lame parameters from Young's modulus E > 0 and Poisson ratio -1 < nu < 1/2:
+ * lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)).  The operator takes
+ * lambda and mu directly (Eq. 3); this helper is a convenience. */
+int pa_lame(double E, double nu, double *lambda, double *mu);
+
+/* ---------------------------------------------------------------- mesh -- */
+
+/* Create a structured mesh (host-side description; copied).
+ *   nx, ny, nz >= 1 : elements per direction.
+ *   box    : host double[6] = {xlo, ylo, zlo, xhi, yhi, zhi}; used only when
+ *            affine is NULL (then element maps are the uniform grid of box).
+ *   affine : host double[n_e][12] or NULL: per element J (row-major 3x3,
+ *            J[i][j] = d x_i / d xi_j) followed by x0[3].
+ * Fails with PA_EINVAL if a dimension is < 1 or some det J <= 0. */
+int pa_mesh_create(int nx, int ny, int nz, const double *box, const double *affine, pa_mesh **out);
+int pa_mesh_destroy(pa_mesh *mesh);
+
+/* ------------------------------------------------------------ operator -- */
+
+/* Partial-assembly setup of the elasticity operator (Sec. 2.2.2 and 4.4: the stored
+ * quadrature data D is J^-1 and w det J folded with lambda, mu per element).
+ *   p in 1..8, q = 0 (meaning p + 2) or q = p + 2.
+ *   lambda, mu : Lame parameters (mu > 0, lambda >= 0 expected).
+ *   precision  : PA_FP64 or PA_FP32 (arithmetic and vector type).
+ *   ess_mask   : host uint8[3*Nn] or NULL.  Non-zero entries are essential
+ *                (Dirichlet) dofs: the operator becomes the constrained one,
+ *                y = A z with z = x zeroed on essential dofs, then y = x there.
+ * The mesh may be destroyed after this call. */
+int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int precision,
+                const uint8_t *ess_mask, pa_op **out);
+int pa_op_destroy(pa_op *op);
+
+/* Sizes: number of L-vector entries (3*Nn), elements, degree, precision. */
+int pa_op_info(const pa_op *op, int64_t *ndofs, int64_t *nelem, int *p, int *precision);
+
+/* y = A x  (Sec. 4.2-4.5: gather, sum-factorised gradient, Voigt stress,
+ * transposed contraction, scatter).  x, y: device L-vectors of the op's
+ * precision; they must not alias.  y is overwritten. */
+int pa_op_apply(pa_op *op, const void *x, void *y, void *stream);
+
+/* Same computation with host buffers: copies x to the device, applies, and
+ * copies y back, all on `stream`; returns after y is on the host.  Host
+ * buffers should be pinned for full copy bandwidth. */
+int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream);
+
+/* d = diag(A) of the constrained operator (essential entries = 1), from the
+ * closed form built on 1D sums of w B^2, w B G, w G^2 (Sec. 3.1: the
+ * diagonal feeding the Chebyshev-Jacobi smoother).  d: device L-vector. */
+int pa_op_diag(pa_op *op, void *d, void *stream);
+
+/* Load vector of a body force (Eq. 5 right-hand side):
+ *   F_(i,c) = sum_e sum_alpha w_alpha det J f_c(x(alpha)) Phi_i(alpha),
+ *   f_c(x)  = f0[c] + sum_k amp sin(kx x + ky y + kz z + phase),
+ * modes: host double[3][nmodes][5] = (amp, kx, ky, kz, phase) or NULL.
+ * Essential entries are set to 0.  F: device L-vector of the op's precision. */
+int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void *F, void *stream);
+
+/* -------------------------------------------------------------- solver -- */
+
+typedef struct pa_solve_info {
+    int iterations;        /* outer iterations done                              */
+    int status;            /* PA_OK, PA_ENOTCONV or PA_EBREAKDOWN                */
+    double rel_residual;   /* true ||b - A x|| / ||b|| recomputed in FP64 at exit */
+    double b_norm;         /* ||b||_2                                             */
+    int inner_iterations;  /* mixed mode: total inner (FP32) iterations           */
+    int refinements;       /* mixed mode: outer refinement steps                  */
+    double lambda_max[8];  /* per level: power-iteration estimate of max eig(D^-1 A) */
+} pa_solve_info;
+
+enum pa_solve_mode { PA_SOLVE_FP64 = 0, PA_SOLVE_MIXED = 1 };
+
+/* GMG-PCG solver on the p-hierarchy of `fine` (Sec. 3): levels
+ * p_levels[0] = fine degree > p_levels[1] > ... > p_levels[nlev-1], all on the
+ * fine mesh with the same essential dofs.  Chebyshev(cheb_order)-Jacobi
+ * smoothing, V(1,1), lambda_max from 10 power iterations, interpolation
+ * prolongation and its transpose as restriction, and an FP64 Jacobi-CG
+ * coarse solve (coarse_rtol, coarse_maxit).  mode PA_SOLVE_MIXED builds FP32
+ * copies of the operators and smoothers for an FP64 iterative-refinement
+ * outer loop.  `fine` must be FP64 and must outlive the solver. */
+int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order, double coarse_rtol,
+                     int coarse_maxit, int mode, pa_solver **out);
+int pa_solver_destroy(pa_solver *s);
+
+/* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 (x: in = initial guess,
+ * out = solution; device double L-vectors).  Synchronises `stream` to test
+ * convergence; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in
+ * every case when non-NULL). */
+int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_ELASTICITY_H */

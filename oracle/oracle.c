@@ -19,7 +19,7 @@
  *   S_mn[a][b] = sum_alpha w_alpha d_m Phi_a(alpha) d_n Phi_b(alpha)
  * built by a brute-force sum over all quadrature points with full 3D basis
  * tables (no sum factorisation), and from the element's constant inverse
- * Jacobian (affine elements, Sec. 4.3).
+ * Jacobian (affine elements, Sec. 4.4).
  *
  * Conventions (shared with the product only through the documented ABI,
  * never through code):

@@ -1,0 +1,232 @@
+"""Python binding of the GB300 matrix-free PA elasticity library.
+
+Thin ctypes marshalling over the C ABI declared in ``include/pa_elasticity.h``
+(same function names).  Every step of the operator and the solver runs in the
+library's CUDA kernels; this module only passes pointers, sizes and streams.
+PyTorch provides device memory and streams.
+
+Importing this package fails loudly if ``libpa_elasticity.so`` has not been
+built (``python paper_2601_08374_gb300/build.py``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY = range(8)
+PA_FP64, PA_FP32 = 0, 1
+PA_SOLVE_FP64, PA_SOLVE_MIXED = 0, 1
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python paper_2601_08374_gb300/build.py`")
+
+lib = ctypes.CDLL(_LIB_PATH)
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class pa_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("b_norm", ctypes.c_double), ("inner_iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("lambda_max", ctypes.c_double * 8)]
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("pa_last_error", [], ctypes.c_char_p)
+_sig("pa_version", [])
+_sig("pa_lame", [ctypes.c_double, ctypes.c_double, _dp, _dp])
+_sig("pa_mesh_create", [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.POINTER(_vp)])
+_sig("pa_mesh_destroy", [_vp])
+_sig("pa_op_setup", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                     ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(_vp)])
+_sig("pa_op_destroy", [_vp])
+_sig("pa_op_info", [_vp, _i64p, _i64p, _ip, _ip])
+_sig("pa_op_apply", [_vp, _vp, _vp, _vp])
+_sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
+_sig("pa_op_diag", [_vp, _vp, _vp])
+_sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
+if hasattr(lib, "pa_solver_create"):
+    _sig("pa_solver_create", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(_vp)])
+    _sig("pa_solver_destroy", [_vp])
+    _sig("pa_gmg_pcg_solve", [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(pa_solve_info), _vp])
+
+
+class PAError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib.pa_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _check(code, where):
+    if code != PA_OK:
+        raise PAError(code, where)
+    return code
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(_dp)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names --
+def pa_version() -> int:
+    return lib.pa_version()
+
+
+def pa_lame(E: float, nu: float):
+    lam, mu = ctypes.c_double(), ctypes.c_double()
+    _check(lib.pa_lame(E, nu, ctypes.byref(lam), ctypes.byref(mu)), "pa_lame")
+    return lam.value, mu.value
+
+
+def pa_mesh_create(nx, ny, nz, box=None, affine=None):
+    h = _vp()
+    aff = None if affine is None else np.ascontiguousarray(affine, dtype=np.float64)
+    if aff is not None and aff.shape != (nx * ny * nz, 12):
+        raise ValueError("affine must be [n_e, 12]")
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    _check(lib.pa_mesh_create(nx, ny, nz, _dptr(bx), _dptr(aff), ctypes.byref(h)), "pa_mesh_create")
+    return h
+
+
+def pa_mesh_destroy(h):
+    lib.pa_mesh_destroy(h)
+
+
+def pa_op_setup(mesh, p, q, lam, mu, precision, ess_mask=None):
+    h = _vp()
+    m = None
+    if ess_mask is not None:
+        m = np.ascontiguousarray(ess_mask, dtype=np.uint8)
+    _check(lib.pa_op_setup(mesh, p, q, lam, mu, precision,
+                           m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if m is not None else None,
+                           ctypes.byref(h)), "pa_op_setup")
+    return h
+
+
+def pa_op_destroy(h):
+    lib.pa_op_destroy(h)
+
+
+def pa_op_info(op):
+    n, ne, p, prec = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.pa_op_info(op, ctypes.byref(n), ctypes.byref(ne), ctypes.byref(p), ctypes.byref(prec)), "pa_op_info")
+    return n.value, ne.value, p.value, prec.value
+
+
+def pa_op_apply(op, x, y, stream=None):
+    _check(lib.pa_op_apply(op, _tptr(x), _tptr(y), _stream_ptr(stream)), "pa_op_apply")
+
+
+def pa_op_apply_host(op, x_host, y_host, stream=None):
+    """x_host, y_host: CPU tensors (pinned for full bandwidth) or numpy arrays."""
+    xp = ctypes.c_void_p(x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data)
+    yp = ctypes.c_void_p(y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data)
+    _check(lib.pa_op_apply_host(op, xp, yp, _stream_ptr(stream)), "pa_op_apply_host")
+
+
+def pa_op_diag(op, d, stream=None):
+    _check(lib.pa_op_diag(op, _tptr(d), _stream_ptr(stream)), "pa_op_diag")
+
+
+def pa_op_rhs(op, F, f0=(0.0, 0.0, 0.0), modes=None, stream=None):
+    f0 = np.ascontiguousarray(f0, dtype=np.float64).reshape(3)
+    nm = 0
+    md = None
+    if modes is not None:
+        md = np.ascontiguousarray(modes, dtype=np.float64)
+        nm = md.shape[1]
+    _check(lib.pa_op_rhs(op, _dptr(f0), nm, _dptr(md) if nm else None, _tptr(F), _stream_ptr(stream)), "pa_op_rhs")
+
+
+def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-2, coarse_maxit=50, mode=PA_SOLVE_FP64):
+    h = _vp()
+    lv = (ctypes.c_int * len(p_levels))(*p_levels)
+    _check(lib.pa_solver_create(op, len(p_levels), lv, cheb_order, coarse_rtol, coarse_maxit, mode,
+                                ctypes.byref(h)), "pa_solver_create")
+    return h
+
+
+def pa_solver_destroy(h):
+    lib.pa_solver_destroy(h)
+
+
+def pa_gmg_pcg_solve(solver, b, x, rtol=1e-10, maxit=500, stream=None):
+    info = pa_solve_info()
+    code = lib.pa_gmg_pcg_solve(solver, _tptr(b), _tptr(x), rtol, maxit, ctypes.byref(info), _stream_ptr(stream))
+    if code not in (PA_OK, PA_ENOTCONV, PA_EBREAKDOWN):
+        raise PAError(code, "pa_gmg_pcg_solve")
+    return code, info
+
+
+# ------------------------------------------------------- object wrappers --
+class Operator:
+    """Owns a mesh + operator handle; vectors are torch CUDA tensors."""
+
+    def __init__(self, nx, ny, nz, affine, p, lam, mu, precision=PA_FP64, ess_mask=None, q=0):
+        import torch
+        self._mesh = pa_mesh_create(nx, ny, nz, affine=affine)
+        try:
+            self.h = pa_op_setup(self._mesh, p, q, lam, mu, precision, ess_mask)
+        finally:
+            pa_mesh_destroy(self._mesh)
+            self._mesh = None
+        self.ndofs, self.nelem, self.p, self.precision = pa_op_info(self.h)
+        self.dtype = torch.float64 if precision == PA_FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            pa_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def empty(self):
+        import torch
+        return torch.empty(self.ndofs, dtype=self.dtype, device="cuda")
+
+    def apply(self, x, y=None, stream=None):
+        if y is None:
+            y = self.empty()
+        pa_op_apply(self.h, x, y, stream)
+        return y
+
+    def diag(self, stream=None):
+        d = self.empty()
+        pa_op_diag(self.h, d, stream)
+        return d
+
+    def rhs(self, f0=(0.0, 0.0, 0.0), modes=None, stream=None):
+        F = self.empty()
+        pa_op_rhs(self.h, F, f0, modes, stream)
+        return F

@@ -1,0 +1,333 @@
+// C ABI of the PA elasticity operator: errors, mesh, operator setup/apply,
+// diagonal and load vector (declarations and contracts in pa_elasticity.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return PA_ECUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+static double det3(const double *J)
+{
+    return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+           J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+// Inverse by the adjugate.
+static void inverse3(const double *J, double det, double *Ji)
+{
+    double id = 1.0 / det;
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) * id;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) * id;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) * id;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+}
+
+// Sweep tuning table: (elements per CTA, threads) per degree and precision,
+// picked so that a CTA's shared memory stays near or below half an SM.
+ApplyLaunch default_apply_launch(int p, int precision)
+{
+    static const int epb64[kMaxP + 1] = {0, 16, 8, 6, 3, 2, 1, 1, 1};
+    static const int thr64[kMaxP + 1] = {0, 256, 256, 256, 256, 256, 256, 256, 512};
+    static const int epb32[kMaxP + 1] = {0, 32, 16, 12, 6, 4, 2, 2, 1};
+    static const int thr32[kMaxP + 1] = {0, 256, 256, 256, 256, 256, 256, 256, 512};
+    ApplyLaunch c;
+    c.variant = 0;
+    if (precision == PA_FP64) {
+        c.epb = epb64[p];
+        c.threads = thr64[p];
+    } else {
+        c.epb = epb32[p];
+        c.threads = thr32[p];
+    }
+    return c;
+}
+
+template <typename T>
+static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t s)
+{
+    ApplyArgs<T> a;
+    a.x = x;
+    a.ye = static_cast<T *>(op->d_ye);
+    a.geo = static_cast<const T *>(op->d_geo);
+    a.ess = op->d_ess;
+    a.g = op->g;
+    const Tables<T> *tab;
+    if constexpr (sizeof(T) == 8) tab = &op->tab64;
+    else tab = &op->tab32;
+    int rc = launch_apply_elements<T>(a, *tab, op->launch, s);
+    if (rc) return rc;
+    return launch_assemble<T>(a.ye, y, x, op->d_ess, T(0), accumulate, op->g, s);
+}
+
+}  // namespace pa
+
+using namespace pa;
+
+extern "C" {
+
+const char *pa_last_error(void) { return g_last_error.c_str(); }
+
+int pa_version(void) { return 100; }
+
+int pa_lame(double E, double nu, double *lambda, double *mu)
+{
+    if (!lambda || !mu) return set_error(PA_EINVAL, "pa_lame: null output");
+    if (!(E > 0) || !(nu > -1.0) || !(nu < 0.5)) return set_error(PA_EINVAL, "pa_lame: need E > 0, -1 < nu < 1/2");
+    *lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    *mu = E / (2.0 * (1.0 + nu));
+    return PA_OK;
+}
+
+int pa_mesh_create(int nx, int ny, int nz, const double *box, const double *affine, pa_mesh **out)
+{
+    if (!out) return set_error(PA_EINVAL, "pa_mesh_create: null output");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return set_error(PA_EINVAL, "pa_mesh_create: dimensions must be >= 1");
+    int64_t ne = (int64_t)nx * ny * nz;
+    if (ne > (int64_t)1 << 31) return set_error(PA_EINVAL, "pa_mesh_create: too many elements");
+    pa_mesh *m = new (std::nothrow) pa_mesh;
+    if (!m) return set_error(PA_ENOMEM, "pa_mesh_create: host allocation");
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    try {
+        m->affine.assign((size_t)ne * 12, 0.0);
+    } catch (...) {
+        delete m;
+        return set_error(PA_ENOMEM, "pa_mesh_create: host allocation");
+    }
+    if (affine) {
+        std::memcpy(m->affine.data(), affine, sizeof(double) * 12 * (size_t)ne);
+    } else {
+        double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+        if (box)
+            for (int i = 0; i < 3; ++i) {
+                lo[i] = box[i];
+                hi[i] = box[3 + i];
+            }
+        double h[3] = {(hi[0] - lo[0]) / nx, (hi[1] - lo[1]) / ny, (hi[2] - lo[2]) / nz};
+        for (int ez = 0; ez < nz; ++ez)
+            for (int ey = 0; ey < ny; ++ey)
+                for (int ex = 0; ex < nx; ++ex) {
+                    double *A = m->affine.data() + 12 * ((size_t)ex + (size_t)nx * (ey + (size_t)ny * ez));
+                    A[0] = h[0];
+                    A[4] = h[1];
+                    A[8] = h[2];
+                    A[9] = lo[0] + ex * h[0];
+                    A[10] = lo[1] + ey * h[1];
+                    A[11] = lo[2] + ez * h[2];
+                }
+    }
+    for (int64_t e = 0; e < ne; ++e) {
+        double d = det3(m->affine.data() + 12 * e);
+        if (!(d > 0.0) || !std::isfinite(d)) {
+            delete m;
+            return set_error(PA_EINVAL, "pa_mesh_create: element " + std::to_string(e) + " has det J <= 0");
+        }
+    }
+    *out = m;
+    clear_error();
+    return PA_OK;
+}
+
+int pa_mesh_destroy(pa_mesh *mesh)
+{
+    delete mesh;
+    return PA_OK;
+}
+
+int pa_op_destroy(pa_op *op)
+{
+    if (!op) return PA_OK;
+    cudaFree(op->d_geo);
+    cudaFree(op->d_affine);
+    cudaFree(op->d_ess);
+    cudaFree(op->d_ye);
+    cudaFree(op->d_xh);
+    cudaFree(op->d_yh);
+    delete op;
+    return PA_OK;
+}
+
+int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int precision,
+                const uint8_t *ess_mask, pa_op **out)
+{
+    if (!out) return set_error(PA_EINVAL, "pa_op_setup: null output");
+    *out = nullptr;
+    if (!mesh) return set_error(PA_EINVAL, "pa_op_setup: null mesh");
+    if (p < 1 || p > kMaxP) return set_error(PA_EINVAL, "pa_op_setup: p must be in 1..8");
+    if (q == 0) q = p + 2;
+    if (q != p + 2) return set_error(PA_EINVAL, "pa_op_setup: only q = p + 2 is instantiated");
+    if (precision != PA_FP64 && precision != PA_FP32) return set_error(PA_EINVAL, "pa_op_setup: bad precision");
+    if (!std::isfinite(lambda) || !std::isfinite(mu)) return set_error(PA_EINVAL, "pa_op_setup: non-finite Lame parameters");
+
+    pa_op *op = new (std::nothrow) pa_op;
+    if (!op) return set_error(PA_ENOMEM, "pa_op_setup: host allocation");
+    op->p = p;
+    op->q = q;
+    op->precision = precision;
+    op->lambda = lambda;
+    op->mu = mu;
+    op->elem = precision == PA_FP64 ? 8 : 4;
+    Grid &g = op->g;
+    g.nx = mesh->nx;
+    g.ny = mesh->ny;
+    g.nz = mesh->nz;
+    g.p = p;
+    g.Mx = mesh->nx * p + 1;
+    g.My = mesh->ny * p + 1;
+    g.Mz = mesh->nz * p + 1;
+    g.ne = (int64_t)mesh->nx * mesh->ny * mesh->nz;
+    g.Nn = (int64_t)g.Mx * g.My * g.Mz;
+    op->basis.build(p, q);
+    fill_tables(op->basis, op->tab64);
+    fill_tables(op->basis, op->tab32);
+    op->launch = default_apply_launch(p, precision);
+
+    const int D = p + 1;
+    const size_t D3 = (size_t)D * D * D;
+    const size_t geo_bytes = (size_t)g.ne * kGeoStride * op->elem;
+    std::vector<unsigned char> geo(geo_bytes);
+    for (int64_t e = 0; e < g.ne; ++e) {
+        const double *J = mesh->affine.data() + 12 * e;
+        double det = det3(J), Ji[9];
+        inverse3(J, det, Ji);
+        double rec[kGeoStride] = {Ji[0], Ji[1], Ji[2], Ji[3], Ji[4], Ji[5], Ji[6], Ji[7], Ji[8],
+                                  lambda * det, mu * det, det};
+        for (int k = 0; k < kGeoStride; ++k) {
+            if (precision == PA_FP64) reinterpret_cast<double *>(geo.data())[e * kGeoStride + k] = rec[k];
+            else reinterpret_cast<float *>(geo.data())[e * kGeoStride + k] = (float)rec[k];
+        }
+    }
+    cudaError_t err;
+    const size_t N = (size_t)3 * g.Nn;
+    if ((err = cudaMalloc(&op->d_geo, geo_bytes)) != cudaSuccess ||
+        (err = cudaMalloc((void **)&op->d_affine, sizeof(double) * 12 * (size_t)g.ne)) != cudaSuccess ||
+        (err = cudaMalloc(&op->d_ye, (size_t)g.ne * 3 * D3 * op->elem)) != cudaSuccess ||
+        (err = cudaMalloc(&op->d_xh, N * op->elem)) != cudaSuccess ||
+        (err = cudaMalloc(&op->d_yh, N * op->elem)) != cudaSuccess) {
+        int rc = err == cudaErrorMemoryAllocation ? set_error(PA_ENOMEM, "pa_op_setup: device allocation failed")
+                                                  : cuda_error(err, "pa_op_setup: cudaMalloc");
+        pa_op_destroy(op);
+        return rc;
+    }
+    if ((err = cudaMemcpy(op->d_geo, geo.data(), geo_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(op->d_affine, mesh->affine.data(), sizeof(double) * 12 * (size_t)g.ne,
+                          cudaMemcpyHostToDevice)) != cudaSuccess) {
+        pa_op_destroy(op);
+        return cuda_error(err, "pa_op_setup: cudaMemcpy");
+    }
+    if (ess_mask) {
+        if ((err = cudaMalloc((void **)&op->d_ess, N)) != cudaSuccess ||
+            (err = cudaMemcpy(op->d_ess, ess_mask, N, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            pa_op_destroy(op);
+            return cuda_error(err, "pa_op_setup: essential mask");
+        }
+    }
+    *out = op;
+    clear_error();
+    return PA_OK;
+}
+
+int pa_op_info(const pa_op *op, int64_t *ndofs, int64_t *nelem, int *p, int *precision)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_info: null op");
+    if (ndofs) *ndofs = op->ndofs();
+    if (nelem) *nelem = op->g.ne;
+    if (p) *p = op->p;
+    if (precision) *precision = op->precision;
+    return PA_OK;
+}
+
+int pa_op_apply(pa_op *op, const void *x, void *y, void *stream)
+{
+    if (!op || !x || !y) return set_error(PA_EINVAL, "pa_op_apply: null argument");
+    if (x == y) return set_error(PA_EINVAL, "pa_op_apply: x and y must not alias");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op->precision == PA_FP64)
+        return apply_impl<double>(op, static_cast<const double *>(x), static_cast<double *>(y), false, s);
+    return apply_impl<float>(op, static_cast<const float *>(x), static_cast<float *>(y), false, s);
+}
+
+int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream)
+{
+    if (!op || !x_host || !y_host) return set_error(PA_EINVAL, "pa_op_apply_host: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t bytes = (size_t)op->ndofs() * op->elem;
+    PA_CUDA_TRY(cudaMemcpyAsync(op->d_xh, x_host, bytes, cudaMemcpyHostToDevice, s));
+    int rc = pa_op_apply(op, op->d_xh, op->d_yh, stream);
+    if (rc) return rc;
+    PA_CUDA_TRY(cudaMemcpyAsync(y_host, op->d_yh, bytes, cudaMemcpyDeviceToHost, s));
+    PA_CUDA_TRY(cudaStreamSynchronize(s));
+    return PA_OK;
+}
+
+int pa_op_diag(pa_op *op, void *d, void *stream)
+{
+    if (!op || !d) return set_error(PA_EINVAL, "pa_op_diag: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (op->precision == PA_FP64) {
+        rc = launch_diag_elements<double>(static_cast<const double *>(op->d_geo), static_cast<double *>(op->d_ye),
+                                          op->basis, op->g, s);
+        if (!rc)
+            rc = launch_assemble<double>(static_cast<const double *>(op->d_ye), static_cast<double *>(d), nullptr,
+                                         op->d_ess, 1.0, false, op->g, s);
+    } else {
+        rc = launch_diag_elements<float>(static_cast<const float *>(op->d_geo), static_cast<float *>(op->d_ye),
+                                         op->basis, op->g, s);
+        if (!rc)
+            rc = launch_assemble<float>(static_cast<const float *>(op->d_ye), static_cast<float *>(d), nullptr,
+                                        op->d_ess, 1.0f, false, op->g, s);
+    }
+    return rc;
+}
+
+int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void *F, void *stream)
+{
+    if (!op || !F) return set_error(PA_EINVAL, "pa_op_rhs: null argument");
+    if (nmodes > 0 && !modes) return set_error(PA_EINVAL, "pa_op_rhs: modes is null");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (op->precision == PA_FP64) {
+        rc = launch_rhs_elements<double>(op->d_affine, static_cast<double *>(op->d_ye), op->basis, op->g, f0, nmodes,
+                                         modes, s);
+        if (!rc)
+            rc = launch_assemble<double>(static_cast<const double *>(op->d_ye), static_cast<double *>(F), nullptr,
+                                         op->d_ess, 0.0, false, op->g, s);
+    } else {
+        rc = launch_rhs_elements<float>(op->d_affine, static_cast<float *>(op->d_ye), op->basis, op->g, f0, nmodes,
+                                        modes, s);
+        if (!rc)
+            rc = launch_assemble<float>(static_cast<const float *>(op->d_ye), static_cast<float *>(F), nullptr,
+                                        op->d_ess, 0.0f, false, op->g, s);
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// Element-to-node assembly, the closed-form PA diagonal and the load vector.
+#include <cstdint>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+__host__ __device__ inline void node_coords(int64_t gn, const Grid &g, int &gx, int &gy, int &gz)
+{
+    gx = (int)(gn % g.Mx);
+    int64_t t = gn / g.Mx;
+    gy = (int)(t % g.My);
+    gz = (int)(t / g.My);
+}
+
+// Elements along one axis that hold global index gi: up to two (lower first).
+__device__ inline int axis_owners(int gi, int n, int p, int *e, int *i)
+{
+    int k = gi / p, r = gi - k * p, cnt = 0;
+    if (r == 0) {
+        if (k - 1 >= 0) { e[cnt] = k - 1; i[cnt] = p; ++cnt; }
+        if (k < n) { e[cnt] = k; i[cnt] = 0; ++cnt; }
+    } else {
+        e[cnt] = k; i[cnt] = r; ++cnt;
+    }
+    return cnt;
+}
+
+unsigned grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > (int64_t)152 * 64) b = (int64_t)152 * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- assembly --
+// Owner-computes Gather-transpose (G^T of the operator chain, Sec. 2.2):
+// every global node sums the E-vector entries of the (at most 8) elements
+// that hold it, in increasing element order, so the result is
+// deterministic.  Essential rows take xin (constrained operator) or
+// ess_value.
+template <typename T>
+__global__ void assemble_kernel(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
+                                const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g)
+{
+    const int p = g.p, D = p + 1, D3 = D * D * D;
+    for (int64_t gn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gn < g.Nn;
+         gn += (int64_t)gridDim.x * blockDim.x) {
+        int gx, gy, gz;
+        node_coords(gn, g, gx, gy, gz);
+        int ex[2], ix[2], ey[2], iy[2], ez[2], iz[2];
+        int nx_ = axis_owners(gx, g.nx, p, ex, ix);
+        int ny_ = axis_owners(gy, g.ny, p, ey, iy);
+        int nz_ = axis_owners(gz, g.nz, p, ez, iz);
+        T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+        for (int c = 0; c < nz_; ++c)
+            for (int b = 0; b < ny_; ++b)
+                for (int a = 0; a < nx_; ++a) {
+                    int64_t e = ex[a] + (int64_t)g.nx * (ey[b] + (int64_t)g.ny * ez[c]);
+                    int loc = ix[a] + D * (iy[b] + D * iz[c]);
+                    const T *base = ye + e * 3 * D3 + loc;
+                    acc0 += base[0];
+                    acc1 += base[D3];
+                    acc2 += base[2 * D3];
+                }
+        T acc[3] = {acc0, acc1, acc2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int64_t k = c * g.Nn + gn;
+            T v = acc[c];
+            if (ess && ess[k]) v = xin ? xin[k] : ess_value;
+            y[k] = accumulate ? y[k] + v : v;
+        }
+    }
+}
+
+template <typename T>
+int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,
+                    const Grid &g, cudaStream_t s)
+{
+    const int th = 256;
+    assemble_kernel<T><<<grid_for(g.Nn, th), th, 0, s>>>(ye, y, xin, ess, ess_value, accumulate ? 1 : 0, g);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_assemble<double>(const double *, double *, const double *, const uint8_t *, double, bool,
+                                     const Grid &, cudaStream_t);
+template int launch_assemble<float>(const float *, float *, const float *, const uint8_t *, float, bool,
+                                    const Grid &, cudaStream_t);
+
+// -------------------------------------------------------------- diagonal --
+struct DiagTables {
+    double M[kMaxD], C[kMaxD], K[kMaxD];  // sum_q w B^2, w B G, w G^2
+};
+
+// Element part of diag(A) in closed form: for dof (a, c) of element e,
+//   sum_mn [ (lambda+mu) detJ Ji[m][c] Ji[n][c] + mu detJ (Ji Ji^T)[m][n] ] S^a_mn
+// where S^a_mn = sum_alpha w d_m Phi_a d_n Phi_a factorises into products of
+// the 1D sums M, C, K (tensor-product basis, Eq. 6).
+template <typename T>
+__global__ void diag_elements_kernel(const T *__restrict__ geo, T *__restrict__ ye, DiagTables t, Grid g)
+{
+    const int D = g.p + 1, D3 = D * D * D;
+    const int64_t total = g.ne * D3;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = o / D3;
+        int a = (int)(o - e * D3);
+        int i3[3] = {a % D, (a / D) % D, a / (D * D)};
+        double S[3][3];
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n) {
+                double v = 1.0;
+                for (int k = 0; k < 3; ++k) {
+                    int i = i3[k];
+                    v *= (k == m && k == n) ? t.K[i] : ((k == m || k == n) ? t.C[i] : t.M[i]);
+                }
+                S[m][n] = v;
+            }
+        const T *gp = geo + e * kGeoStride;
+        double Ji[9];
+        for (int k = 0; k < 9; ++k) Ji[k] = (double)gp[k];
+        double cl = (double)gp[9], cm = (double)gp[10];
+        double JJ[3][3];
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n)
+                JJ[m][n] = Ji[m * 3 + 0] * Ji[n * 3 + 0] + Ji[m * 3 + 1] * Ji[n * 3 + 1] + Ji[m * 3 + 2] * Ji[n * 3 + 2];
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m)
+                for (int n = 0; n < 3; ++n)
+                    s += ((cl + cm) * Ji[m * 3 + c] * Ji[n * 3 + c] + cm * JJ[m][n]) * S[m][n];
+            ye[(e * 3 + c) * D3 + a] = (T)s;
+        }
+    }
+}
+
+template <typename T>
+int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s)
+{
+    DiagTables t{};
+    for (int i = 0; i < b.D; ++i) {
+        t.M[i] = b.Md[i];
+        t.C[i] = b.Cd[i];
+        t.K[i] = b.Kd[i];
+    }
+    const int th = 256;
+    int64_t total = g.ne * b.D * b.D * b.D;
+    diag_elements_kernel<T><<<grid_for(total, th), th, 0, s>>>(geo, ye, t, g);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_diag_elements<double>(const double *, double *, const Basis1D &, const Grid &, cudaStream_t);
+template int launch_diag_elements<float>(const float *, float *, const Basis1D &, const Grid &, cudaStream_t);
+
+// ----------------------------------------------------------- load vector --
+constexpr int kMaxModes = 16;
+struct RhsParams {
+    double B[kMaxD * kMaxQ];
+    double qx[kMaxQ], qw[kMaxQ];
+    double f0[3];
+    double modes[3 * kMaxModes * 5];
+    int nmodes;
+};
+
+// One CTA per element: f_c(x(alpha)) w_alpha detJ at every quadrature point
+// into shared memory, then F_(a,c) = sum_alpha fq_c(alpha) Phi_a(alpha).
+template <typename T>
+__global__ void rhs_elements_kernel(const double *__restrict__ affine, T *__restrict__ ye, RhsParams P, Grid g)
+{
+    extern __shared__ double fq[];  // [3][Q^3]
+    const int D = g.p + 1, D3 = D * D * D;
+    const int Q = g.p + 2, Q3 = Q * Q * Q;
+    for (int64_t e = blockIdx.x; e < g.ne; e += gridDim.x) {
+        const double *A = affine + e * 12;
+        double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+        for (int al = threadIdx.x; al < Q3; al += blockDim.x) {
+            int qx = al % Q, qy = (al / Q) % Q, qz = al / (Q * Q);
+            double xi[3] = {P.qx[qx], P.qx[qy], P.qx[qz]};
+            double X[3];
+            for (int i = 0; i < 3; ++i) X[i] = A[9 + i] + A[3 * i] * xi[0] + A[3 * i + 1] * xi[1] + A[3 * i + 2] * xi[2];
+            double w = P.qw[qx] * P.qw[qy] * P.qw[qz] * det;
+            for (int c = 0; c < 3; ++c) {
+                double f = P.f0[c];
+                for (int k = 0; k < P.nmodes; ++k) {
+                    const double *md = P.modes + (c * P.nmodes + k) * 5;
+                    f += md[0] * sin(md[1] * X[0] + md[2] * X[1] + md[3] * X[2] + md[4]);
+                }
+                fq[c * Q3 + al] = w * f;
+            }
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < 3 * D3; o += blockDim.x) {
+            int c = o / D3, a = o - c * D3;
+            int ix = a % D, iy = (a / D) % D, iz = a / (D * D);
+            double s = 0.0;
+            for (int qz = 0; qz < Q; ++qz)
+                for (int qy = 0; qy < Q; ++qy) {
+                    double byz = P.B[iy * Q + qy] * P.B[iz * Q + qz];
+                    const double *f = fq + c * Q3 + (qz * Q + qy) * Q;
+                    double t = 0.0;
+                    for (int qx = 0; qx < Q; ++qx) t += f[qx] * P.B[ix * Q + qx];
+                    s += t * byz;
+                }
+            ye[(e * 3 + c) * D3 + a] = (T)s;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+int launch_rhs_elements(const double *affine, T *ye, const Basis1D &b, const Grid &g, const double *f0,
+                        int nmodes, const double *modes, cudaStream_t s)
+{
+    if (nmodes < 0 || nmodes > kMaxModes) return set_error(PA_EINVAL, "rhs: at most 16 modes per component");
+    if (b.Q != b.p + 2) return set_error(PA_EINVAL, "rhs: q must be p + 2");
+    RhsParams P{};
+    for (int i = 0; i < b.D * b.Q; ++i) P.B[i] = b.B[i];
+    for (int k = 0; k < b.Q; ++k) {
+        P.qx[k] = b.qpts[k];
+        P.qw[k] = b.qwts[k];
+    }
+    for (int c = 0; c < 3; ++c) P.f0[c] = f0 ? f0[c] : 0.0;
+    P.nmodes = nmodes;
+    for (int i = 0; i < 3 * nmodes * 5; ++i) P.modes[i] = modes[i];
+    size_t smem = sizeof(double) * 3 * b.Q * b.Q * b.Q;
+    int64_t nb = g.ne < (int64_t)152 * 32 ? g.ne : (int64_t)152 * 32;
+    rhs_elements_kernel<T><<<(unsigned)nb, 128, smem, s>>>(affine, ye, P, g);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_rhs_elements<double>(const double *, double *, const Basis1D &, const Grid &, const double *, int,
+                                         const double *, cudaStream_t);
+template int launch_rhs_elements<float>(const double *, float *, const Basis1D &, const Grid &, const double *, int,
+                                        const double *, cudaStream_t);
+
+}  // namespace pa

@@ -1,0 +1,130 @@
+// Internal declarations of the PA elasticity library (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pa_elasticity.h"
+
+namespace pa {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxD = kMaxP + 1;
+constexpr int kMaxQ = kMaxP + 2;
+
+// ---------------------------------------------------------------- errors --
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
+#define PA_CUDA_TRY(call)                                       \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::pa::cuda_error(_e, #call); \
+    } while (0)
+
+// ------------------------------------------------------------ 1D rules --
+// Gauss-Legendre points/weights on [0,1]; GLL nodes on [0,1]; Lagrange
+// values/derivatives (product formula).  Host, double precision.
+void gauss_legendre_01(int q, double *x, double *w);
+void gll_nodes_01(int p, double *x);
+void lagrange_product(int n, const double *nodes, int m, const double *pts, double *val, double *der);
+
+// Reference tables of one (p, q): tab[i*Q + k] layout (dof i, point k).
+struct Basis1D {
+    int p = 0, D = 0, Q = 0;
+    std::vector<double> nodes, qpts, qwts;
+    std::vector<double> B, G;    // l_i(xi_k), l_i'(xi_k)
+    std::vector<double> Bw, Gw;  // times the weight w_k (transposed sweeps)
+    std::vector<double> Md, Cd, Kd;  // sum_k w B^2, w B G, w G^2 per dof i
+    void build(int p, int q);
+};
+
+// Kernel-parameter tables (passed by value; constant-bank operands).
+template <typename T>
+struct Tables {
+    T B[kMaxD * kMaxQ];
+    T G[kMaxD * kMaxQ];
+    T Bw[kMaxD * kMaxQ];
+    T Gw[kMaxD * kMaxQ];
+};
+
+template <typename T>
+void fill_tables(const Basis1D &b, Tables<T> &t);
+
+// Geometry record per element (12 values of the op's precision):
+// J^-1 row-major (9), lambda*detJ, mu*detJ, detJ.
+constexpr int kGeoStride = 12;
+
+struct Grid {
+    int nx, ny, nz, p;
+    int Mx, My, Mz;
+    int64_t ne, Nn;
+};
+
+// --------------------------------------------------------- apply launch --
+struct ApplyLaunch {
+    int variant = 0;  // 0: flattened smem sweeps
+    int epb = 1;      // elements per CTA
+    int threads = 256;
+};
+
+template <typename T>
+struct ApplyArgs {
+    const T *x;          // L-vector (3*Nn)
+    T *ye;               // E-vector scratch [ne][3][D^3]
+    const T *geo;        // [ne][kGeoStride]
+    const uint8_t *ess;  // [3*Nn] or nullptr
+    Grid g;
+};
+
+template <typename T>
+int launch_apply_elements(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg,
+                          cudaStream_t s);
+template <typename T>
+size_t apply_smem_bytes(int p, const ApplyLaunch &cfg);
+ApplyLaunch default_apply_launch(int p, int precision);
+
+// E-vector -> L-vector sum (owner-computes per node, fixed order);
+// constrained rows take xin (or `ess_value` when xin is null).
+template <typename T>
+int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,
+                    const Grid &g, cudaStream_t s);
+
+// Closed-form PA diagonal per element into the E-vector.
+template <typename T>
+int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s);
+
+// Load vector per element into the E-vector.
+template <typename T>
+int launch_rhs_elements(const double *affine, T *ye, const Basis1D &b, const Grid &g, const double *f0,
+                        int nmodes, const double *d_modes, cudaStream_t s);
+
+}  // namespace pa
+
+// ------------------------------------------------------------- handles --
+struct pa_mesh {
+    int nx, ny, nz;
+    std::vector<double> affine;  // [ne][12]
+};
+
+struct pa_op {
+    pa::Grid g{};
+    int p = 0, q = 0, precision = PA_FP64;
+    double lambda = 0, mu = 0;
+    size_t elem = 8;  // bytes per scalar
+    pa::Basis1D basis;
+    pa::Tables<double> tab64{};
+    pa::Tables<float> tab32{};
+    pa::ApplyLaunch launch{};
+    void *d_geo = nullptr;       // [ne][12] of the op's precision
+    double *d_affine = nullptr;  // [ne][12] double (rhs only)
+    uint8_t *d_ess = nullptr;    // [3*Nn] or null
+    void *d_ye = nullptr;        // E-vector scratch
+    void *d_xh = nullptr;        // device staging for apply_host
+    void *d_yh = nullptr;
+    int64_t ndofs() const { return 3 * g.Nn; }
+};

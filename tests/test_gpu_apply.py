@@ -1,0 +1,144 @@
+"""Parity of the CUDA operator (apply, diagonal, load vector) with the CPU
+oracle, element by element, through the C ABI.
+
+Tolerances (relative max-norm, against max |oracle|): FP64 1e-12, FP32 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def pa():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_08374_gb300 as pa
+    return pa
+
+
+def _relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _run_apply(pa, mesh, p, lam, mu, x, prec, ess=None):
+    op = pa.Operator(mesh.nx, mesh.ny, mesh.nz, mesh.affine, p, lam, mu, precision=prec, ess_mask=ess)
+    xt = torch.tensor(x, dtype=op.dtype, device="cuda")
+    y = op.apply(xt)
+    torch.cuda.synchronize()
+    out = y.double().cpu().numpy()
+    op.close()
+    return out
+
+
+# meshes with several CTAs and a ragged last CTA for every degree
+MESH_DIMS = {1: (5, 4, 3), 2: (5, 3, 2), 3: (3, 3, 2), 4: (3, 2, 2), 5: (3, 2, 1), 6: (2, 2, 1), 7: (3, 1, 1),
+             8: (2, 1, 1)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_apply_random_affine(pa, p, prec):
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=100 + p, ny=ny, nz=nz)
+    lam, mu = syn.lame(1.0, 0.3)
+    x = syn.uniform_vector(m.n_dofs(p), seed=p)
+    y = _run_apply(pa, m, p, lam, mu, x, prec)
+    yo = oracle.apply(p, nx, ny, nz, m.affine, lam, mu, x)
+    assert _relerr(y, yo) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config_small_cube_clamped(pa, prec):
+    # 4x4x4 unit cube, p = 2, E = 1, nu = 0.3, x = 0 face clamped, x ~ U[-1,1] seed 0
+    m = syn.box_mesh(4, 4, 4)
+    p = 2
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=0)
+    assert len(x) == 2187
+    y = _run_apply(pa, m, p, lam, mu, x, prec, ess)
+    yo = oracle.apply(p, 4, 4, 4, m.affine, lam, mu, x, ess=ess)
+    assert _relerr(y, yo) <= TOL[prec]
+    e = ess.astype(bool)
+    if prec == 0:
+        np.testing.assert_array_equal(y[e], x[e])
+
+
+@pytest.mark.parametrize("p", [1, 4, 8])
+def test_single_element_and_thin_meshes(pa, p):
+    lam, mu = 0.8, 0.5
+    for dims in [(1, 1, 1), (1, 3, 1), (2, 1, 3)]:
+        m = syn.random_affine_cube(dims[0], seed=7, ny=dims[1], nz=dims[2])
+        x = syn.uniform_vector(m.n_dofs(p), seed=3)
+        y = _run_apply(pa, m, p, lam, mu, x, 0)
+        yo = oracle.apply(p, *dims, m.affine, lam, mu, x)
+        assert _relerr(y, yo) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6, 8])
+def test_apply_full_size_sweep_sampled(pa, p):
+    """Operator-sweep size (~3M dofs, the benchmark's launch configuration):
+    sampled rows checked one by one against the oracle's element-matrix rows."""
+    n = syn.sweep_n(p)
+    m = syn.random_affine_cube(n, seed=1000 + p)
+    lam, mu = syn.lame(1.0, 0.3)
+    N = m.n_dofs(p)
+    x = syn.uniform_vector(N, seed=2000 + p)
+    for prec in (0, 1):
+        y = _run_apply(pa, m, p, lam, mu, x, prec)
+        rng = np.random.default_rng(p)
+        rows = np.concatenate([rng.choice(N, 1500, replace=False), [0, N - 1, N // 3, N // 3 - 1]])
+        yo = oracle.apply_rows(p, n, n, n, m.affine, lam, mu, x, rows)
+        scale = np.max(np.abs(yo))
+        assert np.max(np.abs(y[rows] - yo)) <= TOL[prec] * scale
+
+
+def test_apply_is_deterministic_and_host_path(pa):
+    p = 3
+    m = syn.random_affine_cube(3, seed=5)
+    lam, mu = syn.lame(1.0, 0.3)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu)
+    x = torch.tensor(syn.uniform_vector(m.n_dofs(p), 1), device="cuda", dtype=torch.float64)
+    y1 = op.apply(x)
+    y2 = op.apply(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    pa.pa_op_apply_host(op.h, xh, yh)
+    assert torch.equal(yh, y1.cpu())
+    with pytest.raises(pa.PAError):
+        pa.pa_op_apply(op.h, x, x)
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 4, 8])
+def test_diag(pa, p, prec):
+    m = syn.random_affine_cube(2, seed=40 + p, ny=2, nz=1)
+    lam, mu = syn.lame(2.0, 0.45)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, precision=prec, ess_mask=ess)
+    d = op.diag().double().cpu().numpy()
+    op.close()
+    do = oracle.diag(p, m.nx, m.ny, m.nz, m.affine, lam, mu, ess=ess)
+    assert _relerr(d, do) <= TOL[prec]
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+def test_rhs(pa, p):
+    m = syn.random_affine_cube(3, seed=60 + p, nz=2)
+    ess = syn.clamp_mask(m, p)
+    modes = syn.smooth_force_modes(seed=p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 1.0, ess_mask=ess)
+    F = op.rhs(f0=(0.0, 0.0, -1.0), modes=modes).cpu().numpy()
+    op.close()
+    Fo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), modes=modes, ess=ess)
+    assert _relerr(F, Fo) <= 1e-12
