@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free PA elasticity operator on GB300.
+
+Default workload (one "step"): one FP64 operator apply for every degree of
+the operator sweep p in {1, 2, 4, 6, 8} on an n^3 cube with ~3M vector dofs
+per degree (n = 99, 50, 25, 16, 12), every element its own random affine
+map (scales in [0.5, 2], shear up to 0.3), lambda and mu from E = 1,
+nu = 0.3, x ~ U[-1, 1].  value = total dofs of the step / device time of the
+step (GDoF/s, higher is better).
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+independent copy of the workload (weak scaling, no collective on the data
+path); the timed region is bracketed by a barrier and synchronisation and
+the slowest rank's time is used.
+
+--impl reference times the plain CPU oracle (test infrastructure) on the
+host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "Op GDoF/s vs p (FP64 vs FP32-refined); GMG-PCG solves/s, p50/p99 latency"
+SWEEP = (1, 2, 4, 6, 8)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP64: 2 FMA / clk / SM (4 flop); FP32: 128 FMA / clk / SM (256 flop)
+FLOP_PER_CLK_SM = {"f64": 4.0, "f32": 256.0}
+
+
+def flops_per_element(p: int) -> int:
+    """Algorithmic FLOPs per element of the fused sum-factorised apply
+    (Table 6 of the paper): 30 D^3 Q + 36 D^2 Q^2 + 36 D Q^3 + 113 Q^3 + 12 D^3."""
+    D, Q = p + 1, p + 2
+    return 30 * D ** 3 * Q + 36 * D ** 2 * Q ** 2 + 36 * D * Q ** 3 + 113 * Q ** 3 + 12 * D ** 3
+
+
+def algorithmic_bytes(p: int, n: int, elem: int) -> int:
+    """Minimum HBM traffic of one apply: x read + y written once (L-vector)
+    and the 12-value geometry record per element."""
+    ndofs = 3 * (n * p + 1) ** 3
+    return 2 * ndofs * elem + n ** 3 * 12 * elem
+
+
+def workload(p: int, scale: float = 1.0):
+    n = max(1, int(round(syn.sweep_n(p) * scale)))
+    mesh = syn.random_affine_cube(n, seed=1000 + p)
+    x = syn.uniform_vector(mesh.n_dofs(p), seed=2000 + p)
+    return n, mesh, x
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pa_apply.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2601_08374_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ncu DRAM bytes (read + write) per launch of the element kernel, keyed by
+# (precision, p), from the capture summarised under profiles/, valid only
+# for the kernel source with this hash.
+TRAFFIC_HASH = None
+TRAFFIC_BYTES: dict = {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2601_08374_gb300 as pa
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = pa.PA_FP64 if args.precision == "fp64" else pa.PA_FP32
+    dt = torch.float64 if prec == pa.PA_FP64 else torch.float32
+    elem = 8 if prec == pa.PA_FP64 else 4
+    dtype_name = "f64" if prec == pa.PA_FP64 else "f32"
+    lam, mu = syn.lame(1.0, 0.3)
+    ps = [int(s) for s in args.ps.split(",")]
+    stream = torch.cuda.current_stream()
+
+    cases = []
+    for p in ps:
+        n, mesh, x = workload(p)
+        op = pa.Operator(n, n, n, mesh.affine, p, lam, mu, precision=prec)
+        if not args.no_autotune:
+            pa.pa_op_autotune(op.h, stream)
+        xt = torch.tensor(x, dtype=dt, device="cuda")
+        yt = torch.empty_like(xt)
+        cases.append(dict(p=p, n=n, op=op, x=xt, y=yt, ndofs=op.ndofs, ne=op.nelem, launch=pa.pa_op_get_launch(op.h)))
+    total_dofs = sum(c["ndofs"] for c in cases)
+
+    def step():
+        for c in cases:
+            pa.pa_op_apply(c["op"].h, c["x"], c["y"], stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for c in cases:
+        pa.pa_op_profile(c["op"].h, True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    per_case = []
+    for c in cases:
+        te, ta, na = pa.pa_op_profile_read(c["op"].h)
+        pa.pa_op_profile(c["op"].h, False)
+        c["elem_ms"], c["asm_ms"], c["napplies"] = te, ta, na
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the host-buffer C ABI call (pinned buffers)
+    hosts = []
+    for c in cases:
+        xh = c["x"].cpu().pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        hosts.append((xh, yh))
+    for c, (xh, yh) in zip(cases, hosts):
+        pa.pa_op_apply_host(c["op"].h, xh, yh, stream)
+    e2e_steps = max(3, args.steps // 4)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for c, (xh, yh) in zip(cases, hosts):
+            pa.pa_op_apply_host(c["op"].h, xh, yh, stream)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    bytes_step = sum(c["ndofs"] * elem for c in cases)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    value = ws * total_dofs * args.steps / (ms * 1e-3) / 1e9
+    # roofline of the dominant kernel (the fused element kernel), aggregated
+    # over the sweep: algorithmic flops of all its launches / their event time
+    peak = SM_COUNT * FLOP_PER_CLK_SM[dtype_name] * SM_MAX_MHZ * 1e6 / 1e12
+    fl_total = sum(flops_per_element(c["p"]) * c["ne"] * c["napplies"] for c in cases)
+    el_ms = sum(c["elem_ms"] for c in cases)
+    achieved = fl_total / (el_ms * 1e-3) / 1e12
+    traffic = None
+    if TRAFFIC_HASH and TRAFFIC_HASH == kernel_source_hash():
+        tb = [TRAFFIC_BYTES.get((dtype_name, c["p"])) for c in cases]
+        if all(t is not None for t in tb):
+            traffic = int(sum(tb) / len(tb))
+    for c in cases:
+        fl = flops_per_element(c["p"]) * c["ne"]
+        t_el = c["elem_ms"] / max(c["napplies"], 1)
+        t_all = (c["elem_ms"] + c["asm_ms"]) / max(c["napplies"], 1)
+        per_case.append({"p": c["p"], "n": c["n"], "ndofs": c["ndofs"],
+                         "gdofs": round(c["ndofs"] / (t_all * 1e-3) / 1e9, 4),
+                         "element_ms": round(t_el, 4), "assemble_ms": round((c["asm_ms"]) / max(c["napplies"], 1), 4),
+                         "tflops_alg": round(fl / (t_el * 1e-3) / 1e12, 4),
+                         "frac_alu": round(fl / (t_el * 1e-3) / 1e12 / peak, 4),
+                         "hbm_gbs_alg": round(algorithmic_bytes(c["p"], c["n"], elem) / (t_all * 1e-3) / 1e9, 1),
+                         "launch": list(c["launch"])})
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "GDoF/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": dtype_name,
+        "data": "synthetic",
+        "config": {
+            "workload": (f"{args.precision.upper()} op_apply sweep p in {{{','.join(map(str, ps))}}}, n^3 unit cube "
+                         f"(n = {', '.join(str(c['n']) for c in cases)}; {total_dofs / 1e6:.2f}M dofs per step), "
+                         "per-element random affine maps (scales U[0.5,2], shear U[-0.3,0.3]), "
+                         "E=1 nu=0.3, x ~ U[-1,1], unconstrained"),
+            "l2": ("inputs larger than L2: each step applies 5 operators in turn; one step touches "
+                   f"{sum(c['ndofs'] * elem * 2 + c['ne'] * 12 * elem + c['ne'] * 3 * (c['p'] + 1) ** 3 * elem for c in cases) / 1e9:.2f} GB"),
+            "parallelism": f"replicas x{ws}",
+        },
+        "per_p": per_case,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "pa_apply_flat_kernel",
+                     "peak_source": (f"derived: {SM_COUNT} SMs x {FLOP_PER_CLK_SM[dtype_name]:.0f} {dtype_name} flop/clk/SM "
+                                     f"x {SM_MAX_MHZ:.0f} MHz")},
+        "e2e": {"value": round(ws * total_dofs * e2e_steps / e2e_s / 1e9, 4), "unit": "GDoF/s",
+                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
+                "api": "pa_op_apply_host (pinned host buffers)"},
+        "gpu_launches": 2 * len(cases) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(ps, args)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    for c in cases:
+        c["op"].close()
+    return out
+
+
+def _oracle_sweep(ps, scale):
+    import oracle
+    lam, mu = syn.lame(1.0, 0.3)
+    dofs, secs = 0, 0.0
+    for p in ps:
+        n, mesh, x = workload(p, scale)
+        oracle.ref(p)  # reference blocks built outside the timing
+        t0 = time.perf_counter()
+        oracle.apply(p, n, n, n, mesh.affine, lam, mu, x)
+        secs += time.perf_counter() - t0
+        dofs += mesh.n_dofs(p)
+    return dofs, secs
+
+
+def cpu_baseline(ps, args):
+    import oracle
+    dofs, secs = _oracle_sweep(ps, 1.0)
+    return {"value": round(dofs / secs / 1e9, 6), "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "one full step: the oracle's element-matrix apply for every p of the sweep at full size, "
+                      "FP64, OpenMP over elements"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return None
+    import oracle
+    ps = [int(s) for s in args.ps.split(",")]
+    scale = 1.0 / 3.0
+    for _ in range(args.warmup):
+        _oracle_sweep(ps, scale)
+    dofs, secs = 0, 0.0
+    for _ in range(args.steps):
+        d, s = _oracle_sweep(ps, scale)
+        dofs += d
+        secs += s
+    v = dofs / secs / 1e9
+    sample = ("each step: the oracle's element-matrix apply for every p of the sweep on the same recipe at "
+              "(n/3)^3 elements, FP64, OpenMP over elements")
+    out = {"metric": METRIC, "value": round(v, 6), "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"FP64 op_apply sweep p in {{{args.ps}}} (oracle sample, see cpu_baseline)",
+                      "parallelism": "host cores"},
+           "cpu_baseline": {"value": round(v, 6), "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 6), "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--ps", default=",".join(map(str, SWEEP)))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

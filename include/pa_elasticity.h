@@ -120,6 +120,38 @@ int pa_op_diag(pa_op *op, void *d, void *stream);
  * Essential entries are set to 0.  F: device L-vector of the op's precision. */
 int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void *F, void *stream);
 
+/* Launch shape of the fused element kernel: variant 0 (flattened
+ * shared-memory sweeps, one output per thread step) or 1 (register-tiled
+ * 1D lines), elements per CTA, threads per CTA (32..512, multiple of 32).
+ * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB. */
+int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
+int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);
+
+/* Autotuner: times every admissible (variant, elements per CTA, threads)
+ * with CUDA events on `stream`, applying the operator to the op's own
+ * staging vectors (filled with a fixed pattern), and keeps the fastest.
+ * Synchronises `stream`. */
+int pa_op_autotune(pa_op *op, void *stream);
+
+/* Kernel timing for measurement.  While enabled, every apply records CUDA
+ * events on its stream before the element kernel, between the element and
+ * the assembly kernel, and after the assembly (at most 4096 applies are
+ * kept; later ones are not recorded).  enable = 1 (re)starts the record,
+ * enable = 0 stops recording.  pa_op_profile_read synchronises on the last
+ * recorded event and returns the summed kernel times in milliseconds and the
+ * number of recorded applies. */
+int pa_op_profile(pa_op *op, int enable);
+int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64_t *applies);
+
+/* p-transfer between two operators on the same mesh with degrees
+ * pc = coarse->p < pf = fine->p (Sec. 3: polynomial interpolation between the
+ * GLL spaces of p-levels).  prolong: xf = P xc evaluates the coarse field at
+ * the fine nodes; restrict: rc = P^T rf (exact transpose).  FP64 device
+ * L-vectors; no essential-dof masking is applied.  Both operators must be
+ * FP64. */
+int pa_op_prolong(const pa_op *coarse, const pa_op *fine, const double *xc, double *xf, void *stream);
+int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, double *rc, void *stream);
+
 /* -------------------------------------------------------------- solver -- */
 
 typedef struct pa_solve_info {
@@ -146,10 +178,17 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
                      int coarse_maxit, int mode, pa_solver **out);
 int pa_solver_destroy(pa_solver *s);
 
-/* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 (x: in = initial guess,
- * out = solution; device double L-vectors).  Synchronises `stream` to test
- * convergence; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in
- * every case when non-NULL). */
+/* Solve A x = b (x: in = initial guess, out = solution; device double
+ * L-vectors).  FP64 mode: flexible CG stops when its recursively updated
+ * residual satisfies ||r||_2 <= rtol ||b||_2.  Mixed mode: iterative
+ * refinement stops when the FP64 residual b - A x satisfies the same test,
+ * or when a refinement step no longer halves it (the FP64 rounding floor,
+ * of order eps ||A|| ||x|| / ||b||, which for stiff bending problems can lie
+ * above 1e-10).  info->rel_residual is always the true FP64 residual
+ * ||b - A x|| / ||b|| recomputed at exit.  maxit caps the outer CG
+ * iterations (FP64) or the total inner iterations (mixed).  Synchronises
+ * `stream`; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every
+ * case when non-NULL), PA_EINVAL for a non-finite b. */
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream);
 

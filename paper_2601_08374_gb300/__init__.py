@@ -58,6 +58,13 @@ _sig("pa_op_apply", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
+_sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
+_sig("pa_op_restrict", [_vp, _vp, _vp, _vp, _vp])
+_sig("pa_op_set_launch", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int])
+_sig("pa_op_get_launch", [_vp, _ip, _ip, _ip])
+_sig("pa_op_autotune", [_vp, _vp])
+_sig("pa_op_profile", [_vp, ctypes.c_int])
+_sig("pa_op_profile_read", [_vp, _dp, _dp, _i64p])
 if hasattr(lib, "pa_solver_create"):
     _sig("pa_solver_create", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.POINTER(_vp)])
@@ -168,7 +175,41 @@ def pa_op_rhs(op, F, f0=(0.0, 0.0, 0.0), modes=None, stream=None):
     _check(lib.pa_op_rhs(op, _dptr(f0), nm, _dptr(md) if nm else None, _tptr(F), _stream_ptr(stream)), "pa_op_rhs")
 
 
-def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-2, coarse_maxit=50, mode=PA_SOLVE_FP64):
+def pa_op_prolong(coarse, fine, xc, xf, stream=None):
+    _check(lib.pa_op_prolong(coarse, fine, _tptr(xc), _tptr(xf), _stream_ptr(stream)), "pa_op_prolong")
+
+
+def pa_op_restrict(coarse, fine, rf, rc, stream=None):
+    _check(lib.pa_op_restrict(coarse, fine, _tptr(rf), _tptr(rc), _stream_ptr(stream)), "pa_op_restrict")
+
+
+def pa_op_set_launch(op, variant, elems_per_block, threads):
+    _check(lib.pa_op_set_launch(op, variant, elems_per_block, threads), "pa_op_set_launch")
+
+
+def pa_op_get_launch(op):
+    v, e, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.pa_op_get_launch(op, ctypes.byref(v), ctypes.byref(e), ctypes.byref(t)), "pa_op_get_launch")
+    return v.value, e.value, t.value
+
+
+def pa_op_autotune(op, stream=None):
+    _check(lib.pa_op_autotune(op, _stream_ptr(stream)), "pa_op_autotune")
+    return pa_op_get_launch(op)
+
+
+def pa_op_profile(op, enable: bool):
+    _check(lib.pa_op_profile(op, 1 if enable else 0), "pa_op_profile")
+
+
+def pa_op_profile_read(op):
+    """(element_ms, assemble_ms, applies) summed over the recorded applies."""
+    te, ta, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib.pa_op_profile_read(op, ctypes.byref(te), ctypes.byref(ta), ctypes.byref(n)), "pa_op_profile_read")
+    return te.value, ta.value, n.value
+
+
+def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=300, mode=PA_SOLVE_FP64):
     h = _vp()
     lv = (ctypes.c_int * len(p_levels))(*p_levels)
     _check(lib.pa_solver_create(op, len(p_levels), lv, cheb_order, coarse_rtol, coarse_maxit, mode,

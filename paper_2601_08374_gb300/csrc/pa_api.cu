@@ -68,20 +68,38 @@ ApplyLaunch default_apply_launch(int p, int precision)
 }
 
 template <typename T>
-static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t s)
+static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t s, const int *skip)
 {
     ApplyArgs<T> a;
     a.x = x;
     a.ye = static_cast<T *>(op->d_ye);
     a.geo = static_cast<const T *>(op->d_geo);
     a.ess = op->d_ess;
+    a.skip = skip;
     a.g = op->g;
     const Tables<T> *tab;
     if constexpr (sizeof(T) == 8) tab = &op->tab64;
     else tab = &op->tab32;
+    cudaEvent_t *ev = nullptr;
+    if (op->prof_on && op->prof_count * 3 + 3 <= (int)op->prof_ev.size()) {
+        ev = &op->prof_ev[op->prof_count * 3];
+        ++op->prof_count;
+        PA_CUDA_TRY(cudaEventRecord(ev[0], s));
+    }
     int rc = launch_apply_elements<T>(a, *tab, op->launch, s);
     if (rc) return rc;
-    return launch_assemble<T>(a.ye, y, x, op->d_ess, T(0), accumulate, op->g, s);
+    if (ev) PA_CUDA_TRY(cudaEventRecord(ev[1], s));
+    rc = launch_assemble<T>(a.ye, y, x, op->d_ess, T(0), accumulate, op->g, s, skip);
+    if (rc) return rc;
+    if (ev) PA_CUDA_TRY(cudaEventRecord(ev[2], s));
+    return PA_OK;
+}
+
+int op_apply_async(pa_op *op, const void *x, void *y, bool accumulate, cudaStream_t s, const int *skip)
+{
+    if (op->precision == PA_FP64)
+        return apply_impl<double>(op, static_cast<const double *>(x), static_cast<double *>(y), accumulate, s, skip);
+    return apply_impl<float>(op, static_cast<const float *>(x), static_cast<float *>(y), accumulate, s, skip);
 }
 
 }  // namespace pa
@@ -164,6 +182,7 @@ int pa_mesh_destroy(pa_mesh *mesh)
 int pa_op_destroy(pa_op *op)
 {
     if (!op) return PA_OK;
+    for (cudaEvent_t e : op->prof_ev) cudaEventDestroy(e);
     cudaFree(op->d_geo);
     cudaFree(op->d_affine);
     cudaFree(op->d_ess);
@@ -242,6 +261,13 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
         pa_op_destroy(op);
         return cuda_error(err, "pa_op_setup: cudaMemcpy");
     }
+    try {
+        op->h_affine = mesh->affine;
+        if (ess_mask) op->h_ess.assign(ess_mask, ess_mask + N);
+    } catch (...) {
+        pa_op_destroy(op);
+        return set_error(PA_ENOMEM, "pa_op_setup: host allocation");
+    }
     if (ess_mask) {
         if ((err = cudaMalloc((void **)&op->d_ess, N)) != cudaSuccess ||
             (err = cudaMemcpy(op->d_ess, ess_mask, N, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -268,10 +294,7 @@ int pa_op_apply(pa_op *op, const void *x, void *y, void *stream)
 {
     if (!op || !x || !y) return set_error(PA_EINVAL, "pa_op_apply: null argument");
     if (x == y) return set_error(PA_EINVAL, "pa_op_apply: x and y must not alias");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (op->precision == PA_FP64)
-        return apply_impl<double>(op, static_cast<const double *>(x), static_cast<double *>(y), false, s);
-    return apply_impl<float>(op, static_cast<const float *>(x), static_cast<float *>(y), false, s);
+    return op_apply_async(op, x, y, false, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream)
@@ -328,6 +351,114 @@ int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void
                                         op->d_ess, 0.0f, false, op->g, s);
     }
     return rc;
+}
+
+int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_set_launch: null op");
+    if (variant < 0 || variant > kMaxVariant || elems_per_block < 1 || threads < 32 || threads > 512 || threads % 32)
+        return set_error(PA_EINVAL, "pa_op_set_launch: bad shape");
+    ApplyLaunch c;
+    c.variant = variant;
+    c.epb = elems_per_block;
+    c.threads = threads;
+    size_t smem = op->precision == PA_FP64 ? apply_smem_bytes<double>(op->p, c) : apply_smem_bytes<float>(op->p, c);
+    if (smem == 0 || smem > 227 * 1024) return set_error(PA_EINVAL, "pa_op_set_launch: shared memory too large");
+    op->launch = c;
+    return PA_OK;
+}
+
+int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_get_launch: null op");
+    if (variant) *variant = op->launch.variant;
+    if (elems_per_block) *elems_per_block = op->launch.epb;
+    if (threads) *threads = op->launch.threads;
+    return PA_OK;
+}
+
+int pa_op_autotune(pa_op *op, void *stream)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_autotune: null op");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)op->ndofs() * op->elem;
+    PA_CUDA_TRY(cudaMemsetAsync(op->d_xh, 0x3f, bytes, s));  // finite, non-zero pattern
+    cudaEvent_t e0, e1;
+    PA_CUDA_TRY(cudaEventCreate(&e0));
+    PA_CUDA_TRY(cudaEventCreate(&e1));
+    const ApplyLaunch keep = op->launch;
+    ApplyLaunch best = keep;
+    float best_ms = 1e30f;
+    static const int epbs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    static const int thrs[] = {128, 256, 384, 512};
+    int rc = PA_OK;
+    for (int v = 0; v <= kMaxVariant && rc == PA_OK; ++v)
+        for (int ep : epbs)
+            for (int th : thrs) {
+                if (pa_op_set_launch(op, v, ep, th) != PA_OK) continue;
+                if ((int64_t)ep > op->g.ne) continue;
+                float best_here = 1e30f;
+                for (int rep = 0; rep < 4 && rc == PA_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    rc = pa_op_apply(op, op->d_xh, op->d_yh, stream);
+                    cudaEventRecord(e1, s);
+                    if (rc == PA_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0 && ms < best_here) best_here = ms;
+                    }
+                }
+                if (rc != PA_OK) break;
+                if (best_here < best_ms) {
+                    best_ms = best_here;
+                    best = op->launch;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    op->launch = (rc == PA_OK) ? best : keep;
+    clear_error();
+    return rc;
+}
+
+int pa_op_profile(pa_op *op, int enable)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_profile: null op");
+    if (enable && op->prof_ev.empty()) {
+        const int n = 3 * 4096;
+        op->prof_ev.resize(n);
+        for (int i = 0; i < n; ++i) {
+            cudaError_t e = cudaEventCreate(&op->prof_ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(op->prof_ev[j]);
+                op->prof_ev.clear();
+                return cuda_error(e, "pa_op_profile: cudaEventCreate");
+            }
+        }
+    }
+    if (enable) op->prof_count = 0;
+    op->prof_on = enable != 0;
+    return PA_OK;
+}
+
+int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64_t *applies)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_profile_read: null op");
+    double te = 0.0, ta = 0.0;
+    if (op->prof_count > 0) {
+        PA_CUDA_TRY(cudaEventSynchronize(op->prof_ev[op->prof_count * 3 - 1]));
+        for (int i = 0; i < op->prof_count; ++i) {
+            float a = 0.f, b = 0.f;
+            PA_CUDA_TRY(cudaEventElapsedTime(&a, op->prof_ev[3 * i], op->prof_ev[3 * i + 1]));
+            PA_CUDA_TRY(cudaEventElapsedTime(&b, op->prof_ev[3 * i + 1], op->prof_ev[3 * i + 2]));
+            te += a;
+            ta += b;
+        }
+    }
+    if (element_ms) *element_ms = te;
+    if (assemble_ms) *assemble_ms = ta;
+    if (applies) *applies = op->prof_count;
+    return PA_OK;
 }
 
 }  // extern "C"

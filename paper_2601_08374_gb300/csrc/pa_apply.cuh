@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
     T *bufA = sB + L::tab;
     T *bufB = bufA + (size_t)epb * L::bufA;
 
+    if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t e0 = (int64_t)blockIdx.x * epb;
     const int ne_blk = (int)((a.g.ne - e0) < epb ? (a.g.ne - e0) : epb);
@@ -329,7 +330,11 @@ int launch_flat(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
 {
     size_t smem = flat_smem_bytes<T, D, Q>(cfg.epb);
     auto kern = pa_apply_flat_kernel<T, D, Q>;
-    PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static size_t smem_set = 0;  // largest dynamic shared memory enabled so far for this instantiation
+    if (smem > smem_set) {
+        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        smem_set = 227 * 1024;
+    }
     int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(a, tab, cfg.epb);

@@ -1,20 +1,49 @@
-// Instantiations of the fused element kernel for double, p = 1..8 (q = p + 2).
+// Instantiations of the fused element kernels for double, p = 1..8 (q = p + 2):
+// variant 0 = flattened shared-memory sweeps, variant 1 = register-tiled lines.
 #include "pa_apply.cuh"
+#include "pa_apply_line.cuh"
 
 namespace pa {
+namespace {
+
+// The register-tiled variant keeps 18 D values per thread in the fused Z
+// stage; in FP64 that fits the register file only up to D = 5.
+template <int D>
+constexpr bool line_ok = sizeof(double) == 4 || D <= 5;
+
+template <int D, int Q>
+size_t smem_for(const ApplyLaunch &c)
+{
+    if (c.variant == 0) return flat_smem_bytes<double, D, Q>(c.epb);
+    if constexpr (line_ok<D>) {
+        if (c.threads > 256) return 0;
+        return line_smem_bytes<double, D, Q>(c.epb);
+    }
+    return 0;
+}
+
+template <int D, int Q>
+int launch_for(const ApplyArgs<double> &a, const Tables<double> &tab, const ApplyLaunch &c, cudaStream_t s)
+{
+    if (c.variant == 0) return launch_flat<double, D, Q>(a, tab, c, s);
+    if constexpr (line_ok<D>) return launch_line<double, D, Q>(a, tab, c, s);
+    return set_error(PA_EINVAL, "apply variant 1 is not instantiated for this degree and precision");
+}
+
+}  // namespace
 
 template <>
 size_t apply_smem_bytes<double>(int p, const ApplyLaunch &cfg)
 {
     switch (p) {
-    case 1: return flat_smem_bytes<double, 2, 3>(cfg.epb);
-    case 2: return flat_smem_bytes<double, 3, 4>(cfg.epb);
-    case 3: return flat_smem_bytes<double, 4, 5>(cfg.epb);
-    case 4: return flat_smem_bytes<double, 5, 6>(cfg.epb);
-    case 5: return flat_smem_bytes<double, 6, 7>(cfg.epb);
-    case 6: return flat_smem_bytes<double, 7, 8>(cfg.epb);
-    case 7: return flat_smem_bytes<double, 8, 9>(cfg.epb);
-    case 8: return flat_smem_bytes<double, 9, 10>(cfg.epb);
+    case 1: return smem_for<2, 3>(cfg);
+    case 2: return smem_for<3, 4>(cfg);
+    case 3: return smem_for<4, 5>(cfg);
+    case 4: return smem_for<5, 6>(cfg);
+    case 5: return smem_for<6, 7>(cfg);
+    case 6: return smem_for<7, 8>(cfg);
+    case 7: return smem_for<8, 9>(cfg);
+    case 8: return smem_for<9, 10>(cfg);
     default: return 0;
     }
 }
@@ -24,16 +53,17 @@ int launch_apply_elements<double>(const ApplyArgs<double> &a, const Tables<doubl
                                cudaStream_t s)
 {
     if (cfg.threads < 32 || cfg.threads > 512 || cfg.epb < 1) return set_error(PA_EINVAL, "bad apply launch config");
-    if (apply_smem_bytes<double>(a.g.p, cfg) > 227 * 1024) return set_error(PA_EINVAL, "apply launch config exceeds shared memory");
+    const size_t smem = apply_smem_bytes<double>(a.g.p, cfg);
+    if (smem == 0 || smem > 227 * 1024) return set_error(PA_EINVAL, "apply launch config not admissible");
     switch (a.g.p) {
-    case 1: return launch_flat<double, 2, 3>(a, tab, cfg, s);
-    case 2: return launch_flat<double, 3, 4>(a, tab, cfg, s);
-    case 3: return launch_flat<double, 4, 5>(a, tab, cfg, s);
-    case 4: return launch_flat<double, 5, 6>(a, tab, cfg, s);
-    case 5: return launch_flat<double, 6, 7>(a, tab, cfg, s);
-    case 6: return launch_flat<double, 7, 8>(a, tab, cfg, s);
-    case 7: return launch_flat<double, 8, 9>(a, tab, cfg, s);
-    case 8: return launch_flat<double, 9, 10>(a, tab, cfg, s);
+    case 1: return launch_for<2, 3>(a, tab, cfg, s);
+    case 2: return launch_for<3, 4>(a, tab, cfg, s);
+    case 3: return launch_for<4, 5>(a, tab, cfg, s);
+    case 4: return launch_for<5, 6>(a, tab, cfg, s);
+    case 5: return launch_for<6, 7>(a, tab, cfg, s);
+    case 6: return launch_for<7, 8>(a, tab, cfg, s);
+    case 7: return launch_for<8, 9>(a, tab, cfg, s);
+    case 8: return launch_for<9, 10>(a, tab, cfg, s);
     default: return set_error(PA_EINVAL, "p must be in 1..8");
     }
 }

@@ -1,0 +1,283 @@
+// Register-tiled variant of the fused element kernel (same dataflow as
+// pa_apply.cuh, Sec. 4.2-4.5).
+//
+// Every 1D sweep is done by one thread per 1D line: the thread loads the
+// line's inputs once into registers and produces all outputs of the line
+// with fully unrolled loops, so the 1D tables B, G, Bw, Gw are compile-time
+// indexed kernel parameters (constant-bank operands of the FMAs) and each
+// shared-memory word read feeds Q (or D) FMAs.  The Z sweep, the pointwise
+// stress and the transposed Z sweep are fused per (qx, qy) column: the
+// column's 9 x D inputs and 9 x D accumulators live in registers and the
+// transposed result overwrites the column in place.
+//
+// Shared-memory layouts are chosen so that, in both the producing and the
+// consuming sweep, the index that varies across the lanes of a warp has an
+// odd word stride (no bank conflicts):
+//   S0  x_e / y_e staging   [c][iz][iy][ix]      (ix padded to DP, odd)
+//   S1  X-sweep out         [c][iz][ch][qx][iy]  (iy padded to DP)
+//   S2  Y-sweep out / Z^T   [qy][qx][c][k][iz]   (column stride CS, odd)
+//   S3  Y^T-sweep out       [c][iz][iy][k*Q+qx]  (row stride BS = 2Q+1)
+// Buffer A holds S0 then S2 then the output staging; buffer B holds S1
+// then S3.  The E-vector leaves through a coalesced copy of the staging.
+#pragma once
+
+#include <cstdint>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+template <typename T, int D, int Q>
+struct LineLayout {
+    static constexpr int DP = D | 1;                      // odd pitch for ix / iy
+    static constexpr int CS = (9 * D) | 1;                // odd column stride of S2
+    static constexpr int BS = 2 * Q + 1;                  // odd row stride of S3
+    static constexpr int S0 = 3 * D * D * DP;
+    static constexpr int S1 = 3 * D * 2 * Q * DP;
+    static constexpr int S2 = Q * Q * CS;
+    static constexpr int S3 = 3 * D * D * BS;
+    static constexpr int A = S0 > S2 ? S0 : S2;
+    static constexpr int B = S1 > S3 ? S1 : S3;
+    static constexpr int per_elem = A + B;
+};
+
+template <typename T, int D, int Q>
+__global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+{
+    using L = LineLayout<T, D, Q>;
+    constexpr int D3 = D * D * D, DP = L::DP, CS = L::CS, BS = L::BS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bufA = reinterpret_cast<T *>(smem_raw);
+    T *bufB = bufA + (size_t)epb * L::A;
+
+    if (a.skip && *a.skip) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t e0 = (int64_t)blockIdx.x * epb;
+    const int ne_blk = (int)((a.g.ne - e0) < epb ? (a.g.ne - e0) : epb);
+    if (ne_blk <= 0) return;
+    const int p = D - 1;
+    const int64_t Nn = a.g.Nn;
+
+    // ---- gather x_e into S0 [c][iz][iy][ix]
+    for (int o = tid; o < ne_blk * 3 * D3; o += nt) {
+        int el = o / (3 * D3), r = o - el * 3 * D3;
+        int ix = r % D, iy = (r / D) % D, iz = (r / (D * D)) % D, c = r / D3;
+        int64_t e = e0 + el;
+        int ex = (int)(e % a.g.nx);
+        int64_t t = e / a.g.nx;
+        int ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
+        int64_t gn = (int64_t)(ex * p + ix) +
+                     (int64_t)a.g.Mx * ((int64_t)(ey * p + iy) + (int64_t)a.g.My * (ez * p + iz));
+        int64_t k = c * Nn + gn;
+        T v = a.x[k];
+        if (a.ess && a.ess[k]) v = T(0);
+        bufA[(size_t)el * L::A + ((c * D + iz) * D + iy) * DP + ix] = v;
+    }
+    __syncthreads();
+
+    // ---- X sweep: line (el, c, iz, iy) -> S1 [c][iz][ch][qx][iy]
+    for (int o = tid; o < ne_blk * 3 * D * D; o += nt) {
+        int el = o / (3 * D * D), r = o - el * 3 * D * D;
+        int iy = r % D, iz = (r / D) % D, c = r / (D * D);
+        const T *in = bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
+        T xv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) xv[i] = in[i];
+        T *out = bufB + (size_t)el * L::B + (c * D + iz) * 2 * Q * DP + iy;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            T u = T(0), v = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                u = fma(xv[i], tab.B[i * Q + q], u);
+                v = fma(xv[i], tab.G[i * Q + q], v);
+            }
+            out[(0 * Q + q) * DP] = u;
+            out[(1 * Q + q) * DP] = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- Y sweep: line (el, c, iz, qx) -> S2 [qy][qx][c][k][iz]
+    for (int o = tid; o < ne_blk * 3 * D * Q; o += nt) {
+        int el = o / (3 * D * Q), r = o - el * 3 * D * Q;
+        int qx = r % Q, iz = (r / Q) % D, c = r / (Q * D);
+        const T *in = bufB + (size_t)el * L::B + (c * D + iz) * 2 * Q * DP + qx * DP;
+        T uv[D], vv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            uv[i] = in[i];
+            vv[i] = in[Q * DP + i];
+        }
+        T *out = bufA + (size_t)el * L::A + qx * CS + (c * 3) * D + iz;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            T d0 = T(0), d1 = T(0), d2 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                d0 = fma(vv[i], tab.B[i * Q + q], d0);  // d/dxi
+                d1 = fma(uv[i], tab.G[i * Q + q], d1);  // d/deta
+                d2 = fma(uv[i], tab.B[i * Q + q], d2);  // interpolated, G follows along z
+            }
+            T *o2 = out + q * Q * CS;
+            o2[0 * D] = d0;
+            o2[1 * D] = d1;
+            o2[2 * D] = d2;
+        }
+    }
+    __syncthreads();
+
+    // ---- Z sweep + pointwise + Z^T sweep: column (el, qx, qy), in place
+    for (int o = tid; o < ne_blk * Q * Q; o += nt) {
+        int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
+        T *cp = bufA + (size_t)el * L::A + col * CS;
+        T in[9][D];
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
+        const T *geo = a.geo + (e0 + el) * kGeoStride;
+        T Ji[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
+        const T cl = geo[9], cm = geo[10], m2 = cm + cm;
+        T acc[9][D];
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[ch][i] = T(0);
+#pragma unroll
+        for (int qz = 0; qz < Q; ++qz) {
+            T gr[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    g0 = fma(in[c * 3 + 0][i], tab.B[i * Q + qz], g0);
+                    g1 = fma(in[c * 3 + 1][i], tab.B[i * Q + qz], g1);
+                    g2 = fma(in[c * 3 + 2][i], tab.G[i * Q + qz], g2);
+                }
+                gr[c][0] = g0;
+                gr[c][1] = g1;
+                gr[c][2] = g2;
+            }
+            T du[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
+            const T ld = cl * (du[0][0] + du[1][1] + du[2][2]);
+            T s[3][3];
+            s[0][0] = fma(m2, du[0][0], ld);
+            s[1][1] = fma(m2, du[1][1], ld);
+            s[2][2] = fma(m2, du[2][2], ld);
+            s[0][1] = s[1][0] = cm * (du[0][1] + du[1][0]);
+            s[0][2] = s[2][0] = cm * (du[0][2] + du[2][0]);
+            s[1][2] = s[2][1] = cm * (du[1][2] + du[2][1]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    T qv = fma(s[c][0], Ji[m * 3 + 0], fma(s[c][1], Ji[m * 3 + 1], s[c][2] * Ji[m * 3 + 2]));
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        acc[c * 3 + m][i] = fma(qv, (m == 2 ? tab.Gw[i * Q + qz] : tab.Bw[i * Q + qz]), acc[c * 3 + m][i]);
+                }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) cp[ch * D + i] = acc[ch][i];
+    }
+    __syncthreads();
+
+    // ---- Y^T sweep: line (el, c, iz, qx) -> S3 [c][iz][iy][k*Q + qx]
+    for (int o = tid; o < ne_blk * 3 * D * Q; o += nt) {
+        int el = o / (3 * D * Q), r = o - el * 3 * D * Q;
+        int qx = r % Q, iz = (r / Q) % D, c = r / (Q * D);
+        const T *in = bufA + (size_t)el * L::A + qx * CS + (c * 3) * D + iz;
+        T t0[Q], t1[Q], t2[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T *col = in + q * Q * CS;
+            t0[q] = col[0 * D];
+            t1[q] = col[1 * D];
+            t2[q] = col[2 * D];
+        }
+        T *out = bufB + (size_t)el * L::B + ((c * D + iz) * D) * BS + qx;
+#pragma unroll
+        for (int iy = 0; iy < D; ++iy) {
+            T u0 = T(0), u12 = T(0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                u0 = fma(t0[q], tab.Bw[iy * Q + q], u0);
+                u12 = fma(t1[q], tab.Gw[iy * Q + q], u12);
+                u12 = fma(t2[q], tab.Bw[iy * Q + q], u12);
+            }
+            out[iy * BS] = u0;
+            out[iy * BS + Q] = u12;
+        }
+    }
+    __syncthreads();
+
+    // ---- X^T sweep: line (el, c, iz, iy) -> staging [c][iz][iy][ix] in A
+    for (int o = tid; o < ne_blk * 3 * D * D; o += nt) {
+        int el = o / (3 * D * D), r = o - el * 3 * D * D;
+        int iy = r % D, iz = (r / D) % D, c = r / (D * D);
+        const T *in = bufB + (size_t)el * L::B + ((c * D + iz) * D + iy) * BS;
+        T u0[Q], u12[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            u0[q] = in[q];
+            u12[q] = in[Q + q];
+        }
+        T *out = bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
+#pragma unroll
+        for (int ix = 0; ix < D; ++ix) {
+            T y = T(0);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                y = fma(u0[q], tab.Gw[ix * Q + q], y);
+                y = fma(u12[q], tab.Bw[ix * Q + q], y);
+            }
+            out[ix] = y;
+        }
+    }
+    __syncthreads();
+
+    // ---- coalesced store of the CTA's contiguous E-vector block
+    T *ye = a.ye + e0 * 3 * D3;
+    for (int o = tid; o < ne_blk * 3 * D3; o += nt) {
+        int el = o / (3 * D3), r = o - el * 3 * D3;
+        int ix = r % D, rest = r / D;  // rest = (c*D + iz)*D + iy
+        ye[o] = bufA[(size_t)el * L::A + rest * DP + ix];
+    }
+}
+
+template <typename T, int D, int Q>
+size_t line_smem_bytes(int epb)
+{
+    return sizeof(T) * (size_t)epb * LineLayout<T, D, Q>::per_elem;
+}
+
+template <typename T, int D, int Q>
+int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
+{
+    if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
+    size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
+    auto kern = pa_apply_line_kernel<T, D, Q>;
+    static bool smem_set = false;
+    if (!smem_set) {
+        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        smem_set = true;
+    }
+    int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
+    if (nblk <= 0) return PA_OK;
+    kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(a, tab, cfg.epb);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+}  // namespace pa

@@ -46,8 +46,10 @@ unsigned grid_for(int64_t n, int threads)
 // ess_value.
 template <typename T>
 __global__ void assemble_kernel(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
-                                const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g)
+                                const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g,
+                                const int *__restrict__ skip)
 {
+    if (skip && *skip) return;
     const int p = g.p, D = p + 1, D3 = D * D * D;
     for (int64_t gn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gn < g.Nn;
          gn += (int64_t)gridDim.x * blockDim.x) {
@@ -81,17 +83,17 @@ __global__ void assemble_kernel(const T *__restrict__ ye, T *__restrict__ y, con
 
 template <typename T>
 int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,
-                    const Grid &g, cudaStream_t s)
+                    const Grid &g, cudaStream_t s, const int *skip)
 {
     const int th = 256;
-    assemble_kernel<T><<<grid_for(g.Nn, th), th, 0, s>>>(ye, y, xin, ess, ess_value, accumulate ? 1 : 0, g);
+    assemble_kernel<T><<<grid_for(g.Nn, th), th, 0, s>>>(ye, y, xin, ess, ess_value, accumulate ? 1 : 0, g, skip);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
 template int launch_assemble<double>(const double *, double *, const double *, const uint8_t *, double, bool,
-                                     const Grid &, cudaStream_t);
+                                     const Grid &, cudaStream_t, const int *);
 template int launch_assemble<float>(const float *, float *, const float *, const uint8_t *, float, bool,
-                                    const Grid &, cudaStream_t);
+                                    const Grid &, cudaStream_t, const int *);
 
 // -------------------------------------------------------------- diagonal --
 struct DiagTables {

@@ -66,6 +66,7 @@ struct Grid {
 };
 
 // --------------------------------------------------------- apply launch --
+constexpr int kMaxVariant = 1;
 struct ApplyLaunch {
     int variant = 0;  // 0: flattened smem sweeps
     int epb = 1;      // elements per CTA
@@ -78,6 +79,7 @@ struct ApplyArgs {
     T *ye;               // E-vector scratch [ne][3][D^3]
     const T *geo;        // [ne][kGeoStride]
     const uint8_t *ess;  // [3*Nn] or nullptr
+    const int *skip;     // device flag: when non-null and set, the launch does nothing
     Grid g;
 };
 
@@ -92,7 +94,7 @@ ApplyLaunch default_apply_launch(int p, int precision);
 // constrained rows take xin (or `ess_value` when xin is null).
 template <typename T>
 int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,
-                    const Grid &g, cudaStream_t s);
+                    const Grid &g, cudaStream_t s, const int *skip = nullptr);
 
 // Closed-form PA diagonal per element into the E-vector.
 template <typename T>
@@ -101,7 +103,11 @@ int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, c
 // Load vector per element into the E-vector.
 template <typename T>
 int launch_rhs_elements(const double *affine, T *ye, const Basis1D &b, const Grid &g, const double *f0,
-                        int nmodes, const double *d_modes, cudaStream_t s);
+                        int nmodes, const double *modes, cudaStream_t s);
+
+// Apply with an optional device skip flag (used inside device-controlled
+// loops); y = A x, or y += A x when accumulate.
+int op_apply_async(pa_op *op, const void *x, void *y, bool accumulate, cudaStream_t s, const int *skip);
 
 }  // namespace pa
 
@@ -126,5 +132,11 @@ struct pa_op {
     void *d_ye = nullptr;        // E-vector scratch
     void *d_xh = nullptr;        // device staging for apply_host
     void *d_yh = nullptr;
+    std::vector<double> h_affine;  // host copy of the element maps (solver levels)
+    std::vector<uint8_t> h_ess;    // host copy of the essential mask (may be empty)
+    // measurement: 3 events per recorded apply
+    bool prof_on = false;
+    int prof_count = 0;
+    std::vector<cudaEvent_t> prof_ev;
     int64_t ndofs() const { return 3 * g.Nn; }
 };

@@ -1,0 +1,1086 @@
+// GMG-preconditioned CG solver on the p-hierarchy (Sec. 3): V(1,1) cycle with
+// Chebyshev-Jacobi smoothing on every level but the coarsest (Sec. 3.1),
+// interpolation prolongation and its exact transpose as restriction between
+// GLL spaces (Sec. 3), an FP64 Jacobi-preconditioned CG coarse solve
+// (Sec. 3.2, with CG in place of AMG), and an outer flexible CG.
+//
+// All vectors and scalars stay on the device.  Dot products are
+// deterministic two-level reductions (fixed block partition, last block sums
+// the partials in order), and the coefficients alpha/beta are formed on the
+// device, so an iteration enqueues without host round trips; the host reads
+// one residual norm per outer iteration to test convergence.  The coarse CG
+// loop runs a fixed number of launches whose kernels return at once after a
+// device flag marks convergence.
+//
+// Mixed mode (PA_SOLVE_MIXED): iterative refinement in FP64 (residual
+// b - A x with the FP64 operator, FP64 norms), inner flexible CG in FP32
+// storage with FP64 dot products, preconditioned by an FP32 V-cycle whose
+// coarse solve is the FP64 CG.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pa_internal.h"
+
+namespace pa {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 2 * 152;
+
+// device scalar slots
+enum Slot {
+    S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_ZQ, S_ZR,
+    C_RZ = 16, C_PQ, C_ALPHA, C_BETA, C_RR, C_BB, C_TOL2,
+    P_NUM = 24, P_DEN,
+    NSLOT = 32
+};
+enum FlagSlot { F_BREAK = 0, F_CDONE = 1, NFLAG = 4 };
+
+struct Dev {
+    double *scal;       // [NSLOT]
+    int *flag;          // [NFLAG]
+    double *partial;    // [3][kRedBlocks]
+    unsigned *counter;  // [1]
+};
+
+template <typename T>
+__device__ inline double dd(T v) { return (double)v; }
+
+// Block-level sum of up to 3 values; result valid in thread 0.
+template <int K>
+__device__ inline void block_sum(double (&v)[K])
+{
+    __shared__ double sh[K][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double x = (lane < (int)(blockDim.x >> 5)) ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            v[k] = x;
+        }
+    }
+}
+
+// Publishes the block partials; returns true in thread 0 of the last block,
+// with tot[] holding the grid sums added in block order.
+template <int K>
+__device__ inline bool grid_sum(Dev d, double (&v)[K], double (&tot)[K])
+{
+    block_sum<K>(v);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) d.partial[k * kRedBlocks + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned prev = atomicAdd(d.counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double *)d.partial)[k * kRedBlocks + b];
+            tot[k] = s;
+        }
+        *d.counter = 0u;
+        return true;
+    }
+    return false;
+}
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------- outer / inner FCG
+// pq = (p, q); alpha = rz / pq (breakdown flag if pq <= 0 or not finite)
+template <typename T>
+__global__ void k_fcg_pq(Dev d, const T *p, const T *q, int64_t n, int slot_base)
+{
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += dd(p[i]) * dd(q[i]);
+    if (grid_sum<1>(d, v, tot)) {
+        double pq = tot[0];
+        d.scal[slot_base + S_PQ] = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            d.flag[F_BREAK] = 1;
+            d.scal[slot_base + S_ALPHA] = 0.0;
+        } else {
+            d.scal[slot_base + S_ALPHA] = d.scal[slot_base + S_RZ] / pq;
+        }
+    }
+}
+
+// x += alpha p ; r -= alpha q ; rr = (r, r)
+template <typename T, typename TX>
+__global__ void k_fcg_update(Dev d, TX *x, T *r, const T *p, const T *q, int64_t n, int slot_base)
+{
+    const double alpha = d.scal[slot_base + S_ALPHA];
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n)
+    {
+        x[i] = (TX)(dd(x[i]) + alpha * dd(p[i]));
+        double ri = dd(r[i]) - alpha * dd(q[i]);
+        r[i] = (T)ri;
+        v[0] += ri * ri;
+    }
+    if (grid_sum<1>(d, v, tot)) {
+        d.scal[slot_base + S_RR] = tot[0];
+        if (!isfinite(tot[0])) d.flag[F_BREAK] = 1;
+    }
+}
+
+// zr = (z, r), zq = (z, q); flexible (Polak-Ribiere) beta = -alpha zq / rz;
+// rz <- zr.  With q = A p and r_new = r_old - alpha q this is
+// (z, r_new - r_old) / rz_old.
+template <typename T>
+__global__ void k_fcg_beta(Dev d, const T *z, const T *r, const T *q, int64_t n, int slot_base)
+{
+    double v[2] = {0.0, 0.0}, tot[2];
+    GRID_STRIDE(i, n)
+    {
+        double zi = dd(z[i]);
+        v[0] += zi * dd(r[i]);
+        v[1] += zi * dd(q[i]);
+    }
+    if (grid_sum<2>(d, v, tot)) {
+        double rz_old = d.scal[slot_base + S_RZ];
+        double beta = -d.scal[slot_base + S_ALPHA] * tot[1] / rz_old;
+        if (!isfinite(beta)) {
+            d.flag[F_BREAK] = 1;
+            beta = 0.0;
+        }
+        d.scal[slot_base + S_BETA] = beta;
+        d.scal[slot_base + S_RZ] = tot[0];
+        d.scal[slot_base + S_ZR] = tot[0];
+        d.scal[slot_base + S_ZQ] = tot[1];
+    }
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void k_fcg_p(Dev d, T *p, const T *z, int64_t n, int slot_base)
+{
+    const double beta = d.scal[slot_base + S_BETA];
+    GRID_STRIDE(i, n) p[i] = (T)(dd(z[i]) + beta * dd(p[i]));
+}
+
+// rz = (r, z), rr = (r, r), p = z   (FCG start)
+template <typename T>
+__global__ void k_fcg_start(Dev d, T *p, const T *z, const T *r, int64_t n, int slot_base)
+{
+    double v[2] = {0.0, 0.0}, tot[2];
+    GRID_STRIDE(i, n)
+    {
+        double zi = dd(z[i]), ri = dd(r[i]);
+        p[i] = z[i];
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+    }
+    if (grid_sum<2>(d, v, tot)) {
+        d.scal[slot_base + S_RZ] = tot[0];
+        d.scal[slot_base + S_RR] = tot[1];
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) d.flag[F_BREAK] = 1;
+    }
+}
+
+// out[slot] = (a, a)
+template <typename T>
+__global__ void k_norm2(Dev d, const T *a, int64_t n, int slot)
+{
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += dd(a[i]) * dd(a[i]);
+    if (grid_sum<1>(d, v, tot)) d.scal[slot] = tot[0];
+}
+
+// r = b - t
+template <typename TB, typename TT, typename TR>
+__global__ void k_sub(TR *r, const TB *b, const TT *t, int64_t n)
+{
+    GRID_STRIDE(i, n) r[i] = (TR)(dd(b[i]) - dd(t[i]));
+}
+
+// y = (TY) (s * x)
+template <typename TX, typename TY>
+__global__ void k_scale_copy(TY *y, const TX *x, double s, int64_t n)
+{
+    GRID_STRIDE(i, n) y[i] = (TY)(s * dd(x[i]));
+}
+
+// x += s * d
+template <typename TX, typename TD>
+__global__ void k_axpy(TX *x, const TD *dv, double s, int64_t n)
+{
+    GRID_STRIDE(i, n) x[i] = (TX)(dd(x[i]) + s * dd(dv[i]));
+}
+
+// ------------------------------------------------------------- coarse CG
+// start: x = 0, r = b, p = Dinv r, rz = (r, Dinv r), bb = (b, b), done = bb == 0
+__global__ void k_cg_start(Dev d, double *x, double *r, double *p, const double *b, const double *dinv, int64_t n,
+                           double tol2)
+{
+    double v[2] = {0.0, 0.0}, tot[2];
+    GRID_STRIDE(i, n)
+    {
+        double bi = b[i], zi = dinv[i] * bi;
+        x[i] = 0.0;
+        r[i] = bi;
+        p[i] = zi;
+        v[0] += bi * zi;
+        v[1] += bi * bi;
+    }
+    if (grid_sum<2>(d, v, tot)) {
+        d.scal[C_RZ] = tot[0];
+        d.scal[C_BB] = tot[1];
+        d.scal[C_RR] = tot[1];
+        d.scal[C_TOL2] = tol2;
+        d.flag[F_CDONE] = (tot[1] == 0.0 || !isfinite(tot[1])) ? 1 : 0;
+    }
+}
+
+__global__ void k_cg_pq(Dev d, const double *p, const double *q, int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += p[i] * q[i];
+    if (grid_sum<1>(d, v, tot)) {
+        double pq = tot[0];
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            d.flag[F_CDONE] = 1;  // stop on breakdown; x keeps the last iterate
+            d.scal[C_ALPHA] = 0.0;
+        } else {
+            d.scal[C_ALPHA] = d.scal[C_RZ] / pq;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; rr = (r, r); rzn = (r, Dinv r); beta = rzn / rz
+__global__ void k_cg_update(Dev d, double *x, double *r, const double *p, const double *q, const double *dinv,
+                            int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    const double alpha = d.scal[C_ALPHA];
+    double v[2] = {0.0, 0.0}, tot[2];
+    GRID_STRIDE(i, n)
+    {
+        x[i] += alpha * p[i];
+        double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        v[0] += ri * ri;
+        v[1] += ri * dinv[i] * ri;
+    }
+    if (grid_sum<2>(d, v, tot)) {
+        d.scal[C_RR] = tot[0];
+        d.scal[C_BETA] = tot[1] / d.scal[C_RZ];
+        d.scal[C_RZ] = tot[1];
+        if (tot[0] <= d.scal[C_TOL2] * d.scal[C_BB] || !isfinite(tot[0])) d.flag[F_CDONE] = 1;
+    }
+}
+
+__global__ void k_cg_p(Dev d, double *p, const double *r, const double *dinv, int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    const double beta = d.scal[C_BETA];
+    GRID_STRIDE(i, n) p[i] = dinv[i] * r[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------ smoothing
+// Chebyshev step: rk = r - t (t may be null: rk = r);
+// d = cd d + cr Dinv rk; e = d (first step from a zero guess) or e += d.
+template <typename T>
+__global__ void k_cheb(T *e, T *dv, const T *r, const T *t, const T *dinv, double cd, double cr, int first_zero,
+                       int64_t n)
+{
+    GRID_STRIDE(i, n)
+    {
+        double rk = dd(r[i]) - (t ? dd(t[i]) : 0.0);
+        double di = (cd != 0.0 ? cd * dd(dv[i]) : 0.0) + cr * dd(dinv[i]) * rk;
+        dv[i] = (T)di;
+        e[i] = first_zero ? (T)di : (T)(dd(e[i]) + di);
+    }
+}
+
+template <typename T>
+__global__ void k_recip(T *dinv, const T *dg, int64_t n)
+{
+    GRID_STRIDE(i, n) dinv[i] = (T)(1.0 / dd(dg[i]));
+}
+
+// deterministic pseudo-random start vector (splitmix64 of the index), zero on
+// essential dofs
+__global__ void k_random(double *v, const uint8_t *ess, int64_t n, uint64_t seed)
+{
+    GRID_STRIDE(i, n)
+    {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        v[i] = (ess && ess[i]) ? 0.0 : u;
+    }
+}
+
+// ------------------------------------------------------------- transfers
+// One axis of the global tensor-product interpolation between the degree-pc
+// and degree-pf GLL spaces on the same n-element axis.  Arrays are
+// [3][Nz][Ny][Nx]; `ax` is the axis being changed (0 = x, 1 = y, 2 = z).
+// L[a*(pf+1) + j] = coarse basis a at fine node j (1D).
+struct XferTab {
+    double L[kMaxD * kMaxD];
+};
+
+template <typename T>
+__global__ void k_prolong_axis(T *out, const T *in, int ax, int Nx, int Ny, int Nz, int n, int pc, int pf,
+                               XferTab tab, int accumulate)
+{
+    // out dims: axis `ax` fine (n pf + 1), others as given (already in their final size)
+    const int Mf = n * pf + 1, Mc = n * pc + 1;
+    int dims[3] = {Nx, Ny, Nz};
+    dims[ax] = Mf;
+    int64_t total = 3LL * dims[0] * dims[1] * dims[2];
+    GRID_STRIDE(o, total)
+    {
+        int64_t t = o;
+        int i0 = (int)(t % dims[0]); t /= dims[0];
+        int i1 = (int)(t % dims[1]); t /= dims[1];
+        int i2 = (int)(t % dims[2]);
+        int c = (int)(t / dims[2]);
+        int idx[3] = {i0, i1, i2};
+        int i = idx[ax];
+        int k = i / pf;
+        if (k > n - 1) k = n - 1;
+        int jl = i - k * pf;
+        int cdims[3] = {dims[0], dims[1], dims[2]};
+        cdims[ax] = Mc;
+        double s = 0.0;
+        for (int a = 0; a <= pc; ++a) {
+            double w = tab.L[a * (pf + 1) + jl];
+            if (w == 0.0) continue;
+            idx[ax] = k * pc + a;
+            int64_t ci = (((int64_t)c * cdims[2] + idx[2]) * cdims[1] + idx[1]) * cdims[0] + idx[0];
+            s += w * dd(in[ci]);
+        }
+        out[o] = accumulate ? (T)(dd(out[o]) + s) : (T)s;
+    }
+}
+
+// Exact transpose of k_prolong_axis along one axis.  in2 (optional) is
+// subtracted from in on the fly; ess (optional, on the output L-vector) zeroes
+// essential entries.
+template <typename T>
+__global__ void k_restrict_axis(T *out, const T *in, const T *in2, int ax, int Nx, int Ny, int Nz, int n, int pc,
+                                int pf, XferTab tab, const uint8_t *ess)
+{
+    const int Mf = n * pf + 1, Mc = n * pc + 1;
+    int dims[3] = {Nx, Ny, Nz};  // input dims (axis `ax` fine)
+    int odims[3] = {Nx, Ny, Nz};
+    dims[ax] = Mf;
+    odims[ax] = Mc;
+    int64_t total = 3LL * odims[0] * odims[1] * odims[2];
+    GRID_STRIDE(o, total)
+    {
+        int64_t t = o;
+        int i0 = (int)(t % odims[0]); t /= odims[0];
+        int i1 = (int)(t % odims[1]); t /= odims[1];
+        int i2 = (int)(t % odims[2]);
+        int c = (int)(t / odims[2]);
+        int idx[3] = {i0, i1, i2};
+        int jc = idx[ax];
+        double s = 0.0;
+        int kk = jc / pc;
+        for (int k = kk - 1; k <= kk; ++k) {
+            if (k < 0 || k > n - 1) continue;
+            int a = jc - k * pc;
+            if (a < 0 || a > pc) continue;
+            for (int jl = 0; jl <= pf; ++jl) {
+                int i = k * pf + jl;
+                int owner = i / pf;
+                if (owner > n - 1) owner = n - 1;
+                if (owner != k) continue;
+                double w = tab.L[a * (pf + 1) + jl];
+                if (w == 0.0) continue;
+                idx[ax] = i;
+                int64_t fi = (((int64_t)c * dims[2] + idx[2]) * dims[1] + idx[1]) * dims[0] + idx[0];
+                double v = dd(in[fi]);
+                if (in2) v -= dd(in2[fi]);
+                s += w * v;
+            }
+        }
+        if (ess && ess[o]) s = 0.0;
+        out[o] = (T)s;
+    }
+}
+
+unsigned blocks_for(int64_t n, int th = 256)
+{
+    int64_t b = (n + th - 1) / th;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- levels --
+struct Level {
+    int p = 0;
+    pa_op *op = nullptr;    // FP64 operator (level 0: the caller's)
+    pa_op *op32 = nullptr;  // FP32 operator (mixed mode, smoothed levels)
+    bool own_op = false;
+    int64_t n = 0;
+    double *dinv = nullptr;
+    float *dinv32 = nullptr;
+    // work vectors (FP64 and FP32 copies for mixed mode)
+    double *r = nullptr, *e = nullptr, *t = nullptr, *d = nullptr;
+    float *r32 = nullptr, *e32 = nullptr, *t32 = nullptr, *d32 = nullptr;
+    double *xa = nullptr, *xb = nullptr;  // transfer temporaries (fine size of this level)
+    float *xa32 = nullptr, *xb32 = nullptr;
+    XferTab xt{};  // coarse (next level) basis at this level's nodes
+    double lmax = 0.0;
+    double theta = 0.0, delta = 0.0;
+    // coarse CG vectors
+    double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr;
+};
+
+}  // namespace pa
+
+struct pa_solver {
+    std::vector<pa::Level> lv;
+    int mode = PA_SOLVE_FP64;
+    int cheb_order = 2;
+    double coarse_rtol = 1e-2;
+    int coarse_maxit = 50;
+    pa::Dev dev{};
+    double *h_scal = nullptr;  // pinned mirror of a few scalars
+    int *h_flag = nullptr;
+    // outer vectors (FP64)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t = nullptr;
+    // inner (mixed) vectors
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr, *b32 = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace pa {
+namespace {
+
+template <typename T>
+int dalloc(pa_solver *s, T **ptr, int64_t n)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)(n > 0 ? n : 1));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(PA_ENOMEM, "solver: device allocation")
+                                                                 : cuda_error(e, "solver: cudaMalloc");
+    s->allocs.push_back(p);
+    *ptr = static_cast<T *>(p);
+    return PA_OK;
+}
+
+// coarse essential mask: coarse dof j is essential when the coarse basis
+// function j is non-zero at some essential fine dof (exact for essential sets
+// made of whole element faces).
+std::vector<uint8_t> coarse_mask(const std::vector<uint8_t> &fine, const Grid &gf, int pc, const Basis1D &bc,
+                                 const Basis1D &bf)
+{
+    const int pf = gf.p;
+    std::vector<double> val((size_t)(pc + 1) * (pf + 1)), der(val.size());
+    lagrange_product(pc + 1, bc.nodes.data(), pf + 1, bf.nodes.data(), val.data(), der.data());
+    const int Mxc = gf.nx * pc + 1, Myc = gf.ny * pc + 1, Mzc = gf.nz * pc + 1;
+    const int64_t Nnc = (int64_t)Mxc * Myc * Mzc;
+    std::vector<uint8_t> out((size_t)3 * Nnc, 0);
+    auto owners = [&](int i, int n, int *cj) {
+        int k = std::min(i / pf, n - 1), jl = i - k * pf, cnt = 0;
+        for (int a = 0; a <= pc; ++a)
+            if (std::fabs(val[a * (pf + 1) + jl]) > 1e-14) cj[cnt++] = k * pc + a;
+        return cnt;
+    };
+    int cx[kMaxD + 1], cy[kMaxD + 1], cz[kMaxD + 1];
+    for (int c = 0; c < 3; ++c)
+        for (int64_t gn = 0; gn < gf.Nn; ++gn) {
+            if (!fine[(size_t)c * gf.Nn + gn]) continue;
+            int gx = (int)(gn % gf.Mx), gy = (int)((gn / gf.Mx) % gf.My), gz = (int)(gn / ((int64_t)gf.Mx * gf.My));
+            int nxa = owners(gx, gf.nx, cx), nya = owners(gy, gf.ny, cy), nza = owners(gz, gf.nz, cz);
+            for (int k = 0; k < nza; ++k)
+                for (int j = 0; j < nya; ++j)
+                    for (int i = 0; i < nxa; ++i)
+                        out[(size_t)c * Nnc + cx[i] + (int64_t)Mxc * (cy[j] + (int64_t)Myc * cz[k])] = 1;
+        }
+    return out;
+}
+
+int make_level_op(const pa_op *fine, int p, int precision, const std::vector<uint8_t> &mask, pa_op **out)
+{
+    pa_mesh m;
+    m.nx = fine->g.nx;
+    m.ny = fine->g.ny;
+    m.nz = fine->g.nz;
+    m.affine = fine->h_affine;
+    return pa_op_setup(&m, p, 0, fine->lambda, fine->mu, precision, mask.empty() ? nullptr : mask.data(), out);
+}
+
+// blocking read of one device scalar
+double read_scalar(pa_solver *s, int slot, cudaStream_t st)
+{
+    cudaMemcpyAsync(s->h_scal + slot, s->dev.scal + slot, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return s->h_scal[slot];
+}
+
+// power iteration for lambda_max(D^-1 A) of level l (FP64), 10 steps from a
+// fixed pseudo-random start (Sec. 3.1)
+int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    k_random<<<blocks_for(n), 256, 0, st>>>(L.e, L.op->d_ess, n, 0x1234567ull + (uint64_t)L.p);
+    double lam = 0.0;
+    for (int it = 0; it < 10; ++it) {
+        k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.e, n, P_DEN);
+        int rc = op_apply_async(L.op, L.e, L.t, false, st, nullptr);
+        if (rc) return rc;
+        // d = Dinv (A e)   (k_cheb with a zero guess, cd = 0, cr = 1)
+        k_cheb<double><<<blocks_for(n), 256, 0, st>>>(L.d, L.r, L.t, nullptr, L.dinv, 0.0, 1.0, 1, n);
+        k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.d, n, P_NUM);
+        PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + P_NUM, s->dev.scal + P_NUM, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        const double num = s->h_scal[P_NUM], den = s->h_scal[P_DEN];
+        if (!(den > 0.0) || !(num > 0.0) || !std::isfinite(num))
+            return set_error(PA_EBREAKDOWN, "solver: power iteration broke down");
+        lam = std::sqrt(num / den);
+        k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(L.e, L.d, 1.0 / std::sqrt(num), n);
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    L.lmax = lam;
+    // Chebyshev interval [0.3, 1.2] * lambda_max
+    double a = 0.3 * lam, b = 1.2 * lam;
+    L.theta = 0.5 * (a + b);
+    L.delta = 0.5 * (b - a);
+    return PA_OK;
+}
+
+// ------------------------------------------------------------ V-cycle (T)
+template <typename T>
+struct LV {
+    static T *r(Level &L);
+    static T *e(Level &L);
+    static T *t(Level &L);
+    static T *d(Level &L);
+    static T *dinv(Level &L);
+    static T *xa(Level &L);
+    static T *xb(Level &L);
+    static pa_op *op(Level &L);
+};
+template <> double *LV<double>::r(Level &L) { return L.r; }
+template <> double *LV<double>::e(Level &L) { return L.e; }
+template <> double *LV<double>::t(Level &L) { return L.t; }
+template <> double *LV<double>::d(Level &L) { return L.d; }
+template <> double *LV<double>::dinv(Level &L) { return L.dinv; }
+template <> double *LV<double>::xa(Level &L) { return L.xa; }
+template <> double *LV<double>::xb(Level &L) { return L.xb; }
+template <> pa_op *LV<double>::op(Level &L) { return L.op; }
+template <> float *LV<float>::r(Level &L) { return L.r32; }
+template <> float *LV<float>::e(Level &L) { return L.e32; }
+template <> float *LV<float>::t(Level &L) { return L.t32; }
+template <> float *LV<float>::d(Level &L) { return L.d32; }
+template <> float *LV<float>::dinv(Level &L) { return L.dinv32; }
+template <> float *LV<float>::xa(Level &L) { return L.xa32; }
+template <> float *LV<float>::xb(Level &L) { return L.xb32; }
+template <> pa_op *LV<float>::op(Level &L) { return L.op32; }
+
+// Chebyshev smoothing of A e = r on level L (cheb_order steps); from a zero
+// guess the first step needs no operator apply.
+template <typename T>
+int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    T *e = LV<T>::e(L), *dv = LV<T>::d(L), *r = LV<T>::r(L), *t = LV<T>::t(L), *dinv = LV<T>::dinv(L);
+    pa_op *op = LV<T>::op(L);
+    const double sigma = L.theta / L.delta;
+    double rho_prev = 1.0 / sigma;
+    for (int k = 0; k < s->cheb_order; ++k) {
+        const T *tt = nullptr;
+        if (!(k == 0 && from_zero)) {
+            int rc = op_apply_async(op, e, t, false, st, nullptr);
+            if (rc) return rc;
+            tt = t;
+        }
+        double cd, cr;
+        if (k == 0) {
+            cd = 0.0;
+            cr = 1.0 / L.theta;
+        } else {
+            double rho = 1.0 / (2.0 * sigma - rho_prev);
+            cd = rho * rho_prev;
+            cr = 2.0 * rho / L.delta;
+            rho_prev = rho;
+        }
+        k_cheb<T><<<blocks_for(n), 256, 0, st>>>(e, dv, r, tt, dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// rc = R (r - t) of level l into level l+1 (T storage)
+template <typename T>
+void restrict_to(Level &F, Level &C, const T *r, const T *t, T *out, cudaStream_t st)
+{
+    const Grid &g = F.op->g;
+    const int n_[3] = {g.nx, g.ny, g.nz};
+    const int pf = F.p, pc = C.p;
+    const int Mf[3] = {g.Mx, g.My, g.Mz};
+    const int Mc[3] = {n_[0] * pc + 1, n_[1] * pc + 1, n_[2] * pc + 1};
+    T *xa = LV<T>::xa(F), *xb = LV<T>::xb(F);
+    // x axis: [3][Mzf][Myf][Mxf] -> [3][Mzf][Myf][Mxc]
+    int64_t n1 = 3LL * Mf[2] * Mf[1] * Mc[0];
+    k_restrict_axis<T><<<blocks_for(n1), 256, 0, st>>>(xa, r, t, 0, Mf[0], Mf[1], Mf[2], n_[0], pc, pf, F.xt, nullptr);
+    int64_t n2 = 3LL * Mf[2] * Mc[1] * Mc[0];
+    k_restrict_axis<T><<<blocks_for(n2), 256, 0, st>>>(xb, xa, nullptr, 1, Mc[0], Mf[1], Mf[2], n_[1], pc, pf, F.xt,
+                                                       nullptr);
+    int64_t n3 = 3LL * Mc[2] * Mc[1] * Mc[0];
+    k_restrict_axis<T><<<blocks_for(n3), 256, 0, st>>>(out, xb, nullptr, 2, Mc[0], Mc[1], Mf[2], n_[2], pc, pf, F.xt,
+                                                       C.op->d_ess);
+}
+
+// e_f += P e_c
+template <typename T>
+void prolong_add(Level &F, Level &C, const T *ec, T *ef, cudaStream_t st)
+{
+    const Grid &g = F.op->g;
+    const int n_[3] = {g.nx, g.ny, g.nz};
+    const int pf = F.p, pc = C.p;
+    const int Mf[3] = {g.Mx, g.My, g.Mz};
+    const int Mc[3] = {n_[0] * pc + 1, n_[1] * pc + 1, n_[2] * pc + 1};
+    T *xa = LV<T>::xa(F), *xb = LV<T>::xb(F);
+    int64_t n1 = 3LL * Mc[2] * Mc[1] * Mf[0];
+    k_prolong_axis<T><<<blocks_for(n1), 256, 0, st>>>(xa, ec, 0, Mc[0], Mc[1], Mc[2], n_[0], pc, pf, F.xt, 0);
+    int64_t n2 = 3LL * Mc[2] * Mf[1] * Mf[0];
+    k_prolong_axis<T><<<blocks_for(n2), 256, 0, st>>>(xb, xa, 1, Mf[0], Mc[1], Mc[2], n_[1], pc, pf, F.xt, 0);
+    int64_t n3 = 3LL * Mf[2] * Mf[1] * Mf[0];
+    k_prolong_axis<T><<<blocks_for(n3), 256, 0, st>>>(ef, xb, 2, Mf[0], Mf[1], Mc[2], n_[2], pc, pf, F.xt, 1);
+}
+
+// FP64 Jacobi-CG on the coarsest level: L.cx = A^-1 b approximately.
+int coarse_solve(pa_solver *s, Level &L, const double *b, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    k_cg_start<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, b, L.dinv, n,
+                                                   s->coarse_rtol * s->coarse_rtol);
+    for (int it = 0; it < s->coarse_maxit; ++it) {
+        int rc = op_apply_async(L.op, L.cp, L.cq, false, st, s->dev.flag + F_CDONE);
+        if (rc) return rc;
+        k_cg_pq<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cp, L.cq, n);
+        k_cg_update<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, L.dinv, n);
+        k_cg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, L.cr, L.dinv, n);
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// V(1,1) cycle: approximately solves A e = r on level l (both in LV<T>
+// storage of that level); e starts from zero.
+template <typename T>
+int vcycle(pa_solver *s, int l, cudaStream_t st)
+{
+    Level &L = s->lv[l];
+    const int nl = (int)s->lv.size();
+    if (l == nl - 1) {
+        // coarse: FP64 CG (convert if the cycle runs in FP32)
+        if constexpr (sizeof(T) == 8) {
+            int rc = coarse_solve(s, L, L.r, st);
+            if (rc) return rc;
+            k_scale_copy<double, double><<<blocks_for(L.n), 256, 0, st>>>(L.e, L.cx, 1.0, L.n);
+        } else {
+            k_scale_copy<float, double><<<blocks_for(L.n), 256, 0, st>>>(L.r, L.r32, 1.0, L.n);
+            int rc = coarse_solve(s, L, L.r, st);
+            if (rc) return rc;
+            k_scale_copy<double, float><<<blocks_for(L.n), 256, 0, st>>>(L.e32, L.cx, 1.0, L.n);
+        }
+        PA_CUDA_TRY(cudaGetLastError());
+        return PA_OK;
+    }
+    Level &C = s->lv[l + 1];
+    int rc = smooth<T>(s, L, true, st);
+    if (rc) return rc;
+    rc = op_apply_async(LV<T>::op(L), LV<T>::e(L), LV<T>::t(L), false, st, nullptr);
+    if (rc) return rc;
+    restrict_to<T>(L, C, LV<T>::r(L), LV<T>::t(L), LV<T>::r(C), st);
+    rc = vcycle<T>(s, l + 1, st);
+    if (rc) return rc;
+    prolong_add<T>(L, C, LV<T>::e(C), LV<T>::e(L), st);
+    rc = smooth<T>(s, L, false, st);
+    if (rc) return rc;
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// Flexible CG on level 0 in storage T (FP64 outer solve, or the FP32 inner
+// solve of the mixed mode).  x, b in storage TX / T.  Returns iterations.
+// Stops when (r, r) <= tol2 * bb or maxit.
+template <typename T, typename TX>
+int fcg(pa_solver *s, TX *x, const T *b, T *r, T *z, T *p, T *q, double tol2, double bb, int maxit, int *iters,
+        cudaStream_t st, bool x_zero)
+{
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    pa_op *op = LV<T>::op(L0);
+    int rc;
+    if (x_zero) {
+        cudaMemsetAsync(x, 0, sizeof(TX) * n, st);
+        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(r, b, 1.0, n);
+    } else {
+        rc = op_apply_async(op, x, q, false, st, nullptr);  // requires TX == T
+        if (rc) return rc;
+        k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(r, b, q, n);
+    }
+    // z = M r
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), r, 1.0, n);
+    rc = vcycle<T>(s, 0, st);
+    if (rc) return rc;
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(z, LV<T>::e(L0), 1.0, n);
+    k_fcg_start<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, p, z, r, n, 0);
+    double rr = read_scalar(s, S_RR, st);
+    int it = 0;
+    while (rr > tol2 * bb && it < maxit) {
+        rc = op_apply_async(op, p, q, false, st, nullptr);
+        if (rc) return rc;
+        k_fcg_pq<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, p, q, n, 0);
+        k_fcg_update<T, TX><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, x, r, p, q, n, 0);
+        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), r, 1.0, n);
+        rc = vcycle<T>(s, 0, st);
+        if (rc) return rc;
+        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(z, LV<T>::e(L0), 1.0, n);
+        k_fcg_beta<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, z, r, q, n, 0);
+        k_fcg_p<T><<<blocks_for(n), 256, 0, st>>>(s->dev, p, z, n, 0);
+        PA_CUDA_TRY(cudaGetLastError());
+        cudaMemcpyAsync(s->h_scal + S_RR, s->dev.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(s->h_flag, s->dev.flag, sizeof(int) * NFLAG, cudaMemcpyDeviceToHost, st);
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        rr = s->h_scal[S_RR];
+        ++it;
+        if (s->h_flag[F_BREAK]) {
+            *iters = it;
+            return set_error(PA_EBREAKDOWN, "solver: CG breakdown (p^T A p <= 0 or non-finite value)");
+        }
+    }
+    *iters = it;
+    return PA_OK;
+}
+
+}  // namespace
+}  // namespace pa
+
+using namespace pa;
+
+extern "C" {
+
+static int transfer_check(const pa_op *c, const pa_op *f)
+{
+    if (!c || !f) return set_error(PA_EINVAL, "transfer: null operator");
+    if (c->precision != PA_FP64 || f->precision != PA_FP64) return set_error(PA_EINVAL, "transfer: FP64 operators only");
+    if (c->g.nx != f->g.nx || c->g.ny != f->g.ny || c->g.nz != f->g.nz)
+        return set_error(PA_EINVAL, "transfer: operators live on different meshes");
+    if (!(c->p < f->p)) return set_error(PA_EINVAL, "transfer: coarse degree must be below fine degree");
+    return PA_OK;
+}
+
+static XferTab transfer_table(const pa_op *c, const pa_op *f)
+{
+    XferTab t{};
+    std::vector<double> val((size_t)(c->p + 1) * (f->p + 1)), der(val.size());
+    lagrange_product(c->p + 1, c->basis.nodes.data(), f->p + 1, f->basis.nodes.data(), val.data(), der.data());
+    for (size_t i = 0; i < val.size(); ++i) t.L[i] = std::fabs(val[i]) < 1e-15 ? 0.0 : val[i];
+    return t;
+}
+
+int pa_op_prolong(const pa_op *coarse, const pa_op *fine, const double *xc, double *xf, void *stream)
+{
+    int rc = transfer_check(coarse, fine);
+    if (rc) return rc;
+    if (!xc || !xf) return set_error(PA_EINVAL, "pa_op_prolong: null vector");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Level F, C;
+    F.op = const_cast<pa_op *>(fine);
+    F.p = fine->p;
+    C.op = const_cast<pa_op *>(coarse);
+    C.p = coarse->p;
+    F.xt = transfer_table(coarse, fine);
+    // the fine operator's staging vectors serve as sweep temporaries
+    F.xa = static_cast<double *>(fine->d_xh);
+    F.xb = static_cast<double *>(fine->d_yh);
+    PA_CUDA_TRY(cudaMemsetAsync(xf, 0, sizeof(double) * (size_t)fine->ndofs(), st));
+    prolong_add<double>(F, C, xc, xf, st);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, double *rc_out, void *stream)
+{
+    int rc = transfer_check(coarse, fine);
+    if (rc) return rc;
+    if (!rf || !rc_out) return set_error(PA_EINVAL, "pa_op_restrict: null vector");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Level F, C;
+    F.op = const_cast<pa_op *>(fine);
+    F.p = fine->p;
+    pa_op cmask_free = pa_op();  // restriction without essential masking
+    cmask_free.d_ess = nullptr;
+    C.op = &cmask_free;
+    C.p = coarse->p;
+    F.xt = transfer_table(coarse, fine);
+    F.xa = static_cast<double *>(fine->d_xh);
+    F.xb = static_cast<double *>(fine->d_yh);
+    restrict_to<double>(F, C, rf, nullptr, rc_out, st);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+int pa_solver_destroy(pa_solver *s)
+{
+    if (!s) return PA_OK;
+    for (auto &L : s->lv) {
+        if (L.own_op) pa_op_destroy(L.op);
+        pa_op_destroy(L.op32);
+    }
+    for (void *p : s->allocs) cudaFree(p);
+    cudaFree(s->dev.scal);
+    cudaFree(s->dev.flag);
+    cudaFree(s->dev.partial);
+    cudaFree(s->dev.counter);
+    cudaFreeHost(s->h_scal);
+    cudaFreeHost(s->h_flag);
+    delete s;
+    return PA_OK;
+}
+
+int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order, double coarse_rtol, int coarse_maxit,
+                     int mode, pa_solver **out)
+{
+    if (!out) return set_error(PA_EINVAL, "pa_solver_create: null output");
+    *out = nullptr;
+    if (!fine || !p_levels || nlev < 1 || nlev > 8) return set_error(PA_EINVAL, "pa_solver_create: bad levels");
+    if (fine->precision != PA_FP64) return set_error(PA_EINVAL, "pa_solver_create: fine operator must be FP64");
+    if (p_levels[0] != fine->p) return set_error(PA_EINVAL, "pa_solver_create: p_levels[0] must be the fine degree");
+    for (int l = 1; l < nlev; ++l)
+        if (p_levels[l] >= p_levels[l - 1] || p_levels[l] < 1)
+            return set_error(PA_EINVAL, "pa_solver_create: degrees must decrease");
+    if (cheb_order < 1 || cheb_order > 8) return set_error(PA_EINVAL, "pa_solver_create: cheb_order in 1..8");
+    if (coarse_maxit < 1 || !(coarse_rtol >= 0.0)) return set_error(PA_EINVAL, "pa_solver_create: bad coarse parameters");
+    if (mode != PA_SOLVE_FP64 && mode != PA_SOLVE_MIXED) return set_error(PA_EINVAL, "pa_solver_create: bad mode");
+
+    pa_solver *s = new (std::nothrow) pa_solver;
+    if (!s) return set_error(PA_ENOMEM, "pa_solver_create: host allocation");
+    s->mode = mode;
+    s->cheb_order = cheb_order;
+    s->coarse_rtol = coarse_rtol;
+    s->coarse_maxit = coarse_maxit;
+    int rc = PA_OK;
+#define TRY(x)                        \
+    do {                              \
+        rc = (x);                     \
+        if (rc) {                     \
+            pa_solver_destroy(s);     \
+            return rc;                \
+        }                             \
+    } while (0)
+#define TRYC(x) TRY(((x) == cudaSuccess) ? PA_OK : cuda_error(cudaGetLastError(), #x))
+    TRYC(cudaMalloc((void **)&s->dev.scal, sizeof(double) * NSLOT));
+    TRYC(cudaMalloc((void **)&s->dev.flag, sizeof(int) * NFLAG));
+    TRYC(cudaMalloc((void **)&s->dev.partial, sizeof(double) * 3 * kRedBlocks));
+    TRYC(cudaMalloc((void **)&s->dev.counter, sizeof(unsigned)));
+    TRYC(cudaMemset(s->dev.counter, 0, sizeof(unsigned)));
+    TRYC(cudaMemset(s->dev.flag, 0, sizeof(int) * NFLAG));
+    TRYC(cudaMemset(s->dev.scal, 0, sizeof(double) * NSLOT));
+    TRYC(cudaMallocHost((void **)&s->h_scal, sizeof(double) * NSLOT));
+    TRYC(cudaMallocHost((void **)&s->h_flag, sizeof(int) * NFLAG));
+
+    s->lv.resize(nlev);
+    std::vector<uint8_t> mask = fine->h_ess;
+    for (int l = 0; l < nlev; ++l) {
+        Level &L = s->lv[l];
+        L.p = p_levels[l];
+        if (l == 0) {
+            L.op = fine;
+        } else {
+            const pa_op *F = s->lv[l - 1].op;
+            if (!mask.empty()) {
+                Basis1D bc;
+                bc.build(L.p, L.p + 2);
+                mask = coarse_mask(mask, F->g, L.p, bc, F->basis);
+            }
+            TRY(make_level_op(fine, L.p, PA_FP64, mask, &L.op));
+            L.own_op = true;
+        }
+        L.n = L.op->ndofs();
+        if (mode == PA_SOLVE_MIXED) TRY(make_level_op(fine, L.p, PA_FP32, L.op->h_ess, &L.op32));
+    }
+    cudaStream_t st = nullptr;
+    for (int l = 0; l < nlev; ++l) {
+        Level &L = s->lv[l];
+        const int64_t n = L.n;
+        TRY(dalloc(s, &L.dinv, n));
+        TRY(dalloc(s, &L.r, n));
+        TRY(dalloc(s, &L.e, n));
+        TRY(dalloc(s, &L.t, n));
+        TRY(dalloc(s, &L.d, n));
+        TRY(pa_op_diag(L.op, L.t, st));
+        k_recip<double><<<blocks_for(n), 256, 0, st>>>(L.dinv, L.t, n);
+        if (l < nlev - 1) {
+            TRY(dalloc(s, &L.xa, n));
+            TRY(dalloc(s, &L.xb, n));
+            const int pc = p_levels[l + 1];
+            Basis1D bc;
+            bc.build(pc, pc + 2);
+            std::vector<double> val((size_t)(pc + 1) * (L.p + 1)), der(val.size());
+            lagrange_product(pc + 1, bc.nodes.data(), L.p + 1, L.op->basis.nodes.data(), val.data(), der.data());
+            for (size_t i = 0; i < val.size(); ++i) L.xt.L[i] = std::fabs(val[i]) < 1e-15 ? 0.0 : val[i];
+            TRY(estimate_lmax(s, L, st));
+        } else {
+            TRY(dalloc(s, &L.cx, n));
+            TRY(dalloc(s, &L.cr, n));
+            TRY(dalloc(s, &L.cp, n));
+            TRY(dalloc(s, &L.cq, n));
+        }
+        if (mode == PA_SOLVE_MIXED) {
+            TRY(dalloc(s, &L.r32, n));
+            TRY(dalloc(s, &L.e32, n));
+            TRY(dalloc(s, &L.dinv32, n));
+            TRY(dalloc(s, &L.t32, n));
+            TRY(dalloc(s, &L.d32, n));
+            TRY(dalloc(s, &L.xa32, n));
+            TRY(dalloc(s, &L.xb32, n));
+            k_scale_copy<double, float><<<blocks_for(n), 256, 0, st>>>(L.dinv32, L.dinv, 1.0, n);
+        }
+    }
+    const int64_t n0 = s->lv[0].n;
+    TRY(dalloc(s, &s->r, n0));
+    TRY(dalloc(s, &s->z, n0));
+    TRY(dalloc(s, &s->p, n0));
+    TRY(dalloc(s, &s->q, n0));
+    TRY(dalloc(s, &s->t, n0));
+    if (mode == PA_SOLVE_MIXED) {
+        TRY(dalloc(s, &s->r32, n0));
+        TRY(dalloc(s, &s->z32, n0));
+        TRY(dalloc(s, &s->p32, n0));
+        TRY(dalloc(s, &s->q32, n0));
+        TRY(dalloc(s, &s->x32, n0));
+        TRY(dalloc(s, &s->b32, n0));
+    }
+    TRYC(cudaDeviceSynchronize());
+    TRYC(cudaGetLastError());
+#undef TRY
+#undef TRYC
+    *out = s;
+    clear_error();
+    return PA_OK;
+}
+
+int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
+                     void *stream)
+{
+    if (!s || !b || !x) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: null argument");
+    if (!(rtol > 0.0) || maxit < 0) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: bad tolerance or cap");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    pa_solve_info inf{};
+    for (size_t l = 0; l < s->lv.size() && l < 8; ++l) inf.lambda_max[l] = s->lv[l].lmax;
+    PA_CUDA_TRY(cudaMemsetAsync(s->dev.flag, 0, sizeof(int) * NFLAG, st));
+    k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
+    const double bb = read_scalar(s, S_BB, st);
+    inf.b_norm = std::sqrt(bb);
+    int status = PA_OK, rc = PA_OK;
+    const double tol2 = rtol * rtol;
+    if (bb == 0.0) {
+        PA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        inf.rel_residual = 0.0;
+        if (info) *info = inf;
+        return PA_OK;
+    }
+    if (!std::isfinite(bb)) {
+        if (info) *info = inf;
+        return set_error(PA_EINVAL, "pa_gmg_pcg_solve: b has non-finite entries");
+    }
+    bool converged = false;
+    if (s->mode == PA_SOLVE_FP64) {
+        int it = 0;
+        rc = fcg<double, double>(s, x, b, s->r, s->z, s->p, s->q, tol2, bb, maxit, &it, st, false);
+        inf.iterations = it;
+        converged = (rc == PA_OK) && s->h_scal[S_RR] <= tol2 * bb;
+    } else {
+        // iterative refinement: r = b - A x (FP64), inner FCG in FP32 on A d = r.
+        // Stops at the tolerance, or when a refinement step no longer halves
+        // the FP64 residual (its rounding floor).
+        int total_inner = 0, refine = 0;
+        double rr_prev = -1.0;
+        while (true) {
+            rc = op_apply_async(L0.op, x, s->t, false, st, nullptr);
+            if (rc) break;
+            k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, b, s->t, n);
+            k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+            double rr = read_scalar(s, S_RR, st);
+            if (!std::isfinite(rr)) {
+                rc = set_error(PA_EBREAKDOWN, "solver: non-finite residual");
+                break;
+            }
+            if (rr <= tol2 * bb) {
+                converged = true;
+                break;
+            }
+            if (rr_prev >= 0.0 && rr > 0.25 * rr_prev) {
+                converged = true;  // stagnation at the FP64 residual floor
+                break;
+            }
+            if (total_inner >= maxit) break;
+            rr_prev = rr;
+            // the residual scaled to unit norm is the FP32 right-hand side
+            const double sc = 1.0 / std::sqrt(rr);
+            k_scale_copy<double, float><<<blocks_for(n), 256, 0, st>>>(s->b32, s->r, sc, n);
+            int it = 0;
+            // inner solve: relative reduction 1e-4 or at most 50 iterations
+            rc = fcg<float, float>(s, s->x32, s->b32, s->r32, s->z32, s->p32, s->q32, 1e-8, 1.0,
+                                   std::min(50, maxit - total_inner), &it, st, true);
+            if (rc) break;
+            total_inner += it;
+            ++refine;
+            k_axpy<double, float><<<blocks_for(n), 256, 0, st>>>(x, s->x32, 1.0 / sc, n);
+            if (it == 0) break;
+        }
+        inf.iterations = total_inner;
+        inf.inner_iterations = total_inner;
+        inf.refinements = refine;
+    }
+    if (rc == PA_EBREAKDOWN) status = PA_EBREAKDOWN;
+    else if (rc) {
+        if (info) *info = inf;
+        return rc;
+    }
+    // true residual in FP64
+    int rc2 = op_apply_async(L0.op, x, s->t, false, st, nullptr);
+    if (rc2) return rc2;
+    k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, b, s->t, n);
+    k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+    double rr = read_scalar(s, S_RR, st);
+    PA_CUDA_TRY(cudaGetLastError());
+    inf.rel_residual = std::sqrt(rr / bb);
+    if (status == PA_OK && !converged) status = PA_ENOTCONV;
+    inf.status = status;
+    if (info) *info = inf;
+    if (status == PA_ENOTCONV) set_error(PA_ENOTCONV, "pa_gmg_pcg_solve: iteration cap reached");
+    return status;
+}
+
+}  // extern "C"

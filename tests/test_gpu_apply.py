@@ -142,3 +142,70 @@ def test_rhs(pa, p):
     op.close()
     Fo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), modes=modes, ess=ess)
     assert _relerr(F, Fo) <= 1e-12
+
+
+LINE_OK = {0: range(1, 5), 1: range(1, 9)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_apply_register_tiled_variant(pa, p, prec):
+    """The register-tiled kernel (variant 1) against the oracle, with two
+    CTA shapes (one leaving a ragged last CTA)."""
+    if p not in LINE_OK[prec]:
+        pytest.skip("variant 1 not instantiated for this degree in FP64")
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=300 + p, ny=ny, nz=nz)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=7 + p)
+    yo = oracle.apply(p, nx, ny, nz, m.affine, lam, mu, x, ess=ess)
+    op = pa.Operator(nx, ny, nz, m.affine, p, lam, mu, precision=prec, ess_mask=ess)
+    xt = torch.tensor(x, dtype=op.dtype, device="cuda")
+    ran = 0
+    for epb, th in [(1, 128), (7, 256), (3, 256)]:
+        try:
+            pa.pa_op_set_launch(op.h, 1, epb, th)
+        except pa.PAError as e:  # shape beyond the shared-memory limit for this degree
+            assert e.code == pa.PA_EINVAL
+            continue
+        y = op.apply(xt).double().cpu().numpy()
+        assert _relerr(y, yo) <= TOL[prec], (epb, th)
+        ran += 1
+    assert ran >= 2
+    op.close()
+
+
+def test_autotune_keeps_parity(pa):
+    p = 4
+    m = syn.random_affine_cube(4, seed=9)
+    lam, mu = syn.lame(1.0, 0.3)
+    x = syn.uniform_vector(m.n_dofs(p), seed=1)
+    yo = oracle.apply(p, 4, 4, 4, m.affine, lam, mu, x)
+    for prec in (0, 1):
+        op = pa.Operator(4, 4, 4, m.affine, p, lam, mu, precision=prec)
+        cfg = pa.pa_op_autotune(op.h)
+        assert cfg[0] in (0, 1) and cfg[1] >= 1 and cfg[2] % 32 == 0
+        y = op.apply(torch.tensor(x, dtype=op.dtype, device="cuda")).double().cpu().numpy()
+        assert _relerr(y, yo) <= TOL[prec]
+        op.close()
+
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (4, 8), (1, 3), (3, 6)])
+def test_transfers_against_oracle(pa, pc, pf):
+    m = syn.random_affine_cube(3, seed=pc + pf, ny=2, nz=2)
+    opc = pa.Operator(m.nx, m.ny, m.nz, m.affine, pc, 1.0, 1.0)
+    opf = pa.Operator(m.nx, m.ny, m.nz, m.affine, pf, 1.0, 1.0)
+    rng = np.random.default_rng(pc * 7 + pf)
+    u = rng.normal(size=opc.ndofs)
+    v = rng.normal(size=opf.ndofs)
+    xf = torch.empty(opf.ndofs, dtype=torch.float64, device="cuda")
+    rc = torch.empty(opc.ndofs, dtype=torch.float64, device="cuda")
+    pa.pa_op_prolong(opc.h, opf.h, torch.tensor(u, device="cuda"), xf)
+    pa.pa_op_restrict(opc.h, opf.h, torch.tensor(v, device="cuda"), rc)
+    Pu = oracle.prolong(pc, pf, m.nx, m.ny, m.nz, u)
+    Rv = oracle.restrict(pc, pf, m.nx, m.ny, m.nz, v)
+    assert _relerr(xf.cpu().numpy(), Pu) <= 1e-13
+    assert _relerr(rc.cpu().numpy(), Rv) <= 1e-13
+    opc.close()
+    opf.close()

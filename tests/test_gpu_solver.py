@@ -1,0 +1,113 @@
+"""GMG-PCG solver on the GPU against direct FP64 solves of the oracle's
+assembled matrix, and against the oracle operator's residual at the
+cantilever-beam size (32 x 4 x 4 elements, p = 4)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pa():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_08374_gb300 as pa
+    return pa
+
+
+def _beam(nx, ny, nz):
+    return syn.box_mesh(nx, ny, nz, hi=(8.0, 1.0, 1.0))
+
+
+def _solve(pa, mesh, p, levels, lam, mu, mode=0, rtol=1e-10, maxit=500, f0=(0.0, 0.0, -1.0), modes=None,
+           coarse_rtol=1e-4, coarse_maxit=300):
+    ess = syn.clamp_mask(mesh, p)
+    op = pa.Operator(mesh.nx, mesh.ny, mesh.nz, mesh.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(f0=f0, modes=modes)
+    x = torch.zeros_like(b)
+    s = pa.pa_solver_create(op.h, levels, 2, coarse_rtol, coarse_maxit, mode)
+    code, info = pa.pa_gmg_pcg_solve(s, b, x, rtol, maxit)
+    pa.pa_solver_destroy(s)
+    out = (code, info, x.cpu().numpy(), b.cpu().numpy(), ess)
+    op.close()
+    return out
+
+
+@pytest.mark.parametrize("p,levels", [(2, [2, 1]), (4, [4, 2, 1]), (3, [3, 1])])
+def test_small_beam_matches_direct_solve(pa, p, levels):
+    m = _beam(4, 1, 1)
+    lam, mu = syn.lame(1.0, 0.3)
+    code, info, x, b, ess = _solve(pa, m, p, levels, lam, mu)
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    assert info.rel_residual <= 1e-10
+    xo = oracle.solve_dense(p, m.nx, m.ny, m.nz, m.affine, lam, mu, b, ess)
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert 1 <= info.iterations <= 60
+
+
+def test_medium_beam_matches_direct_solve_fp64_and_mixed(pa):
+    m = _beam(8, 2, 2)
+    p = 4
+    lam, mu = syn.lame(1.0, 0.3)
+    code, info, x, b, ess = _solve(pa, m, p, [4, 2, 1], lam, mu, coarse_rtol=1e-4, coarse_maxit=300)
+    assert code == pa.PA_OK
+    xo = oracle.solve_dense(p, m.nx, m.ny, m.nz, m.affine, lam, mu, b, ess)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, err
+    # the FP64 residual floor of this problem lies above 1e-10 (a direct
+    # solve reaches ~4e-10): the true residual is reported, not forced
+    assert info.rel_residual <= 2e-9
+    code, info2, x2, _, _ = _solve(pa, m, p, [4, 2, 1], lam, mu, mode=pa.PA_SOLVE_MIXED, coarse_rtol=1e-4,
+                                   coarse_maxit=300)
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    assert info2.rel_residual <= 2e-9
+    assert np.linalg.norm(x2 - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert info2.refinements >= 1
+
+
+def test_beam_32x4x4_p4_true_residual_against_oracle(pa):
+    m = _beam(32, 4, 4)
+    p = 4
+    lam, mu = syn.lame(1.0, 0.3)
+    code, info, x, b, ess = _solve(pa, m, p, [4, 2, 1], lam, mu, coarse_rtol=1e-4, coarse_maxit=300)
+    assert code == pa.PA_OK
+    assert info.rel_residual <= 1e-8  # FP64 residual floor of this problem is ~1e-9
+    # residual with the oracle's operator and load vector
+    bo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+    assert np.max(np.abs(b - bo)) <= 1e-12 * np.max(np.abs(bo))
+    r = bo - oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, x, ess=ess)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(bo)
+    assert info.iterations <= 40
+    # mixed precision reaches the same solution
+    code2, info2, x2, _, _ = _solve(pa, m, p, [4, 2, 1], lam, mu, mode=pa.PA_SOLVE_MIXED, coarse_rtol=1e-4,
+                                    coarse_maxit=300)
+    assert code2 == pa.PA_OK
+    assert np.linalg.norm(x2 - x) <= 1e-8 * np.linalg.norm(x)
+    assert all(info.lambda_max[l] > 0 for l in range(2))
+
+
+def test_status_codes(pa):
+    m = _beam(4, 1, 1)
+    lam, mu = syn.lame(1.0, 0.3)
+    code, info, x, b, ess = _solve(pa, m, 2, [2, 1], lam, mu, maxit=1, rtol=1e-14)
+    assert code == pa.PA_ENOTCONV and info.iterations == 1
+    code, info, x, b, ess = _solve(pa, m, 2, [2, 1], lam, mu, f0=(0.0, 0.0, 0.0))
+    assert code == pa.PA_OK and np.all(x == 0.0) and info.b_norm == 0.0
+
+
+def test_nan_rhs_is_rejected(pa):
+    m = _beam(2, 1, 1)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, 2, 1.0, 1.0, ess_mask=syn.clamp_mask(m, 2))
+    b = op.rhs(f0=(0, 0, -1.0))
+    b[5] = float("nan")
+    x = torch.zeros_like(b)
+    s = pa.pa_solver_create(op.h, [2, 1])
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_gmg_pcg_solve(s, b, x)
+    assert ei.value.code == pa.PA_EINVAL
+    pa.pa_solver_destroy(s)
+    op.close()
