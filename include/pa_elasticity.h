@@ -152,6 +152,32 @@ int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64
 int pa_op_prolong(const pa_op *coarse, const pa_op *fine, const double *xc, double *xf, void *stream);
 int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, double *rc, void *stream);
 
+/* Operator apply that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- plugins whose host framework owns all device memory through
+ * its own pool, and latency-critical loops that must not block on the
+ * implicit synchronisation of cudaMalloc/cudaFree.  It computes the same
+ * y = A x as pa_op_setup + pa_op_apply, with everything passed in:
+ *   nx, ny, nz, p, lambda, mu, precision : as for pa_mesh_create/pa_op_setup
+ *                                          (q = p + 2);
+ *   affine   : DEVICE double[n_e][12], per element J (row-major) then x0;
+ *   ess_mask : DEVICE uint8[3*Nn] or NULL (constrained operator as above);
+ *   x, y     : DEVICE L-vectors of `precision`, not aliased.
+ * Scratch (geometry records and the element output vector,
+ * 12 + 3 (p+1)^3 values per element, the geometry part rounded up to 256
+ * bytes, plus 4 bytes) lives in one fixed
+ * 64 MiB array in device memory that every GPU loading this library holds
+ * until the process exits; meshes needing more are rejected with PA_EINVAL
+ * and a message giving the required size.  Nothing in the scratch needs to
+ * start at zero: every call overwrites what it reads.  All calls on a device
+ * share that array, so calls that overlap on the GPU (other streams, other
+ * host threads) race; serialise them.  The first call on a device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  Asynchronous on `stream`; an element map with
+ * det J <= 0 makes every entry of y NaN. */
+int pa_apply_noalloc(int nx, int ny, int nz, int p, double lambda, double mu, int precision, const double *affine,
+                     const uint8_t *ess_mask, const void *x, void *y, void *stream);
+
 /* -------------------------------------------------------------- solver -- */
 
 typedef struct pa_solve_info {

@@ -60,6 +60,8 @@ _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_op_restrict", [_vp, _vp, _vp, _vp, _vp])
+_sig("pa_apply_noalloc", [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("pa_op_set_launch", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int])
 _sig("pa_op_get_launch", [_vp, _ip, _ip, _ip])
 _sig("pa_op_autotune", [_vp, _vp])
@@ -181,6 +183,13 @@ def pa_op_prolong(coarse, fine, xc, xf, stream=None):
 
 def pa_op_restrict(coarse, fine, rf, rc, stream=None):
     _check(lib.pa_op_restrict(coarse, fine, _tptr(rf), _tptr(rc), _stream_ptr(stream)), "pa_op_restrict")
+
+
+def pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, affine, x, y, ess_mask=None, stream=None):
+    """Allocation-free apply; affine, x, y (and ess_mask) are CUDA tensors."""
+    _check(lib.pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, _tptr(affine),
+                                _tptr(ess_mask) if ess_mask is not None else None, _tptr(x), _tptr(y),
+                                _stream_ptr(stream)), "pa_apply_noalloc")
 
 
 def pa_op_set_launch(op, variant, elems_per_block, threads):
