@@ -164,7 +164,10 @@ def run_ours(args):
     for p in ps:
         n, mesh, x = workload(p)
         op = pa.Operator(n, n, n, mesh.affine, p, lam, mu, precision=prec)
-        if not args.no_autotune:
+        if args.launch:
+            v, e, t = (int(a) for a in args.launch.split(","))
+            pa.pa_op_set_launch(op.h, v, e, t)
+        elif not args.no_autotune:
             pa.pa_op_autotune(op.h, stream)
         xt = torch.tensor(x, dtype=dt, device="cuda")
         yt = torch.empty_like(xt)
@@ -288,6 +291,10 @@ def run_ours(args):
         "gpu_launches": 2 * len(cases) * args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_solve:
+        out["solve"] = run_solves(args, pa, torch)
+    if args.serve_requests > 0:
+        out["serving"] = run_serving(args, pa, torch)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(ps, args)
     print(json.dumps(out), flush=True)
@@ -296,6 +303,135 @@ def run_ours(args):
     for c in cases:
         c["op"].close()
     return out
+
+
+def run_solves(args, pa, torch):
+    """GMG-PCG solves/s: the cantilever beam (32x4x4 elements, p = 4 -> 2 -> 1,
+    FP64 and mixed) and the near-incompressible random-affine cubes (~8M
+    dofs, p = 6 and 8, FP64 and mixed).  Setup (operators, diagonals,
+    eigenvalue estimates, graph capture on the first solve) is untimed."""
+    out = []
+    cases = [dict(name="beam 32x4x4 p=4 (4->2->1) E=1 nu=0.3 f=(0,0,-1), x=0 clamped", mesh=syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0)),
+                  p=4, levels=[4, 2, 1], nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
+    if not args.quick_solves:
+        for p, n in ((6, syn.mixed_n(6)), (8, syn.mixed_n(8))):
+            lv = [p, p // 2, 1] if p == 6 else [8, 4, 2, 1]
+            cases.append(dict(name=f"cube {n}^3 p={p} random affine maps nu=0.45 smooth force, x=0 clamped",
+                              mesh=syn.random_affine_cube(n, seed=3000 + p), p=p, levels=lv, nu=0.45,
+                              modes=syn.smooth_force_modes(seed=3100 + p), f0=(0.0, 0.0, 0.0), reps=max(1, args.solve_reps // 2)))
+    for c in cases:
+        m, p = c["mesh"], c["p"]
+        lam, mu = syn.lame(1.0, c["nu"])
+        ess = syn.clamp_mask(m, p)
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+        b = op.rhs(f0=c["f0"], modes=c["modes"])
+        row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "rtol": 1e-10}
+        sols = {}
+        for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed")):
+            s = pa.pa_solver_create(op.h, c["levels"], 2, 1e-3, 300, mode)
+            x = torch.zeros_like(b)
+            code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)  # warm-up (captures the graphs)
+            times = []
+            for _ in range(c["reps"]):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+                times.append(time.perf_counter() - t0)
+            sols[key] = x.clone()
+            row[key] = {"status": int(code), "solves_per_s": round(1.0 / statistics.median(times), 3),
+                        "median_s": round(statistics.median(times), 5), "iterations": info.iterations,
+                        "true_rel_residual": float(f"{info.rel_residual:.3e}")}
+            if mode == pa.PA_SOLVE_MIXED:
+                row[key]["refinements"] = info.refinements
+            pa.pa_solver_destroy(s)
+        d = (sols["mixed"] - sols["fp64"]).norm() / sols["fp64"].norm()
+        row["mixed_vs_fp64_rel_diff"] = float(f"{float(d):.3e}")
+        row["speedup_mixed_over_fp64"] = round(row["mixed"]["solves_per_s"] / row["fp64"]["solves_per_s"], 3)
+        out.append(row)
+        op.close()
+    return out
+
+
+def serving_requests(pa, count, seed):
+    """The served stream: p uniform in {2,4,6,8}; a cube n^3 (n ~ U{8..32}) or
+    an 8:1:1 beam (8k x k x k, k ~ U{4..16}); E log-uniform in [0.1, 10];
+    nu ~ U[0.2, 0.45]; 3 seeded sine modes of body force per component;
+    clamped at x = 0; mixed-precision solve to 1e-10."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        p = int(rng.choice([2, 4, 6, 8]))
+        if rng.random() < 0.5:
+            n = int(rng.integers(8, 33))
+            dims, box = (n, n, n), (0, 0, 0, 1.0, 1.0, 1.0)
+        else:
+            kk = int(rng.integers(4, 17))
+            dims, box = (8 * kk, kk, kk), (0, 0, 0, 8.0, 1.0, 1.0)
+        E = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        nu = float(rng.uniform(0.2, 0.45))
+        modes = syn.smooth_force_modes(seed=int(rng.integers(1 << 30)))
+        out.append(pa.make_request(*dims, box, p, E, nu, modes=modes, rtol=1e-10, maxit=1000,
+                                   mode=pa.PA_SOLVE_MIXED, keep_solution=False))
+    return out
+
+
+def run_serving(args, pa, torch):
+    """Continuous-admission serving of a Poisson stream.  The arrival rate is
+    a fraction of the capacity measured on a calibration burst of the same
+    recipe (all submitted at once).  Reports p50/p99 latency (submit to
+    completion) and completed solves/s."""
+    import threading
+    reqs = serving_requests(pa, args.serve_requests, seed=4242)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    # calibration: a burst of the first requests, all at once
+    ncal = min(len(reqs), args.serve_calibration)
+    srv = pa.pa_server_create(budget, args.serve_slots)
+    t0 = time.perf_counter()
+    ts = [pa.pa_server_submit(srv, r) for r in reqs[:ncal]]
+    for t in ts:
+        pa.pa_server_wait(srv, t)
+    cap = ncal / (time.perf_counter() - t0)
+    pa.pa_server_destroy(srv)
+    rate = args.serve_load * cap
+    arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
+    srv = pa.pa_server_create(budget, args.serve_slots)
+    tickets = [None] * len(reqs)
+    start = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            delay = arrivals[i] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = pa.pa_server_submit(srv, r)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, statuses, iters, solve_s = [], [], [], []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.001)
+        code, info, tm, _ = pa.pa_server_wait(srv, tickets[i])
+        statuses.append(code)
+        lat.append(tm.latency_s)
+        iters.append(info.iterations)
+        solve_s.append(tm.solve_s)
+    th.join()
+    wall = time.perf_counter() - start
+    st = pa.pa_server_stats(srv)
+    pa.pa_server_destroy(srv)
+    lat = np.array(lat)
+    return {"requests": len(reqs), "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+            "calibration_capacity_solves_per_s": round(cap, 3), "arrival_rate_per_s": round(rate, 3),
+            "load_fraction": args.serve_load, "solves_per_s": round(len(reqs) / wall, 3),
+            "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+            "mean_solve_s": round(float(np.mean(solve_s)), 4), "mean_iterations": round(float(np.mean(iters)), 1),
+            "ok": int(sum(1 for c in statuses if c == pa.PA_OK)),
+            "peak_used_gb": round(st.peak_used_bytes / (1 << 30), 2),
+            "recipe": "Poisson arrivals; p U{2,4,6,8}; cube n^3 n~U{8..32} or beam 8k x k x k k~U{4..16}; "
+                      "E log-U[0.1,10]; nu U[0.2,0.45]; 3 sine modes/component; x=0 clamped; mixed precision, rtol 1e-10"}
 
 
 def _oracle_sweep(ps, scale):
@@ -359,6 +495,16 @@ def main(argv=None):
     ap.add_argument("--ps", default=",".join(map(str, SWEEP)))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the GMG-PCG solve measurements")
+    ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")
+    ap.add_argument("--solve-reps", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=256, help="0 skips the serving measurement")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
+    ap.add_argument("--serve-calibration", type=int, default=24)
+    ap.add_argument("--launch", default="", help="fixed element-kernel shape 'variant,elems_per_cta,threads' "
+                                                 "(skips the autotuner)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -56,6 +56,7 @@ enum pa_precision { PA_FP64 = 0, PA_FP32 = 1 };
 typedef struct pa_mesh pa_mesh;
 typedef struct pa_op pa_op;
 typedef struct pa_solver pa_solver;
+typedef struct pa_server pa_server;
 
 /* Message describing the last error on this thread ("" if none). */
 const char *pa_last_error(void);
@@ -178,6 +179,15 @@ int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, dou
 int pa_apply_noalloc(int nx, int ny, int nz, int p, double lambda, double mu, int precision, const double *affine,
                      const uint8_t *ess_mask, const void *x, void *y, void *stream);
 
+/* Assembled matrix of an FP64 p = 1 operator (Sec. 3.2: the coarsest level
+ * is the one level that is assembled), as a 27-point nodal stencil without
+ * essential-dof handling: vals is a DEVICE double array of 81 * 3Nn entries,
+ * entry (row, k) at k * 3Nn + row, row = c*Nn + i, k = s*3 + d, where column
+ * (d, j) with j = i + dx + Mx (dy + My dz), s = (dx+1) + 3(dy+1) + 9(dz+1);
+ * entries whose neighbour lies outside the grid are 0.  The solver uses it
+ * for its FP64 coarse CG. */
+int pa_op_assemble_p1(const pa_op *op, double *vals, void *stream);
+
 /* -------------------------------------------------------------- solver -- */
 
 typedef struct pa_solve_info {
@@ -204,6 +214,12 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
                      int coarse_maxit, int mode, pa_solver **out);
 int pa_solver_destroy(pa_solver *s);
 
+/* Solver options: PA_SOLVER_OPT_GRAPHS (value 1, default: each CG step runs
+ * as one captured CUDA graph with a device-controlled coarse loop; value 0:
+ * the same kernels are launched one by one). */
+enum pa_solver_option { PA_SOLVER_OPT_GRAPHS = 1 };
+int pa_solver_set_option(pa_solver *s, int option, double value);
+
 /* Solve A x = b (x: in = initial guess, out = solution; device double
  * L-vectors).  FP64 mode: flexible CG stops when its recursively updated
  * residual satisfies ||r||_2 <= rtol ||b||_2.  Mixed mode: iterative
@@ -212,11 +228,68 @@ int pa_solver_destroy(pa_solver *s);
  * of order eps ||A|| ||x|| / ||b||, which for stiff bending problems can lie
  * above 1e-10).  info->rel_residual is always the true FP64 residual
  * ||b - A x|| / ||b|| recomputed at exit.  maxit caps the outer CG
- * iterations (FP64) or the total inner iterations (mixed).  Synchronises
- * `stream`; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every
- * case when non-NULL), PA_EINVAL for a non-finite b. */
+ * iterations (FP64) or the total inner iterations (mixed).  Waits for
+ * `stream`, runs on the solver's own stream and returns when x is written;
+ * returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every case when
+ * non-NULL), PA_EINVAL for a non-finite b. */
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream);
+
+/* -------------------------------------------------------------- server -- */
+
+/* Serving of many solves with continuous admission (no counterpart in the
+ * paper's CPU study; it drives the same operator and solver).  Requests are
+ * queued in arrival order; a request is admitted when one of `max_slots`
+ * slots is free and its estimated device footprint fits in the memory budget
+ * still available, and it then runs (setup, load vector, GMG-PCG solve) on a
+ * worker thread and CUDA stream of its own, so the work of admitted requests
+ * overlaps on the GPU.  Finished requests release their memory and the next
+ * queued ones are admitted.  Solves are deterministic: a request gives the
+ * same bits alone or in any mix. */
+#define PA_REQUEST_MAX_MODES 16
+
+typedef struct pa_request {
+    int nx, ny, nz;        /* elements per direction                              */
+    double box[6];         /* xlo, ylo, zlo, xhi, yhi, zhi of the structured mesh */
+    int p;                 /* degree 1..8; levels p, p/2, ..., 1                   */
+    double E, nu;          /* material (Lame parameters via pa_lame)               */
+    double f0[3];          /* constant body force                                 */
+    int nmodes;            /* sine modes per component, <= PA_REQUEST_MAX_MODES    */
+    double modes[3 * PA_REQUEST_MAX_MODES * 5]; /* [3][nmodes][5] (amp, kx, ky, kz, phase) */
+    int clamp_x0;          /* non-zero: all dofs on the x = xlo face are essential */
+    double rtol;           /* solve tolerance (see pa_gmg_pcg_solve)               */
+    int maxit;             /* iteration cap                                        */
+    int mode;              /* PA_SOLVE_FP64 or PA_SOLVE_MIXED                      */
+    int keep_solution;     /* non-zero: keep x on the host for pa_server_wait      */
+} pa_request;
+
+typedef struct pa_request_timing {
+    double latency_s;        /* submit to completion                      */
+    double queue_s;          /* submit to admission                       */
+    double setup_s;          /* operators, diagonals, eigenvalue estimates */
+    double solve_s;          /* pa_gmg_pcg_solve                          */
+    int64_t footprint_bytes; /* admission estimate of device memory       */
+} pa_request_timing;
+
+typedef struct pa_server_stats_t {
+    int64_t queued, running, completed, used_bytes, peak_used_bytes;
+} pa_server_stats_t;
+
+/* Uses the device current at creation; budget_bytes > 0; 1 <= max_slots <= 64. */
+int pa_server_create(size_t budget_bytes, int max_slots, pa_server **out);
+/* Copies *req and queues it; returns at once with a ticket.  A request whose
+ * footprint exceeds the whole budget completes with PA_EBUSY. */
+int pa_server_submit(pa_server *s, const pa_request *req, int64_t *ticket);
+/* *done = 1 once the request has finished. */
+int pa_server_poll(pa_server *s, int64_t ticket, int *done);
+/* Blocks until the request finishes, then returns its solve status and
+ * releases the ticket.  x_host (length x_len = 3 Nn, or NULL) receives the
+ * solution if the request kept it; info and timing may be NULL. */
+int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, pa_solve_info *info,
+                   pa_request_timing *timing);
+int pa_server_stats(pa_server *s, pa_server_stats_t *out);
+/* Finishes queued and running requests, then stops the workers. */
+int pa_server_destroy(pa_server *s);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,27 @@ class pa_solve_info(ctypes.Structure):
                 ("lambda_max", ctypes.c_double * 8)]
 
 
+PA_REQUEST_MAX_MODES = 16
+
+
+class pa_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("box", ctypes.c_double * 6),
+                ("p", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double), ("f0", ctypes.c_double * 3),
+                ("nmodes", ctypes.c_int), ("modes", ctypes.c_double * (3 * PA_REQUEST_MAX_MODES * 5)),
+                ("clamp_x0", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("mode", ctypes.c_int),
+                ("keep_solution", ctypes.c_int)]
+
+
+class pa_request_timing(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("setup_s", ctypes.c_double),
+                ("solve_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64)]
+
+
+class pa_server_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("used_bytes", ctypes.c_int64), ("peak_used_bytes", ctypes.c_int64)]
+
+
 def _sig(name, args, res=ctypes.c_int):
     f = getattr(lib, name)
     f.argtypes = args
@@ -58,6 +79,7 @@ _sig("pa_op_apply", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
+_sig("pa_op_assemble_p1", [_vp, _vp, _vp])
 _sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_op_restrict", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_apply_noalloc", [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -67,10 +89,18 @@ _sig("pa_op_get_launch", [_vp, _ip, _ip, _ip])
 _sig("pa_op_autotune", [_vp, _vp])
 _sig("pa_op_profile", [_vp, ctypes.c_int])
 _sig("pa_op_profile_read", [_vp, _dp, _dp, _i64p])
+_sig("pa_server_create", [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)])
+_sig("pa_server_submit", [_vp, ctypes.POINTER(pa_request), _i64p])
+_sig("pa_server_poll", [_vp, ctypes.c_int64, _ip])
+_sig("pa_server_wait", [_vp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.POINTER(pa_solve_info),
+                        ctypes.POINTER(pa_request_timing)])
+_sig("pa_server_stats", [_vp, ctypes.POINTER(pa_server_stats_t)])
+_sig("pa_server_destroy", [_vp])
 if hasattr(lib, "pa_solver_create"):
     _sig("pa_solver_create", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.POINTER(_vp)])
     _sig("pa_solver_destroy", [_vp])
+    _sig("pa_solver_set_option", [_vp, ctypes.c_int, ctypes.c_double])
     _sig("pa_gmg_pcg_solve", [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(pa_solve_info), _vp])
 
 
@@ -177,6 +207,10 @@ def pa_op_rhs(op, F, f0=(0.0, 0.0, 0.0), modes=None, stream=None):
     _check(lib.pa_op_rhs(op, _dptr(f0), nm, _dptr(md) if nm else None, _tptr(F), _stream_ptr(stream)), "pa_op_rhs")
 
 
+def pa_op_assemble_p1(op, vals, stream=None):
+    _check(lib.pa_op_assemble_p1(op, _tptr(vals), _stream_ptr(stream)), "pa_op_assemble_p1")
+
+
 def pa_op_prolong(coarse, fine, xc, xf, stream=None):
     _check(lib.pa_op_prolong(coarse, fine, _tptr(xc), _tptr(xf), _stream_ptr(stream)), "pa_op_prolong")
 
@@ -226,6 +260,13 @@ def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=
     return h
 
 
+PA_SOLVER_OPT_GRAPHS = 1
+
+
+def pa_solver_set_option(h, option, value):
+    _check(lib.pa_solver_set_option(h, option, value), "pa_solver_set_option")
+
+
 def pa_solver_destroy(h):
     lib.pa_solver_destroy(h)
 
@@ -236,6 +277,65 @@ def pa_gmg_pcg_solve(solver, b, x, rtol=1e-10, maxit=500, stream=None):
     if code not in (PA_OK, PA_ENOTCONV, PA_EBREAKDOWN):
         raise PAError(code, "pa_gmg_pcg_solve")
     return code, info
+
+
+def make_request(nx, ny, nz, box, p, E, nu, f0=(0.0, 0.0, 0.0), modes=None, clamp_x0=True, rtol=1e-10, maxit=1000,
+                 mode=PA_SOLVE_MIXED, keep_solution=False):
+    r = pa_request()
+    r.nx, r.ny, r.nz, r.p, r.E, r.nu = nx, ny, nz, p, E, nu
+    for i in range(6):
+        r.box[i] = float(box[i])
+    for i in range(3):
+        r.f0[i] = float(f0[i])
+    if modes is not None:
+        m = np.ascontiguousarray(modes, dtype=np.float64)
+        r.nmodes = m.shape[1]
+        if r.nmodes > PA_REQUEST_MAX_MODES:
+            raise ValueError("too many modes")
+        flat = m.reshape(-1)
+        for i, v in enumerate(flat):
+            r.modes[i] = float(v)
+    r.clamp_x0, r.rtol, r.maxit, r.mode, r.keep_solution = int(bool(clamp_x0)), rtol, maxit, mode, int(bool(keep_solution))
+    return r
+
+
+def pa_server_create(budget_bytes, max_slots):
+    h = _vp()
+    _check(lib.pa_server_create(int(budget_bytes), max_slots, ctypes.byref(h)), "pa_server_create")
+    return h
+
+
+def pa_server_submit(srv, req):
+    t = ctypes.c_int64()
+    _check(lib.pa_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "pa_server_submit")
+    return t.value
+
+
+def pa_server_poll(srv, ticket):
+    d = ctypes.c_int()
+    _check(lib.pa_server_poll(srv, ticket, ctypes.byref(d)), "pa_server_poll")
+    return bool(d.value)
+
+
+def pa_server_wait(srv, ticket, x_len=0):
+    """Returns (status, info, timing, x or None)."""
+    info, tm = pa_solve_info(), pa_request_timing()
+    x = np.empty(x_len) if x_len else None
+    code = lib.pa_server_wait(srv, ticket, x.ctypes.data_as(_dp) if x is not None else None, x_len,
+                              ctypes.byref(info), ctypes.byref(tm))
+    if code == PA_EINVAL:
+        raise PAError(code, "pa_server_wait")
+    return code, info, tm, x
+
+
+def pa_server_stats(srv):
+    st = pa_server_stats_t()
+    _check(lib.pa_server_stats(srv, ctypes.byref(st)), "pa_server_stats")
+    return st
+
+
+def pa_server_destroy(srv):
+    lib.pa_server_destroy(srv)
 
 
 # ------------------------------------------------------- object wrappers --

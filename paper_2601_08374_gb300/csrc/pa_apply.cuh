@@ -43,6 +43,8 @@ struct FlatLayout {
     static constexpr int bufB = (n1 > n3 ? (n1 > n5 ? n1 : n5) : (n3 > n5 ? n3 : n5));
     static constexpr int tab = 4 * D * Q;
     static constexpr int per_elem = bufA + bufB;
+    // byte offset of the per-CTA element table (global base node per element)
+    __host__ __device__ static size_t table_offset(int epb) { return (((size_t)tab + (size_t)epb * per_elem) * sizeof(T) + 15) & ~(size_t)15; }
 };
 
 template <typename T, int D, int Q>
@@ -73,6 +75,15 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
 
     const int p = D - 1;
     const int64_t Nn = a.g.Nn;
+    const int64_t Mx = a.g.Mx, MxMy = (int64_t)a.g.Mx * a.g.My;
+    int64_t *gbase = reinterpret_cast<int64_t *>(smem_raw + L::table_offset(epb));
+    for (int el = tid; el < ne_blk; el += nt) {
+        const int64_t e = e0 + el;
+        const int64_t t = e / a.g.nx;
+        const int ex = (int)(e - t * a.g.nx), ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
+        gbase[el] = (int64_t)ex * p + Mx * ((int64_t)ey * p) + MxMy * ((int64_t)ez * p);
+    }
+    __syncthreads();
     // ---- P0: gather x_e[el][c][iz][iy][ix] into bufA
     {
         const int total = ne_blk * L::nX;
@@ -80,12 +91,7 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
             int el = o / L::nX, r = o - el * L::nX;
             int c = r / D3, a3 = r - c * D3;
             int iz = a3 / (D * D), iy = (a3 / D) % D, ix = a3 % D;
-            int64_t e = e0 + el;
-            int ex = (int)(e % a.g.nx);
-            int64_t t = e / a.g.nx;
-            int ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
-            int64_t gn = (int64_t)(ex * p + ix) + (int64_t)a.g.Mx * ((int64_t)(ey * p + iy) + (int64_t)a.g.My * (ez * p + iz));
-            int64_t k = c * Nn + gn;
+            int64_t k = c * Nn + gbase[el] + ix + Mx * iy + MxMy * iz;
             T v = a.x[k];
             if (a.ess && a.ess[k]) v = T(0);
             bufA[(size_t)el * L::bufA + r] = v;
@@ -321,8 +327,7 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
 template <typename T, int D, int Q>
 size_t flat_smem_bytes(int epb)
 {
-    using L = FlatLayout<T, D, Q>;
-    return sizeof(T) * ((size_t)L::tab + (size_t)epb * L::per_elem);
+    return FlatLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
 }
 
 template <typename T, int D, int Q>

@@ -39,6 +39,9 @@ struct LineLayout {
     static constexpr int A = S0 > S2 ? S0 : S2;
     static constexpr int B = S1 > S3 ? S1 : S3;
     static constexpr int per_elem = A + B;
+    // bytes of the per-CTA element table (global base node of each element),
+    // placed after the value buffers
+    __host__ __device__ static size_t table_offset(int epb) { return (((size_t)epb * per_elem * sizeof(T)) + 15) & ~(size_t)15; }
 };
 
 template <typename T, int D, int Q>
@@ -57,18 +60,23 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
     if (ne_blk <= 0) return;
     const int p = D - 1;
     const int64_t Nn = a.g.Nn;
+    const int64_t Mx = a.g.Mx, MxMy = (int64_t)a.g.Mx * a.g.My;
+    int64_t *gbase = reinterpret_cast<int64_t *>(smem_raw + L::table_offset(epb));
+    for (int el = tid; el < ne_blk; el += nt) {
+        // global node of the element's local node (0,0,0): one runtime
+        // division per element instead of one per gathered value
+        const int64_t e = e0 + el;
+        const int64_t t = e / a.g.nx;
+        const int ex = (int)(e - t * a.g.nx), ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
+        gbase[el] = (int64_t)ex * p + Mx * ((int64_t)ey * p) + MxMy * ((int64_t)ez * p);
+    }
+    __syncthreads();
 
     // ---- gather x_e into S0 [c][iz][iy][ix]
     for (int o = tid; o < ne_blk * 3 * D3; o += nt) {
         int el = o / (3 * D3), r = o - el * 3 * D3;
         int ix = r % D, iy = (r / D) % D, iz = (r / (D * D)) % D, c = r / D3;
-        int64_t e = e0 + el;
-        int ex = (int)(e % a.g.nx);
-        int64_t t = e / a.g.nx;
-        int ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
-        int64_t gn = (int64_t)(ex * p + ix) +
-                     (int64_t)a.g.Mx * ((int64_t)(ey * p + iy) + (int64_t)a.g.My * (ez * p + iz));
-        int64_t k = c * Nn + gn;
+        int64_t k = c * Nn + gbase[el] + ix + Mx * iy + MxMy * iz;
         T v = a.x[k];
         if (a.ess && a.ess[k]) v = T(0);
         bufA[(size_t)el * L::A + ((c * D + iz) * D + iy) * DP + ix] = v;
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
 template <typename T, int D, int Q>
 size_t line_smem_bytes(int epb)
 {
-    return sizeof(T) * (size_t)epb * LineLayout<T, D, Q>::per_elem;
+    return LineLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
 }
 
 template <typename T, int D, int Q>

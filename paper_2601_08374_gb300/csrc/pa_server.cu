@@ -1,0 +1,332 @@
+// Solve server: continuous admission of elasticity solve requests.
+//
+// Requests are queued in arrival order.  A request is admitted as soon as a
+// slot is free and its estimated device footprint fits in what the memory
+// budget has left; it then runs on a worker thread of its own -- setup
+// (mesh, operators on every level, diagonals, eigenvalue estimates), load
+// vector and GMG-PCG solve -- on the solver's own CUDA stream, so the kernels
+// of all admitted requests overlap on the GPU.  When a request finishes its
+// memory is released and the next queued requests are admitted.  Every solve
+// is deterministic (fixed-order reductions, no atomics in the arithmetic), so
+// a request gives the same bits alone or in any mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pa_internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Ticket {
+    int64_t id = 0;
+    pa_request req{};
+    std::vector<int> levels;
+    size_t footprint = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int status = PA_OK;
+    std::string error;
+    pa_solve_info info{};
+    clk::time_point t_submit, t_start, t_end;
+    double setup_s = 0.0, solve_s = 0.0;
+    std::vector<double> x;  // host copy of the solution when requested
+};
+
+// Degrees of the p-hierarchy: halve down to 1 (8-4-2-1, 6-3-1, 4-2-1, 2-1).
+std::vector<int> p_levels_for(int p)
+{
+    std::vector<int> lv{p};
+    while (lv.back() > 1) lv.push_back(lv.back() / 2);
+    return lv;
+}
+
+// Device bytes that pa_op_setup + pa_solver_create + the request's own
+// vectors allocate (sum of the documented allocations).
+size_t footprint_bytes(const pa_request &r, const std::vector<int> &levels)
+{
+    const size_t ne = (size_t)r.nx * r.ny * r.nz;
+    size_t total = 0, n0 = 0;
+    for (size_t l = 0; l < levels.size(); ++l) {
+        const int p = levels[l], D = p + 1;
+        const size_t N = 3 * (size_t)(r.nx * p + 1) * (r.ny * p + 1) * (r.nz * p + 1);
+        if (l == 0) n0 = N;
+        auto op_bytes = [&](size_t elem) {
+            return ne * 12 * elem + ne * 96 + ne * 3 * (size_t)D * D * D * elem + 2 * N * elem + N;
+        };
+        total += op_bytes(8) + 5 * N * 8 + (l + 1 < levels.size() ? 2 : 4) * N * 8;
+        if (r.mode == PA_SOLVE_MIXED) total += op_bytes(4) + 7 * N * 4;
+    }
+    total += 7 * n0 * 8 + (r.mode == PA_SOLVE_MIXED ? 6 * n0 * 4 : 0);
+    total += 2 * n0 * 8;  // b and x of the request
+    return total + total / 10 + ((size_t)16 << 20);
+}
+
+}  // namespace
+
+struct pa_server {
+    size_t budget = 0, used = 0, peak_used = 0;
+    int max_slots = 1, running = 0, device = 0;
+    int64_t next_id = 1, completed = 0;
+    std::deque<std::shared_ptr<Ticket>> queue;
+    std::unordered_map<int64_t, std::shared_ptr<Ticket>> tickets;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::vector<std::thread> workers;
+    bool stop = false;
+};
+
+namespace {
+
+// Runs one admitted request end to end on the calling worker thread.
+void run_request(pa_server *srv, Ticket &t)
+{
+    const pa_request &r = t.req;
+    pa_mesh *mesh = nullptr;
+    pa_op *op = nullptr;
+    pa_solver *sol = nullptr;
+    double *b = nullptr, *x = nullptr;
+    int rc = PA_OK;
+    cudaStream_t st = nullptr;
+    auto fail = [&](int code) {
+        t.status = code;
+        t.error = pa_last_error();
+    };
+    do {
+        if (cudaSetDevice(srv->device) != cudaSuccess) { fail(pa::cuda_error(cudaGetLastError(), "cudaSetDevice")); break; }
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(pa::cuda_error(cudaGetLastError(), "cudaStreamCreate"));
+            break;
+        }
+        double lam = 0, mu = 0;
+        if ((rc = pa_lame(r.E, r.nu, &lam, &mu))) { fail(rc); break; }
+        if ((rc = pa_mesh_create(r.nx, r.ny, r.nz, r.box, nullptr, &mesh))) { fail(rc); break; }
+        std::vector<uint8_t> ess;
+        if (r.clamp_x0) {
+            const int64_t Mx = (int64_t)r.nx * r.p + 1, My = (int64_t)r.ny * r.p + 1, Mz = (int64_t)r.nz * r.p + 1;
+            const int64_t Nn = Mx * My * Mz;
+            ess.assign((size_t)(3 * Nn), 0);
+            for (int c = 0; c < 3; ++c)
+                for (int64_t g = 0; g < Nn; g += Mx) ess[(size_t)(c * Nn + g)] = 1;  // gx = 0
+        }
+        if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &op))) { fail(rc); break; }
+        pa_mesh_destroy(mesh);
+        mesh = nullptr;
+        if ((rc = pa_solver_create(op, (int)t.levels.size(), t.levels.data(), 2, 1e-3, 300, r.mode, &sol))) {
+            fail(rc);
+            break;
+        }
+        const size_t n = (size_t)op->ndofs();
+        if (cudaMalloc((void **)&b, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&x, n * sizeof(double)) != cudaSuccess) {
+            fail(pa::set_error(PA_ENOMEM, "server: device allocation for b, x"));
+            break;
+        }
+        if ((rc = pa_op_rhs(op, r.f0, r.nmodes, r.nmodes ? r.modes : nullptr, b, st))) { fail(rc); break; }
+        if (cudaMemsetAsync(x, 0, n * sizeof(double), st) != cudaSuccess) {
+            fail(pa::cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+            break;
+        }
+        auto t_setup = clk::now();
+        t.setup_s = std::chrono::duration<double>(t_setup - t.t_start).count();
+        rc = pa_gmg_pcg_solve(sol, b, x, r.rtol, r.maxit, &t.info, st);
+        t.solve_s = std::chrono::duration<double>(clk::now() - t_setup).count();
+        t.status = rc;
+        if (rc != PA_OK) t.error = pa_last_error();
+        if (r.keep_solution && rc != PA_EINVAL) {
+            t.x.resize(n);
+            if (cudaMemcpy(t.x.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+                fail(pa::cuda_error(cudaGetLastError(), "cudaMemcpy solution"));
+        }
+    } while (false);
+    cudaFree(b);
+    cudaFree(x);
+    pa_solver_destroy(sol);
+    pa_op_destroy(op);
+    pa_mesh_destroy(mesh);
+    if (st) cudaStreamDestroy(st);
+}
+
+void worker_main(pa_server *srv)
+{
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (true) {
+        // admit the head of the queue when a slot and memory are free; a
+        // request larger than the whole budget is rejected instead of waiting
+        std::shared_ptr<Ticket> t;
+        srv->cv_work.wait(lk, [&] {
+            if (srv->stop) return true;
+            if (srv->queue.empty() || srv->running >= srv->max_slots) return false;
+            const auto &h = srv->queue.front();
+            return h->footprint > srv->budget || srv->used + h->footprint <= srv->budget;
+        });
+        if (srv->stop) return;
+        t = srv->queue.front();
+        srv->queue.pop_front();
+        if (t->footprint > srv->budget) {
+            t->state = 2;
+            t->status = PA_EBUSY;
+            t->error = "server: request footprint exceeds the whole memory budget";
+            t->t_start = t->t_end = clk::now();
+            ++srv->completed;
+            srv->cv_done.notify_all();
+            srv->cv_work.notify_all();
+            continue;
+        }
+        srv->used += t->footprint;
+        srv->peak_used = std::max(srv->peak_used, srv->used);
+        ++srv->running;
+        t->state = 1;
+        t->t_start = clk::now();
+        // another request may fit as well
+        srv->cv_work.notify_all();
+        lk.unlock();
+        run_request(srv, *t);
+        lk.lock();
+        t->t_end = clk::now();
+        t->state = 2;
+        srv->used -= t->footprint;
+        --srv->running;
+        ++srv->completed;
+        srv->cv_done.notify_all();
+        srv->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+
+using namespace pa;
+
+extern "C" {
+
+int pa_server_create(size_t budget_bytes, int max_slots, pa_server **out)
+{
+    if (!out) return set_error(PA_EINVAL, "pa_server_create: null output");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 64) return set_error(PA_EINVAL, "pa_server_create: max_slots in 1..64");
+    if (budget_bytes == 0) return set_error(PA_EINVAL, "pa_server_create: zero memory budget");
+    pa_server *s = new (std::nothrow) pa_server;
+    if (!s) return set_error(PA_ENOMEM, "pa_server_create: host allocation");
+    s->budget = budget_bytes;
+    s->max_slots = max_slots;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return cuda_error(cudaGetLastError(), "pa_server_create: cudaGetDevice");
+    }
+    try {
+        for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        for (auto &w : s->workers) w.join();
+        delete s;
+        return set_error(PA_ENOMEM, "pa_server_create: could not start worker threads");
+    }
+    *out = s;
+    return PA_OK;
+}
+
+int pa_server_submit(pa_server *s, const pa_request *req, int64_t *ticket)
+{
+    if (!s || !req || !ticket) return set_error(PA_EINVAL, "pa_server_submit: null argument");
+    if (req->nx < 1 || req->ny < 1 || req->nz < 1 || req->p < 1 || req->p > kMaxP)
+        return set_error(PA_EINVAL, "pa_server_submit: bad mesh size or degree");
+    if (req->nmodes < 0 || req->nmodes > PA_REQUEST_MAX_MODES) return set_error(PA_EINVAL, "pa_server_submit: nmodes");
+    if (req->mode != PA_SOLVE_FP64 && req->mode != PA_SOLVE_MIXED) return set_error(PA_EINVAL, "pa_server_submit: mode");
+    if (!(req->rtol > 0.0) || req->maxit < 1) return set_error(PA_EINVAL, "pa_server_submit: rtol or maxit");
+    auto t = std::make_shared<Ticket>();
+    t->req = *req;
+    t->levels = p_levels_for(req->p);
+    t->footprint = footprint_bytes(*req, t->levels);
+    t->t_submit = clk::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        t->id = s->next_id++;
+        s->tickets[t->id] = t;
+        s->queue.push_back(t);
+    }
+    s->cv_work.notify_all();
+    *ticket = t->id;
+    return PA_OK;
+}
+
+int pa_server_poll(pa_server *s, int64_t ticket, int *done)
+{
+    if (!s || !done) return set_error(PA_EINVAL, "pa_server_poll: null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return set_error(PA_EINVAL, "pa_server_poll: unknown ticket");
+    *done = it->second->state == 2;
+    return PA_OK;
+}
+
+int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, pa_solve_info *info,
+                   pa_request_timing *timing)
+{
+    if (!s) return set_error(PA_EINVAL, "pa_server_wait: null server");
+    std::shared_ptr<Ticket> t;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return set_error(PA_EINVAL, "pa_server_wait: unknown ticket");
+        t = it->second;
+        s->cv_done.wait(lk, [&] { return t->state == 2; });
+        s->tickets.erase(it);
+    }
+    if (info) *info = t->info;
+    if (timing) {
+        timing->latency_s = std::chrono::duration<double>(t->t_end - t->t_submit).count();
+        timing->queue_s = std::chrono::duration<double>(t->t_start - t->t_submit).count();
+        timing->setup_s = t->setup_s;
+        timing->solve_s = t->solve_s;
+        timing->footprint_bytes = (int64_t)t->footprint;
+    }
+    if (x_host) {
+        if (t->x.empty()) return set_error(PA_EINVAL, "pa_server_wait: the request did not keep its solution");
+        if (x_len != (int64_t)t->x.size()) return set_error(PA_EINVAL, "pa_server_wait: x_len does not match");
+        std::memcpy(x_host, t->x.data(), t->x.size() * sizeof(double));
+    }
+    if (t->status != PA_OK) set_error(t->status, t->error);
+    return t->status;
+}
+
+int pa_server_stats(pa_server *s, pa_server_stats_t *out)
+{
+    if (!s || !out) return set_error(PA_EINVAL, "pa_server_stats: null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->queued = (int64_t)s->queue.size();
+    out->running = s->running;
+    out->completed = s->completed;
+    out->used_bytes = (int64_t)s->used;
+    out->peak_used_bytes = (int64_t)s->peak_used;
+    return PA_OK;
+}
+
+int pa_server_destroy(pa_server *s)
+{
+    if (!s) return PA_OK;
+    {
+        // finish what is queued or running, then stop the workers
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_done.wait(lk, [&] { return s->queue.empty() && s->running == 0; });
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &w : s->workers) w.join();
+    delete s;
+    return PA_OK;
+}
+
+}  // extern "C"

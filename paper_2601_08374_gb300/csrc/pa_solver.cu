@@ -8,9 +8,11 @@
 // deterministic two-level reductions (fixed block partition, last block sums
 // the partials in order), and the coefficients alpha/beta are formed on the
 // device, so an iteration enqueues without host round trips; the host reads
-// one residual norm per outer iteration to test convergence.  The coarse CG
-// loop runs a fixed number of launches whose kernels return at once after a
-// device flag marks convergence.
+// one residual norm per outer iteration to test convergence.  Each CG step
+// is captured once into a CUDA graph whose coarse CG is a conditional WHILE
+// node driven by a device-side stop flag, so a step is one graph launch and
+// the coarse solve runs only the iterations it needs (an eager path with a
+// fixed-length coarse loop of early-returning kernels remains as fallback).
 //
 // Mixed mode (PA_SOLVE_MIXED): iterative refinement in FP64 (residual
 // b - A x with the FP64 operator, FP64 norms), inner flexible CG in FP32
@@ -37,7 +39,7 @@ enum Slot {
     P_NUM = 24, P_DEN,
     NSLOT = 32
 };
-enum FlagSlot { F_BREAK = 0, F_CDONE = 1, NFLAG = 4 };
+enum FlagSlot { F_BREAK = 0, F_CDONE = 1, F_CIT = 2, NFLAG = 4 };
 
 struct Dev {
     double *scal;       // [NSLOT]
@@ -73,7 +75,9 @@ __device__ inline void block_sum(double (&v)[K])
 }
 
 // Publishes the block partials; returns true in thread 0 of the last block,
-// with tot[] holding the grid sums added in block order.
+// with tot[] holding the grid sums.  The last block adds the partials with
+// all its threads in a fixed assignment and a fixed tree, so the result is
+// deterministic for a given grid size.
 template <int K>
 __device__ inline bool grid_sum(Dev d, double (&v)[K], double (&tot)[K])
 {
@@ -88,14 +92,19 @@ __device__ inline bool grid_sum(Dev d, double (&v)[K], double (&tot)[K])
     }
     __syncthreads();
     if (!last) return false;
-    if (threadIdx.x == 0) {
-        __threadfence();
+    __threadfence();
+    double w[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double *)d.partial)[k * kRedBlocks + b];
-            tot[k] = s;
-        }
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            acc += ((volatile double *)d.partial)[k * kRedBlocks + b];
+        w[k] = acc;
+    }
+    block_sum<K>(w);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] = w[k];
         *d.counter = 0u;
         return true;
     }
@@ -111,7 +120,7 @@ template <typename T>
 __global__ void k_fcg_pq(Dev d, const T *p, const T *q, int64_t n, int slot_base)
 {
     double v[1] = {0.0}, tot[1];
-    GRID_STRIDE(i, n) v[0] += dd(p[i]) * dd(q[i]);
+    GRID_STRIDE(i, n) v[0] += dd(p[i] * q[i]);
     if (grid_sum<1>(d, v, tot)) {
         double pq = tot[0];
         d.scal[slot_base + S_PQ] = pq;
@@ -128,14 +137,14 @@ __global__ void k_fcg_pq(Dev d, const T *p, const T *q, int64_t n, int slot_base
 template <typename T, typename TX>
 __global__ void k_fcg_update(Dev d, TX *x, T *r, const T *p, const T *q, int64_t n, int slot_base)
 {
-    const double alpha = d.scal[slot_base + S_ALPHA];
+    const T alpha = (T)d.scal[slot_base + S_ALPHA];
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n)
     {
-        x[i] = (TX)(dd(x[i]) + alpha * dd(p[i]));
-        double ri = dd(r[i]) - alpha * dd(q[i]);
-        r[i] = (T)ri;
-        v[0] += ri * ri;
+        x[i] = (TX)(x[i] + (TX)(alpha * p[i]));
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        v[0] += dd(ri * ri);
     }
     if (grid_sum<1>(d, v, tot)) {
         d.scal[slot_base + S_RR] = tot[0];
@@ -152,9 +161,9 @@ __global__ void k_fcg_beta(Dev d, const T *z, const T *r, const T *q, int64_t n,
     double v[2] = {0.0, 0.0}, tot[2];
     GRID_STRIDE(i, n)
     {
-        double zi = dd(z[i]);
-        v[0] += zi * dd(r[i]);
-        v[1] += zi * dd(q[i]);
+        const T zi = z[i];
+        v[0] += dd(zi * r[i]);
+        v[1] += dd(zi * q[i]);
     }
     if (grid_sum<2>(d, v, tot)) {
         double rz_old = d.scal[slot_base + S_RZ];
@@ -174,8 +183,8 @@ __global__ void k_fcg_beta(Dev d, const T *z, const T *r, const T *q, int64_t n,
 template <typename T>
 __global__ void k_fcg_p(Dev d, T *p, const T *z, int64_t n, int slot_base)
 {
-    const double beta = d.scal[slot_base + S_BETA];
-    GRID_STRIDE(i, n) p[i] = (T)(dd(z[i]) + beta * dd(p[i]));
+    const T beta = (T)d.scal[slot_base + S_BETA];
+    GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
 }
 
 // rz = (r, z), rr = (r, r), p = z   (FCG start)
@@ -185,10 +194,10 @@ __global__ void k_fcg_start(Dev d, T *p, const T *z, const T *r, int64_t n, int 
     double v[2] = {0.0, 0.0}, tot[2];
     GRID_STRIDE(i, n)
     {
-        double zi = dd(z[i]), ri = dd(r[i]);
-        p[i] = z[i];
-        v[0] += ri * zi;
-        v[1] += ri * ri;
+        const T zi = z[i], ri = r[i];
+        p[i] = zi;
+        v[0] += dd(ri * zi);
+        v[1] += dd(ri * ri);
     }
     if (grid_sum<2>(d, v, tot)) {
         d.scal[slot_base + S_RZ] = tot[0];
@@ -202,7 +211,7 @@ template <typename T>
 __global__ void k_norm2(Dev d, const T *a, int64_t n, int slot)
 {
     double v[1] = {0.0}, tot[1];
-    GRID_STRIDE(i, n) v[0] += dd(a[i]) * dd(a[i]);
+    GRID_STRIDE(i, n) v[0] += dd(a[i] * a[i]);
     if (grid_sum<1>(d, v, tot)) d.scal[slot] = tot[0];
 }
 
@@ -217,7 +226,11 @@ __global__ void k_sub(TR *r, const TB *b, const TT *t, int64_t n)
 template <typename TX, typename TY>
 __global__ void k_scale_copy(TY *y, const TX *x, double s, int64_t n)
 {
-    GRID_STRIDE(i, n) y[i] = (TY)(s * dd(x[i]));
+    if (s == 1.0) {
+        GRID_STRIDE(i, n) y[i] = (TY)x[i];
+    } else {
+        GRID_STRIDE(i, n) y[i] = (TY)(s * dd(x[i]));
+    }
 }
 
 // x += s * d
@@ -248,6 +261,7 @@ __global__ void k_cg_start(Dev d, double *x, double *r, double *p, const double 
         d.scal[C_RR] = tot[1];
         d.scal[C_TOL2] = tol2;
         d.flag[F_CDONE] = (tot[1] == 0.0 || !isfinite(tot[1])) ? 1 : 0;
+        d.flag[F_CIT] = 0;
     }
 }
 
@@ -297,6 +311,138 @@ __global__ void k_cg_p(Dev d, double *p, const double *r, const double *dinv, in
     GRID_STRIDE(i, n) p[i] = dinv[i] * r[i] + beta * p[i];
 }
 
+// ------------------------------------------------ assembled coarse matrix
+// The coarsest level (p = 1) is assembled once, as the coarse level of the
+// paper's hierarchy is (Sec. 3.2), into a 27-point nodal stencil: row (c, i),
+// column (d, i + offset) with offset in {-1,0,1}^3.  Values are stored as 81
+// planes of N (plane s*3 + d, s the stencil index) so that consecutive rows
+// read consecutive addresses.  Each entry sums the element-matrix entries of
+// the (at most 8) elements holding both nodes, in increasing element order.
+struct P1Tables {
+    double M[2][2], C[2][2], K[2][2];  // sum_q w B_i B_j, w G_i B_j, w G_i G_j
+};
+
+__global__ void k_assemble_p1(const double *__restrict__ geo, double *__restrict__ vals, P1Tables t, Grid g)
+{
+    const int64_t Nn = g.Nn, nrow = 3 * Nn;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nrow;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(row / Nn);
+        const int64_t i = row - c * Nn;
+        const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
+        double acc[81];
+        for (int k = 0; k < 81; ++k) acc[k] = 0.0;
+        for (int ez = iz - 1; ez <= iz; ++ez)
+            for (int ey = iy - 1; ey <= iy; ++ey)
+                for (int ex = ix - 1; ex <= ix; ++ex) {
+                    if (ex < 0 || ey < 0 || ez < 0 || ex >= g.nx || ey >= g.ny || ez >= g.nz) continue;
+                    const int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
+                    const double *gp = geo + e * kGeoStride;
+                    const double cl = gp[9], cm = gp[10];
+                    double Ji[9];
+                    for (int k = 0; k < 9; ++k) Ji[k] = gp[k];
+                    // C[m][n][d] = lambda detJ Ji[m][c] Ji[n][d] + mu detJ Ji[m][d] Ji[n][c]
+                    //              + mu detJ delta_cd (Ji Ji^T)[m][n]
+                    double Cmn[3][3][3];
+                    for (int m = 0; m < 3; ++m)
+                        for (int n = 0; n < 3; ++n) {
+                            double jj = Ji[m * 3] * Ji[n * 3] + Ji[m * 3 + 1] * Ji[n * 3 + 1] + Ji[m * 3 + 2] * Ji[n * 3 + 2];
+                            for (int d = 0; d < 3; ++d)
+                                Cmn[m][n][d] = cl * Ji[m * 3 + c] * Ji[n * 3 + d] + cm * Ji[m * 3 + d] * Ji[n * 3 + c] +
+                                               (c == d ? cm * jj : 0.0);
+                        }
+                    const int a[3] = {ix - ex, iy - ey, iz - ez};
+                    for (int bz = 0; bz < 2; ++bz)
+                        for (int by = 0; by < 2; ++by)
+                            for (int bx = 0; bx < 2; ++bx) {
+                                const int b[3] = {bx, by, bz};
+                                double S[3][3];
+                                for (int m = 0; m < 3; ++m)
+                                    for (int n = 0; n < 3; ++n) {
+                                        double v = 1.0;
+                                        for (int k = 0; k < 3; ++k) {
+                                            const int ak = a[k], bk = b[k];
+                                            v *= (k == m && k == n) ? t.K[ak][bk]
+                                                 : (k == m)         ? t.C[ak][bk]
+                                                 : (k == n)         ? t.C[bk][ak]
+                                                                    : t.M[ak][bk];
+                                        }
+                                        S[m][n] = v;
+                                    }
+                                const int sidx = (ex + bx - ix + 1) + 3 * (ey + by - iy + 1) + 9 * (ez + bz - iz + 1);
+                                for (int d = 0; d < 3; ++d) {
+                                    double v = 0.0;
+                                    for (int m = 0; m < 3; ++m)
+                                        for (int n = 0; n < 3; ++n) v += S[m][n] * Cmn[m][n][d];
+                                    acc[sidx * 3 + d] += v;
+                                }
+                            }
+                }
+        for (int k = 0; k < 81; ++k) vals[(int64_t)k * nrow + row] = acc[k];
+    }
+}
+
+// q = A p with the assembled stencil (constrained rows/columns as the
+// operator: essential columns read as 0, essential rows return p), fused with
+// pq = (p, q) and alpha = rz / pq.
+__global__ void k_cg_spmv_pq(Dev d, const double *__restrict__ vals, const double *__restrict__ p,
+                             double *__restrict__ q, const uint8_t *__restrict__ ess, Grid g)
+{
+    if (d.flag[F_CDONE]) return;
+    const int64_t Nn = g.Nn, nrow = 3 * Nn;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(row, nrow)
+    {
+        const int c = (int)(row / Nn);
+        const int64_t i = row - c * Nn;
+        double y;
+        if (ess && ess[row]) {
+            y = p[row];
+        } else {
+            const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
+            y = 0.0;
+            for (int dz = -1; dz <= 1; ++dz) {
+                if (iz + dz < 0 || iz + dz >= g.Mz) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    if (iy + dy < 0 || iy + dy >= g.My) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (ix + dx < 0 || ix + dx >= g.Mx) continue;
+                        const int sidx = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                        const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
+#pragma unroll
+                        for (int dd2 = 0; dd2 < 3; ++dd2) {
+                            const int64_t col = dd2 * Nn + j;
+                            const double xv = (ess && ess[col]) ? 0.0 : p[col];
+                            y += vals[(int64_t)(sidx * 3 + dd2) * nrow + row] * xv;
+                        }
+                    }
+                }
+            }
+        }
+        q[row] = y;
+        v[0] += p[row] * y;
+    }
+    if (grid_sum<1>(d, v, tot)) {
+        double pq = tot[0];
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            d.flag[F_CDONE] = 1;
+            d.scal[C_ALPHA] = 0.0;
+        } else {
+            d.scal[C_ALPHA] = d.scal[C_RZ] / pq;
+        }
+    }
+}
+
+// Loop condition of the graph's coarse WHILE node: continue while the coarse
+// CG has not stopped and the iteration cap is not reached.
+__global__ void k_cg_cond(Dev d, int maxit, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x == 0) {
+        int it = ++d.flag[F_CIT];
+        cudaGraphSetConditional(h, (!d.flag[F_CDONE] && it < maxit) ? 1u : 0u);
+    }
+}
+
 // ------------------------------------------------------------ smoothing
 // Chebyshev step: rk = r - t (t may be null: rk = r);
 // d = cd d + cr Dinv rk; e = d (first step from a zero guess) or e += d.
@@ -304,12 +450,13 @@ template <typename T>
 __global__ void k_cheb(T *e, T *dv, const T *r, const T *t, const T *dinv, double cd, double cr, int first_zero,
                        int64_t n)
 {
+    const T cdt = (T)cd, crt = (T)cr;
     GRID_STRIDE(i, n)
     {
-        double rk = dd(r[i]) - (t ? dd(t[i]) : 0.0);
-        double di = (cd != 0.0 ? cd * dd(dv[i]) : 0.0) + cr * dd(dinv[i]) * rk;
-        dv[i] = (T)di;
-        e[i] = first_zero ? (T)di : (T)(dd(e[i]) + di);
+        const T rk = t ? r[i] - t[i] : r[i];
+        const T di = (cd != 0.0 ? cdt * dv[i] : T(0)) + crt * dinv[i] * rk;
+        dv[i] = di;
+        e[i] = first_zero ? di : e[i] + di;
     }
 }
 
@@ -366,15 +513,15 @@ __global__ void k_prolong_axis(T *out, const T *in, int ax, int Nx, int Ny, int 
         int jl = i - k * pf;
         int cdims[3] = {dims[0], dims[1], dims[2]};
         cdims[ax] = Mc;
-        double s = 0.0;
+        T s = T(0);
         for (int a = 0; a <= pc; ++a) {
-            double w = tab.L[a * (pf + 1) + jl];
+            const double w = tab.L[a * (pf + 1) + jl];
             if (w == 0.0) continue;
             idx[ax] = k * pc + a;
             int64_t ci = (((int64_t)c * cdims[2] + idx[2]) * cdims[1] + idx[1]) * cdims[0] + idx[0];
-            s += w * dd(in[ci]);
+            s += (T)w * in[ci];
         }
-        out[o] = accumulate ? (T)(dd(out[o]) + s) : (T)s;
+        out[o] = accumulate ? out[o] + s : s;
     }
 }
 
@@ -400,7 +547,7 @@ __global__ void k_restrict_axis(T *out, const T *in, const T *in2, int ax, int N
         int c = (int)(t / odims[2]);
         int idx[3] = {i0, i1, i2};
         int jc = idx[ax];
-        double s = 0.0;
+        T s = T(0);
         int kk = jc / pc;
         for (int k = kk - 1; k <= kk; ++k) {
             if (k < 0 || k > n - 1) continue;
@@ -411,18 +558,27 @@ __global__ void k_restrict_axis(T *out, const T *in, const T *in2, int ax, int N
                 int owner = i / pf;
                 if (owner > n - 1) owner = n - 1;
                 if (owner != k) continue;
-                double w = tab.L[a * (pf + 1) + jl];
+                const double w = tab.L[a * (pf + 1) + jl];
                 if (w == 0.0) continue;
                 idx[ax] = i;
                 int64_t fi = (((int64_t)c * dims[2] + idx[2]) * dims[1] + idx[1]) * dims[0] + idx[0];
-                double v = dd(in[fi]);
-                if (in2) v -= dd(in2[fi]);
-                s += w * v;
+                T v = in[fi];
+                if (in2) v -= in2[fi];
+                s += (T)w * v;
             }
         }
-        if (ess && ess[o]) s = 0.0;
-        out[o] = (T)s;
+        if (ess && ess[o]) s = T(0);
+        out[o] = s;
     }
+}
+
+// Grid of a reduction kernel: about 4 elements per thread, at most kRedBlocks.
+unsigned red_blocks(int64_t n)
+{
+    int64_t b = (n + 4 * kRedThreads - 1) / (4 * kRedThreads);
+    if (b > kRedBlocks) b = kRedBlocks;
+    if (b < 1) b = 1;
+    return (unsigned)b;
 }
 
 unsigned blocks_for(int64_t n, int th = 256)
@@ -454,12 +610,23 @@ struct Level {
     double theta = 0.0, delta = 0.0;
     // coarse CG vectors
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr;
+    double *stencil = nullptr;  // assembled p = 1 coarse matrix (81 planes of n), or null
 };
 
 }  // namespace pa
 
+namespace pa {
+struct StepGraphs {
+    cudaGraphExec_t init = nullptr, iter = nullptr;
+};
+}  // namespace pa
+
 struct pa_solver {
     std::vector<pa::Level> lv;
+    bool use_graphs = true;
+    cudaStream_t stream = nullptr;  // the solver's own stream (capture needs a non-legacy stream)
+    pa::StepGraphs g64, g32;
+    double *xin = nullptr, *bin = nullptr;  // FP64 solve operates on these copies
     int mode = PA_SOLVE_FP64;
     int cheb_order = 2;
     double coarse_rtol = 1e-2;
@@ -547,12 +714,12 @@ int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
     k_random<<<blocks_for(n), 256, 0, st>>>(L.e, L.op->d_ess, n, 0x1234567ull + (uint64_t)L.p);
     double lam = 0.0;
     for (int it = 0; it < 10; ++it) {
-        k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.e, n, P_DEN);
+        k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.e, n, P_DEN);
         int rc = op_apply_async(L.op, L.e, L.t, false, st, nullptr);
         if (rc) return rc;
         // d = Dinv (A e)   (k_cheb with a zero guess, cd = 0, cr = 1)
         k_cheb<double><<<blocks_for(n), 256, 0, st>>>(L.d, L.r, L.t, nullptr, L.dinv, 0.0, 1.0, 1, n);
-        k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.d, n, P_NUM);
+        k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.d, n, P_NUM);
         PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + P_NUM, s->dev.scal + P_NUM, 2 * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         PA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -672,102 +839,279 @@ void prolong_add(Level &F, Level &C, const T *ec, T *ef, cudaStream_t st)
     k_prolong_axis<T><<<blocks_for(n3), 256, 0, st>>>(ef, xb, 2, Mf[0], Mf[1], Mc[2], n_[2], pc, pf, F.xt, 1);
 }
 
-// FP64 Jacobi-CG on the coarsest level: L.cx = A^-1 b approximately.
-int coarse_solve(pa_solver *s, Level &L, const double *b, cudaStream_t st)
+// ---------------------------------------------------------- coarse solve
+// FP64 Jacobi-CG on the coarsest level: L.cx ~ A^-1 L.r.  The start kernel
+// resets the device stop flag and iteration counter; every iteration's
+// kernels return at once after the flag is set.
+void coarse_start(pa_solver *s, Level &L, cudaStream_t st)
+{
+    k_cg_start<<<red_blocks(L.n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.r, L.dinv, L.n,
+                                                   s->coarse_rtol * s->coarse_rtol);
+}
+
+int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
 {
     const int64_t n = L.n;
-    k_cg_start<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, b, L.dinv, n,
-                                                   s->coarse_rtol * s->coarse_rtol);
-    for (int it = 0; it < s->coarse_maxit; ++it) {
+    if (L.stencil) {
+        // FP64 work per row: spread the rows over the SMs (64 threads per CTA)
+        int64_t nb = (n + 63) / 64;
+        if (nb > kRedBlocks) nb = kRedBlocks;
+        k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->d_ess, L.op->g);
+    } else {
         int rc = op_apply_async(L.op, L.cp, L.cq, false, st, s->dev.flag + F_CDONE);
         if (rc) return rc;
-        k_cg_pq<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cp, L.cq, n);
-        k_cg_update<<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, L.dinv, n);
-        k_cg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, L.cr, L.dinv, n);
+        k_cg_pq<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cp, L.cq, n);
     }
+    k_cg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, L.dinv, n);
+    k_cg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, L.cr, L.dinv, n);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
 
-// V(1,1) cycle: approximately solves A e = r on level l (both in LV<T>
-// storage of that level); e starts from zero.
-template <typename T>
-int vcycle(pa_solver *s, int l, cudaStream_t st)
+// Eager coarse loop: a fixed number of launches (used without graphs).
+int coarse_eager(pa_solver *s, cudaStream_t st)
 {
-    Level &L = s->lv[l];
-    const int nl = (int)s->lv.size();
-    if (l == nl - 1) {
-        // coarse: FP64 CG (convert if the cycle runs in FP32)
-        if constexpr (sizeof(T) == 8) {
-            int rc = coarse_solve(s, L, L.r, st);
-            if (rc) return rc;
-            k_scale_copy<double, double><<<blocks_for(L.n), 256, 0, st>>>(L.e, L.cx, 1.0, L.n);
-        } else {
-            k_scale_copy<float, double><<<blocks_for(L.n), 256, 0, st>>>(L.r, L.r32, 1.0, L.n);
-            int rc = coarse_solve(s, L, L.r, st);
-            if (rc) return rc;
-            k_scale_copy<double, float><<<blocks_for(L.n), 256, 0, st>>>(L.e32, L.cx, 1.0, L.n);
-        }
-        PA_CUDA_TRY(cudaGetLastError());
-        return PA_OK;
+    Level &L = s->lv.back();
+    for (int it = 0; it < s->coarse_maxit; ++it) {
+        int rc = coarse_iter(s, L, st);
+        if (rc) return rc;
     }
-    Level &C = s->lv[l + 1];
-    int rc = smooth<T>(s, L, true, st);
-    if (rc) return rc;
-    rc = op_apply_async(LV<T>::op(L), LV<T>::e(L), LV<T>::t(L), false, st, nullptr);
-    if (rc) return rc;
-    restrict_to<T>(L, C, LV<T>::r(L), LV<T>::t(L), LV<T>::r(C), st);
-    rc = vcycle<T>(s, l + 1, st);
-    if (rc) return rc;
-    prolong_add<T>(L, C, LV<T>::e(C), LV<T>::e(L), st);
-    rc = smooth<T>(s, L, false, st);
-    if (rc) return rc;
+    return PA_OK;
+}
+
+// ------------------------------------------------------------- V(1,1) cycle
+// Down half: pre-smoothing, residual and restriction from level 0 to the
+// coarsest level, whose FP64 right-hand side ends in L.r; then the coarse
+// CG start.  Input: LV<T>::r(level 0).
+template <typename T>
+int vcycle_down(pa_solver *s, cudaStream_t st)
+{
+    const int nl = (int)s->lv.size();
+    for (int l = 0; l < nl - 1; ++l) {
+        Level &L = s->lv[l], &C = s->lv[l + 1];
+        int rc = smooth<T>(s, L, true, st);
+        if (rc) return rc;
+        rc = op_apply_async(LV<T>::op(L), LV<T>::e(L), LV<T>::t(L), false, st, nullptr);
+        if (rc) return rc;
+        restrict_to<T>(L, C, LV<T>::r(L), LV<T>::t(L), LV<T>::r(C), st);
+    }
+    Level &Lc = s->lv.back();
+    if constexpr (sizeof(T) == 4) k_scale_copy<float, double><<<blocks_for(Lc.n), 256, 0, st>>>(Lc.r, Lc.r32, 1.0, Lc.n);
+    coarse_start(s, Lc, st);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
 
-// Flexible CG on level 0 in storage T (FP64 outer solve, or the FP32 inner
-// solve of the mixed mode).  x, b in storage TX / T.  Returns iterations.
-// Stops when (r, r) <= tol2 * bb or maxit.
-template <typename T, typename TX>
-int fcg(pa_solver *s, TX *x, const T *b, T *r, T *z, T *p, T *q, double tol2, double bb, int maxit, int *iters,
-        cudaStream_t st, bool x_zero)
+// Up half: coarse correction into LV<T>::e(coarsest), then prolongation and
+// post-smoothing back to level 0.  Output: LV<T>::e(level 0).
+template <typename T>
+int vcycle_up(pa_solver *s, cudaStream_t st)
+{
+    const int nl = (int)s->lv.size();
+    Level &Lc = s->lv.back();
+    k_scale_copy<double, T><<<blocks_for(Lc.n), 256, 0, st>>>(LV<T>::e(Lc), Lc.cx, 1.0, Lc.n);
+    for (int l = nl - 2; l >= 0; --l) {
+        Level &L = s->lv[l], &C = s->lv[l + 1];
+        prolong_add<T>(L, C, LV<T>::e(C), LV<T>::e(L), st);
+        int rc = smooth<T>(s, L, false, st);
+        if (rc) return rc;
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// ------------------------------------------------------------ flexible CG
+// One FCG step is two segments around the coarse solve of its V-cycle:
+//   init  A: r = b - A x (or x = 0, r = b), V-cycle down
+//   init  B: V-cycle up, z = M r, p = z, rz = (r, z), rr = (r, r)
+//   iter  A: q = A p, alpha, x += alpha p, r -= alpha q, V-cycle down
+//   iter  B: V-cycle up, z = M r, beta, p = z + beta p
+// Both B segments end with an asynchronous copy of rr and the flags to
+// pinned host memory.
+template <typename T>
+struct FcgVecs {
+    T *x, *b, *r, *z, *p, *q;
+    bool x_zero;
+};
+
+template <typename T>
+int fcg_init_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
-    pa_op *op = LV<T>::op(L0);
-    int rc;
-    if (x_zero) {
-        cudaMemsetAsync(x, 0, sizeof(TX) * n, st);
-        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(r, b, 1.0, n);
+    if (v.x_zero) {
+        PA_CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(T) * n, st));
+        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, 1.0, n);
     } else {
-        rc = op_apply_async(op, x, q, false, st, nullptr);  // requires TX == T
+        int rc = op_apply_async(LV<T>::op(L0), v.x, v.q, false, st, nullptr);
         if (rc) return rc;
-        k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(r, b, q, n);
+        k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, v.q, n);
     }
-    // z = M r
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), r, 1.0, n);
-    rc = vcycle<T>(s, 0, st);
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), v.r, 1.0, n);
+    return vcycle_down<T>(s, st);
+}
+
+template <typename T>
+int publish_scalars(pa_solver *s, cudaStream_t st)
+{
+    PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + S_RR, s->dev.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PA_CUDA_TRY(cudaMemcpyAsync(s->h_flag, s->dev.flag, sizeof(int) * NFLAG, cudaMemcpyDeviceToHost, st));
+    return PA_OK;
+}
+
+template <typename T>
+int fcg_init_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
+{
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    int rc = vcycle_up<T>(s, st);
     if (rc) return rc;
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(z, LV<T>::e(L0), 1.0, n);
-    k_fcg_start<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, p, z, r, n, 0);
-    double rr = read_scalar(s, S_RR, st);
-    int it = 0;
-    while (rr > tol2 * bb && it < maxit) {
-        rc = op_apply_async(op, p, q, false, st, nullptr);
-        if (rc) return rc;
-        k_fcg_pq<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, p, q, n, 0);
-        k_fcg_update<T, TX><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, x, r, p, q, n, 0);
-        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), r, 1.0, n);
-        rc = vcycle<T>(s, 0, st);
-        if (rc) return rc;
-        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(z, LV<T>::e(L0), 1.0, n);
-        k_fcg_beta<T><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, z, r, q, n, 0);
-        k_fcg_p<T><<<blocks_for(n), 256, 0, st>>>(s->dev, p, z, n, 0);
-        PA_CUDA_TRY(cudaGetLastError());
-        cudaMemcpyAsync(s->h_scal + S_RR, s->dev.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(s->h_flag, s->dev.flag, sizeof(int) * NFLAG, cudaMemcpyDeviceToHost, st);
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<T>::e(L0), 1.0, n);
+    k_fcg_start<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.z, v.r, n, 0);
+    PA_CUDA_TRY(cudaGetLastError());
+    return publish_scalars<T>(s, st);
+}
+
+template <typename T>
+int fcg_iter_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
+{
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    int rc = op_apply_async(LV<T>::op(L0), v.p, v.q, false, st, nullptr);
+    if (rc) return rc;
+    k_fcg_pq<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.q, n, 0);
+    k_fcg_update<T, T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.x, v.r, v.p, v.q, n, 0);
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), v.r, 1.0, n);
+    return vcycle_down<T>(s, st);
+}
+
+template <typename T>
+int fcg_iter_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
+{
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    int rc = vcycle_up<T>(s, st);
+    if (rc) return rc;
+    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<T>::e(L0), 1.0, n);
+    k_fcg_beta<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.z, v.r, v.q, n, 0);
+    k_fcg_p<T><<<blocks_for(n), 256, 0, st>>>(s->dev, v.p, v.z, n, 0);
+    PA_CUDA_TRY(cudaGetLastError());
+    return publish_scalars<T>(s, st);
+}
+
+// Captures [segment A] -> WHILE(coarse CG iteration) -> [segment B] into an
+// executable graph; the loop's condition is set on the device after every
+// coarse iteration (stop flag or iteration cap), so only the iterations the
+// coarse solve needs are executed.
+template <typename FA, typename FB>
+int build_step_graph(pa_solver *s, cudaStream_t st, FA seg_a, FB seg_b, cudaGraphExec_t *out)
+{
+    cudaGraph_t G = nullptr, gA = nullptr, gB = nullptr, gBody = nullptr;
+    int rc = PA_OK;
+    auto capture = [&](cudaGraph_t *g, auto &&fn) -> int {
+        PA_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        int r = fn();
+        cudaGraph_t tmp = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &tmp);
+        if (r) {
+            if (tmp) cudaGraphDestroy(tmp);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "solver graph: cudaStreamEndCapture");
+        *g = tmp;
+        return PA_OK;
+    };
+    do {
+        if (cudaGraphCreate(&G, 0) != cudaSuccess) { rc = cuda_error(cudaGetLastError(), "cudaGraphCreate"); break; }
+        if ((rc = capture(&gA, seg_a))) break;
+        cudaGraphNode_t nA, nC, nB, nBody;
+        cudaError_t e = cudaGraphAddChildGraphNode(&nA, G, nullptr, 0, gA);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddChildGraphNode"); break; }
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphConditionalHandleCreate"); break; }
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&nC, G, &nA, nullptr, 1, &cp);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddNode(conditional)"); break; }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        Level &Lc = s->lv.back();
+        const int maxit = s->coarse_maxit;
+        if ((rc = capture(&gBody, [&]() -> int {
+                 int r = coarse_iter(s, Lc, st);
+                 if (r) return r;
+                 k_cg_cond<<<1, 32, 0, st>>>(s->dev, maxit, h);
+                 PA_CUDA_TRY(cudaGetLastError());
+                 return PA_OK;
+             })))
+            break;
+        e = cudaGraphAddChildGraphNode(&nBody, body, nullptr, 0, gBody);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddChildGraphNode(body)"); break; }
+        if ((rc = capture(&gB, seg_b))) break;
+        e = cudaGraphAddChildGraphNode(&nB, G, &nC, 1, gB);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddChildGraphNode"); break; }
+        e = cudaGraphInstantiate(out, G, 0);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphInstantiate"); break; }
+    } while (false);
+    if (gA) cudaGraphDestroy(gA);
+    if (gB) cudaGraphDestroy(gB);
+    if (gBody) cudaGraphDestroy(gBody);
+    if (G) cudaGraphDestroy(G);
+    return rc;
+}
+
+// Flexible CG on level 0 in storage T (FP64 outer solve, or the FP32 inner
+// solve of the mixed mode).  Stops when (r, r) <= tol2 * bb or after maxit
+// iterations.  With graphs, each step is one graph launch; otherwise the
+// same segments run eagerly with the fixed-length coarse loop.
+template <typename T>
+int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double bb, int maxit, int *iters,
+        cudaStream_t st)
+{
+    int rc;
+    if (s->use_graphs && !sg.init) {
+        rc = build_step_graph(
+            s, st, [&]() { return fcg_init_a<T>(s, v, st); }, [&]() { return fcg_init_b<T>(s, v, st); }, &sg.init);
+        if (!rc)
+            rc = build_step_graph(
+                s, st, [&]() { return fcg_iter_a<T>(s, v, st); }, [&]() { return fcg_iter_b<T>(s, v, st); }, &sg.iter);
+        if (rc) {
+            // fall back to eager execution for this solver
+            if (sg.init) cudaGraphExecDestroy(sg.init);
+            if (sg.iter) cudaGraphExecDestroy(sg.iter);
+            sg.init = sg.iter = nullptr;
+            s->use_graphs = false;
+            cudaGetLastError();
+        }
+    }
+    auto step = [&](bool init) -> int {
+        if (s->use_graphs) {
+            PA_CUDA_TRY(cudaGraphLaunch(init ? sg.init : sg.iter, st));
+        } else {
+            int r = init ? fcg_init_a<T>(s, v, st) : fcg_iter_a<T>(s, v, st);
+            if (r) return r;
+            r = coarse_eager(s, st);
+            if (r) return r;
+            r = init ? fcg_init_b<T>(s, v, st) : fcg_iter_b<T>(s, v, st);
+            if (r) return r;
+        }
         PA_CUDA_TRY(cudaStreamSynchronize(st));
+        return PA_OK;
+    };
+    rc = step(true);
+    if (rc) return rc;
+    double rr = s->h_scal[S_RR];
+    int it = 0;
+    if (s->h_flag[F_BREAK]) {
+        *iters = 0;
+        return set_error(PA_EBREAKDOWN, "solver: non-finite value in the first preconditioned residual");
+    }
+    while (rr > tol2 * bb && it < maxit) {
+        rc = step(false);
+        if (rc) return rc;
         rr = s->h_scal[S_RR];
         ++it;
         if (s->h_flag[F_BREAK]) {
@@ -785,6 +1129,27 @@ int fcg(pa_solver *s, TX *x, const T *b, T *r, T *z, T *p, T *q, double tol2, do
 using namespace pa;
 
 extern "C" {
+
+int pa_op_assemble_p1(const pa_op *op, double *vals, void *stream)
+{
+    if (!op || !vals) return set_error(PA_EINVAL, "pa_op_assemble_p1: null argument");
+    if (op->p != 1 || op->precision != PA_FP64) return set_error(PA_EINVAL, "pa_op_assemble_p1: needs an FP64 p = 1 operator");
+    const Basis1D &bb = op->basis;
+    P1Tables t{};
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int q = 0; q < bb.Q; ++q) {
+                const double w = bb.qwts[q];
+                t.M[i][j] += w * bb.B[i * bb.Q + q] * bb.B[j * bb.Q + q];
+                t.C[i][j] += w * bb.G[i * bb.Q + q] * bb.B[j * bb.Q + q];
+                t.K[i][j] += w * bb.G[i * bb.Q + q] * bb.G[j * bb.Q + q];
+            }
+    const int64_t n = op->ndofs();
+    k_assemble_p1<<<blocks_for(n, 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const double *>(op->d_geo), vals, t, op->g);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
 
 static int transfer_check(const pa_op *c, const pa_op *f)
 {
@@ -854,6 +1219,11 @@ int pa_solver_destroy(pa_solver *s)
         if (L.own_op) pa_op_destroy(L.op);
         pa_op_destroy(L.op32);
     }
+    for (StepGraphs *g : {&s->g64, &s->g32}) {
+        if (g->init) cudaGraphExecDestroy(g->init);
+        if (g->iter) cudaGraphExecDestroy(g->iter);
+    }
+    if (s->stream) cudaStreamDestroy(s->stream);
     for (void *p : s->allocs) cudaFree(p);
     cudaFree(s->dev.scal);
     cudaFree(s->dev.flag);
@@ -905,6 +1275,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
     TRYC(cudaMemset(s->dev.scal, 0, sizeof(double) * NSLOT));
     TRYC(cudaMallocHost((void **)&s->h_scal, sizeof(double) * NSLOT));
     TRYC(cudaMallocHost((void **)&s->h_flag, sizeof(int) * NFLAG));
+    TRYC(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
 
     s->lv.resize(nlev);
     std::vector<uint8_t> mask = fine->h_ess;
@@ -926,7 +1297,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
         L.n = L.op->ndofs();
         if (mode == PA_SOLVE_MIXED) TRY(make_level_op(fine, L.p, PA_FP32, L.op->h_ess, &L.op32));
     }
-    cudaStream_t st = nullptr;
+    cudaStream_t st = s->stream;
     for (int l = 0; l < nlev; ++l) {
         Level &L = s->lv[l];
         const int64_t n = L.n;
@@ -952,6 +1323,11 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             TRY(dalloc(s, &L.cr, n));
             TRY(dalloc(s, &L.cp, n));
             TRY(dalloc(s, &L.cq, n));
+            if (L.p == 1) {
+                // assemble the coarse matrix (same quadrature as the operator)
+                TRY(dalloc(s, &L.stencil, 81 * n));
+                TRY(pa_op_assemble_p1(L.op, L.stencil, st));
+            }
         }
         if (mode == PA_SOLVE_MIXED) {
             TRY(dalloc(s, &L.r32, n));
@@ -962,9 +1338,13 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             TRY(dalloc(s, &L.xa32, n));
             TRY(dalloc(s, &L.xb32, n));
             k_scale_copy<double, float><<<blocks_for(n), 256, 0, st>>>(L.dinv32, L.dinv, 1.0, n);
+            // one eager apply per FP32 operator before any graph capture
+            TRY(op_apply_async(L.op32, L.dinv32, L.t32, false, st, nullptr));
         }
     }
     const int64_t n0 = s->lv[0].n;
+    TRY(dalloc(s, &s->xin, n0));
+    TRY(dalloc(s, &s->bin, n0));
     TRY(dalloc(s, &s->r, n0));
     TRY(dalloc(s, &s->z, n0));
     TRY(dalloc(s, &s->p, n0));
@@ -978,7 +1358,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
         TRY(dalloc(s, &s->x32, n0));
         TRY(dalloc(s, &s->b32, n0));
     }
-    TRYC(cudaDeviceSynchronize());
+    TRYC(cudaStreamSynchronize(st));
     TRYC(cudaGetLastError());
 #undef TRY
 #undef TRYC
@@ -987,18 +1367,30 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
     return PA_OK;
 }
 
+int pa_solver_set_option(pa_solver *s, int option, double value)
+{
+    if (!s) return set_error(PA_EINVAL, "pa_solver_set_option: null solver");
+    switch (option) {
+    case PA_SOLVER_OPT_GRAPHS: s->use_graphs = value != 0.0; return PA_OK;
+    default: return set_error(PA_EINVAL, "pa_solver_set_option: unknown option");
+    }
+}
+
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream)
 {
     if (!s || !b || !x) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: null argument");
     if (!(rtol > 0.0) || maxit < 0) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: bad tolerance or cap");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the caller's stream first finishes producing b and x; the solve runs on
+    // the solver's own stream
+    PA_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    cudaStream_t st = s->stream;
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
     pa_solve_info inf{};
     for (size_t l = 0; l < s->lv.size() && l < 8; ++l) inf.lambda_max[l] = s->lv[l].lmax;
     PA_CUDA_TRY(cudaMemsetAsync(s->dev.flag, 0, sizeof(int) * NFLAG, st));
-    k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
+    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
     const double bb = read_scalar(s, S_BB, st);
     inf.b_norm = std::sqrt(bb);
     int status = PA_OK, rc = PA_OK;
@@ -1014,10 +1406,14 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         if (info) *info = inf;
         return set_error(PA_EINVAL, "pa_gmg_pcg_solve: b has non-finite entries");
     }
+    double *xs = s->xin, *bs = s->bin;
+    PA_CUDA_TRY(cudaMemcpyAsync(xs, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    PA_CUDA_TRY(cudaMemcpyAsync(bs, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bool converged = false;
     if (s->mode == PA_SOLVE_FP64) {
         int it = 0;
-        rc = fcg<double, double>(s, x, b, s->r, s->z, s->p, s->q, tol2, bb, maxit, &it, st, false);
+        FcgVecs<double> v{xs, bs, s->r, s->z, s->p, s->q, false};
+        rc = fcg<double>(s, v, s->g64, tol2, bb, maxit, &it, st);
         inf.iterations = it;
         converged = (rc == PA_OK) && s->h_scal[S_RR] <= tol2 * bb;
     } else {
@@ -1026,11 +1422,12 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         // the FP64 residual (its rounding floor).
         int total_inner = 0, refine = 0;
         double rr_prev = -1.0;
+        FcgVecs<float> v{s->x32, s->b32, s->r32, s->z32, s->p32, s->q32, true};
         while (true) {
-            rc = op_apply_async(L0.op, x, s->t, false, st, nullptr);
+            rc = op_apply_async(L0.op, xs, s->t, false, st, nullptr);
             if (rc) break;
-            k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, b, s->t, n);
-            k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+            k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, bs, s->t, n);
+            k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
             double rr = read_scalar(s, S_RR, st);
             if (!std::isfinite(rr)) {
                 rc = set_error(PA_EBREAKDOWN, "solver: non-finite residual");
@@ -1051,12 +1448,11 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
             k_scale_copy<double, float><<<blocks_for(n), 256, 0, st>>>(s->b32, s->r, sc, n);
             int it = 0;
             // inner solve: relative reduction 1e-4 or at most 50 iterations
-            rc = fcg<float, float>(s, s->x32, s->b32, s->r32, s->z32, s->p32, s->q32, 1e-8, 1.0,
-                                   std::min(50, maxit - total_inner), &it, st, true);
+            rc = fcg<float>(s, v, s->g32, 1e-8, 1.0, std::min(50, maxit - total_inner), &it, st);
             if (rc) break;
             total_inner += it;
             ++refine;
-            k_axpy<double, float><<<blocks_for(n), 256, 0, st>>>(x, s->x32, 1.0 / sc, n);
+            k_axpy<double, float><<<blocks_for(n), 256, 0, st>>>(xs, s->x32, 1.0 / sc, n);
             if (it == 0) break;
         }
         inf.iterations = total_inner;
@@ -1068,11 +1464,12 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         if (info) *info = inf;
         return rc;
     }
-    // true residual in FP64
-    int rc2 = op_apply_async(L0.op, x, s->t, false, st, nullptr);
+    // true residual in FP64, and the solution back to the caller
+    int rc2 = op_apply_async(L0.op, xs, s->t, false, st, nullptr);
     if (rc2) return rc2;
-    k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, b, s->t, n);
-    k_norm2<double><<<kRedBlocks, kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+    k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, bs, s->t, n);
+    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+    PA_CUDA_TRY(cudaMemcpyAsync(x, xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     double rr = read_scalar(s, S_RR, st);
     PA_CUDA_TRY(cudaGetLastError());
     inf.rel_residual = std::sqrt(rr / bb);

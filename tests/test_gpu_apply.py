@@ -209,3 +209,32 @@ def test_transfers_against_oracle(pa, pc, pf):
     assert _relerr(rc.cpu().numpy(), Rv) <= 1e-13
     opc.close()
     opf.close()
+
+
+def test_assembled_p1_stencil_against_oracle_matrix(pa):
+    """The assembled coarse matrix (27-point stencil) against the oracle's
+    assembled global matrix, entry by entry."""
+    m = syn.random_affine_cube(3, seed=77, ny=2, nz=2)
+    lam, mu = syn.lame(1.0, 0.35)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, 1, lam, mu)
+    N = op.ndofs
+    vals = torch.zeros(81 * N, dtype=torch.float64, device="cuda")
+    pa.pa_op_assemble_p1(op.h, vals)
+    V = vals.cpu().numpy().reshape(81, N)
+    A = oracle.assemble_dense(1, m.nx, m.ny, m.nz, m.affine, lam, mu)
+    Nn = N // 3
+    Mx, My, Mz = m.nx + 1, m.ny + 1, m.nz + 1
+    S = np.zeros_like(A)
+    for row in range(N):
+        c, i = divmod(row, Nn)
+        ix, iy, iz = i % Mx, (i // Mx) % My, i // (Mx * My)
+        for k in range(81):
+            s, d = divmod(k, 3)
+            dx, dy, dz = s % 3 - 1, (s // 3) % 3 - 1, s // 9 - 1
+            jx, jy, jz = ix + dx, iy + dy, iz + dz
+            if 0 <= jx < Mx and 0 <= jy < My and 0 <= jz < Mz:
+                S[row, d * Nn + jx + Mx * (jy + My * jz)] = V[k, row]
+            else:
+                assert V[k, row] == 0.0
+    assert np.max(np.abs(S - A)) <= 1e-13 * np.max(np.abs(A))
+    op.close()

@@ -111,3 +111,30 @@ def test_nan_rhs_is_rejected(pa):
     assert ei.value.code == pa.PA_EINVAL
     pa.pa_solver_destroy(s)
     op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_and_eager_paths_agree_bitwise(pa, mode):
+    """Each CG step captured as a CUDA graph (device-controlled coarse loop)
+    and the same kernels launched one by one give the same bits."""
+    m = _beam(8, 2, 2)
+    p = 4
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(f0=(0.0, 0.0, -1.0))
+    out = []
+    for graphs in (1, 0):
+        s = pa.pa_solver_create(op.h, [4, 2, 1], 2, 1e-4, 300, mode)
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, graphs)
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 200)
+        assert code == pa.PA_OK
+        out.append((x.clone(), info.iterations))
+        # a second solve with the same solver reuses its graphs
+        x2 = torch.zeros_like(b)
+        code, info2 = pa.pa_gmg_pcg_solve(s, b, x2, 1e-10, 200)
+        assert torch.equal(x, x2) and info2.iterations == info.iterations
+        pa.pa_solver_destroy(s)
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    op.close()
