@@ -214,10 +214,16 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
                      int coarse_maxit, int mode, pa_solver **out);
 int pa_solver_destroy(pa_solver *s);
 
-/* Solver options: PA_SOLVER_OPT_GRAPHS (value 1, default: each CG step runs
- * as one captured CUDA graph with a device-controlled coarse loop; value 0:
- * the same kernels are launched one by one). */
-enum pa_solver_option { PA_SOLVER_OPT_GRAPHS = 1 };
+/* Solver options:
+ *  PA_SOLVER_OPT_GRAPHS (default 1): each CG step runs as one captured CUDA
+ *    graph; 0: the same kernels are launched one by one.
+ *  PA_SOLVER_OPT_PERSISTENT_COARSE (default 1): the FP64 coarse CG on the
+ *    assembled p = 1 level runs as one cooperative kernel with bounded grid
+ *    barriers (a barrier that waits more than ~2 s makes the solve return
+ *    PA_ETIMEOUT); 0: one launch per kernel of every coarse iteration (a
+ *    device-controlled graph loop when graphs are on).  Solvers that run
+ *    concurrently on one GPU (the server) use 0. */
+enum pa_solver_option { PA_SOLVER_OPT_GRAPHS = 1, PA_SOLVER_OPT_PERSISTENT_COARSE = 2 };
 int pa_solver_set_option(pa_solver *s, int option, double value);
 
 /* Solve A x = b (x: in = initial guess, out = solution; device double

@@ -261,6 +261,7 @@ def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=
 
 
 PA_SOLVER_OPT_GRAPHS = 1
+PA_SOLVER_OPT_PERSISTENT_COARSE = 2
 
 
 def pa_solver_set_option(h, option, value):

@@ -125,6 +125,8 @@ void run_request(pa_server *srv, Ticket &t)
             fail(rc);
             break;
         }
+        // concurrent solvers must not each hold a grid-wide barrier
+        pa_solver_set_option(sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);
         const size_t n = (size_t)op->ndofs();
         if (cudaMalloc((void **)&b, n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void **)&x, n * sizeof(double)) != cudaSuccess) {

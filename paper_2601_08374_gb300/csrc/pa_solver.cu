@@ -39,7 +39,7 @@ enum Slot {
     P_NUM = 24, P_DEN,
     NSLOT = 32
 };
-enum FlagSlot { F_BREAK = 0, F_CDONE = 1, F_CIT = 2, NFLAG = 4 };
+enum FlagSlot { F_BREAK = 0, F_CDONE = 1, F_CIT = 2, NFLAG = 4 };  // slot 3: coarse barrier timeout
 
 struct Dev {
     double *scal;       // [NSLOT]
@@ -433,6 +433,175 @@ __global__ void k_cg_spmv_pq(Dev d, const double *__restrict__ vals, const doubl
     }
 }
 
+// ------------------------------------------------- persistent coarse CG
+// The whole Jacobi-CG of the assembled coarse level in one cooperative
+// launch (all CTAs co-resident): three grid barriers per iteration replace
+// four kernel launches.  Every CTA adds the per-CTA partial sums itself in
+// the same fixed order, so all CTAs take the same decisions and the result
+// is deterministic.  The barrier's spin is bounded by time; on expiry the
+// kernel raises F_CTIMEOUT and returns.
+enum { F_CTIMEOUT = 3 };
+constexpr long long kBarrierLimitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ inline bool grid_barrier(unsigned *bar, int *timeout_flag)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > kBarrierLimitCycles || *(volatile int *)timeout_flag) {
+                    atomicExch(timeout_flag, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum over CTAs of K per-CTA partials (same order in every CTA); all threads
+// receive the totals.
+template <int K>
+__device__ inline void all_sum(const double *part, double (&tot)[K])
+{
+    __shared__ double res[K];
+    double w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) acc += ((volatile const double *)part)[k * kRedBlocks + b];
+        w[k] = acc;
+    }
+    block_sum<K>(w);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) res[k] = w[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = res[k];
+    __syncthreads();
+}
+
+template <int K>
+__device__ inline void publish(double *part, double (&v)[K])
+{
+    block_sum<K>(v);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[k * kRedBlocks + blockIdx.x] = v[k];
+}
+
+__device__ inline double stencil_row(const double *__restrict__ vals, const double *__restrict__ p,
+                                     const uint8_t *__restrict__ ess, const Grid &g, int64_t row)
+{
+    const int64_t Nn = g.Nn, nrow = 3 * Nn;
+    if (ess && ess[row]) return p[row];
+    const int c = (int)(row / Nn);
+    const int64_t i = row - c * Nn;
+    const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
+    double y = 0.0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (iz + dz < 0 || iz + dz >= g.Mz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (iy + dy < 0 || iy + dy >= g.My) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (ix + dx < 0 || ix + dx >= g.Mx) continue;
+                const int sidx = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
+#pragma unroll
+                for (int d2 = 0; d2 < 3; ++d2) {
+                    const int64_t col = d2 * Nn + j;
+                    const double xv = (ess && ess[col]) ? 0.0 : p[col];
+                    y += vals[(int64_t)(sidx * 3 + d2) * nrow + row] * xv;
+                }
+            }
+        }
+    }
+    return y;
+}
+
+__global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict__ vals, double *__restrict__ x,
+                                                 double *__restrict__ r, double *__restrict__ p, double *__restrict__ q,
+                                                 const double *__restrict__ dinv, const double *__restrict__ b,
+                                                 const uint8_t *__restrict__ ess, Grid g, double tol2, int maxit,
+                                                 unsigned *bar, double *part)
+{
+    const int64_t n = 3 * g.Nn;
+    double *pA = part, *pB = part + 3 * kRedBlocks, *pC = part + 6 * kRedBlocks;
+    int *tflag = d.flag + F_CTIMEOUT;
+    // start: x = 0, r = b, p = Dinv b
+    double v2[2] = {0.0, 0.0}, t2[2];
+    GRID_STRIDE(i, n)
+    {
+        const double bi = b[i], zi = dinv[i] * bi;
+        x[i] = 0.0;
+        r[i] = bi;
+        p[i] = zi;
+        v2[0] += bi * zi;
+        v2[1] += bi * bi;
+    }
+    publish<2>(pC, v2);
+    if (!grid_barrier(bar, tflag)) return;
+    all_sum<2>(pC, t2);
+    double rz = t2[0];
+    const double bb = t2[1];
+    double rr = bb;
+    int it = 0;
+    bool stop = !(bb > 0.0) || !isfinite(bb);
+    while (!stop && it < maxit) {
+        double v1[1] = {0.0}, t1[1];
+        GRID_STRIDE(row, n)
+        {
+            const double y = stencil_row(vals, p, ess, g, row);
+            q[row] = y;
+            v1[0] += p[row] * y;
+        }
+        publish<1>(pA, v1);
+        if (!grid_barrier(bar, tflag)) return;
+        all_sum<1>(pA, t1);
+        const double pq = t1[0];
+        if (!(pq > 0.0) || !isfinite(pq)) break;
+        const double alpha = rz / pq;
+        v2[0] = v2[1] = 0.0;
+        GRID_STRIDE(i, n)
+        {
+            x[i] += alpha * p[i];
+            const double ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            v2[0] += ri * ri;
+            v2[1] += ri * dinv[i] * ri;
+        }
+        publish<2>(pB, v2);
+        if (!grid_barrier(bar, tflag)) return;
+        all_sum<2>(pB, t2);
+        rr = t2[0];
+        const double beta = t2[1] / rz;
+        rz = t2[1];
+        ++it;
+        if (rr <= tol2 * bb || !isfinite(rr)) break;
+        GRID_STRIDE(i, n) p[i] = dinv[i] * r[i] + beta * p[i];
+        if (!grid_barrier(bar, tflag)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.scal[C_RR] = rr;
+        d.scal[C_BB] = bb;
+        d.flag[F_CIT] = it;
+    }
+}
+
 // Loop condition of the graph's coarse WHILE node: continue while the coarse
 // CG has not stopped and the iteration cap is not reached.
 __global__ void k_cg_cond(Dev d, int maxit, cudaGraphConditionalHandle h)
@@ -626,6 +795,10 @@ struct pa_solver {
     bool use_graphs = true;
     cudaStream_t stream = nullptr;  // the solver's own stream (capture needs a non-legacy stream)
     pa::StepGraphs g64, g32;
+    unsigned *bar = nullptr;      // grid barrier state of the persistent coarse CG
+    double *coop_part = nullptr;  // its per-CTA partial sums [3][3][kRedBlocks]
+    int coop_blocks = 0;          // co-resident CTAs (0: no cooperative launch)
+    bool allow_coop = true;
     double *xin = nullptr, *bin = nullptr;  // FP64 solve operates on these copies
     int mode = PA_SOLVE_FP64;
     int cheb_order = 2;
@@ -868,9 +1041,33 @@ int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
     return PA_OK;
 }
 
-// Eager coarse loop: a fixed number of launches (used without graphs).
+// The persistent cooperative coarse CG applies when the coarse level is
+// assembled and co-resident CTAs are available.
+bool use_coop(pa_solver *s) { return s->allow_coop && s->coop_blocks > 0 && s->lv.back().stencil != nullptr; }
+
+int coarse_coop(pa_solver *s, cudaStream_t st)
+{
+    Level &L = s->lv.back();
+    PA_CUDA_TRY(cudaMemsetAsync(s->bar, 0, 2 * sizeof(unsigned), st));
+    Dev dv = s->dev;
+    const double *vals = L.stencil, *dinv = L.dinv, *b = L.r;
+    double *x = L.cx, *r = L.cr, *p = L.cp, *q = L.cq;
+    const uint8_t *ess = L.op->d_ess;
+    Grid g = L.op->g;
+    double tol2 = s->coarse_rtol * s->coarse_rtol;
+    int maxit = s->coarse_maxit;
+    unsigned *bar = s->bar;
+    double *part = s->coop_part;
+    void *args[] = {&dv, &vals, &x, &r, &p, &q, &dinv, &b, &ess, &g, &tol2, &maxit, &bar, &part};
+    PA_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_cg_coop, dim3(s->coop_blocks), dim3(256), args, 0, st));
+    return PA_OK;
+}
+
+// Eager coarse solve: the persistent kernel, or a fixed number of launches
+// of the iteration kernels (which return at once after convergence).
 int coarse_eager(pa_solver *s, cudaStream_t st)
 {
+    if (use_coop(s)) return coarse_coop(s, st);
     Level &L = s->lv.back();
     for (int it = 0; it < s->coarse_maxit; ++it) {
         int rc = coarse_iter(s, L, st);
@@ -897,7 +1094,7 @@ int vcycle_down(pa_solver *s, cudaStream_t st)
     }
     Level &Lc = s->lv.back();
     if constexpr (sizeof(T) == 4) k_scale_copy<float, double><<<blocks_for(Lc.n), 256, 0, st>>>(Lc.r, Lc.r32, 1.0, Lc.n);
-    coarse_start(s, Lc, st);
+    if (!use_coop(s)) coarse_start(s, Lc, st);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -1006,6 +1203,24 @@ int fcg_iter_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 template <typename FA, typename FB>
 int build_step_graph(pa_solver *s, cudaStream_t st, FA seg_a, FB seg_b, cudaGraphExec_t *out)
 {
+    if (use_coop(s)) {
+        // one capture: segment A, the persistent coarse CG, segment B
+        cudaGraph_t g = nullptr;
+        PA_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        int r = seg_a();
+        if (!r) r = coarse_coop(s, st);
+        if (!r) r = seg_b();
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (r) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "solver graph: cudaStreamEndCapture");
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        return PA_OK;
+    }
     cudaGraph_t G = nullptr, gA = nullptr, gB = nullptr, gBody = nullptr;
     int rc = PA_OK;
     auto capture = [&](cudaGraph_t *g, auto &&fn) -> int {
@@ -1105,6 +1320,7 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
     if (rc) return rc;
     double rr = s->h_scal[S_RR];
     int it = 0;
+    if (s->h_flag[F_CTIMEOUT]) return set_error(PA_ETIMEOUT, "solver: coarse-solve grid barrier timed out");
     if (s->h_flag[F_BREAK]) {
         *iters = 0;
         return set_error(PA_EBREAKDOWN, "solver: non-finite value in the first preconditioned residual");
@@ -1114,6 +1330,10 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
         if (rc) return rc;
         rr = s->h_scal[S_RR];
         ++it;
+        if (s->h_flag[F_CTIMEOUT]) {
+            *iters = it;
+            return set_error(PA_ETIMEOUT, "solver: coarse-solve grid barrier timed out");
+        }
         if (s->h_flag[F_BREAK]) {
             *iters = it;
             return set_error(PA_EBREAKDOWN, "solver: CG breakdown (p^T A p <= 0 or non-finite value)");
@@ -1276,6 +1496,17 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
     TRYC(cudaMallocHost((void **)&s->h_scal, sizeof(double) * NSLOT));
     TRYC(cudaMallocHost((void **)&s->h_flag, sizeof(int) * NFLAG));
     TRYC(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    TRY(dalloc(s, &s->bar, 2));
+    TRY(dalloc(s, &s->coop_part, 9 * (int64_t)kRedBlocks));
+    {
+        int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_coop, 256, 0) == cudaSuccess)
+            s->coop_blocks = std::min(kRedBlocks, per_sm * nsm);
+        cudaGetLastError();
+    }
 
     s->lv.resize(nlev);
     std::vector<uint8_t> mask = fine->h_ess;
@@ -1371,7 +1602,18 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
 {
     if (!s) return set_error(PA_EINVAL, "pa_solver_set_option: null solver");
     switch (option) {
-    case PA_SOLVER_OPT_GRAPHS: s->use_graphs = value != 0.0; return PA_OK;
+    case PA_SOLVER_OPT_GRAPHS:
+    case PA_SOLVER_OPT_PERSISTENT_COARSE: {
+        // both change what the step graphs contain: drop any built graphs
+        for (StepGraphs *g : {&s->g64, &s->g32}) {
+            if (g->init) cudaGraphExecDestroy(g->init);
+            if (g->iter) cudaGraphExecDestroy(g->iter);
+            g->init = g->iter = nullptr;
+        }
+        if (option == PA_SOLVER_OPT_GRAPHS) s->use_graphs = value != 0.0;
+        else s->allow_coop = value != 0.0;
+        return PA_OK;
+    }
     default: return set_error(PA_EINVAL, "pa_solver_set_option: unknown option");
     }
 }

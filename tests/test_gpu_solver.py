@@ -113,8 +113,9 @@ def test_nan_rhs_is_rejected(pa):
     op.close()
 
 
+@pytest.mark.parametrize("coop", [1, 0])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_graph_and_eager_paths_agree_bitwise(pa, mode):
+def test_graph_and_eager_paths_agree_bitwise(pa, mode, coop):
     """Each CG step captured as a CUDA graph (device-controlled coarse loop)
     and the same kernels launched one by one give the same bits."""
     m = _beam(8, 2, 2)
@@ -127,6 +128,7 @@ def test_graph_and_eager_paths_agree_bitwise(pa, mode):
     for graphs in (1, 0):
         s = pa.pa_solver_create(op.h, [4, 2, 1], 2, 1e-4, 300, mode)
         pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, graphs)
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_PERSISTENT_COARSE, coop)
         x = torch.zeros_like(b)
         code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 200)
         assert code == pa.PA_OK
