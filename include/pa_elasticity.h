@@ -200,7 +200,14 @@ typedef struct pa_solve_info {
     double lambda_max[8];  /* per level: power-iteration estimate of max eig(D^-1 A) */
 } pa_solve_info;
 
-enum pa_solve_mode { PA_SOLVE_FP64 = 0, PA_SOLVE_MIXED = 1 };
+/* PA_SOLVE_FP64: everything in FP64.
+ * PA_SOLVE_MIXED: FP64 iterative refinement (residual b - A x with the FP64
+ *   operator) around an FP32 flexible CG preconditioned by an FP32 V-cycle.
+ * PA_SOLVE_MIXED_FCG: FP64 flexible CG (FP64 apply, residual and dot
+ *   products) preconditioned by an FP32 V-cycle (FP32 operators, smoothers,
+ *   transfers); no restarts, so it keeps the FP64 iteration count.
+ * In both mixed modes the coarse-level solve and every dot product are FP64. */
+enum pa_solve_mode { PA_SOLVE_FP64 = 0, PA_SOLVE_MIXED = 1, PA_SOLVE_MIXED_FCG = 2 };
 
 /* GMG-PCG solver on the p-hierarchy of `fine` (Sec. 3): levels
  * p_levels[0] = fine degree > p_levels[1] > ... > p_levels[nlev-1], all on the
@@ -222,8 +229,18 @@ int pa_solver_destroy(pa_solver *s);
  *    barriers (a barrier that waits more than ~2 s makes the solve return
  *    PA_ETIMEOUT); 0: one launch per kernel of every coarse iteration (a
  *    device-controlled graph loop when graphs are on).  Solvers that run
- *    concurrently on one GPU (the server) use 0. */
-enum pa_solver_option { PA_SOLVER_OPT_GRAPHS = 1, PA_SOLVER_OPT_PERSISTENT_COARSE = 2 };
+ *    concurrently on one GPU (the server) use 0.
+ *  PA_SOLVER_OPT_COARSE_HMG (default 1): the coarse CG on the assembled
+ *    p = 1 level is preconditioned by geometric h-multigrid on that level
+ *    (structured coarsening, Galerkin stencils, Chebyshev-Jacobi smoothing,
+ *    dense solve of the last level) -- the h-levels under the p-levels of the
+ *    paper's hierarchy (Sec. 3); 0: Jacobi-preconditioned coarse CG.
+ */
+enum pa_solver_option {
+    PA_SOLVER_OPT_GRAPHS = 1,
+    PA_SOLVER_OPT_PERSISTENT_COARSE = 2,
+    PA_SOLVER_OPT_COARSE_HMG = 3
+};
 int pa_solver_set_option(pa_solver *s, int option, double value);
 
 /* Solve A x = b (x: in = initial guess, out = solution; device double

@@ -19,7 +19,7 @@ from .build import LIB as _LIB_PATH
 
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY = range(8)
 PA_FP64, PA_FP32 = 0, 1
-PA_SOLVE_FP64, PA_SOLVE_MIXED = 0, 1
+PA_SOLVE_FP64, PA_SOLVE_MIXED, PA_SOLVE_MIXED_FCG = 0, 1, 2
 
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: build it with `python paper_2601_08374_gb300/build.py`")
@@ -262,6 +262,7 @@ def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=
 
 PA_SOLVER_OPT_GRAPHS = 1
 PA_SOLVER_OPT_PERSISTENT_COARSE = 2
+PA_SOLVER_OPT_COARSE_HMG = 3
 
 
 def pa_solver_set_option(h, option, value):

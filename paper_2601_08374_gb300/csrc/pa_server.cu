@@ -64,7 +64,7 @@ size_t footprint_bytes(const pa_request &r, const std::vector<int> &levels)
             return ne * 12 * elem + ne * 96 + ne * 3 * (size_t)D * D * D * elem + 2 * N * elem + N;
         };
         total += op_bytes(8) + 5 * N * 8 + (l + 1 < levels.size() ? 2 : 4) * N * 8;
-        if (r.mode == PA_SOLVE_MIXED) total += op_bytes(4) + 7 * N * 4;
+        if (r.mode != PA_SOLVE_FP64) total += op_bytes(4) + 7 * N * 4;
     }
     total += 7 * n0 * 8 + (r.mode == PA_SOLVE_MIXED ? 6 * n0 * 4 : 0);
     total += 2 * n0 * 8;  // b and x of the request
@@ -246,7 +246,8 @@ int pa_server_submit(pa_server *s, const pa_request *req, int64_t *ticket)
     if (req->nx < 1 || req->ny < 1 || req->nz < 1 || req->p < 1 || req->p > kMaxP)
         return set_error(PA_EINVAL, "pa_server_submit: bad mesh size or degree");
     if (req->nmodes < 0 || req->nmodes > PA_REQUEST_MAX_MODES) return set_error(PA_EINVAL, "pa_server_submit: nmodes");
-    if (req->mode != PA_SOLVE_FP64 && req->mode != PA_SOLVE_MIXED) return set_error(PA_EINVAL, "pa_server_submit: mode");
+    if (req->mode != PA_SOLVE_FP64 && req->mode != PA_SOLVE_MIXED && req->mode != PA_SOLVE_MIXED_FCG)
+        return set_error(PA_EINVAL, "pa_server_submit: mode");
     if (!(req->rtol > 0.0) || req->maxit < 1) return set_error(PA_EINVAL, "pa_server_submit: rtol or maxit");
     auto t = std::make_shared<Ticket>();
     t->req = *req;

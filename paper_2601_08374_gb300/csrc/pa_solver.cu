@@ -14,10 +14,11 @@
 // the coarse solve runs only the iterations it needs (an eager path with a
 // fixed-length coarse loop of early-returning kernels remains as fallback).
 //
-// Mixed mode (PA_SOLVE_MIXED): iterative refinement in FP64 (residual
-// b - A x with the FP64 operator, FP64 norms), inner flexible CG in FP32
-// storage with FP64 dot products, preconditioned by an FP32 V-cycle whose
-// coarse solve is the FP64 CG.
+// Mixed modes: PA_SOLVE_MIXED is iterative refinement in FP64 (residual
+// b - A x with the FP64 operator, FP64 norms) around an inner flexible CG in
+// FP32 storage with FP64 dot products, preconditioned by an FP32 V-cycle;
+// PA_SOLVE_MIXED_FCG is the FP64 flexible CG preconditioned by the FP32
+// V-cycle.  The coarse-level solve is FP64 in every mode.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -602,6 +603,277 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
     }
 }
 
+
+// ------------------------------------------------------ h-multigrid (p = 1)
+// Geometric coarsening of the assembled p = 1 level below the p-hierarchy
+// (the paper's hierarchy has h-levels at p = 1 under its p-levels, Sec. 3).
+// Along an axis with M fine nodes the coarse nodes sit at the even fine
+// indices and at the last node: Mc = (M + 1) / 2 for odd M, M / 2 + 1 for
+// even M.  Prolongation is linear interpolation between coarse nodes (per
+// component); restriction is its exact transpose; coarse operators are the
+// Galerkin products P^T A P in the same 27-point stencil form.
+__host__ __device__ inline int h_coarse_size(int M) { return (M & 1) ? (M + 1) / 2 : M / 2 + 1; }
+
+__host__ __device__ inline int h_pos(int J, int Mf, int Mc) { return (J == Mc - 1) ? Mf - 1 : 2 * J; }
+
+// coarse parents of fine index i along one axis: 1 or 2 (index, weight)
+__host__ __device__ inline int h_parents(int i, int Mf, int Mc, int *J, double *w)
+{
+    if (i == Mf - 1) {
+        J[0] = Mc - 1;
+        w[0] = 1.0;
+        return 1;
+    }
+    if ((i & 1) == 0) {
+        J[0] = i / 2;
+        w[0] = 1.0;
+        return 1;
+    }
+    J[0] = (i - 1) / 2;
+    w[0] = 0.5;
+    J[1] = (i + 1) / 2;
+    w[1] = 0.5;
+    return 2;
+}
+
+// weight of coarse index J in the interpolation of fine index i (0 if none)
+__host__ __device__ inline double h_weight(int i, int J, int Mf, int Mc)
+{
+    int Jp[2];
+    double w[2];
+    const int n = h_parents(i, Mf, Mc, Jp, w);
+    for (int k = 0; k < n; ++k)
+        if (Jp[k] == J) return w[k];
+    return 0.0;
+}
+
+// y = A x on an assembled stencil level (constrained like the operator)
+__global__ void k_stencil_apply(const double *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y,
+                                const uint8_t *__restrict__ ess, Grid g)
+{
+    GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, ess, g, row);
+}
+
+// One axis of the h-prolongation: out (axis `ax` fine, size Mf) from in
+// (axis coarse, size Mc); dims of out given in Nx, Ny, Nz.
+__global__ void k_hprolong_axis(double *out, const double *in, int ax, int Nx, int Ny, int Nz, int Mf, int Mc,
+                                int accumulate)
+{
+    const int dims[3] = {Nx, Ny, Nz};
+    int cdims[3] = {Nx, Ny, Nz};
+    cdims[ax] = Mc;
+    const int64_t total = 3LL * Nx * Ny * Nz;
+    GRID_STRIDE(o, total)
+    {
+        int64_t t = o;
+        int idx[3];
+        idx[0] = (int)(t % dims[0]); t /= dims[0];
+        idx[1] = (int)(t % dims[1]); t /= dims[1];
+        idx[2] = (int)(t % dims[2]);
+        const int c = (int)(t / dims[2]);
+        int J[2];
+        double w[2];
+        const int np = h_parents(idx[ax], Mf, Mc, J, w);
+        double s2 = 0.0;
+        for (int k = 0; k < np; ++k) {
+            idx[ax] = J[k];
+            s2 += w[k] * in[(((int64_t)c * cdims[2] + idx[2]) * cdims[1] + idx[1]) * cdims[0] + idx[0]];
+        }
+        out[o] = accumulate ? out[o] + s2 : s2;
+    }
+}
+
+// Exact transpose of k_hprolong_axis: out (axis coarse, size Mc) from in
+// (axis fine, size Mf); optional in2 subtracted on the fly; optional ess mask
+// (on the output L-vector) zeroes essential entries.
+__global__ void k_hrestrict_axis(double *out, const double *in, const double *in2, int ax, int Nx, int Ny, int Nz,
+                                 int Mf, int Mc, const uint8_t *ess)
+{
+    int odims[3] = {Nx, Ny, Nz}, fdims[3] = {Nx, Ny, Nz};
+    odims[ax] = Mc;
+    fdims[ax] = Mf;
+    const int64_t total = 3LL * odims[0] * odims[1] * odims[2];
+    GRID_STRIDE(o, total)
+    {
+        int64_t t = o;
+        int idx[3];
+        idx[0] = (int)(t % odims[0]); t /= odims[0];
+        idx[1] = (int)(t % odims[1]); t /= odims[1];
+        idx[2] = (int)(t % odims[2]);
+        const int c = (int)(t / odims[2]);
+        const int J = idx[ax], pj = h_pos(J, Mf, Mc);
+        double s2 = 0.0;
+        for (int i = pj - 1; i <= pj + 1; ++i) {
+            if (i < 0 || i >= Mf) continue;
+            const double w = h_weight(i, J, Mf, Mc);
+            if (w == 0.0) continue;
+            idx[ax] = i;
+            const int64_t fi = (((int64_t)c * fdims[2] + idx[2]) * fdims[1] + idx[1]) * fdims[0] + idx[0];
+            s2 += w * (in2 ? in[fi] - in2[fi] : in[fi]);
+        }
+        out[o] = (ess && ess[o]) ? 0.0 : s2;
+    }
+}
+
+// Galerkin coarse stencil: one thread per coarse row (c, I); essential fine
+// rows and columns are left out of the product (the constrained operator).
+__global__ void k_rap_stencil(const double *__restrict__ fv, const uint8_t *__restrict__ fess, Grid gf,
+                              double *__restrict__ cv, Grid gc)
+{
+    const int64_t nrow_c = 3 * gc.Nn, nrow_f = 3 * gf.Nn;
+    GRID_STRIDE(row, nrow_c)
+    {
+        const int c = (int)(row / gc.Nn);
+        const int64_t I = row - c * gc.Nn;
+        const int Ic[3] = {(int)(I % gc.Mx), (int)((I / gc.Mx) % gc.My), (int)(I / ((int64_t)gc.Mx * gc.My))};
+        const int Mf[3] = {gf.Mx, gf.My, gf.Mz}, Mc[3] = {gc.Mx, gc.My, gc.Mz};
+        double acc[81];
+        for (int k = 0; k < 81; ++k) acc[k] = 0.0;
+        int pos[3];
+        for (int a = 0; a < 3; ++a) pos[a] = h_pos(Ic[a], Mf[a], Mc[a]);
+        for (int iz = pos[2] - 1; iz <= pos[2] + 1; ++iz) {
+            if (iz < 0 || iz >= Mf[2]) continue;
+            const double wz = h_weight(iz, Ic[2], Mf[2], Mc[2]);
+            if (wz == 0.0) continue;
+            for (int iy = pos[1] - 1; iy <= pos[1] + 1; ++iy) {
+                if (iy < 0 || iy >= Mf[1]) continue;
+                const double wy = h_weight(iy, Ic[1], Mf[1], Mc[1]);
+                if (wy == 0.0) continue;
+                for (int ix = pos[0] - 1; ix <= pos[0] + 1; ++ix) {
+                    if (ix < 0 || ix >= Mf[0]) continue;
+                    const double wx = h_weight(ix, Ic[0], Mf[0], Mc[0]);
+                    if (wx == 0.0) continue;
+                    const double wi = wx * wy * wz;
+                    const int64_t i = ix + (int64_t)gf.Mx * (iy + (int64_t)gf.My * iz);
+                    const int64_t frow = c * gf.Nn + i;
+                    if (fess && fess[frow]) continue;
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int jz = iz + dz;
+                        if (jz < 0 || jz >= Mf[2]) continue;
+                        int Jz[2];
+                        double wjz[2];
+                        const int nz2 = h_parents(jz, Mf[2], Mc[2], Jz, wjz);
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            const int jy = iy + dy;
+                            if (jy < 0 || jy >= Mf[1]) continue;
+                            int Jy[2];
+                            double wjy[2];
+                            const int ny2 = h_parents(jy, Mf[1], Mc[1], Jy, wjy);
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int jx = ix + dx;
+                                if (jx < 0 || jx >= Mf[0]) continue;
+                                int Jx[2];
+                                double wjx[2];
+                                const int nx2 = h_parents(jx, Mf[0], Mc[0], Jx, wjx);
+                                const int fs = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                                const int64_t j = jx + (int64_t)gf.Mx * (jy + (int64_t)gf.My * jz);
+                                for (int d = 0; d < 3; ++d) {
+                                    if (fess && fess[d * gf.Nn + j]) continue;
+                                    const double a = wi * fv[(int64_t)(fs * 3 + d) * nrow_f + frow];
+                                    if (a == 0.0) continue;
+                                    for (int kz = 0; kz < nz2; ++kz)
+                                        for (int ky = 0; ky < ny2; ++ky)
+                                            for (int kx = 0; kx < nx2; ++kx) {
+                                                const int cs = (Jx[kx] - Ic[0] + 1) + 3 * (Jy[ky] - Ic[1] + 1) +
+                                                               9 * (Jz[kz] - Ic[2] + 1);
+                                                acc[cs * 3 + d] += a * wjx[kx] * wjy[ky] * wjz[kz];
+                                            }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        for (int k = 0; k < 81; ++k) cv[(int64_t)k * nrow_c + row] = acc[k];
+    }
+}
+
+// y = Ainv x with a dense (coarsest-level) inverse, one thread per row
+__global__ void k_dense_matvec(const double *__restrict__ Ainv, const double *__restrict__ x, double *__restrict__ y,
+                               int64_t n)
+{
+    GRID_STRIDE(i, n)
+    {
+        double s2 = 0.0;
+        const double *row = Ainv + i * n;
+        for (int64_t j = 0; j < n; ++j) s2 += row[j] * x[j];
+        y[i] = s2;
+    }
+}
+
+// preconditioned coarse CG (z = M r from the h-cycle)
+// start 1: x = 0, r = b, bb = (b, b), done = bb == 0
+__global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64_t n, double tol2)
+{
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n)
+    {
+        const double bi = b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        v[0] += bi * bi;
+    }
+    if (grid_sum<1>(d, v, tot)) {
+        d.scal[C_BB] = tot[0];
+        d.scal[C_RR] = tot[0];
+        d.scal[C_TOL2] = tol2;
+        d.flag[F_CDONE] = (tot[0] == 0.0 || !isfinite(tot[0])) ? 1 : 0;
+        d.flag[F_CIT] = 0;
+    }
+}
+
+// start 2: p = z, rz = (r, z)
+__global__ void k_pcg_start2(Dev d, double *p, const double *z, const double *r, int64_t n)
+{
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n)
+    {
+        p[i] = z[i];
+        v[0] += r[i] * z[i];
+    }
+    if (grid_sum<1>(d, v, tot)) d.scal[C_RZ] = tot[0];
+}
+
+// x += alpha p; r -= alpha q; rr = (r, r); done when rr <= tol2 bb
+__global__ void k_pcg_update(Dev d, double *x, double *r, const double *p, const double *q, int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    const double alpha = d.scal[C_ALPHA];
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n)
+    {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        v[0] += ri * ri;
+    }
+    if (grid_sum<1>(d, v, tot)) {
+        d.scal[C_RR] = tot[0];
+        if (tot[0] <= d.scal[C_TOL2] * d.scal[C_BB] || !isfinite(tot[0])) d.flag[F_CDONE] = 1;
+    }
+}
+
+// rz_new = (r, z); beta = rz_new / rz; rz = rz_new
+__global__ void k_pcg_beta(Dev d, const double *r, const double *z, int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    double v[1] = {0.0}, tot[1];
+    GRID_STRIDE(i, n) v[0] += r[i] * z[i];
+    if (grid_sum<1>(d, v, tot)) {
+        d.scal[C_BETA] = tot[0] / d.scal[C_RZ];
+        d.scal[C_RZ] = tot[0];
+    }
+}
+
+// p = z + beta p
+__global__ void k_pcg_p(Dev d, double *p, const double *z, int64_t n)
+{
+    if (d.flag[F_CDONE]) return;
+    const double beta = d.scal[C_BETA];
+    GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+}
+
 // Loop condition of the graph's coarse WHILE node: continue while the coarse
 // CG has not stopped and the iteration cap is not reached.
 __global__ void k_cg_cond(Dev d, int maxit, cudaGraphConditionalHandle h)
@@ -782,6 +1054,19 @@ struct Level {
     double *stencil = nullptr;  // assembled p = 1 coarse matrix (81 planes of n), or null
 };
 
+// One level of the h-hierarchy below the p = 1 level (assembled stencils).
+struct HLevel {
+    Grid g{};                   // grid of this level (nodes Mx x My x Mz)
+    int64_t n = 0;              // 3 Nn
+    double *vals = nullptr;     // stencil (81 planes of n); level 0 borrows the p = 1 stencil
+    uint8_t *ess = nullptr;     // essential mask (level 0 borrows the operator's)
+    double *dinv = nullptr;     // 1 / diag
+    double *r = nullptr, *e = nullptr, *t = nullptr, *d = nullptr;
+    double *xa = nullptr, *xb = nullptr;  // transfer temporaries (size of this level)
+    double theta = 0.0, delta = 0.0, lmax = 0.0;
+    double *Ainv = nullptr;     // dense inverse on the coarsest level
+};
+
 }  // namespace pa
 
 namespace pa {
@@ -794,11 +1079,13 @@ struct pa_solver {
     std::vector<pa::Level> lv;
     bool use_graphs = true;
     cudaStream_t stream = nullptr;  // the solver's own stream (capture needs a non-legacy stream)
-    pa::StepGraphs g64, g32;
+    pa::StepGraphs g64, g32, gmx;
     unsigned *bar = nullptr;      // grid barrier state of the persistent coarse CG
     double *coop_part = nullptr;  // its per-CTA partial sums [3][3][kRedBlocks]
     int coop_blocks = 0;          // co-resident CTAs (0: no cooperative launch)
     bool allow_coop = true;
+    std::vector<pa::HLevel> hl;   // h-multigrid under the p = 1 level (empty: Jacobi-CG coarse)
+    bool use_hmg = true;
     double *xin = nullptr, *bin = nullptr;  // FP64 solve operates on these copies
     int mode = PA_SOLVE_FP64;
     int cheb_order = 2;
@@ -911,6 +1198,296 @@ int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
     return PA_OK;
 }
 
+
+// ------------------------------------------------------- h-hierarchy setup
+int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
+{
+    const int64_t n = H.n;
+    k_random<<<blocks_for(n), 256, 0, st>>>(H.e, H.ess, n, 0x5151ull + (uint64_t)n);
+    double lam = 0.0;
+    for (int it = 0; it < 10; ++it) {
+        k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.e, n, P_DEN);
+        k_stencil_apply<<<blocks_for(n), 256, 0, st>>>(H.vals, H.e, H.t, H.ess, H.g);
+        k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.d, H.r, H.t, nullptr, H.dinv, 0.0, 1.0, 1, n);
+        k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.d, n, P_NUM);
+        PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + P_NUM, s->dev.scal + P_NUM, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        const double num = s->h_scal[P_NUM], den = s->h_scal[P_DEN];
+        if (!(den > 0.0) || !(num > 0.0) || !std::isfinite(num)) return set_error(PA_EBREAKDOWN, "solver: h-level power iteration");
+        lam = std::sqrt(num / den);
+        k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.e, H.d, 1.0 / std::sqrt(num), n);
+    }
+    H.lmax = lam;
+    const double a = 0.3 * lam, b = 1.2 * lam;
+    H.theta = 0.5 * (a + b);
+    H.delta = 0.5 * (b - a);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// Cholesky inverse of a small SPD matrix (host, in place on a copy).
+bool spd_inverse(std::vector<double> &A, int n)
+{
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(d > 0.0)) return false;
+        const double ljj = std::sqrt(d);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = v / ljj;
+        }
+    }
+    // inverse columns by forward/back substitution
+    std::vector<double> col(n);
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < n; ++i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= L[(size_t)i * n + k] * col[k];
+            col[i] = v / L[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double v = col[i];
+            for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * col[k];
+            col[i] = v / L[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; ++i) A[(size_t)i * n + c] = col[i];
+    }
+    return true;
+}
+
+// Builds the h-hierarchy under the p = 1 level: Galerkin stencils, masks,
+// diagonals, Chebyshev intervals, and a dense inverse on the coarsest level.
+int build_h_levels(pa_solver *s, cudaStream_t st)
+{
+    Level &L = s->lv.back();
+    if (!L.stencil) return PA_OK;
+    const int64_t kMaxDense = 650;
+    HLevel H0;
+    H0.g = L.op->g;
+    H0.n = L.n;
+    H0.vals = L.stencil;
+    H0.ess = L.op->d_ess;
+    H0.dinv = L.dinv;
+    s->hl.push_back(H0);
+    while (true) {
+        HLevel &F = s->hl.back();
+        if (F.n <= kMaxDense) break;
+        Grid c = F.g;
+        c.Mx = h_coarse_size(F.g.Mx);
+        c.My = h_coarse_size(F.g.My);
+        c.Mz = h_coarse_size(F.g.Mz);
+        if (c.Mx == F.g.Mx && c.My == F.g.My && c.Mz == F.g.Mz) break;
+        c.nx = c.Mx - 1;
+        c.ny = c.My - 1;
+        c.nz = c.Mz - 1;
+        c.p = 1;
+        c.ne = (int64_t)c.nx * c.ny * c.nz;
+        c.Nn = (int64_t)c.Mx * c.My * c.Mz;
+        HLevel C;
+        C.g = c;
+        C.n = 3 * c.Nn;
+        int rc;
+        if ((rc = dalloc(s, &C.vals, 81 * C.n))) return rc;
+        k_rap_stencil<<<blocks_for(C.n, 64), 64, 0, st>>>(F.vals, F.ess, F.g, C.vals, c);
+        PA_CUDA_TRY(cudaGetLastError());
+        if (F.ess) {
+            // coarse essential dofs: those whose interpolation reaches an
+            // essential fine dof (restrict the fine mask as a 0/1 field)
+            std::vector<uint8_t> fm((size_t)F.n);
+            PA_CUDA_TRY(cudaMemcpyAsync(fm.data(), F.ess, F.n, cudaMemcpyDeviceToHost, st));
+            PA_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<uint8_t> cm((size_t)C.n, 0);
+            const int Mf[3] = {F.g.Mx, F.g.My, F.g.Mz}, Mc[3] = {c.Mx, c.My, c.Mz};
+            for (int comp = 0; comp < 3; ++comp)
+                for (int64_t i = 0; i < F.g.Nn; ++i) {
+                    if (!fm[(size_t)(comp * F.g.Nn + i)]) continue;
+                    const int f[3] = {(int)(i % F.g.Mx), (int)((i / F.g.Mx) % F.g.My), (int)(i / ((int64_t)F.g.Mx * F.g.My))};
+                    int J[3][2], nJ[3];
+                    double w[3][2];
+                    for (int a = 0; a < 3; ++a) nJ[a] = h_parents(f[a], Mf[a], Mc[a], J[a], w[a]);
+                    for (int kz = 0; kz < nJ[2]; ++kz)
+                        for (int ky = 0; ky < nJ[1]; ++ky)
+                            for (int kx = 0; kx < nJ[0]; ++kx)
+                                cm[(size_t)(comp * c.Nn + J[0][kx] + (int64_t)c.Mx * (J[1][ky] + (int64_t)c.My * J[2][kz]))] = 1;
+                }
+            if ((rc = dalloc(s, &C.ess, C.n))) return rc;
+            PA_CUDA_TRY(cudaMemcpyAsync(C.ess, cm.data(), C.n, cudaMemcpyHostToDevice, st));
+            PA_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        if ((rc = dalloc(s, &C.dinv, C.n))) return rc;
+        s->hl.push_back(C);
+    }
+    // work vectors, diagonals, Chebyshev intervals, coarsest inverse
+    for (size_t k = 0; k < s->hl.size(); ++k) {
+        HLevel &H = s->hl[k];
+        int rc;
+        if ((rc = dalloc(s, &H.r, H.n)) || (rc = dalloc(s, &H.e, H.n)) || (rc = dalloc(s, &H.t, H.n)) ||
+            (rc = dalloc(s, &H.d, H.n)) || (rc = dalloc(s, &H.xa, H.n)) || (rc = dalloc(s, &H.xb, H.n)))
+            return rc;
+        if (k > 0) {
+            // diagonal = stencil centre entry (s = 13) of the own component; 1 on essential rows
+            std::vector<double> cen((size_t)H.n);
+            std::vector<uint8_t> em;
+            for (int comp = 0; comp < 3; ++comp)
+                PA_CUDA_TRY(cudaMemcpyAsync(cen.data() + comp * H.g.Nn, H.vals + (int64_t)(13 * 3 + comp) * H.n + comp * H.g.Nn,
+                                            sizeof(double) * H.g.Nn, cudaMemcpyDeviceToHost, st));
+            if (H.ess) {
+                em.resize((size_t)H.n);
+                PA_CUDA_TRY(cudaMemcpyAsync(em.data(), H.ess, H.n, cudaMemcpyDeviceToHost, st));
+            }
+            PA_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int64_t i = 0; i < H.n; ++i) cen[(size_t)i] = (H.ess && em[(size_t)i]) ? 1.0 : 1.0 / cen[(size_t)i];
+            PA_CUDA_TRY(cudaMemcpyAsync(H.dinv, cen.data(), sizeof(double) * H.n, cudaMemcpyHostToDevice, st));
+            PA_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        if (k + 1 < s->hl.size()) {
+            if ((rc = h_power_lmax(s, H, st))) return rc;
+        }
+    }
+    // dense inverse of the coarsest level (constrained: identity on essential dofs)
+    HLevel &Hc = s->hl.back();
+    if (Hc.n > 4 * kMaxDense) return set_error(PA_EINVAL, "solver: h-hierarchy coarsest level too large for a dense solve");
+    const int n = (int)Hc.n;
+    std::vector<double> V((size_t)81 * n);
+    std::vector<uint8_t> em((size_t)n, 0);
+    PA_CUDA_TRY(cudaMemcpyAsync(V.data(), Hc.vals, sizeof(double) * V.size(), cudaMemcpyDeviceToHost, st));
+    if (Hc.ess) PA_CUDA_TRY(cudaMemcpyAsync(em.data(), Hc.ess, n, cudaMemcpyDeviceToHost, st));
+    PA_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> A((size_t)n * n, 0.0);
+    const Grid &g = Hc.g;
+    for (int row = 0; row < n; ++row) {
+        if (em[row]) {
+            A[(size_t)row * n + row] = 1.0;
+            continue;
+        }
+        const int c = (int)(row / g.Nn);
+        const int64_t i = row - c * g.Nn;
+        const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (ix + dx < 0 || ix + dx >= g.Mx || iy + dy < 0 || iy + dy >= g.My || iz + dz < 0 || iz + dz >= g.Mz)
+                        continue;
+                    const int sidx = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+                    const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
+                    for (int d = 0; d < 3; ++d) {
+                        const int64_t col = d * g.Nn + j;
+                        if (em[col]) continue;
+                        A[(size_t)row * n + col] += V[(size_t)(sidx * 3 + d) * n + row];
+                    }
+                }
+    }
+    // symmetrise the rounding, then invert
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+            A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
+        }
+    if (!spd_inverse(A, n)) return set_error(PA_EBREAKDOWN, "solver: coarsest h-level matrix is not SPD");
+    int rc = dalloc(s, &Hc.Ainv, (int64_t)n * n);
+    if (rc) return rc;
+    PA_CUDA_TRY(cudaMemcpyAsync(Hc.Ainv, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, st));
+    PA_CUDA_TRY(cudaStreamSynchronize(st));
+    return PA_OK;
+}
+
+// Chebyshev smoothing on an h-level (stencil operator), e <- S(r)
+int h_smooth(pa_solver *s, HLevel &H, bool from_zero, cudaStream_t st)
+{
+    const int64_t n = H.n;
+    const double sigma = H.theta / H.delta;
+    double rho_prev = 1.0 / sigma;
+    for (int k = 0; k < s->cheb_order; ++k) {
+        const double *tt = nullptr;
+        if (!(k == 0 && from_zero)) {
+            k_stencil_apply<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, H.e, H.t, H.ess, H.g);
+            tt = H.t;
+        }
+        double cd, cr;
+        if (k == 0) {
+            cd = 0.0;
+            cr = 1.0 / H.theta;
+        } else {
+            const double rho = 1.0 / (2.0 * sigma - rho_prev);
+            cd = rho * rho_prev;
+            cr = 2.0 * rho / H.delta;
+            rho_prev = rho;
+        }
+        k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.e, H.d, H.r, tt, H.dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// h-V(1,1) cycle from h-level k: e_k ~ A_k^-1 r_k
+int h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
+{
+    HLevel &F = s->hl[k];
+    if (k + 1 == s->hl.size()) {
+        k_dense_matvec<<<blocks_for(F.n, 64), 64, 0, st>>>(F.Ainv, F.r, F.e, F.n);
+        PA_CUDA_TRY(cudaGetLastError());
+        return PA_OK;
+    }
+    HLevel &C = s->hl[k + 1];
+    int rc = h_smooth(s, F, true, st);
+    if (rc) return rc;
+    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, F.e, F.t, F.ess, F.g);
+    // restrict r - t: x axis, y axis, z axis
+    const Grid &gf = F.g, &gc = C.g;
+    int64_t n1 = 3LL * gf.Mz * gf.My * gc.Mx, n2 = 3LL * gf.Mz * gc.My * gc.Mx, n3 = C.n;
+    k_hrestrict_axis<<<blocks_for(n1), 256, 0, st>>>(F.xa, F.r, F.t, 0, gf.Mx, gf.My, gf.Mz, gf.Mx, gc.Mx, nullptr);
+    k_hrestrict_axis<<<blocks_for(n2), 256, 0, st>>>(F.xb, F.xa, nullptr, 1, gc.Mx, gf.My, gf.Mz, gf.My, gc.My, nullptr);
+    k_hrestrict_axis<<<blocks_for(n3), 256, 0, st>>>(C.r, F.xb, nullptr, 2, gc.Mx, gc.My, gf.Mz, gf.Mz, gc.Mz, C.ess);
+    rc = h_vcycle(s, k + 1, st);
+    if (rc) return rc;
+    // prolong-add: x axis from the coarse grid, then y, then z (accumulate)
+    int64_t m1 = 3LL * gc.Mz * gc.My * gf.Mx, m2 = 3LL * gc.Mz * gf.My * gf.Mx;
+    k_hprolong_axis<<<blocks_for(m1), 256, 0, st>>>(F.xa, C.e, 0, gf.Mx, gc.My, gc.Mz, gf.Mx, gc.Mx, 0);
+    k_hprolong_axis<<<blocks_for(m2), 256, 0, st>>>(F.xb, F.xa, 1, gf.Mx, gf.My, gc.Mz, gf.My, gc.My, 0);
+    k_hprolong_axis<<<blocks_for(F.n), 256, 0, st>>>(F.e, F.xb, 2, gf.Mx, gf.My, gf.Mz, gf.Mz, gc.Mz, 1);
+    rc = h_smooth(s, F, false, st);
+    PA_CUDA_TRY(cudaGetLastError());
+    return rc;
+}
+
+bool use_hmg(pa_solver *s) { return s->use_hmg && s->hl.size() > 1; }
+
+// start of the h-multigrid preconditioned coarse CG: x = 0, r = b, z = M r, p = z
+int coarse_start_hmg(pa_solver *s, Level &L, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    HLevel &H = s->hl[0];
+    k_pcg_start1<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.r, n, s->coarse_rtol * s->coarse_rtol);
+    k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.r, L.cr, 1.0, n);
+    int rc = h_vcycle(s, 0, st);
+    if (rc) return rc;
+    k_pcg_start2<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cp, H.e, L.cr, n);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+// one iteration: q = A p, alpha, x, r, rr; z = M r; beta; p = z + beta p
+int coarse_iter_hmg(pa_solver *s, Level &L, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    HLevel &H = s->hl[0];
+    int64_t nb = (n + 63) / 64;
+    if (nb > kRedBlocks) nb = kRedBlocks;
+    k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->d_ess, L.op->g);
+    k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n);
+    k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.r, L.cr, 1.0, n);
+    int rc = h_vcycle(s, 0, st);
+    if (rc) return rc;
+    k_pcg_beta<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cr, H.e, n);
+    k_pcg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, H.e, n);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
 // ------------------------------------------------------------ V-cycle (T)
 template <typename T>
 struct LV {
@@ -1016,14 +1593,18 @@ void prolong_add(Level &F, Level &C, const T *ec, T *ef, cudaStream_t st)
 // FP64 Jacobi-CG on the coarsest level: L.cx ~ A^-1 L.r.  The start kernel
 // resets the device stop flag and iteration counter; every iteration's
 // kernels return at once after the flag is set.
-void coarse_start(pa_solver *s, Level &L, cudaStream_t st)
+int coarse_start(pa_solver *s, Level &L, cudaStream_t st)
 {
+    if (use_hmg(s)) return coarse_start_hmg(s, L, st);
     k_cg_start<<<red_blocks(L.n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.r, L.dinv, L.n,
                                                    s->coarse_rtol * s->coarse_rtol);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
 }
 
 int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
 {
+    if (use_hmg(s)) return coarse_iter_hmg(s, L, st);
     const int64_t n = L.n;
     if (L.stencil) {
         // FP64 work per row: spread the rows over the SMs (64 threads per CTA)
@@ -1043,7 +1624,10 @@ int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
 
 // The persistent cooperative coarse CG applies when the coarse level is
 // assembled and co-resident CTAs are available.
-bool use_coop(pa_solver *s) { return s->allow_coop && s->coop_blocks > 0 && s->lv.back().stencil != nullptr; }
+bool use_coop(pa_solver *s)
+{
+    return !use_hmg(s) && s->allow_coop && s->coop_blocks > 0 && s->lv.back().stencil != nullptr;
+}
 
 int coarse_coop(pa_solver *s, cudaStream_t st)
 {
@@ -1094,7 +1678,10 @@ int vcycle_down(pa_solver *s, cudaStream_t st)
     }
     Level &Lc = s->lv.back();
     if constexpr (sizeof(T) == 4) k_scale_copy<float, double><<<blocks_for(Lc.n), 256, 0, st>>>(Lc.r, Lc.r32, 1.0, Lc.n);
-    if (!use_coop(s)) coarse_start(s, Lc, st);
+    if (!use_coop(s)) {
+        int rc = coarse_start(s, Lc, st);
+        if (rc) return rc;
+    }
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -1131,7 +1718,7 @@ struct FcgVecs {
     bool x_zero;
 };
 
-template <typename T>
+template <typename T, typename TP>
 int fcg_init_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
@@ -1144,8 +1731,8 @@ int fcg_init_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
         if (rc) return rc;
         k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, v.q, n);
     }
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), v.r, 1.0, n);
-    return vcycle_down<T>(s, st);
+    k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
+    return vcycle_down<TP>(s, st);
 }
 
 template <typename T>
@@ -1156,20 +1743,20 @@ int publish_scalars(pa_solver *s, cudaStream_t st)
     return PA_OK;
 }
 
-template <typename T>
+template <typename T, typename TP>
 int fcg_init_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
-    int rc = vcycle_up<T>(s, st);
+    int rc = vcycle_up<TP>(s, st);
     if (rc) return rc;
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<T>::e(L0), 1.0, n);
+    k_scale_copy<TP, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<TP>::e(L0), 1.0, n);
     k_fcg_start<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.z, v.r, n, 0);
     PA_CUDA_TRY(cudaGetLastError());
     return publish_scalars<T>(s, st);
 }
 
-template <typename T>
+template <typename T, typename TP>
 int fcg_iter_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
@@ -1178,18 +1765,18 @@ int fcg_iter_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
     if (rc) return rc;
     k_fcg_pq<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.q, n, 0);
     k_fcg_update<T, T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.x, v.r, v.p, v.q, n, 0);
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(LV<T>::r(L0), v.r, 1.0, n);
-    return vcycle_down<T>(s, st);
+    k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
+    return vcycle_down<TP>(s, st);
 }
 
-template <typename T>
+template <typename T, typename TP>
 int fcg_iter_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
-    int rc = vcycle_up<T>(s, st);
+    int rc = vcycle_up<TP>(s, st);
     if (rc) return rc;
-    k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<T>::e(L0), 1.0, n);
+    k_scale_copy<TP, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<TP>::e(L0), 1.0, n);
     k_fcg_beta<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.z, v.r, v.q, n, 0);
     k_fcg_p<T><<<blocks_for(n), 256, 0, st>>>(s->dev, v.p, v.z, n, 0);
     PA_CUDA_TRY(cudaGetLastError());
@@ -1282,17 +1869,17 @@ int build_step_graph(pa_solver *s, cudaStream_t st, FA seg_a, FB seg_b, cudaGrap
 // solve of the mixed mode).  Stops when (r, r) <= tol2 * bb or after maxit
 // iterations.  With graphs, each step is one graph launch; otherwise the
 // same segments run eagerly with the fixed-length coarse loop.
-template <typename T>
+template <typename T, typename TP = T>
 int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double bb, int maxit, int *iters,
         cudaStream_t st)
 {
     int rc;
     if (s->use_graphs && !sg.init) {
         rc = build_step_graph(
-            s, st, [&]() { return fcg_init_a<T>(s, v, st); }, [&]() { return fcg_init_b<T>(s, v, st); }, &sg.init);
+            s, st, [&]() { return fcg_init_a<T, TP>(s, v, st); }, [&]() { return fcg_init_b<T, TP>(s, v, st); }, &sg.init);
         if (!rc)
             rc = build_step_graph(
-                s, st, [&]() { return fcg_iter_a<T>(s, v, st); }, [&]() { return fcg_iter_b<T>(s, v, st); }, &sg.iter);
+                s, st, [&]() { return fcg_iter_a<T, TP>(s, v, st); }, [&]() { return fcg_iter_b<T, TP>(s, v, st); }, &sg.iter);
         if (rc) {
             // fall back to eager execution for this solver
             if (sg.init) cudaGraphExecDestroy(sg.init);
@@ -1306,11 +1893,11 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
         if (s->use_graphs) {
             PA_CUDA_TRY(cudaGraphLaunch(init ? sg.init : sg.iter, st));
         } else {
-            int r = init ? fcg_init_a<T>(s, v, st) : fcg_iter_a<T>(s, v, st);
+            int r = init ? fcg_init_a<T, TP>(s, v, st) : fcg_iter_a<T, TP>(s, v, st);
             if (r) return r;
             r = coarse_eager(s, st);
             if (r) return r;
-            r = init ? fcg_init_b<T>(s, v, st) : fcg_iter_b<T>(s, v, st);
+            r = init ? fcg_init_b<T, TP>(s, v, st) : fcg_iter_b<T, TP>(s, v, st);
             if (r) return r;
         }
         PA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1439,7 +2026,7 @@ int pa_solver_destroy(pa_solver *s)
         if (L.own_op) pa_op_destroy(L.op);
         pa_op_destroy(L.op32);
     }
-    for (StepGraphs *g : {&s->g64, &s->g32}) {
+    for (StepGraphs *g : {&s->g64, &s->g32, &s->gmx}) {
         if (g->init) cudaGraphExecDestroy(g->init);
         if (g->iter) cudaGraphExecDestroy(g->iter);
     }
@@ -1468,7 +2055,9 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             return set_error(PA_EINVAL, "pa_solver_create: degrees must decrease");
     if (cheb_order < 1 || cheb_order > 8) return set_error(PA_EINVAL, "pa_solver_create: cheb_order in 1..8");
     if (coarse_maxit < 1 || !(coarse_rtol >= 0.0)) return set_error(PA_EINVAL, "pa_solver_create: bad coarse parameters");
-    if (mode != PA_SOLVE_FP64 && mode != PA_SOLVE_MIXED) return set_error(PA_EINVAL, "pa_solver_create: bad mode");
+    if (mode != PA_SOLVE_FP64 && mode != PA_SOLVE_MIXED && mode != PA_SOLVE_MIXED_FCG)
+        return set_error(PA_EINVAL, "pa_solver_create: bad mode");
+    const bool fp32_levels = mode != PA_SOLVE_FP64;
 
     pa_solver *s = new (std::nothrow) pa_solver;
     if (!s) return set_error(PA_ENOMEM, "pa_solver_create: host allocation");
@@ -1526,7 +2115,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             L.own_op = true;
         }
         L.n = L.op->ndofs();
-        if (mode == PA_SOLVE_MIXED) TRY(make_level_op(fine, L.p, PA_FP32, L.op->h_ess, &L.op32));
+        if (fp32_levels) TRY(make_level_op(fine, L.p, PA_FP32, L.op->h_ess, &L.op32));
     }
     cudaStream_t st = s->stream;
     for (int l = 0; l < nlev; ++l) {
@@ -1560,7 +2149,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
                 TRY(pa_op_assemble_p1(L.op, L.stencil, st));
             }
         }
-        if (mode == PA_SOLVE_MIXED) {
+        if (fp32_levels) {
             TRY(dalloc(s, &L.r32, n));
             TRY(dalloc(s, &L.e32, n));
             TRY(dalloc(s, &L.dinv32, n));
@@ -1573,6 +2162,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             TRY(op_apply_async(L.op32, L.dinv32, L.t32, false, st, nullptr));
         }
     }
+    if (s->lv.back().stencil) TRY(build_h_levels(s, st));
     const int64_t n0 = s->lv[0].n;
     TRY(dalloc(s, &s->xin, n0));
     TRY(dalloc(s, &s->bin, n0));
@@ -1603,15 +2193,17 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
     if (!s) return set_error(PA_EINVAL, "pa_solver_set_option: null solver");
     switch (option) {
     case PA_SOLVER_OPT_GRAPHS:
-    case PA_SOLVER_OPT_PERSISTENT_COARSE: {
+    case PA_SOLVER_OPT_PERSISTENT_COARSE:
+    case PA_SOLVER_OPT_COARSE_HMG: {
         // both change what the step graphs contain: drop any built graphs
-        for (StepGraphs *g : {&s->g64, &s->g32}) {
+        for (StepGraphs *g : {&s->g64, &s->g32, &s->gmx}) {
             if (g->init) cudaGraphExecDestroy(g->init);
             if (g->iter) cudaGraphExecDestroy(g->iter);
             g->init = g->iter = nullptr;
         }
         if (option == PA_SOLVER_OPT_GRAPHS) s->use_graphs = value != 0.0;
-        else s->allow_coop = value != 0.0;
+        else if (option == PA_SOLVER_OPT_PERSISTENT_COARSE) s->allow_coop = value != 0.0;
+        else s->use_hmg = value != 0.0;
         return PA_OK;
     }
     default: return set_error(PA_EINVAL, "pa_solver_set_option: unknown option");
@@ -1652,10 +2244,11 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
     PA_CUDA_TRY(cudaMemcpyAsync(xs, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     PA_CUDA_TRY(cudaMemcpyAsync(bs, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bool converged = false;
-    if (s->mode == PA_SOLVE_FP64) {
+    if (s->mode == PA_SOLVE_FP64 || s->mode == PA_SOLVE_MIXED_FCG) {
         int it = 0;
         FcgVecs<double> v{xs, bs, s->r, s->z, s->p, s->q, false};
-        rc = fcg<double>(s, v, s->g64, tol2, bb, maxit, &it, st);
+        if (s->mode == PA_SOLVE_FP64) rc = fcg<double>(s, v, s->g64, tol2, bb, maxit, &it, st);
+        else rc = fcg<double, float>(s, v, s->gmx, tol2, bb, maxit, &it, st);
         inf.iterations = it;
         converged = (rc == PA_OK) && s->h_scal[S_RR] <= tol2 * bb;
     } else {

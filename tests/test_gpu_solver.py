@@ -67,6 +67,11 @@ def test_medium_beam_matches_direct_solve_fp64_and_mixed(pa):
     assert info2.rel_residual <= 2e-9
     assert np.linalg.norm(x2 - xo) <= 1e-8 * np.linalg.norm(xo)
     assert info2.refinements >= 1
+    # FP64 flexible CG preconditioned by the FP32 V-cycle
+    code, info3, x3, _, _ = _solve(pa, m, p, [4, 2, 1], lam, mu, mode=pa.PA_SOLVE_MIXED_FCG, coarse_rtol=1e-4,
+                                   coarse_maxit=300)
+    assert code == pa.PA_OK
+    assert np.linalg.norm(x3 - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
 def test_beam_32x4x4_p4_true_residual_against_oracle(pa):
@@ -113,12 +118,14 @@ def test_nan_rhs_is_rejected(pa):
     op.close()
 
 
-@pytest.mark.parametrize("coop", [1, 0])
-@pytest.mark.parametrize("mode", [0, 1])
-def test_graph_and_eager_paths_agree_bitwise(pa, mode, coop):
+@pytest.mark.parametrize("coop,hmg", [(1, 0), (0, 0), (0, 1)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_graph_and_eager_paths_agree_bitwise(pa, mode, coop, hmg):
     """Each CG step captured as a CUDA graph (device-controlled coarse loop)
-    and the same kernels launched one by one give the same bits."""
-    m = _beam(8, 2, 2)
+    and the same kernels launched one by one give the same bits, for every
+    coarse-solve variant (persistent Jacobi-CG, launched Jacobi-CG,
+    h-multigrid preconditioned CG)."""
+    m = _beam(32, 2, 2)  # p = 1 level of 2,673 dofs: one h-coarsening
     p = 4
     lam, mu = syn.lame(1.0, 0.3)
     ess = syn.clamp_mask(m, p)
@@ -129,6 +136,7 @@ def test_graph_and_eager_paths_agree_bitwise(pa, mode, coop):
         s = pa.pa_solver_create(op.h, [4, 2, 1], 2, 1e-4, 300, mode)
         pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, graphs)
         pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_PERSISTENT_COARSE, coop)
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_COARSE_HMG, hmg)
         x = torch.zeros_like(b)
         code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 200)
         assert code == pa.PA_OK
