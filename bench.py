@@ -293,6 +293,8 @@ def run_ours(args):
     }
     if not args.no_solve:
         out["solve"] = run_solves(args, pa, torch)
+    if args.batch_ops > 0:
+        out["batched_apply"] = run_batched_apply(args, pa, torch)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, pa, torch)
     if not args.no_cpu_baseline and ws == 1:
@@ -327,7 +329,7 @@ def run_solves(args, pa, torch):
         b = op.rhs(f0=c["f0"], modes=c["modes"])
         row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "rtol": 1e-10}
         sols = {}
-        for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed")):
+        for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):
             s = pa.pa_solver_create(op.h, c["levels"], 2, 1e-3, 300, mode)
             x = torch.zeros_like(b)
             code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)  # warm-up (captures the graphs)
@@ -345,19 +347,68 @@ def run_solves(args, pa, torch):
             if mode == pa.PA_SOLVE_MIXED:
                 row[key]["refinements"] = info.refinements
             pa.pa_solver_destroy(s)
-        d = (sols["mixed"] - sols["fp64"]).norm() / sols["fp64"].norm()
-        row["mixed_vs_fp64_rel_diff"] = float(f"{float(d):.3e}")
-        row["speedup_mixed_over_fp64"] = round(row["mixed"]["solves_per_s"] / row["fp64"]["solves_per_s"], 3)
+        for key in ("mixed_ir", "mixed_fcg"):
+            d = (sols[key] - sols["fp64"]).norm() / sols["fp64"].norm()
+            row[key]["rel_diff_vs_fp64"] = float(f"{float(d):.3e}")
+            row[key]["speedup_over_fp64"] = round(row[key]["solves_per_s"] / row["fp64"]["solves_per_s"], 3)
         out.append(row)
         op.close()
     return out
+
+
+def run_batched_apply(args, pa, torch):
+    """Many small operators (the sizes of the served requests' fine levels,
+    p in {2,4,6,8}, n^3 with n in 4..8, FP32) applied one launch pair each
+    versus one batched launch pair per degree."""
+    rng = np.random.default_rng(77)
+    ops, xs, ys = [], [], []
+    for k in range(args.batch_ops):
+        p = int(rng.choice([2, 4, 6, 8]))
+        n = int(rng.integers(4, 9))
+        m = syn.random_affine_cube(n, seed=5000 + k)
+        op = pa.Operator(n, n, n, m.affine, p, 1.0, 0.5, precision=pa.PA_FP32)
+        x = torch.tensor(syn.uniform_vector(op.ndofs, seed=k), dtype=torch.float32, device="cuda")
+        ops.append(op)
+        xs.append(x)
+        ys.append(torch.empty_like(x))
+    stream = torch.cuda.current_stream()
+    handles = [o.h for o in ops]
+    dofs = sum(o.ndofs for o in ops)
+
+    def one_by_one():
+        for o, x, y in zip(ops, xs, ys):
+            pa.pa_op_apply(o.h, x, y, stream)
+
+    def batched():
+        pa.pa_op_apply_batch(handles, xs, ys, stream)
+
+    res = {}
+    for name, fn in (("individual", one_by_one), ("batched", batched)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.batch_reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.batch_reps
+        res[name] = {"ms": round(ms, 4), "gdofs": round(dofs / (ms * 1e-3) / 1e9, 3)}
+    for o in ops:
+        o.close()
+    res["operators"] = args.batch_ops
+    res["total_dofs"] = dofs
+    res["speedup"] = round(res["individual"]["ms"] / res["batched"]["ms"], 3)
+    return res
 
 
 def serving_requests(pa, count, seed):
     """The served stream: p uniform in {2,4,6,8}; a cube n^3 (n ~ U{8..32}) or
     an 8:1:1 beam (8k x k x k, k ~ U{4..16}); E log-uniform in [0.1, 10];
     nu ~ U[0.2, 0.45]; 3 seeded sine modes of body force per component;
-    clamped at x = 0; mixed-precision solve to 1e-10."""
+    clamped at x = 0; mixed-precision solve (FP64 flexible CG, FP32 V-cycle)
+    to 1e-10."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):
@@ -372,27 +423,38 @@ def serving_requests(pa, count, seed):
         nu = float(rng.uniform(0.2, 0.45))
         modes = syn.smooth_force_modes(seed=int(rng.integers(1 << 30)))
         out.append(pa.make_request(*dims, box, p, E, nu, modes=modes, rtol=1e-10, maxit=1000,
-                                   mode=pa.PA_SOLVE_MIXED, keep_solution=False))
+                                   mode=pa.PA_SOLVE_MIXED_FCG, keep_solution=False))
     return out
 
 
 def run_serving(args, pa, torch):
-    """Continuous-admission serving of a Poisson stream.  The arrival rate is
-    a fraction of the capacity measured on a calibration burst of the same
-    recipe (all submitted at once).  Reports p50/p99 latency (submit to
+    """Continuous-admission serving of a Poisson stream.  A calibration burst
+    of the first requests is solved twice, all submitted at once: in plain
+    FP64 with one slot (the FP64-alone capacity) and in the served form
+    (mixed precision, several slots).  The Poisson arrival rate is a
+    fraction of the served capacity.  Reports p50/p99 latency (submit to
     completion) and completed solves/s."""
     import threading
     reqs = serving_requests(pa, args.serve_requests, seed=4242)
     budget = int(args.serve_budget_gb * (1 << 30))
-    # calibration: a burst of the first requests, all at once
     ncal = min(len(reqs), args.serve_calibration)
-    srv = pa.pa_server_create(budget, args.serve_slots)
-    t0 = time.perf_counter()
-    ts = [pa.pa_server_submit(srv, r) for r in reqs[:ncal]]
-    for t in ts:
-        pa.pa_server_wait(srv, t)
-    cap = ncal / (time.perf_counter() - t0)
-    pa.pa_server_destroy(srv)
+
+    def burst(rs, slots):
+        srv = pa.pa_server_create(budget, slots)
+        t0 = time.perf_counter()
+        ts = [pa.pa_server_submit(srv, r) for r in rs]
+        codes = [pa.pa_server_wait(srv, t)[0] for t in ts]
+        dt = time.perf_counter() - t0
+        pa.pa_server_destroy(srv)
+        return len(rs) / dt, sum(1 for c in codes if c == pa.PA_OK)
+
+    fp64_reqs = []
+    for r in reqs[:ncal]:
+        r2 = pa.pa_request.from_buffer_copy(r)
+        r2.mode = pa.PA_SOLVE_FP64
+        fp64_reqs.append(r2)
+    fp64_cap, fp64_ok = burst(fp64_reqs, 1)
+    cap, cal_ok = burst(reqs[:ncal], args.serve_slots)
     rate = args.serve_load * cap
     arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
     srv = pa.pa_server_create(budget, args.serve_slots)
@@ -423,15 +485,21 @@ def run_serving(args, pa, torch):
     pa.pa_server_destroy(srv)
     lat = np.array(lat)
     return {"requests": len(reqs), "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
-            "calibration_capacity_solves_per_s": round(cap, 3), "arrival_rate_per_s": round(rate, 3),
-            "load_fraction": args.serve_load, "solves_per_s": round(len(reqs) / wall, 3),
+            "calibration_requests": ncal,
+            "fp64_alone_solves_per_s": round(fp64_cap, 3),
+            "served_burst_solves_per_s": round(cap, 3),
+            "served_over_fp64_alone": round(cap / fp64_cap, 3),
+            "arrival_rate_per_s": round(rate, 3), "load_fraction": args.serve_load,
+            "solves_per_s": round(len(reqs) / wall, 3),
             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "mean_solve_s": round(float(np.mean(solve_s)), 4), "mean_iterations": round(float(np.mean(iters)), 1),
             "ok": int(sum(1 for c in statuses if c == pa.PA_OK)),
+            "calibration_ok": [fp64_ok, cal_ok],
             "peak_used_gb": round(st.peak_used_bytes / (1 << 30), 2),
             "recipe": "Poisson arrivals; p U{2,4,6,8}; cube n^3 n~U{8..32} or beam 8k x k x k k~U{4..16}; "
-                      "E log-U[0.1,10]; nu U[0.2,0.45]; 3 sine modes/component; x=0 clamped; mixed precision, rtol 1e-10"}
+                      "E log-U[0.1,10]; nu U[0.2,0.45]; 3 sine modes/component; x=0 clamped; FP64 flexible CG with an "
+                      "FP32 V-cycle (mixed precision), rtol 1e-10"}
 
 
 def _oracle_sweep(ps, scale):
@@ -498,11 +566,13 @@ def main(argv=None):
     ap.add_argument("--no-solve", action="store_true", help="skip the GMG-PCG solve measurements")
     ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")
     ap.add_argument("--solve-reps", type=int, default=4)
+    ap.add_argument("--batch-ops", type=int, default=96, help="0 skips the batched-apply measurement")
+    ap.add_argument("--batch-reps", type=int, default=20)
     ap.add_argument("--serve-requests", type=int, default=256, help="0 skips the serving measurement")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
-    ap.add_argument("--serve-calibration", type=int, default=24)
+    ap.add_argument("--serve-calibration", type=int, default=16)
     ap.add_argument("--launch", default="", help="fixed element-kernel shape 'variant,elems_per_cta,threads' "
                                                  "(skips the autotuner)")
     args = ap.parse_args(argv)

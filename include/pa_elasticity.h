@@ -104,6 +104,15 @@ int pa_op_info(const pa_op *op, int64_t *ndofs, int64_t *nelem, int *p, int *pre
  * precision; they must not alias.  y is overwritten. */
 int pa_op_apply(pa_op *op, const void *x, void *y, void *stream);
 
+/* y_k = A_k x_k for k < count in few launches: operators of equal degree and
+ * precision are applied together, one launch of the element kernel over all
+ * their elements (uneven sizes allowed) and one launch of the node
+ * assembly over all their nodes, up to 24 operators per launch.  Each group
+ * uses the launch shape of its first operator.  No counterpart in the
+ * paper (it batches independent applies of Sec. 4.2-4.5).  An operator may
+ * appear only once; x_k and y_k must not alias. */
+int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream);
+
 /* Same computation with host buffers: copies x to the device, applies, and
  * copies y back, all on `stream`; returns after y is on the host.  Host
  * buffers should be pinned for full copy bandwidth. */
@@ -122,8 +131,10 @@ int pa_op_diag(pa_op *op, void *d, void *stream);
 int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void *F, void *stream);
 
 /* Launch shape of the fused element kernel: variant 0 (flattened
- * shared-memory sweeps, one output per thread step) or 1 (register-tiled
- * 1D lines), elements per CTA, threads per CTA (32..512, multiple of 32).
+ * shared-memory sweeps, one output per thread step), 1 (register-tiled 1D
+ * lines) or 2 (register-tiled lines whose X-sweep threads gather and whose
+ * X^T-sweep threads store their own lines), elements per CTA, threads per
+ * CTA (32..512, multiple of 32; variants 1 and 2 at most 256).
  * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB. */
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);

@@ -77,6 +77,7 @@ _sig("pa_op_destroy", [_vp])
 _sig("pa_op_info", [_vp, _i64p, _i64p, _ip, _ip])
 _sig("pa_op_apply", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
+_sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp])
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
@@ -184,6 +185,15 @@ def pa_op_info(op):
 
 def pa_op_apply(op, x, y, stream=None):
     _check(lib.pa_op_apply(op, _tptr(x), _tptr(y), _stream_ptr(stream)), "pa_op_apply")
+
+
+def pa_op_apply_batch(ops, xs, ys, stream=None):
+    """One batched apply of several operators (lists of handles / tensors)."""
+    n = len(ops)
+    ha = (_vp * n)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops])
+    xa = (_vp * n)(*[x.data_ptr() for x in xs])
+    ya = (_vp * n)(*[y.data_ptr() for y in ys])
+    _check(lib.pa_op_apply_batch(ha, xa, ya, n, _stream_ptr(stream)), "pa_op_apply_batch")
 
 
 def pa_op_apply_host(op, x_host, y_host, stream=None):

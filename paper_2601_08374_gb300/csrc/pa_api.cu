@@ -3,8 +3,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "pa_internal.h"
 
@@ -102,6 +105,45 @@ int op_apply_async(pa_op *op, const void *x, void *y, bool accumulate, cudaStrea
     return apply_impl<float>(op, static_cast<const float *>(x), static_cast<float *>(y), accumulate, s, skip);
 }
 
+template <typename T>
+int apply_batch_group(pa_op *const *ops, const void *const *xs, void *const *ys, const std::vector<int> &idx,
+                      cudaStream_t s)
+{
+    for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxBatch) {
+        const size_t m = std::min(idx.size() - c0, (size_t)kMaxBatch);
+        pa_op *first = ops[idx[c0]];
+        const ApplyLaunch cfg = first->launch;
+        BatchArgs<T> b{};
+        AssembleBatch<T> ab{};
+        b.count = ab.count = (int)m;
+        b.cta_start[0] = ab.node_start[0] = 0;
+        for (size_t j = 0; j < m; ++j) {
+            pa_op *op = ops[idx[c0 + j]];
+            ApplyArgs<T> &a = b.args[j];
+            a.x = static_cast<const T *>(xs[idx[c0 + j]]);
+            a.ye = static_cast<T *>(op->d_ye);
+            a.geo = static_cast<const T *>(op->d_geo);
+            a.ess = op->d_ess;
+            a.skip = nullptr;
+            a.g = op->g;
+            b.cta_start[j + 1] = b.cta_start[j] + (op->g.ne + cfg.epb - 1) / cfg.epb;
+            ab.node_start[j + 1] = ab.node_start[j] + op->g.Nn;
+            ab.ye[j] = a.ye;
+            ab.y[j] = static_cast<T *>(ys[idx[c0 + j]]);
+            ab.x[j] = a.x;
+            ab.ess[j] = op->d_ess;
+            ab.g[j] = op->g;
+        }
+        const Tables<T> *tab;
+        if constexpr (sizeof(T) == 8) tab = &first->tab64;
+        else tab = &first->tab32;
+        int rc = launch_apply_batch<T>(b, first->p, *tab, cfg, s);
+        if (rc) return rc;
+        rc = launch_assemble_batch<T>(ab, s);
+        if (rc) return rc;
+    }
+    return PA_OK;
+}
 }  // namespace pa
 
 using namespace pa;
@@ -295,6 +337,37 @@ int pa_op_apply(pa_op *op, const void *x, void *y, void *stream)
     if (!op || !x || !y) return set_error(PA_EINVAL, "pa_op_apply: null argument");
     if (x == y) return set_error(PA_EINVAL, "pa_op_apply: x and y must not alias");
     return op_apply_async(op, x, y, false, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!ops || !xs || !ys))) return set_error(PA_EINVAL, "pa_op_apply_batch: bad arguments");
+    for (int k = 0; k < count; ++k) {
+        if (!ops[k] || !xs[k] || !ys[k]) return set_error(PA_EINVAL, "pa_op_apply_batch: null entry");
+        if (xs[k] == ys[k]) return set_error(PA_EINVAL, "pa_op_apply_batch: x and y must not alias");
+        for (int j = 0; j < k; ++j)
+            if (ops[j] == ops[k]) return set_error(PA_EINVAL, "pa_op_apply_batch: an operator appears twice");
+    }
+    // groups of equal (precision, degree), in first-appearance order
+    std::vector<std::vector<int>> groups;
+    std::vector<std::pair<int, int>> keys;
+    for (int k = 0; k < count; ++k) {
+        std::pair<int, int> key{ops[k]->precision, ops[k]->p};
+        size_t g = 0;
+        while (g < keys.size() && keys[g] != key) ++g;
+        if (g == keys.size()) {
+            keys.push_back(key);
+            groups.emplace_back();
+        }
+        groups[g].push_back(k);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        int rc = keys[g].first == PA_FP64 ? apply_batch_group<double>(ops, xs, ys, groups[g], s)
+                                          : apply_batch_group<float>(ops, xs, ys, groups[g], s);
+        if (rc) return rc;
+    }
+    return PA_OK;
 }
 
 int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream)

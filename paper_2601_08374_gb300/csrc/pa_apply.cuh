@@ -48,7 +48,7 @@ struct FlatLayout {
 };
 
 template <typename T, int D, int Q>
-__global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+__device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
     using L = FlatLayout<T, D, Q>;
     constexpr int D3 = L::D3, Q3 = L::Q3, DQ = D * Q;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
 
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t e0 = (int64_t)blockIdx.x * epb;
+    const int64_t e0 = blk * epb;
     const int ne_blk = (int)((a.g.ne - e0) < epb ? (a.g.ne - e0) : epb);
     if (ne_blk <= 0) return;
 
@@ -325,6 +325,22 @@ __global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tabl
 }
 
 template <typename T, int D, int Q>
+__global__ void __launch_bounds__(512) pa_apply_flat_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+{
+    flat_body<T, D, Q>(a, tab, epb, blockIdx.x);
+}
+
+// Several operators of the same degree and precision in one launch: CTA b
+// belongs to the operator k with cta_start[k] <= b < cta_start[k + 1].
+template <typename T, int D, int Q>
+__global__ void __launch_bounds__(512) pa_apply_flat_batch_kernel(BatchArgs<T> bt, Tables<T> tab, int epb)
+{
+    int k = 0;
+    while (k + 1 < bt.count && (int64_t)blockIdx.x >= bt.cta_start[k + 1]) ++k;
+    flat_body<T, D, Q>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
+}
+
+template <typename T, int D, int Q>
 size_t flat_smem_bytes(int epb)
 {
     return FlatLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
@@ -347,4 +363,22 @@ int launch_flat(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
     return PA_OK;
 }
 
+template <typename T, int D, int Q>
+int launch_flat_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
+{
+    const size_t smem = flat_smem_bytes<T, D, Q>(cfg.epb);
+    auto kern = pa_apply_flat_batch_kernel<T, D, Q>;
+    static bool smem_set = false;
+    if (!smem_set) {
+        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        smem_set = true;
+    }
+    const int64_t nblk = b.cta_start[b.count];
+    if (nblk <= 0) return PA_OK;
+    kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(b, tab, cfg.epb);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
 }  // namespace pa
+

@@ -1,5 +1,6 @@
 // Instantiations of the fused element kernels for double, p = 1..8 (q = p + 2):
-// variant 0 = flattened shared-memory sweeps, variant 1 = register-tiled lines.
+// variant 0 = flattened shared-memory sweeps, variant 1 = register-tiled lines,
+// variant 2 = register-tiled lines with the gather and store fused into the X sweeps.
 #include "pa_apply.cuh"
 #include "pa_apply_line.cuh"
 
@@ -26,7 +27,17 @@ template <int D, int Q>
 int launch_for(const ApplyArgs<double> &a, const Tables<double> &tab, const ApplyLaunch &c, cudaStream_t s)
 {
     if (c.variant == 0) return launch_flat<double, D, Q>(a, tab, c, s);
-    if constexpr (line_ok<D>) return launch_line<double, D, Q>(a, tab, c, s);
+    if constexpr (line_ok<D>) return c.variant == 1 ? launch_line<double, D, Q, false>(a, tab, c, s)
+                                                    : launch_line<double, D, Q, true>(a, tab, c, s);
+    return set_error(PA_EINVAL, "apply variant 1 is not instantiated for this degree and precision");
+}
+
+template <int D, int Q>
+int launch_batch_for(const BatchArgs<double> &b, const Tables<double> &tab, const ApplyLaunch &c, cudaStream_t s)
+{
+    if (c.variant == 0) return launch_flat_batch<double, D, Q>(b, tab, c, s);
+    if constexpr (line_ok<D>) return c.variant == 1 ? launch_line_batch<double, D, Q, false>(b, tab, c, s)
+                                                    : launch_line_batch<double, D, Q, true>(b, tab, c, s);
     return set_error(PA_EINVAL, "apply variant 1 is not instantiated for this degree and precision");
 }
 
@@ -64,6 +75,25 @@ int launch_apply_elements<double>(const ApplyArgs<double> &a, const Tables<doubl
     case 6: return launch_for<7, 8>(a, tab, cfg, s);
     case 7: return launch_for<8, 9>(a, tab, cfg, s);
     case 8: return launch_for<9, 10>(a, tab, cfg, s);
+    default: return set_error(PA_EINVAL, "p must be in 1..8");
+    }
+}
+
+template <>
+int launch_apply_batch<double>(const BatchArgs<double> &b, int p, const Tables<double> &tab, const ApplyLaunch &cfg,
+                              cudaStream_t s)
+{
+    const size_t smem = apply_smem_bytes<double>(p, cfg);
+    if (smem == 0 || smem > 227 * 1024) return set_error(PA_EINVAL, "apply launch config not admissible");
+    switch (p) {
+    case 1: return launch_batch_for<2, 3>(b, tab, cfg, s);
+    case 2: return launch_batch_for<3, 4>(b, tab, cfg, s);
+    case 3: return launch_batch_for<4, 5>(b, tab, cfg, s);
+    case 4: return launch_batch_for<5, 6>(b, tab, cfg, s);
+    case 5: return launch_batch_for<6, 7>(b, tab, cfg, s);
+    case 6: return launch_batch_for<7, 8>(b, tab, cfg, s);
+    case 7: return launch_batch_for<8, 9>(b, tab, cfg, s);
+    case 8: return launch_batch_for<9, 10>(b, tab, cfg, s);
     default: return set_error(PA_EINVAL, "p must be in 1..8");
     }
 }

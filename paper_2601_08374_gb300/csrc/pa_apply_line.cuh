@@ -44,8 +44,11 @@ struct LineLayout {
     __host__ __device__ static size_t table_offset(int epb) { return (((size_t)epb * per_elem * sizeof(T)) + 15) & ~(size_t)15; }
 };
 
-template <typename T, int D, int Q>
-__global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+// FUSE: the gather is done by the X-sweep threads (one contiguous line of D
+// values each) and the X^T-sweep threads write their line of the E-vector
+// directly, instead of separate gather / store phases through shared memory.
+template <typename T, int D, int Q, bool FUSE>
+__device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
     using L = LineLayout<T, D, Q>;
     constexpr int D3 = D * D * D, DP = L::DP, CS = L::CS, BS = L::BS;
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
 
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t e0 = (int64_t)blockIdx.x * epb;
+    const int64_t e0 = blk * epb;
     const int ne_blk = (int)((a.g.ne - e0) < epb ? (a.g.ne - e0) : epb);
     if (ne_blk <= 0) return;
     const int p = D - 1;
@@ -73,6 +76,7 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
     __syncthreads();
 
     // ---- gather x_e into S0 [c][iz][iy][ix]
+    if (!FUSE)
     for (int o = tid; o < ne_blk * 3 * D3; o += nt) {
         int el = o / (3 * D3), r = o - el * 3 * D3;
         int ix = r % D, iy = (r / D) % D, iz = (r / (D * D)) % D, c = r / D3;
@@ -81,16 +85,26 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
         if (a.ess && a.ess[k]) v = T(0);
         bufA[(size_t)el * L::A + ((c * D + iz) * D + iy) * DP + ix] = v;
     }
-    __syncthreads();
+    if (!FUSE) __syncthreads();
 
     // ---- X sweep: line (el, c, iz, iy) -> S1 [c][iz][ch][qx][iy]
     for (int o = tid; o < ne_blk * 3 * D * D; o += nt) {
         int el = o / (3 * D * D), r = o - el * 3 * D * D;
         int iy = r % D, iz = (r / D) % D, c = r / (D * D);
-        const T *in = bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
         T xv[D];
+        if (FUSE) {
+            const int64_t k0 = c * Nn + gbase[el] + Mx * iy + MxMy * iz;
 #pragma unroll
-        for (int i = 0; i < D; ++i) xv[i] = in[i];
+            for (int i = 0; i < D; ++i) {
+                T v = a.x[k0 + i];
+                if (a.ess && a.ess[k0 + i]) v = T(0);
+                xv[i] = v;
+            }
+        } else {
+            const T *in = bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
+#pragma unroll
+            for (int i = 0; i < D; ++i) xv[i] = in[i];
+        }
         T *out = bufB + (size_t)el * L::B + (c * D + iz) * 2 * Q * DP + iy;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -241,7 +255,8 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
             u0[q] = in[q];
             u12[q] = in[Q + q];
         }
-        T *out = bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
+        T *out = FUSE ? a.ye + (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D
+                      : bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
 #pragma unroll
         for (int ix = 0; ix < D; ++ix) {
             T y = T(0);
@@ -253,6 +268,7 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
             out[ix] = y;
         }
     }
+    if (FUSE) return;
     __syncthreads();
 
     // ---- coalesced store of the CTA's contiguous E-vector block
@@ -264,18 +280,34 @@ __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tabl
     }
 }
 
+template <typename T, int D, int Q, bool FUSE>
+__global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+{
+    line_body<T, D, Q, FUSE>(a, tab, epb, blockIdx.x);
+}
+
+// Several operators of the same degree and precision in one launch: CTA b
+// belongs to the operator k with cta_start[k] <= b < cta_start[k + 1].
+template <typename T, int D, int Q, bool FUSE>
+__global__ void __launch_bounds__(256) pa_apply_line_batch_kernel(BatchArgs<T> bt, Tables<T> tab, int epb)
+{
+    int k = 0;
+    while (k + 1 < bt.count && (int64_t)blockIdx.x >= bt.cta_start[k + 1]) ++k;
+    line_body<T, D, Q, FUSE>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
+}
+
 template <typename T, int D, int Q>
 size_t line_smem_bytes(int epb)
 {
     return LineLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
 }
 
-template <typename T, int D, int Q>
+template <typename T, int D, int Q, bool FUSE>
 int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
     size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_line_kernel<T, D, Q>;
+    auto kern = pa_apply_line_kernel<T, D, Q, FUSE>;
     static bool smem_set = false;
     if (!smem_set) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -288,4 +320,22 @@ int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
     return PA_OK;
 }
 
+template <typename T, int D, int Q, bool FUSE>
+int launch_line_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
+{
+    const size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
+    auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE>;
+    static bool smem_set = false;
+    if (!smem_set) {
+        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        smem_set = true;
+    }
+    const int64_t nblk = b.cta_start[b.count];
+    if (nblk <= 0) return PA_OK;
+    kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(b, tab, cfg.epb);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
 }  // namespace pa
+

@@ -45,41 +45,71 @@ unsigned grid_for(int64_t n, int threads)
 // deterministic.  Essential rows take xin (constrained operator) or
 // ess_value.
 template <typename T>
+__device__ __forceinline__ void assemble_node(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
+                                              const uint8_t *__restrict__ ess, T ess_value, int accumulate,
+                                              const Grid &g, int64_t gn)
+{
+    const int p = g.p, D = p + 1, D3 = D * D * D;
+    int gx, gy, gz;
+    node_coords(gn, g, gx, gy, gz);
+    int ex[2], ix[2], ey[2], iy[2], ez[2], iz[2];
+    int nx_ = axis_owners(gx, g.nx, p, ex, ix);
+    int ny_ = axis_owners(gy, g.ny, p, ey, iy);
+    int nz_ = axis_owners(gz, g.nz, p, ez, iz);
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+    for (int c = 0; c < nz_; ++c)
+        for (int b = 0; b < ny_; ++b)
+            for (int a = 0; a < nx_; ++a) {
+                int64_t e = ex[a] + (int64_t)g.nx * (ey[b] + (int64_t)g.ny * ez[c]);
+                int loc = ix[a] + D * (iy[b] + D * iz[c]);
+                const T *base = ye + e * 3 * D3 + loc;
+                acc0 += base[0];
+                acc1 += base[D3];
+                acc2 += base[2 * D3];
+            }
+    T acc[3] = {acc0, acc1, acc2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int64_t k = c * g.Nn + gn;
+        T v = acc[c];
+        if (ess && ess[k]) v = xin ? xin[k] : ess_value;
+        y[k] = accumulate ? y[k] + v : v;
+    }
+}
+
+template <typename T>
 __global__ void assemble_kernel(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
                                 const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g,
                                 const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    const int p = g.p, D = p + 1, D3 = D * D * D;
     for (int64_t gn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gn < g.Nn;
-         gn += (int64_t)gridDim.x * blockDim.x) {
-        int gx, gy, gz;
-        node_coords(gn, g, gx, gy, gz);
-        int ex[2], ix[2], ey[2], iy[2], ez[2], iz[2];
-        int nx_ = axis_owners(gx, g.nx, p, ex, ix);
-        int ny_ = axis_owners(gy, g.ny, p, ey, iy);
-        int nz_ = axis_owners(gz, g.nz, p, ez, iz);
-        T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-        for (int c = 0; c < nz_; ++c)
-            for (int b = 0; b < ny_; ++b)
-                for (int a = 0; a < nx_; ++a) {
-                    int64_t e = ex[a] + (int64_t)g.nx * (ey[b] + (int64_t)g.ny * ez[c]);
-                    int loc = ix[a] + D * (iy[b] + D * iz[c]);
-                    const T *base = ye + e * 3 * D3 + loc;
-                    acc0 += base[0];
-                    acc1 += base[D3];
-                    acc2 += base[2 * D3];
-                }
-        T acc[3] = {acc0, acc1, acc2};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int64_t k = c * g.Nn + gn;
-            T v = acc[c];
-            if (ess && ess[k]) v = xin ? xin[k] : ess_value;
-            y[k] = accumulate ? y[k] + v : v;
-        }
+         gn += (int64_t)gridDim.x * blockDim.x)
+        assemble_node<T>(ye, y, xin, ess, ess_value, accumulate, g, gn);
+}
+
+// The node sums of several operators in one launch (constrained rows take x).
+template <typename T>
+__global__ void assemble_batch_kernel(AssembleBatch<T> b)
+{
+    const int64_t total = b.node_start[b.count];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < b.count && t >= b.node_start[k + 1]) ++k;
+        assemble_node<T>(b.ye[k], b.y[k], b.x[k], b.ess[k], T(0), 0, b.g[k], t - b.node_start[k]);
     }
 }
+
+template <typename T>
+int launch_assemble_batch(const AssembleBatch<T> &b, cudaStream_t s)
+{
+    const int th = 256;
+    assemble_batch_kernel<T><<<grid_for(b.node_start[b.count], th), th, 0, s>>>(b);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_assemble_batch<double>(const AssembleBatch<double> &, cudaStream_t);
+template int launch_assemble_batch<float>(const AssembleBatch<float> &, cudaStream_t);
 
 template <typename T>
 int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,

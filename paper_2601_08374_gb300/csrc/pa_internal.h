@@ -66,9 +66,9 @@ struct Grid {
 };
 
 // --------------------------------------------------------- apply launch --
-constexpr int kMaxVariant = 1;
+constexpr int kMaxVariant = 2;
 struct ApplyLaunch {
-    int variant = 0;  // 0: flattened smem sweeps
+    int variant = 0;  // 0: flattened smem sweeps, 1: register-tiled lines, 2: lines + fused gather/store
     int epb = 1;      // elements per CTA
     int threads = 256;
 };
@@ -86,6 +86,30 @@ struct ApplyArgs {
 template <typename T>
 int launch_apply_elements(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg,
                           cudaStream_t s);
+
+// Operators of one degree and precision applied by one launch.
+constexpr int kMaxBatch = 24;
+template <typename T>
+struct BatchArgs {
+    int count;
+    int64_t cta_start[kMaxBatch + 1];  // prefix sum of CTAs per operator
+    ApplyArgs<T> args[kMaxBatch];
+};
+template <typename T>
+int launch_apply_batch(const BatchArgs<T> &b, int p, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s);
+
+template <typename T>
+struct AssembleBatch {
+    int count;
+    int64_t node_start[kMaxBatch + 1];  // prefix sum of nodes per operator
+    const T *ye[kMaxBatch];
+    T *y[kMaxBatch];
+    const T *x[kMaxBatch];
+    const uint8_t *ess[kMaxBatch];
+    Grid g[kMaxBatch];
+};
+template <typename T>
+int launch_assemble_batch(const AssembleBatch<T> &b, cudaStream_t s);
 template <typename T>
 size_t apply_smem_bytes(int p, const ApplyLaunch &cfg);
 ApplyLaunch default_apply_launch(int p, int precision);

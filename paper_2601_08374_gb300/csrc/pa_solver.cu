@@ -1265,7 +1265,7 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
 {
     Level &L = s->lv.back();
     if (!L.stencil) return PA_OK;
-    const int64_t kMaxDense = 650;
+    const int64_t kMaxDense = 320;
     HLevel H0;
     H0.g = L.op->g;
     H0.n = L.n;

@@ -147,11 +147,13 @@ def test_rhs(pa, p):
 LINE_OK = {0: range(1, 5), 1: range(1, 9)}
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("p", range(1, 9))
-def test_apply_register_tiled_variant(pa, p, prec):
-    """The register-tiled kernel (variant 1) against the oracle, with two
-    CTA shapes (one leaving a ragged last CTA)."""
+def test_apply_register_tiled_variant(pa, p, prec, variant):
+    """The register-tiled kernels (variant 1; variant 2 with the gather and
+    the store fused into the X sweeps) against the oracle, with several CTA
+    shapes (some leaving a ragged last CTA)."""
     if p not in LINE_OK[prec]:
         pytest.skip("variant 1 not instantiated for this degree in FP64")
     nx, ny, nz = MESH_DIMS[p]
@@ -165,7 +167,7 @@ def test_apply_register_tiled_variant(pa, p, prec):
     ran = 0
     for epb, th in [(1, 128), (7, 256), (3, 256)]:
         try:
-            pa.pa_op_set_launch(op.h, 1, epb, th)
+            pa.pa_op_set_launch(op.h, variant, epb, th)
         except pa.PAError as e:  # shape beyond the shared-memory limit for this degree
             assert e.code == pa.PA_EINVAL
             continue
@@ -185,7 +187,7 @@ def test_autotune_keeps_parity(pa):
     for prec in (0, 1):
         op = pa.Operator(4, 4, 4, m.affine, p, lam, mu, precision=prec)
         cfg = pa.pa_op_autotune(op.h)
-        assert cfg[0] in (0, 1) and cfg[1] >= 1 and cfg[2] % 32 == 0
+        assert cfg[0] in (0, 1, 2) and cfg[1] >= 1 and cfg[2] % 32 == 0
         y = op.apply(torch.tensor(x, dtype=op.dtype, device="cuda")).double().cpu().numpy()
         assert _relerr(y, yo) <= TOL[prec]
         op.close()
@@ -238,3 +240,30 @@ def test_assembled_p1_stencil_against_oracle_matrix(pa):
                 assert V[k, row] == 0.0
     assert np.max(np.abs(S - A)) <= 1e-13 * np.max(np.abs(A))
     op.close()
+
+
+def test_batched_apply_matches_individual_applies(pa):
+    """One batched launch over operators of uneven sizes, degrees and
+    precisions (more than 24 in one group) equals the one-by-one applies."""
+    rng = np.random.default_rng(31)
+    ops, xs, refs = [], [], []
+    specs = [(int(rng.choice([2, 4, 8])), int(rng.integers(0, 2)), tuple(int(v) for v in rng.integers(1, 4, 3)))
+             for _ in range(12)]
+    specs += [(2, 0, (2, 1, 1))] * 26  # one group larger than a launch
+    for k, (p, prec, dims) in enumerate(specs):
+        m = syn.random_affine_cube(dims[0], seed=900 + k, ny=dims[1], nz=dims[2])
+        ess = syn.clamp_mask(m, p) if k % 3 == 0 else None
+        op = pa.Operator(*dims, m.affine, p, 1.0, 0.7, precision=prec, ess_mask=ess)
+        x = torch.tensor(syn.uniform_vector(op.ndofs, seed=k), dtype=op.dtype, device="cuda")
+        ops.append(op)
+        xs.append(x)
+        refs.append(op.apply(x).clone())
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    pa.pa_op_apply_batch([o.h for o in ops], xs, ys)
+    torch.cuda.synchronize()
+    for y, r in zip(ys, refs):
+        assert torch.equal(y, r)
+    with pytest.raises(pa.PAError):
+        pa.pa_op_apply_batch([ops[0].h, ops[0].h], [xs[0], xs[0]], [ys[0], ys[1]])
+    for o in ops:
+        o.close()
