@@ -65,18 +65,32 @@ def workload(p: int, scale: float = 1.0):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the element kernels' source and of the default launch table
+    (the shapes the sweep runs), so stored ncu traffic goes stale with them."""
     h = hashlib.sha256()
-    for f in ("pa_apply.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
-        with open(os.path.join(ROOT, "paper_2601_08374_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2601_08374_gb300", "csrc")
+    for f in ("pa_apply.cuh", "pa_apply_line.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "pa_api.cu"), "rb") as fh:
+        api = fh.read()
+    i = api.index(b"ApplyLaunch default_apply_launch(")
+    h.update(api[i:api.index(b"\n}\n", i)])
     return h.hexdigest()[:16]
 
 
 # ncu DRAM bytes (read + write) per launch of the element kernel, keyed by
-# (precision, p), from the capture summarised under profiles/, valid only
-# for the kernel source with this hash.
-TRAFFIC_HASH = None
-TRAFFIC_BYTES: dict = {}
+# (precision, p): the median over the launches of the sweep's launch list
+# (profiles/pa_apply_sweep_launches.md), valid only for the kernel source
+# and launch table with this hash.  The E-vector writes mostly stay in L2
+# and reach DRAM during the assembly kernel, so for p >= 4 the figure is
+# essentially the reads of x and of the geometry records.
+TRAFFIC_HASH = "1dea2309d720e077"
+ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>"}
+TRAFFIC_BYTES: dict = {
+    ("f64", 1): 249046528, ("f64", 2): 60151168, ("f64", 4): 26915712, ("f64", 6): 22379264, ("f64", 8): 22179328,
+    ("f32", 1): 96714752, ("f32", 2): 18397056, ("f32", 4): 13158144, ("f32", 6): 11214848, ("f32", 8): 11122688,
+}
 
 
 class ClockSampler:
@@ -282,7 +296,7 @@ def run_ours(args):
         "per_p": per_case,
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "pa_apply_flat_kernel",
+                     "kernel": " + ".join(ELEMENT_KERNEL_NAMES[v] for v in sorted({c["launch"][0] for c in cases})),
                      "peak_source": (f"derived: {SM_COUNT} SMs x {FLOP_PER_CLK_SM[dtype_name]:.0f} {dtype_name} flop/clk/SM "
                                      f"x {SM_MAX_MHZ:.0f} MHz")},
         "e2e": {"value": round(ws * total_dofs * e2e_steps / e2e_s / 1e9, 4), "unit": "GDoF/s",

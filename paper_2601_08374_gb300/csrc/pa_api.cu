@@ -50,20 +50,23 @@ static void inverse3(const double *J, double det, double *Ji)
     Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
 }
 
-// Sweep tuning table: (elements per CTA, threads) per degree and precision,
-// picked so that a CTA's shared memory stays near or below half an SM.
+// Launch table per degree and precision: the shapes the autotuner picks for
+// the ~3M-dof operator sweep on GB300 (variant, elements per CTA, threads).
 ApplyLaunch default_apply_launch(int p, int precision)
 {
-    static const int epb64[kMaxP + 1] = {0, 16, 8, 6, 3, 2, 1, 1, 1};
-    static const int thr64[kMaxP + 1] = {0, 256, 256, 256, 256, 256, 256, 256, 512};
-    static const int epb32[kMaxP + 1] = {0, 32, 16, 12, 6, 4, 2, 2, 1};
-    static const int thr32[kMaxP + 1] = {0, 256, 256, 256, 256, 256, 256, 256, 512};
+    static const int v64[kMaxP + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    static const int epb64[kMaxP + 1] = {0, 32, 6, 6, 4, 2, 1, 1, 1};
+    static const int thr64[kMaxP + 1] = {0, 384, 128, 256, 256, 256, 128, 256, 512};
+    static const int v32[kMaxP + 1] = {0, 2, 2, 2, 2, 2, 2, 2, 2};
+    static const int epb32[kMaxP + 1] = {0, 24, 8, 4, 3, 2, 2, 2, 2};
+    static const int thr32[kMaxP + 1] = {0, 128, 128, 128, 128, 128, 128, 128, 128};
     ApplyLaunch c;
-    c.variant = 0;
     if (precision == PA_FP64) {
+        c.variant = v64[p];
         c.epb = epb64[p];
         c.threads = thr64[p];
     } else {
+        c.variant = v32[p];
         c.epb = epb32[p];
         c.threads = thr32[p];
     }
