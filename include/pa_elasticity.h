@@ -269,6 +269,23 @@ int pa_solver_set_option(pa_solver *s, int option, double value);
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream);
 
+/* Solve count independent systems A_k x_k = b_k together (flexible-CG modes
+ * PA_SOLVE_FP64 and PA_SOLVE_MIXED_FCG only; all solvers with the same number
+ * of levels, mode and Chebyshev order; each solver at most once).  The
+ * solves advance in lockstep, one CG step per tick, and at every operator
+ * apply of the step (Sec. 4.2-4.5 on each level of the V-cycle, Sec. 3) the
+ * applies of all unfinished solves form one batched launch per (precision,
+ * degree) instead of one launch each; a solve leaves the batch when it
+ * converges or reaches maxit.  Every x_k, iteration count and residual is
+ * bitwise that of pa_gmg_pcg_solve on the same solver.  b_k, x_k: device
+ * double L-vectors (x_k in = initial guess, out = solution); infos: count
+ * entries or NULL.  Waits for `stream`, returns when every x_k is written:
+ * PA_OK when every solve converged, else the first failing solve's status
+ * (each info has its own), PA_EINVAL for bad arguments, a mixed hierarchy or
+ * the iterative-refinement mode. */
+int pa_gmg_pcg_solve_batch(pa_solver *const *solvers, const double *const *b, double *const *x, int count,
+                           double rtol, int maxit, pa_solve_info *infos, void *stream);
+
 /* -------------------------------------------------------------- server -- */
 
 /* Serving of many solves with continuous admission (no counterpart in the

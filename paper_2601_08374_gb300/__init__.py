@@ -103,6 +103,8 @@ if hasattr(lib, "pa_solver_create"):
     _sig("pa_solver_destroy", [_vp])
     _sig("pa_solver_set_option", [_vp, ctypes.c_int, ctypes.c_double])
     _sig("pa_gmg_pcg_solve", [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(pa_solve_info), _vp])
+    _sig("pa_gmg_pcg_solve_batch", [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(pa_solve_info), _vp])
 
 
 class PAError(RuntimeError):
@@ -289,6 +291,20 @@ def pa_gmg_pcg_solve(solver, b, x, rtol=1e-10, maxit=500, stream=None):
     if code not in (PA_OK, PA_ENOTCONV, PA_EBREAKDOWN):
         raise PAError(code, "pa_gmg_pcg_solve")
     return code, info
+
+
+def pa_gmg_pcg_solve_batch(solvers, bs, xs, rtol=1e-10, maxit=500, stream=None):
+    """Lockstep solve of several systems with batched operator applies;
+    returns (first status, [info per solve])."""
+    n = len(solvers)
+    ha = (_vp * n)(*[s.value if isinstance(s, ctypes.c_void_p) else s for s in solvers])
+    ba = (_vp * n)(*[b.data_ptr() for b in bs])
+    xa = (_vp * n)(*[x.data_ptr() for x in xs])
+    infos = (pa_solve_info * max(n, 1))()
+    code = lib.pa_gmg_pcg_solve_batch(ha, ba, xa, n, rtol, maxit, infos, _stream_ptr(stream))
+    if code not in (PA_OK, PA_ENOTCONV, PA_EBREAKDOWN):
+        raise PAError(code, "pa_gmg_pcg_solve_batch")
+    return code, [infos[k] for k in range(n)]
 
 
 def make_request(nx, ny, nz, box, p, E, nu, f0=(0.0, 0.0, 0.0), modes=None, clamp_x0=True, rtol=1e-10, maxit=1000,

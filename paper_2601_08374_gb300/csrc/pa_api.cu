@@ -351,6 +351,15 @@ int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys,
         for (int j = 0; j < k; ++j)
             if (ops[j] == ops[k]) return set_error(PA_EINVAL, "pa_op_apply_batch: an operator appears twice");
     }
+    return apply_batch_async(ops, xs, ys, count, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace pa {
+
+int apply_batch_async(pa_op *const *ops, const void *const *xs, void *const *ys, int count, cudaStream_t s)
+{
     // groups of equal (precision, degree), in first-appearance order
     std::vector<std::vector<int>> groups;
     std::vector<std::pair<int, int>> keys;
@@ -364,7 +373,6 @@ int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys,
         }
         groups[g].push_back(k);
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (size_t g = 0; g < groups.size(); ++g) {
         int rc = keys[g].first == PA_FP64 ? apply_batch_group<double>(ops, xs, ys, groups[g], s)
                                           : apply_batch_group<float>(ops, xs, ys, groups[g], s);
@@ -372,6 +380,10 @@ int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys,
     }
     return PA_OK;
 }
+
+}  // namespace pa
+
+extern "C" {
 
 int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream)
 {

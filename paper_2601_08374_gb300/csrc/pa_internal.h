@@ -133,6 +133,31 @@ int launch_rhs_elements(const double *affine, T *ye, const Basis1D &b, const Gri
 // loops); y = A x, or y += A x when accumulate.
 int op_apply_async(pa_op *op, const void *x, void *y, bool accumulate, cudaStream_t s, const int *skip);
 
+// y_k = A_k x_k for count operators (not validated): one element launch and
+// one assembly launch per (precision, degree) and per kMaxBatch operators.
+int apply_batch_async(pa_op *const *ops, const void *const *xs, void *const *ys, int count, cudaStream_t s);
+
+// --------------------------------------------------- lockstep solving --
+// Several GMG-PCG solvers (flexible-CG modes) advanced one CG step per tick,
+// with the operator applies of all members batched per phase of the step
+// (pa_solver.cu).  Members join (lockstep_add: the solve's start, graphs of
+// its step) and leave (when converged or capped: true residual, x written)
+// between ticks.  Solvers with equal lockstep_key share a lockstep.
+struct Lockstep;
+struct LockstepDone {
+    void *tag = nullptr;
+    int status = 0;
+    std::string error;
+    pa_solve_info info{};
+};
+int lockstep_create(Lockstep **out);
+void lockstep_destroy(Lockstep *L);
+int lockstep_add(Lockstep *L, pa_solver *s, const double *b, double *x, double rtol, int maxit, void *tag);
+int lockstep_tick(Lockstep *L);
+int lockstep_active(const Lockstep *L);
+void lockstep_take_done(Lockstep *L, std::vector<LockstepDone> &out);
+int lockstep_key(const pa_solver *s);
+
 }  // namespace pa
 
 // ------------------------------------------------------------- handles --

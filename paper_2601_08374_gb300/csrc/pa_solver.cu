@@ -1099,6 +1099,16 @@ struct pa_solver {
     // inner (mixed) vectors
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *x32 = nullptr, *b32 = nullptr;
     std::vector<void *> allocs;
+    // Phase filter of lockstep capture (several solvers stepped together):
+    // the step functions run with only the kernels of phase ph_target
+    // emitted; phases are separated by the operator applies, and the apply
+    // that ends phase ph_target is recorded (ph_op, ph_x, ph_y) instead of
+    // launched.  Off: every kernel and apply is launched as usual.
+    bool ph_on = false;
+    int ph_target = 0, ph_counter = 0;
+    pa_op *ph_op = nullptr;
+    const void *ph_x = nullptr;
+    void *ph_y = nullptr;
 };
 
 namespace pa {
@@ -1517,6 +1527,31 @@ template <> float *LV<float>::xa(Level &L) { return L.xa32; }
 template <> float *LV<float>::xb(Level &L) { return L.xb32; }
 template <> pa_op *LV<float>::op(Level &L) { return L.op32; }
 
+// True when the kernels of the code being run are to be launched (always,
+// unless a lockstep capture filters one phase).
+inline bool emit(const pa_solver *s) { return !s->ph_on || s->ph_counter == s->ph_target; }
+
+// An operator apply of a step function: launched, or under the phase filter
+// recorded when it ends the filtered phase; either way the next phase starts.
+int step_apply(pa_solver *s, pa_op *op, const void *x, void *y, cudaStream_t st)
+{
+    if (!s->ph_on) return op_apply_async(op, x, y, false, st, nullptr);
+    if (s->ph_counter == s->ph_target) {
+        s->ph_op = op;
+        s->ph_x = x;
+        s->ph_y = y;
+    }
+    ++s->ph_counter;
+    return PA_OK;
+}
+
+// A phase boundary without an apply (keeps the phases of solvers whose step
+// skips an apply aligned with the others').
+void step_gap(pa_solver *s)
+{
+    if (s->ph_on) ++s->ph_counter;
+}
+
 // Chebyshev smoothing of A e = r on level L (cheb_order steps); from a zero
 // guess the first step needs no operator apply.
 template <typename T>
@@ -1530,7 +1565,7 @@ int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
     for (int k = 0; k < s->cheb_order; ++k) {
         const T *tt = nullptr;
         if (!(k == 0 && from_zero)) {
-            int rc = op_apply_async(op, e, t, false, st, nullptr);
+            int rc = step_apply(s, op, e, t, st);
             if (rc) return rc;
             tt = t;
         }
@@ -1544,7 +1579,8 @@ int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
             cr = 2.0 * rho / L.delta;
             rho_prev = rho;
         }
-        k_cheb<T><<<blocks_for(n), 256, 0, st>>>(e, dv, r, tt, dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
+        if (emit(s))
+            k_cheb<T><<<blocks_for(n), 256, 0, st>>>(e, dv, r, tt, dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
     }
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
@@ -1672,10 +1708,11 @@ int vcycle_down(pa_solver *s, cudaStream_t st)
         Level &L = s->lv[l], &C = s->lv[l + 1];
         int rc = smooth<T>(s, L, true, st);
         if (rc) return rc;
-        rc = op_apply_async(LV<T>::op(L), LV<T>::e(L), LV<T>::t(L), false, st, nullptr);
+        rc = step_apply(s, LV<T>::op(L), LV<T>::e(L), LV<T>::t(L), st);
         if (rc) return rc;
-        restrict_to<T>(L, C, LV<T>::r(L), LV<T>::t(L), LV<T>::r(C), st);
+        if (emit(s)) restrict_to<T>(L, C, LV<T>::r(L), LV<T>::t(L), LV<T>::r(C), st);
     }
+    if (!emit(s)) return PA_OK;
     Level &Lc = s->lv.back();
     if constexpr (sizeof(T) == 4) k_scale_copy<float, double><<<blocks_for(Lc.n), 256, 0, st>>>(Lc.r, Lc.r32, 1.0, Lc.n);
     if (!use_coop(s)) {
@@ -1693,10 +1730,10 @@ int vcycle_up(pa_solver *s, cudaStream_t st)
 {
     const int nl = (int)s->lv.size();
     Level &Lc = s->lv.back();
-    k_scale_copy<double, T><<<blocks_for(Lc.n), 256, 0, st>>>(LV<T>::e(Lc), Lc.cx, 1.0, Lc.n);
+    if (emit(s)) k_scale_copy<double, T><<<blocks_for(Lc.n), 256, 0, st>>>(LV<T>::e(Lc), Lc.cx, 1.0, Lc.n);
     for (int l = nl - 2; l >= 0; --l) {
         Level &L = s->lv[l], &C = s->lv[l + 1];
-        prolong_add<T>(L, C, LV<T>::e(C), LV<T>::e(L), st);
+        if (emit(s)) prolong_add<T>(L, C, LV<T>::e(C), LV<T>::e(L), st);
         int rc = smooth<T>(s, L, false, st);
         if (rc) return rc;
     }
@@ -1724,14 +1761,17 @@ int fcg_init_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
     if (v.x_zero) {
-        PA_CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(T) * n, st));
-        k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, 1.0, n);
+        if (emit(s)) {
+            PA_CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(T) * n, st));
+            k_scale_copy<T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, 1.0, n);
+        }
+        step_gap(s);  // in the place of the apply below
     } else {
-        int rc = op_apply_async(LV<T>::op(L0), v.x, v.q, false, st, nullptr);
+        int rc = step_apply(s, LV<T>::op(L0), v.x, v.q, st);
         if (rc) return rc;
-        k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, v.q, n);
+        if (emit(s)) k_sub<T, T, T><<<blocks_for(n), 256, 0, st>>>(v.r, v.b, v.q, n);
     }
-    k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
+    if (emit(s)) k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
     return vcycle_down<TP>(s, st);
 }
 
@@ -1750,6 +1790,7 @@ int fcg_init_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
     const int64_t n = L0.n;
     int rc = vcycle_up<TP>(s, st);
     if (rc) return rc;
+    if (!emit(s)) return PA_OK;
     k_scale_copy<TP, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<TP>::e(L0), 1.0, n);
     k_fcg_start<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.z, v.r, n, 0);
     PA_CUDA_TRY(cudaGetLastError());
@@ -1761,11 +1802,13 @@ int fcg_iter_a(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
 {
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
-    int rc = op_apply_async(LV<T>::op(L0), v.p, v.q, false, st, nullptr);
+    int rc = step_apply(s, LV<T>::op(L0), v.p, v.q, st);
     if (rc) return rc;
-    k_fcg_pq<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.q, n, 0);
-    k_fcg_update<T, T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.x, v.r, v.p, v.q, n, 0);
-    k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
+    if (emit(s)) {
+        k_fcg_pq<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.p, v.q, n, 0);
+        k_fcg_update<T, T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.x, v.r, v.p, v.q, n, 0);
+        k_scale_copy<T, TP><<<blocks_for(n), 256, 0, st>>>(LV<TP>::r(L0), v.r, 1.0, n);
+    }
     return vcycle_down<TP>(s, st);
 }
 
@@ -1776,6 +1819,7 @@ int fcg_iter_b(pa_solver *s, const FcgVecs<T> &v, cudaStream_t st)
     const int64_t n = L0.n;
     int rc = vcycle_up<TP>(s, st);
     if (rc) return rc;
+    if (!emit(s)) return PA_OK;
     k_scale_copy<TP, T><<<blocks_for(n), 256, 0, st>>>(v.z, LV<TP>::e(L0), 1.0, n);
     k_fcg_beta<T><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, v.z, v.r, v.q, n, 0);
     k_fcg_p<T><<<blocks_for(n), 256, 0, st>>>(s->dev, v.p, v.z, n, 0);
@@ -1930,6 +1974,399 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
     return PA_OK;
 }
 
+// Start of a solve: flags cleared, (b, b) computed; b = 0 gives x = 0 at
+// once (*trivial), non-finite b is rejected; b and x copied into the
+// solver's own vectors.  Blocks until (b, b) is on the host.
+int solve_begin(pa_solver *s, const double *b, double *x, double *bb_out, pa_solve_info *inf, bool *trivial)
+{
+    cudaStream_t st = s->stream;
+    const int64_t n = s->lv[0].n;
+    *inf = pa_solve_info{};
+    *trivial = false;
+    for (size_t l = 0; l < s->lv.size() && l < 8; ++l) inf->lambda_max[l] = s->lv[l].lmax;
+    PA_CUDA_TRY(cudaMemsetAsync(s->dev.flag, 0, sizeof(int) * NFLAG, st));
+    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
+    const double bb = read_scalar(s, S_BB, st);
+    inf->b_norm = std::sqrt(bb);
+    *bb_out = bb;
+    if (bb == 0.0) {
+        PA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        inf->rel_residual = 0.0;
+        *trivial = true;
+        return PA_OK;
+    }
+    if (!std::isfinite(bb)) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: b has non-finite entries");
+    PA_CUDA_TRY(cudaMemcpyAsync(s->xin, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    PA_CUDA_TRY(cudaMemcpyAsync(s->bin, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    return PA_OK;
+}
+
+// End of a solve: the true FP64 residual of the solver's iterate, which is
+// copied to x.  rc_loop is the iteration loop's return code (breakdown is
+// reported as a status with the residual; other errors are returned as is).
+int solve_finish(pa_solver *s, double *x, int rc_loop, bool converged, double bb, pa_solve_info *inf)
+{
+    cudaStream_t st = s->stream;
+    Level &L0 = s->lv[0];
+    const int64_t n = L0.n;
+    int status = PA_OK;
+    if (rc_loop == PA_EBREAKDOWN) status = PA_EBREAKDOWN;
+    else if (rc_loop) return rc_loop;
+    int rc = op_apply_async(L0.op, s->xin, s->t, false, st, nullptr);
+    if (rc) return rc;
+    k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, s->bin, s->t, n);
+    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
+    PA_CUDA_TRY(cudaMemcpyAsync(x, s->xin, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    const double rr = read_scalar(s, S_RR, st);
+    PA_CUDA_TRY(cudaGetLastError());
+    inf->rel_residual = std::sqrt(rr / bb);
+    if (status == PA_OK && !converged) status = PA_ENOTCONV;
+    inf->status = status;
+    if (status == PA_ENOTCONV) set_error(PA_ENOTCONV, "pa_gmg_pcg_solve: iteration cap reached");
+    return status;
+}
+
+FcgVecs<double> outer_vecs(pa_solver *s) { return FcgVecs<double>{s->xin, s->bin, s->r, s->z, s->p, s->q, false}; }
+
+// Executable graph of the coarse solve alone: a WHILE node whose body is one
+// coarse iteration; the condition is set on the device after every
+// iteration (stop flag or iteration cap).
+int build_coarse_graph(pa_solver *s, cudaStream_t st, cudaGraphExec_t *out)
+{
+    cudaGraph_t G = nullptr, gBody = nullptr;
+    int rc = PA_OK;
+    do {
+        cudaError_t e = cudaGraphCreate(&G, 0);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphCreate"); break; }
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphConditionalHandleCreate"); break; }
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t nC, nBody;
+        e = cudaGraphAddNode(&nC, G, nullptr, nullptr, 0, &cp);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddNode(conditional)"); break; }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        Level &Lc = s->lv.back();
+        const int maxit = s->coarse_maxit;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaStreamBeginCapture"); break; }
+        int r = coarse_iter(s, Lc, st);
+        if (!r) k_cg_cond<<<1, 32, 0, st>>>(s->dev, maxit, h);
+        e = cudaStreamEndCapture(st, &gBody);
+        if (r) { rc = r; break; }
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaStreamEndCapture"); break; }
+        e = cudaGraphAddChildGraphNode(&nBody, body, nullptr, 0, gBody);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphAddChildGraphNode(body)"); break; }
+        e = cudaGraphInstantiate(out, G, 0);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaGraphInstantiate"); break; }
+    } while (false);
+    if (gBody) cudaGraphDestroy(gBody);
+    if (G) cudaGraphDestroy(G);
+    return rc;
+}
+
+// ------------------------------------------------------------ lockstep
+// Several solvers advanced together, one flexible-CG step per tick.  Each
+// solver's step is captured once per phase (the kernels between two
+// operator applies) into small executable graphs on its own stream; a tick
+// runs phase j of every member, then the applies that end phase j -- one per
+// member, all on the same level -- as one batched launch per (precision,
+// degree) on the lockstep's stream, then phase j + 1.  The coarse solve of
+// each member is its own device-controlled loop between the two halves of
+// the step.  Members join and leave between ticks.  The kernels, their
+// order per member and the applies' arithmetic are those of the solver's
+// own step, so a member's iterates are bitwise those of its solo solve.
+struct ApplyRec {
+    pa_op *op = nullptr;
+    const void *x = nullptr;
+    void *y = nullptr;
+};
+
+struct Segment {
+    std::vector<cudaGraphExec_t> g;  // per phase (null: nothing to launch)
+    std::vector<ApplyRec> ap;        // apply ending each phase but the last (op null: none)
+};
+
+struct LockMember {
+    pa_solver *s = nullptr;
+    double *x_out = nullptr;
+    void *tag = nullptr;
+    double bb = 0.0, tol2 = 0.0;
+    int maxit = 0, it = 0;
+    bool started = false;
+    cudaEvent_t ev = nullptr;
+    Segment a[2], b[2];  // [0] first step, [1] iteration step
+    cudaGraphExec_t coarse = nullptr;
+    pa_solve_info info{};
+};
+
+void free_segment(Segment &sg)
+{
+    for (cudaGraphExec_t g : sg.g)
+        if (g) cudaGraphExecDestroy(g);
+    sg.g.clear();
+    sg.ap.clear();
+}
+
+void free_member(LockMember &m)
+{
+    for (int k = 0; k < 2; ++k) {
+        free_segment(m.a[k]);
+        free_segment(m.b[k]);
+    }
+    if (m.coarse) cudaGraphExecDestroy(m.coarse);
+    if (m.ev) cudaEventDestroy(m.ev);
+    m.coarse = nullptr;
+    m.ev = nullptr;
+}
+
+// Captures every phase of a step segment of solver s into sg.
+template <typename F>
+int capture_segment(pa_solver *s, F fn, Segment &sg)
+{
+    cudaStream_t st = s->stream;
+    s->ph_on = true;
+    s->ph_target = -1;  // count the phases: nothing is emitted
+    s->ph_counter = 0;
+    int rc = fn();
+    const int napply = s->ph_counter;
+    for (int j = 0; !rc && j <= napply; ++j) {
+        s->ph_target = j;
+        s->ph_counter = 0;
+        s->ph_op = nullptr;
+        s->ph_x = nullptr;
+        s->ph_y = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "lockstep: cudaStreamBeginCapture");
+            break;
+        }
+        int r = fn();
+        e = cudaStreamEndCapture(st, &g);
+        if (!r && e != cudaSuccess) r = cuda_error(e, "lockstep: cudaStreamEndCapture");
+        if (!r && s->ph_counter != napply) r = set_error(PA_EINVAL, "lockstep: step phases differ between captures");
+        cudaGraphExec_t ex = nullptr;
+        if (!r) {
+            size_t nn = 0;
+            e = cudaGraphGetNodes(g, nullptr, &nn);
+            if (e != cudaSuccess) r = cuda_error(e, "lockstep: cudaGraphGetNodes");
+            else if (nn > 0 && (e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess)
+                r = cuda_error(e, "lockstep: cudaGraphInstantiate");
+        }
+        if (g) cudaGraphDestroy(g);
+        if (r) {
+            rc = r;
+            break;
+        }
+        sg.g.push_back(ex);
+        if (j < napply) sg.ap.push_back(ApplyRec{s->ph_op, s->ph_x, s->ph_y});
+    }
+    s->ph_on = false;
+    return rc;
+}
+
+template <typename TP>
+int capture_member(LockMember &m)
+{
+    pa_solver *s = m.s;
+    FcgVecs<double> v = outer_vecs(s);
+    const cudaStream_t st = s->stream;
+    int rc = capture_segment(s, [&]() { return fcg_init_a<double, TP>(s, v, st); }, m.a[0]);
+    if (!rc) rc = capture_segment(s, [&]() { return fcg_iter_a<double, TP>(s, v, st); }, m.a[1]);
+    if (!rc) rc = capture_segment(s, [&]() { return fcg_init_b<double, TP>(s, v, st); }, m.b[0]);
+    if (!rc) rc = capture_segment(s, [&]() { return fcg_iter_b<double, TP>(s, v, st); }, m.b[1]);
+    if (!rc && (m.a[0].g.size() != m.a[1].g.size() || m.b[0].g.size() != m.b[1].g.size()))
+        rc = set_error(PA_EINVAL, "lockstep: first and later steps have different phases");
+    if (!rc) rc = build_coarse_graph(s, st, &m.coarse);
+    return rc;
+}
+
+}  // namespace
+
+struct Lockstep {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<LockMember> m;
+    std::vector<LockstepDone> done;
+    size_t na = 0, nb = 0;  // phases per segment (equal for all members)
+};
+
+namespace {
+
+// Finishes member m (true residual, solution copy) into L.done.
+void retire(Lockstep &L, LockMember &m, int rc_loop, bool converged)
+{
+    LockstepDone d;
+    d.tag = m.tag;
+    m.info.iterations = m.it;
+    int st = solve_finish(m.s, m.x_out, rc_loop, converged, m.bb, &m.info);
+    d.status = st;
+    if (st != PA_OK) d.error = pa_last_error();
+    d.info = m.info;
+    L.done.push_back(d);
+    free_member(m);
+}
+
+// Runs phases 0 .. n-1 of one segment kind for all members, batching the
+// applies between phases; the last phase is launched but not joined.
+int run_segment(Lockstep &L, bool second_half)
+{
+    const size_t nph = second_half ? L.nb : L.na;
+    std::vector<pa_op *> ops;
+    std::vector<const void *> xs;
+    std::vector<void *> ys;
+    for (size_t j = 0; j < nph; ++j) {
+        for (LockMember &m : L.m) {
+            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
+            if (sg.g[j]) PA_CUDA_TRY(cudaGraphLaunch(sg.g[j], m.s->stream));
+        }
+        if (j + 1 == nph) break;
+        ops.clear();
+        xs.clear();
+        ys.clear();
+        for (LockMember &m : L.m) {
+            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
+            const ApplyRec &ap = sg.ap[j];
+            if (!ap.op) continue;
+            PA_CUDA_TRY(cudaEventRecord(m.ev, m.s->stream));
+            PA_CUDA_TRY(cudaStreamWaitEvent(L.st, m.ev, 0));
+            ops.push_back(ap.op);
+            xs.push_back(ap.x);
+            ys.push_back(ap.y);
+        }
+        if (ops.empty()) continue;
+        int rc = apply_batch_async(ops.data(), xs.data(), ys.data(), (int)ops.size(), L.st);
+        if (rc) return rc;
+        PA_CUDA_TRY(cudaEventRecord(L.ev, L.st));
+        for (LockMember &m : L.m) {
+            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
+            if (sg.ap[j].op) PA_CUDA_TRY(cudaStreamWaitEvent(m.s->stream, L.ev, 0));
+        }
+    }
+    return PA_OK;
+}
+
+}  // namespace
+
+int lockstep_create(Lockstep **out)
+{
+    *out = nullptr;
+    Lockstep *L = new (std::nothrow) Lockstep;
+    if (!L) return set_error(PA_ENOMEM, "lockstep: host allocation");
+    cudaError_t e = cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lockstep_destroy(L);
+        return cuda_error(e, "lockstep: stream or event creation");
+    }
+    *out = L;
+    return PA_OK;
+}
+
+void lockstep_destroy(Lockstep *L)
+{
+    if (!L) return;
+    for (LockMember &m : L->m) free_member(m);
+    if (L->ev) cudaEventDestroy(L->ev);
+    if (L->st) cudaStreamDestroy(L->st);
+    delete L;
+}
+
+int lockstep_active(const Lockstep *L) { return (int)L->m.size(); }
+
+void lockstep_take_done(Lockstep *L, std::vector<LockstepDone> &out)
+{
+    for (LockstepDone &d : L->done) out.push_back(d);
+    L->done.clear();
+}
+
+int lockstep_add(Lockstep *L, pa_solver *s, const double *b, double *x, double rtol, int maxit, void *tag)
+{
+    if (s->mode != PA_SOLVE_FP64 && s->mode != PA_SOLVE_MIXED_FCG)
+        return set_error(PA_EINVAL, "lockstep: only the flexible-CG modes (FP64, MIXED_FCG) step in lockstep");
+    // a grid-wide persistent coarse kernel must not run beside other members
+    s->allow_coop = false;
+    LockMember m;
+    m.s = s;
+    m.x_out = x;
+    m.tag = tag;
+    m.maxit = maxit;
+    m.tol2 = rtol * rtol;
+    bool trivial = false;
+    int rc = solve_begin(s, b, x, &m.bb, &m.info, &trivial);
+    if (rc || trivial) {
+        LockstepDone d;
+        d.tag = tag;
+        d.status = rc;
+        if (rc) d.error = pa_last_error();
+        d.info = m.info;
+        d.info.status = rc;
+        L->done.push_back(d);
+        return PA_OK;
+    }
+    rc = s->mode == PA_SOLVE_FP64 ? capture_member<double>(m) : capture_member<float>(m);
+    if (!rc && cudaEventCreateWithFlags(&m.ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = cuda_error(cudaGetLastError(), "lockstep: cudaEventCreate");
+    if (!rc && !L->m.empty() && (m.a[0].g.size() != L->na || m.b[0].g.size() != L->nb))
+        rc = set_error(PA_EINVAL, "lockstep: solver hierarchy does not match the other members'");
+    if (rc) {
+        free_member(m);
+        return rc;
+    }
+    if (L->m.empty()) {
+        L->na = m.a[0].g.size();
+        L->nb = m.b[0].g.size();
+    }
+    L->m.push_back(m);
+    return PA_OK;
+}
+
+int lockstep_key(const pa_solver *s) { return (int)s->lv.size() * 16 + s->mode * 4 + s->cheb_order; }
+
+int lockstep_tick(Lockstep *L)
+{
+    if (L->m.empty()) return PA_OK;
+    int rc = run_segment(*L, false);
+    if (rc) return rc;
+    for (LockMember &m : L->m) PA_CUDA_TRY(cudaGraphLaunch(m.coarse, m.s->stream));
+    rc = run_segment(*L, true);
+    if (rc) return rc;
+    for (LockMember &m : L->m) PA_CUDA_TRY(cudaStreamSynchronize(m.s->stream));
+    // convergence test of every member, as in the solo loop
+    std::vector<LockMember> keep;
+    for (LockMember &m : L->m) {
+        pa_solver *s = m.s;
+        const double rr = s->h_scal[S_RR];
+        if (m.started) ++m.it;
+        m.started = true;
+        if (s->h_flag[F_CTIMEOUT]) {
+            retire(*L, m, set_error(PA_ETIMEOUT, "solver: coarse-solve grid barrier timed out"), false);
+            continue;
+        }
+        if (s->h_flag[F_BREAK]) {
+            retire(*L, m,
+                   set_error(PA_EBREAKDOWN, m.it == 0 ? "solver: non-finite value in the first preconditioned residual"
+                                                      : "solver: CG breakdown (p^T A p <= 0 or non-finite value)"),
+                   false);
+            continue;
+        }
+        if (rr <= m.tol2 * m.bb || m.it >= m.maxit) {
+            retire(*L, m, PA_OK, rr <= m.tol2 * m.bb);
+            continue;
+        }
+        keep.push_back(m);
+    }
+    L->m.swap(keep);
+    return PA_OK;
+}
+
+namespace {
 }  // namespace
 }  // namespace pa
 
@@ -2222,31 +2659,19 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
     Level &L0 = s->lv[0];
     const int64_t n = L0.n;
     pa_solve_info inf{};
-    for (size_t l = 0; l < s->lv.size() && l < 8; ++l) inf.lambda_max[l] = s->lv[l].lmax;
-    PA_CUDA_TRY(cudaMemsetAsync(s->dev.flag, 0, sizeof(int) * NFLAG, st));
-    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
-    const double bb = read_scalar(s, S_BB, st);
-    inf.b_norm = std::sqrt(bb);
-    int status = PA_OK, rc = PA_OK;
-    const double tol2 = rtol * rtol;
-    if (bb == 0.0) {
-        PA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-        PA_CUDA_TRY(cudaStreamSynchronize(st));
-        inf.rel_residual = 0.0;
+    double bb = 0.0;
+    bool trivial = false;
+    int rc = solve_begin(s, b, x, &bb, &inf, &trivial);
+    if (rc || trivial) {
         if (info) *info = inf;
-        return PA_OK;
-    }
-    if (!std::isfinite(bb)) {
-        if (info) *info = inf;
-        return set_error(PA_EINVAL, "pa_gmg_pcg_solve: b has non-finite entries");
+        return rc;
     }
     double *xs = s->xin, *bs = s->bin;
-    PA_CUDA_TRY(cudaMemcpyAsync(xs, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    PA_CUDA_TRY(cudaMemcpyAsync(bs, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    const double tol2 = rtol * rtol;
     bool converged = false;
     if (s->mode == PA_SOLVE_FP64 || s->mode == PA_SOLVE_MIXED_FCG) {
         int it = 0;
-        FcgVecs<double> v{xs, bs, s->r, s->z, s->p, s->q, false};
+        FcgVecs<double> v = outer_vecs(s);
         if (s->mode == PA_SOLVE_FP64) rc = fcg<double>(s, v, s->g64, tol2, bb, maxit, &it, st);
         else rc = fcg<double, float>(s, v, s->gmx, tol2, bb, maxit, &it, st);
         inf.iterations = it;
@@ -2294,25 +2719,49 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         inf.inner_iterations = total_inner;
         inf.refinements = refine;
     }
-    if (rc == PA_EBREAKDOWN) status = PA_EBREAKDOWN;
-    else if (rc) {
-        if (info) *info = inf;
-        return rc;
-    }
-    // true residual in FP64, and the solution back to the caller
-    int rc2 = op_apply_async(L0.op, xs, s->t, false, st, nullptr);
-    if (rc2) return rc2;
-    k_sub<double, double, double><<<blocks_for(n), 256, 0, st>>>(s->r, bs, s->t, n);
-    k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, s->r, n, S_RR);
-    PA_CUDA_TRY(cudaMemcpyAsync(x, xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    double rr = read_scalar(s, S_RR, st);
-    PA_CUDA_TRY(cudaGetLastError());
-    inf.rel_residual = std::sqrt(rr / bb);
-    if (status == PA_OK && !converged) status = PA_ENOTCONV;
-    inf.status = status;
+    const int status = solve_finish(s, x, rc, converged, bb, &inf);
     if (info) *info = inf;
-    if (status == PA_ENOTCONV) set_error(PA_ENOTCONV, "pa_gmg_pcg_solve: iteration cap reached");
     return status;
+}
+
+int pa_gmg_pcg_solve_batch(pa_solver *const *solvers, const double *const *b, double *const *x, int count,
+                           double rtol, int maxit, pa_solve_info *infos, void *stream)
+{
+    if (count < 0 || (count > 0 && (!solvers || !b || !x)))
+        return set_error(PA_EINVAL, "pa_gmg_pcg_solve_batch: bad arguments");
+    if (!(rtol > 0.0) || maxit < 0) return set_error(PA_EINVAL, "pa_gmg_pcg_solve_batch: bad tolerance or cap");
+    for (int k = 0; k < count; ++k) {
+        if (!solvers[k] || !b[k] || !x[k]) return set_error(PA_EINVAL, "pa_gmg_pcg_solve_batch: null entry");
+        for (int j = 0; j < k; ++j)
+            if (solvers[j] == solvers[k]) return set_error(PA_EINVAL, "pa_gmg_pcg_solve_batch: a solver appears twice");
+    }
+    PA_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    Lockstep *L = nullptr;
+    int rc = lockstep_create(&L);
+    if (rc) return rc;
+    std::vector<int> status(count, PA_OK);
+    std::vector<std::string> errors(count);
+    for (int k = 0; k < count && !rc; ++k) rc = lockstep_add(L, solvers[k], b[k], x[k], rtol, maxit, (void *)(intptr_t)k);
+    while (!rc && lockstep_active(L) > 0) rc = lockstep_tick(L);
+    std::vector<LockstepDone> done;
+    lockstep_take_done(L, done);
+    lockstep_destroy(L);
+    if (rc) return rc;
+    int first = PA_OK;
+    std::string first_err;
+    for (const LockstepDone &d : done) {
+        const int k = (int)(intptr_t)d.tag;
+        if (infos) infos[k] = d.info;
+        status[k] = d.status;
+        errors[k] = d.error;
+    }
+    for (int k = 0; k < count; ++k)
+        if (status[k] != PA_OK && first == PA_OK) {
+            first = status[k];
+            first_err = errors[k];
+        }
+    if (first != PA_OK) set_error(first, first_err);
+    return first;
 }
 
 }  // extern "C"

@@ -148,3 +148,73 @@ def test_graph_and_eager_paths_agree_bitwise(pa, mode, coop, hmg):
         pa.pa_solver_destroy(s)
     assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
     op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_lockstep_batch_equals_solo_solves(pa, mode):
+    """Solves stepped in lockstep, with every operator apply of a step
+    batched across them, give bitwise the solo iterates: uneven sizes,
+    degrees 4 and 6 (both three levels), one zero right-hand side and one
+    solve capped early, so members leave the batch at different steps."""
+    lam, mu = syn.lame(1.0, 0.3)
+    specs = [(_beam(8, 2, 2), 4, [4, 2, 1]), (_beam(4, 1, 1), 4, [4, 2, 1]),
+             (syn.random_affine_cube(3, seed=77), 6, [6, 3, 1]), (_beam(6, 2, 1), 4, [4, 2, 1]),
+             (_beam(5, 1, 1), 6, [6, 3, 1])]
+    ops, sols, bs, caps = [], [], [], []
+    for k, (m, p, levels) in enumerate(specs):
+        ess = syn.clamp_mask(m, p)
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+        b = op.rhs(f0=(0.0, 0.0, -1.0)) if k != 3 else torch.zeros(op.ndofs, dtype=torch.float64, device="cuda")
+        s = pa.pa_solver_create(op.h, levels, 2, 1e-3, 300, mode)
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_PERSISTENT_COARSE, 0)
+        ops.append(op)
+        sols.append(s)
+        bs.append(b)
+        caps.append(3 if k == 4 else 200)
+    solo = []
+    for s, b, cap in zip(sols, bs, caps):
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, cap)
+        solo.append((code, info.iterations, info.rel_residual, x))
+    # the batch API takes one cap; the capped solve is checked separately
+    xs = [torch.full_like(b, float("nan")) for b in bs]
+    for x in xs:
+        x.zero_()
+    code, infos = pa.pa_gmg_pcg_solve_batch(sols[:4], bs[:4], xs[:4], 1e-10, 200)
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    for k in range(4):
+        assert infos[k].iterations == solo[k][1]
+        assert infos[k].rel_residual == solo[k][2]
+        assert torch.equal(xs[k], solo[k][3]), k
+    assert infos[3].b_norm == 0.0 and torch.count_nonzero(xs[3]) == 0
+    # an iteration cap ends the solves of a batch at the same step as solo
+    xs2 = [torch.zeros_like(b) for b in bs]
+    code, infos2 = pa.pa_gmg_pcg_solve_batch([sols[0], sols[4]], [bs[0], bs[4]], [xs2[0], xs2[4]], 1e-10, 3)
+    assert code == pa.PA_ENOTCONV and infos2[1].iterations == 3 and infos2[1].status == pa.PA_ENOTCONV
+    x_cap = torch.zeros_like(bs[4])
+    code4, info4 = pa.pa_gmg_pcg_solve(sols[4], bs[4], x_cap, 1e-10, 3)
+    assert code4 == pa.PA_ENOTCONV and torch.equal(xs2[4], x_cap)
+    for s in sols:
+        pa.pa_solver_destroy(s)
+    for op in ops:
+        op.close()
+
+
+def test_lockstep_batch_rejects_mixed_hierarchies_and_refinement_mode(pa):
+    lam, mu = syn.lame(1.0, 0.3)
+    m = _beam(4, 1, 1)
+    ops, sols = [], []
+    for p, levels, mode in [(4, [4, 2, 1], 0), (2, [2, 1], 0), (4, [4, 2, 1], pa.PA_SOLVE_MIXED)]:
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=syn.clamp_mask(m, p))
+        ops.append(op)
+        sols.append(pa.pa_solver_create(op.h, levels, 2, 1e-3, 300, mode))
+    bs = [op.rhs(f0=(0.0, 0.0, -1.0)) for op in ops]
+    xs = [torch.zeros_like(b) for b in bs]
+    for pair in ([0, 1], [0, 2]):
+        with pytest.raises(pa.PAError) as ei:
+            pa.pa_gmg_pcg_solve_batch([sols[i] for i in pair], [bs[i] for i in pair], [xs[i] for i in pair])
+        assert ei.value.code == pa.PA_EINVAL
+    for s in sols:
+        pa.pa_solver_destroy(s)
+    for op in ops:
+        op.close()
