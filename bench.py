@@ -441,34 +441,60 @@ def serving_requests(pa, count, seed):
     return out
 
 
+def small_requests(pa, count, seed):
+    """A burst of small solves (the batch lane's workload): p uniform in
+    {2,4,6,8}, cube n^3 with n ~ U{3..8}, otherwise the served stream's
+    recipe."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        p = int(rng.choice([2, 4, 6, 8]))
+        n = int(rng.integers(3, 9))
+        E = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        nu = float(rng.uniform(0.2, 0.45))
+        modes = syn.smooth_force_modes(seed=int(rng.integers(1 << 30)))
+        out.append(pa.make_request(n, n, n, (0, 0, 0, 1.0, 1.0, 1.0), p, E, nu, modes=modes, rtol=1e-10, maxit=1000,
+                                   mode=pa.PA_SOLVE_MIXED_FCG, keep_solution=False))
+    return out
+
+
 def run_serving(args, pa, torch):
     """Continuous-admission serving of a Poisson stream.  A calibration burst
     of the first requests is solved twice, all submitted at once: in plain
-    FP64 with one slot (the FP64-alone capacity) and in the served form
-    (mixed precision, several slots).  The Poisson arrival rate is a
-    fraction of the served capacity.  Reports p50/p99 latency (submit to
-    completion) and completed solves/s."""
+    FP64 with one slot and no batching (the FP64-alone capacity) and in the
+    served form (mixed precision, several slots, small solves in the lockstep
+    batch lane).  The Poisson arrival rate is a fraction of the served
+    capacity.  Reports p50/p99 latency (submit to completion) and completed
+    solves/s, and a burst of small solves served with and without the batch
+    lane."""
     import threading
     reqs = serving_requests(pa, args.serve_requests, seed=4242)
     budget = int(args.serve_budget_gb * (1 << 30))
     ncal = min(len(reqs), args.serve_calibration)
 
-    def burst(rs, slots):
+    def burst(rs, slots, batch=1):
         srv = pa.pa_server_create(budget, slots)
+        pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_BATCH, batch)
         t0 = time.perf_counter()
         ts = [pa.pa_server_submit(srv, r) for r in rs]
-        codes = [pa.pa_server_wait(srv, t)[0] for t in ts]
+        res = [pa.pa_server_wait(srv, t) for t in ts]
         dt = time.perf_counter() - t0
+        st = pa.pa_server_stats(srv)
         pa.pa_server_destroy(srv)
-        return len(rs) / dt, sum(1 for c in codes if c == pa.PA_OK)
+        st.mean_setup_s = float(np.mean([r[2].setup_s for r in res]))
+        st.mean_solve_s = float(np.mean([r[2].solve_s for r in res]))
+        return len(rs) / dt, sum(1 for r in res if r[0] == pa.PA_OK), st
 
     fp64_reqs = []
     for r in reqs[:ncal]:
         r2 = pa.pa_request.from_buffer_copy(r)
         r2.mode = pa.PA_SOLVE_FP64
         fp64_reqs.append(r2)
-    fp64_cap, fp64_ok = burst(fp64_reqs, 1)
-    cap, cal_ok = burst(reqs[:ncal], args.serve_slots)
+    fp64_cap, fp64_ok, _ = burst(fp64_reqs, 1, batch=0)
+    cap, cal_ok, _ = burst(reqs[:ncal], args.serve_slots)
+    small = small_requests(pa, args.serve_small, seed=99)
+    small_off, small_off_ok, st_off = burst(small, args.serve_slots, batch=0)
+    small_on, small_on_ok, st_small = burst(small, args.serve_slots, batch=1)
     rate = args.serve_load * cap
     arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
     srv = pa.pa_server_create(budget, args.serve_slots)
@@ -510,6 +536,16 @@ def run_serving(args, pa, torch):
             "mean_solve_s": round(float(np.mean(solve_s)), 4), "mean_iterations": round(float(np.mean(iters)), 1),
             "ok": int(sum(1 for c in statuses if c == pa.PA_OK)),
             "calibration_ok": [fp64_ok, cal_ok],
+            "batch_lane": {"batched": int(st.batched), "ticks": int(st.batch_ticks),
+                           "mean_members_per_tick": round(st.batch_member_ticks / max(st.batch_ticks, 1), 2),
+                           "max_members": int(st.batch_max_members)},
+            "small_burst": {"requests": len(small), "recipe": "p U{2,4,6,8}; cube n^3, n ~ U{3..8}; mixed precision",
+                            "solves_per_s_lane_off": round(small_off, 3), "solves_per_s_lane_on": round(small_on, 3),
+                            "lane_speedup": round(small_on / small_off, 3), "ok": [small_off_ok, small_on_ok],
+                            "mean_setup_s_off_on": [round(st_off.mean_setup_s, 4), round(st_small.mean_setup_s, 4)],
+                            "mean_solve_s_off_on": [round(st_off.mean_solve_s, 4), round(st_small.mean_solve_s, 4)],
+                            "mean_members_per_tick": round(st_small.batch_member_ticks / max(st_small.batch_ticks, 1), 2),
+                            "max_members": int(st_small.batch_max_members)},
             "peak_used_gb": round(st.peak_used_bytes / (1 << 30), 2),
             "recipe": "Poisson arrivals; p U{2,4,6,8}; cube n^3 n~U{8..32} or beam 8k x k x k k~U{4..16}; "
                       "E log-U[0.1,10]; nu U[0.2,0.45]; 3 sine modes/component; x=0 clamped; FP64 flexible CG with an "
@@ -587,6 +623,7 @@ def main(argv=None):
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
     ap.add_argument("--serve-calibration", type=int, default=16)
+    ap.add_argument("--serve-small", type=int, default=64, help="small-solve burst served with and without batching")
     ap.add_argument("--launch", default="", help="fixed element-kernel shape 'variant,elems_per_cta,threads' "
                                                  "(skips the autotuner)")
     args = ap.parse_args(argv)

@@ -291,12 +291,22 @@ int pa_gmg_pcg_solve_batch(pa_solver *const *solvers, const double *const *b, do
 /* Serving of many solves with continuous admission (no counterpart in the
  * paper's CPU study; it drives the same operator and solver).  Requests are
  * queued in arrival order; a request is admitted when one of `max_slots`
- * slots is free and its estimated device footprint fits in the memory budget
- * still available, and it then runs (setup, load vector, GMG-PCG solve) on a
- * worker thread and CUDA stream of its own, so the work of admitted requests
- * overlaps on the GPU.  Finished requests release their memory and the next
- * queued ones are admitted.  Solves are deterministic: a request gives the
- * same bits alone or in any mix. */
+ * setup slots is free and its estimated device footprint fits in the memory
+ * budget still available.  Its setup (mesh, operators on every level,
+ * diagonals, eigenvalue estimates, load vector) runs on a worker thread and
+ * CUDA stream of its own.  Then:
+ *  - batch lane (flexible-CG modes PA_SOLVE_FP64 / PA_SOLVE_MIXED_FCG, at
+ *    most PA_SERVER_OPT_BATCH_MAX_DOFS fine dofs): the request leaves its
+ *    slot and joins the lockstep batch of its hierarchy (number of levels,
+ *    mode), whose stepper thread advances every member one CG step per tick
+ *    with the operator applies of all members batched into one launch per
+ *    (precision, degree) (see pa_gmg_pcg_solve_batch); members join and
+ *    leave between ticks (continuous batching);
+ *  - otherwise the worker solves it with pa_gmg_pcg_solve on the solver's
+ *    stream, overlapping with everything else on the GPU.
+ * Finished requests release their memory and the next queued ones are
+ * admitted.  Solves are deterministic: a request gives the same bits alone
+ * or in any mix, in either lane. */
 #define PA_REQUEST_MAX_MODES 16
 
 typedef struct pa_request {
@@ -310,7 +320,7 @@ typedef struct pa_request {
     int clamp_x0;          /* non-zero: all dofs on the x = xlo face are essential */
     double rtol;           /* solve tolerance (see pa_gmg_pcg_solve)               */
     int maxit;             /* iteration cap                                        */
-    int mode;              /* PA_SOLVE_FP64 or PA_SOLVE_MIXED                      */
+    int mode;              /* PA_SOLVE_FP64, PA_SOLVE_MIXED or PA_SOLVE_MIXED_FCG  */
     int keep_solution;     /* non-zero: keep x on the host for pa_server_wait      */
 } pa_request;
 
@@ -318,13 +328,32 @@ typedef struct pa_request_timing {
     double latency_s;        /* submit to completion                      */
     double queue_s;          /* submit to admission                       */
     double setup_s;          /* operators, diagonals, eigenvalue estimates */
-    double solve_s;          /* pa_gmg_pcg_solve                          */
+    double solve_s;          /* the solve (in either lane)                */
     int64_t footprint_bytes; /* admission estimate of device memory       */
+    int batched;             /* 1: solved in the lockstep batch lane      */
 } pa_request_timing;
 
 typedef struct pa_server_stats_t {
     int64_t queued, running, completed, used_bytes, peak_used_bytes;
+    int64_t batched;          /* requests solved in the batch lane          */
+    int64_t batch_ticks;      /* lockstep steps run (all batches)           */
+    int64_t batch_member_ticks; /* sum over steps of the members stepped    */
+    int64_t batch_max_members;  /* largest batch seen                       */
 } pa_server_stats_t;
+
+/* Server options (pa_server_set_option, before the first submit):
+ *  PA_SERVER_OPT_BATCH (default 1): 0 turns the batch lane off (every
+ *    request is solved by its worker).
+ *  PA_SERVER_OPT_BATCH_MAX_DOFS (default 2,000,000): largest fine-level dof
+ *    count that joins the batch lane (larger solves fill the GPU alone).
+ *  PA_SERVER_OPT_BATCH_MAX_MEMBERS (default 64, at most 256): members per
+ *    lockstep batch; further requests wait for a member to leave. */
+enum pa_server_option {
+    PA_SERVER_OPT_BATCH = 1,
+    PA_SERVER_OPT_BATCH_MAX_DOFS = 2,
+    PA_SERVER_OPT_BATCH_MAX_MEMBERS = 3
+};
+int pa_server_set_option(pa_server *s, int option, double value);
 
 /* Uses the device current at creation; budget_bytes > 0; 1 <= max_slots <= 64. */
 int pa_server_create(size_t budget_bytes, int max_slots, pa_server **out);

@@ -51,12 +51,14 @@ class pa_request(ctypes.Structure):
 
 class pa_request_timing(ctypes.Structure):
     _fields_ = [("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("setup_s", ctypes.c_double),
-                ("solve_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64)]
+                ("solve_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64), ("batched", ctypes.c_int)]
 
 
 class pa_server_stats_t(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("used_bytes", ctypes.c_int64), ("peak_used_bytes", ctypes.c_int64)]
+                ("used_bytes", ctypes.c_int64), ("peak_used_bytes", ctypes.c_int64), ("batched", ctypes.c_int64),
+                ("batch_ticks", ctypes.c_int64), ("batch_member_ticks", ctypes.c_int64),
+                ("batch_max_members", ctypes.c_int64)]
 
 
 def _sig(name, args, res=ctypes.c_int):
@@ -97,6 +99,7 @@ _sig("pa_server_wait", [_vp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.POINTER
                         ctypes.POINTER(pa_request_timing)])
 _sig("pa_server_stats", [_vp, ctypes.POINTER(pa_server_stats_t)])
 _sig("pa_server_destroy", [_vp])
+_sig("pa_server_set_option", [_vp, ctypes.c_int, ctypes.c_double])
 if hasattr(lib, "pa_solver_create"):
     _sig("pa_solver_create", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.POINTER(_vp)])
@@ -354,6 +357,15 @@ def pa_server_wait(srv, ticket, x_len=0):
     if code == PA_EINVAL:
         raise PAError(code, "pa_server_wait")
     return code, info, tm, x
+
+
+PA_SERVER_OPT_BATCH = 1
+PA_SERVER_OPT_BATCH_MAX_DOFS = 2
+PA_SERVER_OPT_BATCH_MAX_MEMBERS = 3
+
+
+def pa_server_set_option(srv, option, value):
+    _check(lib.pa_server_set_option(srv, option, float(value)), "pa_server_set_option")
 
 
 def pa_server_stats(srv):

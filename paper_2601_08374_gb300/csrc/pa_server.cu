@@ -1,14 +1,19 @@
 // Solve server: continuous admission of elasticity solve requests.
 //
 // Requests are queued in arrival order.  A request is admitted as soon as a
-// slot is free and its estimated device footprint fits in what the memory
-// budget has left; it then runs on a worker thread of its own -- setup
-// (mesh, operators on every level, diagonals, eigenvalue estimates), load
-// vector and GMG-PCG solve -- on the solver's own CUDA stream, so the kernels
-// of all admitted requests overlap on the GPU.  When a request finishes its
-// memory is released and the next queued requests are admitted.  Every solve
-// is deterministic (fixed-order reductions, no atomics in the arithmetic), so
-// a request gives the same bits alone or in any mix.
+// setup slot is free and its estimated device footprint fits in what the
+// memory budget has left; a worker thread then builds it -- mesh, operators
+// on every level, diagonals, eigenvalue estimates, load vector -- on a CUDA
+// stream of its own.  Small flexible-CG requests then leave the slot for the
+// batch lane of their hierarchy: a stepper thread advances all of its
+// requests one CG step per tick with their operator applies batched into
+// one launch per (precision, degree), and new requests join between ticks
+// (continuous batching).  Other requests are solved by their worker on the
+// solver's own stream, overlapping with everything else.  When a request
+// finishes its memory is released and the next queued requests are
+// admitted.  Every solve is deterministic (fixed-order reductions, no
+// atomics in the arithmetic, batched applies with the arithmetic of single
+// ones), so a request gives the same bits alone or in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -39,7 +44,31 @@ struct Ticket {
     pa_solve_info info{};
     clk::time_point t_submit, t_start, t_end;
     double setup_s = 0.0, solve_s = 0.0;
+    int batched = 0;
     std::vector<double> x;  // host copy of the solution when requested
+};
+
+// Device resources of one request between setup and completion.
+struct Res {
+    pa_op *op = nullptr;
+    pa_solver *sol = nullptr;
+    double *b = nullptr, *x = nullptr;
+    cudaStream_t st = nullptr;
+};
+
+// A request in the batch lane.
+struct BatchJob {
+    std::shared_ptr<Ticket> t;
+    Res res;
+    clk::time_point t_join;
+};
+
+// One lockstep batch (requests of one hierarchy) and its stepper thread.
+struct Stepper {
+    int key = 0;
+    std::thread th;
+    std::deque<BatchJob *> inbox;
+    int members = 0;
 };
 
 // Degrees of the p-hierarchy: halve down to 1 (8-4-2-1, 6-3-1, 4-2-1, 2-1).
@@ -83,33 +112,45 @@ struct pa_server {
     std::condition_variable cv_work, cv_done;
     std::vector<std::thread> workers;
     bool stop = false;
+    // batch lane
+    bool batch = true;
+    int64_t batch_max_dofs = 2000000;
+    int batch_max_members = 64;
+    int64_t in_lane = 0;  // handed to a stepper, not finished
+    std::vector<std::unique_ptr<Stepper>> steppers;
+    std::condition_variable cv_lane;
+    bool stop_lanes = false;
+    int64_t batched = 0, batch_ticks = 0, batch_member_ticks = 0, batch_max_seen = 0;
 };
 
 namespace {
 
-// Runs one admitted request end to end on the calling worker thread.
-void run_request(pa_server *srv, Ticket &t)
+void release(Res &r)
+{
+    cudaFree(r.b);
+    cudaFree(r.x);
+    pa_solver_destroy(r.sol);
+    pa_op_destroy(r.op);
+    if (r.st) cudaStreamDestroy(r.st);
+    r = Res{};
+}
+
+// Builds an admitted request on the calling thread: operators, solver, load
+// vector b and x = 0 (all ready on the device when it returns PA_OK).
+int setup_request(pa_server *srv, Ticket &t, Res &res)
 {
     const pa_request &r = t.req;
     pa_mesh *mesh = nullptr;
-    pa_op *op = nullptr;
-    pa_solver *sol = nullptr;
-    double *b = nullptr, *x = nullptr;
     int rc = PA_OK;
-    cudaStream_t st = nullptr;
-    auto fail = [&](int code) {
-        t.status = code;
-        t.error = pa_last_error();
-    };
     do {
-        if (cudaSetDevice(srv->device) != cudaSuccess) { fail(pa::cuda_error(cudaGetLastError(), "cudaSetDevice")); break; }
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            fail(pa::cuda_error(cudaGetLastError(), "cudaStreamCreate"));
+        if (cudaSetDevice(srv->device) != cudaSuccess) { rc = pa::cuda_error(cudaGetLastError(), "cudaSetDevice"); break; }
+        if (cudaStreamCreateWithFlags(&res.st, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = pa::cuda_error(cudaGetLastError(), "cudaStreamCreate");
             break;
         }
         double lam = 0, mu = 0;
-        if ((rc = pa_lame(r.E, r.nu, &lam, &mu))) { fail(rc); break; }
-        if ((rc = pa_mesh_create(r.nx, r.ny, r.nz, r.box, nullptr, &mesh))) { fail(rc); break; }
+        if ((rc = pa_lame(r.E, r.nu, &lam, &mu))) break;
+        if ((rc = pa_mesh_create(r.nx, r.ny, r.nz, r.box, nullptr, &mesh))) break;
         std::vector<uint8_t> ess;
         if (r.clamp_x0) {
             const int64_t Mx = (int64_t)r.nx * r.p + 1, My = (int64_t)r.ny * r.p + 1, Mz = (int64_t)r.nz * r.p + 1;
@@ -118,44 +159,161 @@ void run_request(pa_server *srv, Ticket &t)
             for (int c = 0; c < 3; ++c)
                 for (int64_t g = 0; g < Nn; g += Mx) ess[(size_t)(c * Nn + g)] = 1;  // gx = 0
         }
-        if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &op))) { fail(rc); break; }
+        if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &res.op))) break;
         pa_mesh_destroy(mesh);
         mesh = nullptr;
-        if ((rc = pa_solver_create(op, (int)t.levels.size(), t.levels.data(), 2, 1e-3, 300, r.mode, &sol))) {
-            fail(rc);
+        if ((rc = pa_solver_create(res.op, (int)t.levels.size(), t.levels.data(), 2, 1e-3, 300, r.mode, &res.sol)))
             break;
-        }
         // concurrent solvers must not each hold a grid-wide barrier
-        pa_solver_set_option(sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);
-        const size_t n = (size_t)op->ndofs();
-        if (cudaMalloc((void **)&b, n * sizeof(double)) != cudaSuccess ||
-            cudaMalloc((void **)&x, n * sizeof(double)) != cudaSuccess) {
-            fail(pa::set_error(PA_ENOMEM, "server: device allocation for b, x"));
+        pa_solver_set_option(res.sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);
+        const size_t n = (size_t)res.op->ndofs();
+        if (cudaMalloc((void **)&res.b, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&res.x, n * sizeof(double)) != cudaSuccess) {
+            rc = pa::set_error(PA_ENOMEM, "server: device allocation for b, x");
             break;
         }
-        if ((rc = pa_op_rhs(op, r.f0, r.nmodes, r.nmodes ? r.modes : nullptr, b, st))) { fail(rc); break; }
-        if (cudaMemsetAsync(x, 0, n * sizeof(double), st) != cudaSuccess) {
-            fail(pa::cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+        if ((rc = pa_op_rhs(res.op, r.f0, r.nmodes, r.nmodes ? r.modes : nullptr, res.b, res.st))) break;
+        if (cudaMemsetAsync(res.x, 0, n * sizeof(double), res.st) != cudaSuccess ||
+            cudaStreamSynchronize(res.st) != cudaSuccess) {
+            rc = pa::cuda_error(cudaGetLastError(), "server: load vector");
             break;
-        }
-        auto t_setup = clk::now();
-        t.setup_s = std::chrono::duration<double>(t_setup - t.t_start).count();
-        rc = pa_gmg_pcg_solve(sol, b, x, r.rtol, r.maxit, &t.info, st);
-        t.solve_s = std::chrono::duration<double>(clk::now() - t_setup).count();
-        t.status = rc;
-        if (rc != PA_OK) t.error = pa_last_error();
-        if (r.keep_solution && rc != PA_EINVAL) {
-            t.x.resize(n);
-            if (cudaMemcpy(t.x.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-                fail(pa::cuda_error(cudaGetLastError(), "cudaMemcpy solution"));
         }
     } while (false);
-    cudaFree(b);
-    cudaFree(x);
-    pa_solver_destroy(sol);
-    pa_op_destroy(op);
     pa_mesh_destroy(mesh);
-    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
+// Records a finished solve in the ticket (solution copied to the host when
+// kept) and frees the request's device resources.
+void record_result(Ticket &t, Res &res, int status, const pa_solve_info &info, const std::string &err)
+{
+    t.status = status;
+    t.info = info;
+    if (status != PA_OK) t.error = err;
+    if (t.req.keep_solution && res.x && status != PA_EINVAL) {
+        const size_t n = (size_t)res.op->ndofs();
+        t.x.resize(n);
+        if (cudaMemcpy(t.x.data(), res.x, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            t.status = pa::cuda_error(cudaGetLastError(), "cudaMemcpy solution");
+            t.error = pa_last_error();
+        }
+    }
+    release(res);
+}
+
+// Marks a ticket done and returns its memory (caller holds srv->mu).
+void complete_locked(pa_server *srv, Ticket &t)
+{
+    t.t_end = clk::now();
+    t.state = 2;
+    srv->used -= t.footprint;
+    ++srv->completed;
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+}
+
+bool batchable(const pa_server *srv, const Ticket &t)
+{
+    const pa_request &r = t.req;
+    const int64_t n = 3LL * (r.nx * (int64_t)r.p + 1) * (r.ny * (int64_t)r.p + 1) * (r.nz * (int64_t)r.p + 1);
+    return srv->batch && (r.mode == PA_SOLVE_FP64 || r.mode == PA_SOLVE_MIXED_FCG) && n <= srv->batch_max_dofs;
+}
+
+void stepper_main(pa_server *srv, Stepper *sp);
+
+// Hands a built request to the stepper of its hierarchy (caller holds
+// srv->mu); the stepper is started on first use.
+void hand_to_lane(pa_server *srv, BatchJob *job)
+{
+    const int key = pa::lockstep_key(job->res.sol);
+    Stepper *sp = nullptr;
+    for (auto &x : srv->steppers)
+        if (x->key == key) sp = x.get();
+    if (!sp) {
+        srv->steppers.emplace_back(new Stepper);
+        sp = srv->steppers.back().get();
+        sp->key = key;
+        sp->th = std::thread(stepper_main, srv, sp);
+    }
+    sp->inbox.push_back(job);
+    srv->cv_lane.notify_all();
+}
+
+// Stepper thread: joins waiting requests between ticks, runs one lockstep
+// tick for all members, completes the members that finished.
+void stepper_main(pa_server *srv, Stepper *sp)
+{
+    cudaSetDevice(srv->device);
+    pa::Lockstep *L = nullptr;
+    int rc_create = pa::lockstep_create(&L);
+    std::string create_err = rc_create ? pa_last_error() : "";
+    std::vector<BatchJob *> active;
+    std::vector<pa::LockstepDone> done;
+    auto finish = [&](BatchJob *job, int status, const pa_solve_info &info, const std::string &err) {
+        job->t->solve_s = std::chrono::duration<double>(clk::now() - job->t_join).count();
+        record_result(*job->t, job->res, status, info, err);
+        std::lock_guard<std::mutex> lk(srv->mu);
+        --srv->in_lane;
+        ++srv->batched;
+        complete_locked(srv, *job->t);
+        delete job;
+    };
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (true) {
+        srv->cv_lane.wait(lk, [&] { return srv->stop_lanes || !sp->inbox.empty() || sp->members > 0; });
+        if (sp->inbox.empty() && sp->members == 0) {
+            if (srv->stop_lanes) break;
+            continue;
+        }
+        std::vector<BatchJob *> joining;
+        while (!sp->inbox.empty() && (int)(active.size() + joining.size()) < srv->batch_max_members) {
+            joining.push_back(sp->inbox.front());
+            sp->inbox.pop_front();
+        }
+        lk.unlock();
+        for (BatchJob *job : joining) {
+            job->t_join = clk::now();
+            int rc = rc_create ? rc_create
+                               : pa::lockstep_add(L, job->res.sol, job->res.b, job->res.x, job->t->req.rtol,
+                                                  job->t->req.maxit, job);
+            if (rc) finish(job, rc, pa_solve_info{}, rc_create ? create_err : std::string(pa_last_error()));
+            else active.push_back(job);
+        }
+        int stepped = 0;
+        if (!rc_create && pa::lockstep_active(L) > 0) {
+            stepped = pa::lockstep_active(L);
+            int rc = pa::lockstep_tick(L);
+            if (rc) {
+                // a failed launch: every member ends with the error, and the
+                // batch starts afresh
+                std::string err = pa_last_error();
+                pa::lockstep_destroy(L);
+                L = nullptr;
+                for (BatchJob *job : active) finish(job, rc, pa_solve_info{}, err);
+                active.clear();
+                rc_create = pa::lockstep_create(&L);
+                create_err = rc_create ? pa_last_error() : "";
+            }
+        }
+        if (L) {
+            done.clear();
+            pa::lockstep_take_done(L, done);
+            for (const pa::LockstepDone &d : done) {
+                BatchJob *job = static_cast<BatchJob *>(d.tag);
+                active.erase(std::find(active.begin(), active.end(), job));
+                finish(job, d.status, d.info, d.error);
+            }
+        }
+        lk.lock();
+        sp->members = (int)active.size();
+        if (stepped) {
+            ++srv->batch_ticks;
+            srv->batch_member_ticks += stepped;
+            srv->batch_max_seen = std::max<int64_t>(srv->batch_max_seen, stepped);
+        }
+    }
+    lk.unlock();
+    pa::lockstep_destroy(L);
 }
 
 void worker_main(pa_server *srv)
@@ -189,18 +347,35 @@ void worker_main(pa_server *srv)
         ++srv->running;
         t->state = 1;
         t->t_start = clk::now();
+        const bool lane = batchable(srv, *t);
         // another request may fit as well
         srv->cv_work.notify_all();
         lk.unlock();
-        run_request(srv, *t);
+        Res res;
+        int rc = setup_request(srv, *t, res);
+        auto t_setup = clk::now();
+        t->setup_s = std::chrono::duration<double>(t_setup - t->t_start).count();
+        if (rc == PA_OK && lane) {
+            BatchJob *job = new BatchJob{t, res, t_setup};
+            lk.lock();
+            t->batched = 1;
+            --srv->running;
+            ++srv->in_lane;
+            hand_to_lane(srv, job);
+            srv->cv_work.notify_all();
+            continue;
+        }
+        if (rc == PA_OK) {
+            pa_solve_info info{};
+            rc = pa_gmg_pcg_solve(res.sol, res.b, res.x, t->req.rtol, t->req.maxit, &info, res.st);
+            t->solve_s = std::chrono::duration<double>(clk::now() - t_setup).count();
+            record_result(*t, res, rc, info, rc != PA_OK ? std::string(pa_last_error()) : std::string());
+        } else {
+            record_result(*t, res, rc, pa_solve_info{}, pa_last_error());
+        }
         lk.lock();
-        t->t_end = clk::now();
-        t->state = 2;
-        srv->used -= t->footprint;
         --srv->running;
-        ++srv->completed;
-        srv->cv_done.notify_all();
-        srv->cv_work.notify_all();
+        complete_locked(srv, *t);
     }
 }
 
@@ -290,6 +465,7 @@ int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, 
     }
     if (info) *info = t->info;
     if (timing) {
+        timing->batched = t->batched;
         timing->latency_s = std::chrono::duration<double>(t->t_end - t->t_submit).count();
         timing->queue_s = std::chrono::duration<double>(t->t_start - t->t_submit).count();
         timing->setup_s = t->setup_s;
@@ -314,20 +490,45 @@ int pa_server_stats(pa_server *s, pa_server_stats_t *out)
     out->completed = s->completed;
     out->used_bytes = (int64_t)s->used;
     out->peak_used_bytes = (int64_t)s->peak_used;
+    out->batched = s->batched;
+    out->batch_ticks = s->batch_ticks;
+    out->batch_member_ticks = s->batch_member_ticks;
+    out->batch_max_members = s->batch_max_seen;
     return PA_OK;
+}
+
+int pa_server_set_option(pa_server *s, int option, double value)
+{
+    if (!s) return set_error(PA_EINVAL, "pa_server_set_option: null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    switch (option) {
+    case PA_SERVER_OPT_BATCH: s->batch = value != 0.0; return PA_OK;
+    case PA_SERVER_OPT_BATCH_MAX_DOFS:
+        if (!(value >= 0.0)) return set_error(PA_EINVAL, "pa_server_set_option: negative dof count");
+        s->batch_max_dofs = (int64_t)value;
+        return PA_OK;
+    case PA_SERVER_OPT_BATCH_MAX_MEMBERS:
+        if (!(value >= 1.0 && value <= 256.0)) return set_error(PA_EINVAL, "pa_server_set_option: members in 1..256");
+        s->batch_max_members = (int)value;
+        return PA_OK;
+    default: return set_error(PA_EINVAL, "pa_server_set_option: unknown option");
+    }
 }
 
 int pa_server_destroy(pa_server *s)
 {
     if (!s) return PA_OK;
     {
-        // finish what is queued or running, then stop the workers
+        // finish what is queued, running or batched, then stop the threads
         std::unique_lock<std::mutex> lk(s->mu);
-        s->cv_done.wait(lk, [&] { return s->queue.empty() && s->running == 0; });
+        s->cv_done.wait(lk, [&] { return s->queue.empty() && s->running == 0 && s->in_lane == 0; });
         s->stop = true;
+        s->stop_lanes = true;
     }
     s->cv_work.notify_all();
+    s->cv_lane.notify_all();
     for (auto &w : s->workers) w.join();
+    for (auto &sp : s->steppers) sp->th.join();
     delete s;
     return PA_OK;
 }

@@ -18,9 +18,9 @@ def pa():
     return pa
 
 
-def _req(pa, k, keep=True, mode=1):
+def _req(pa, k, keep=True, mode=1, p=None):
     rng = np.random.default_rng(k)
-    p = int(rng.choice([2, 4]))
+    p = int(rng.choice([2, 4])) if p is None else p
     n = int(rng.integers(2, 5))
     beam = bool(k % 2)
     dims = (4 * n, n, n) if beam else (n, n, n)
@@ -54,6 +54,39 @@ def test_result_is_identical_alone_and_in_a_mix(pa):
     assert np.array_equal(x_alone, x_mix)  # deterministic: the same bits
     assert info2.iterations == info.iterations
     assert st.completed == 8 and st.peak_used_bytes > 0
+
+
+def test_batch_lane_gives_the_solo_lane_bits(pa):
+    """Flexible-CG requests of one hierarchy solved in the lockstep batch
+    lane (continuous batching, batched applies) give bitwise the results of
+    the same requests solved one per worker with the lane off."""
+    reqs = [_req(pa, 40 + k, mode=pa.PA_SOLVE_MIXED_FCG, p=4) for k in range(8)]
+    reqs[3].mode = pa.PA_SOLVE_FP64  # another hierarchy key: its own batch
+
+    def serve(batch):
+        srv = pa.pa_server_create(64 << 30, 8)
+        pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_BATCH, batch)
+        ts = [pa.pa_server_submit(srv, r) for r in reqs]
+        out = [pa.pa_server_wait(srv, t, _ndofs(r)) for t, r in zip(ts, reqs)]
+        st = pa.pa_server_stats(srv)
+        pa.pa_server_destroy(srv)
+        return out, st
+
+    solo, st0 = serve(0)
+    lane, st1 = serve(1)
+    assert st0.batched == 0 and st1.batched == 8
+    assert st1.batch_max_members >= 2 and st1.batch_member_ticks > st1.batch_ticks
+    for (c0, i0, t0, x0), (c1, i1, t1, x1) in zip(solo, lane):
+        assert c0 == pa.PA_OK and c1 == pa.PA_OK
+        assert t0.batched == 0 and t1.batched == 1
+        assert i0.iterations == i1.iterations and i0.rel_residual == i1.rel_residual
+        assert np.array_equal(x0, x1)
+    with pytest.raises(pa.PAError):
+        srv = pa.pa_server_create(1 << 30, 1)
+        try:
+            pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_BATCH_MAX_MEMBERS, 0)
+        finally:
+            pa.pa_server_destroy(srv)
 
 
 def test_admission_respects_the_memory_budget(pa):
