@@ -209,6 +209,8 @@ typedef struct pa_solve_info {
     int inner_iterations;  /* mixed mode: total inner (FP32) iterations           */
     int refinements;       /* mixed mode: outer refinement steps                  */
     double lambda_max[8];  /* per level: power-iteration estimate of max eig(D^-1 A) */
+    int coarse_iterations; /* coarse-level CG iterations summed over all V-cycles
+                              (counted with graphs on, the default; 0 otherwise) */
 } pa_solve_info;
 
 /* PA_SOLVE_FP64: everything in FP64.

@@ -35,7 +35,7 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 class pa_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("b_norm", ctypes.c_double), ("inner_iterations", ctypes.c_int), ("refinements", ctypes.c_int),
-                ("lambda_max", ctypes.c_double * 8)]
+                ("lambda_max", ctypes.c_double * 8), ("coarse_iterations", ctypes.c_int)]
 
 
 PA_REQUEST_MAX_MODES = 16

@@ -162,7 +162,7 @@ int setup_request(pa_server *srv, Ticket &t, Res &res)
         if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &res.op))) break;
         pa_mesh_destroy(mesh);
         mesh = nullptr;
-        if ((rc = pa_solver_create(res.op, (int)t.levels.size(), t.levels.data(), 2, 1e-3, 300, r.mode, &res.sol)))
+        if ((rc = pa_solver_create(res.op, (int)t.levels.size(), t.levels.data(), 2, 1e-2, 10, r.mode, &res.sol)))
             break;
         // concurrent solvers must not each hold a grid-wide barrier
         pa_solver_set_option(res.sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);

@@ -383,43 +383,80 @@ __global__ void k_assemble_p1(const double *__restrict__ geo, double *__restrict
     }
 }
 
+// Row of y = A p on an assembled stencil level whose planes are masked
+// (k_mask_stencil): essential rows are identity rows, couplings to essential
+// dofs and to neighbours outside the grid are zero.  The row is then a
+// branch-free sum of 81 terms; a neighbour outside the grid is read at the
+// row's own node (its coefficient is 0), so all loads are independent and in
+// flight together.  One partial sum per column component.
+__device__ inline double stencil_row(const double *__restrict__ vals, const double *__restrict__ p, const Grid &g,
+                                     int64_t row)
+{
+    const int Nn = (int)g.Nn, Mx = g.Mx, My = g.My, Mz = g.Mz;
+    const int64_t nrow = 3 * (int64_t)Nn;
+    const int c = (int)(row / Nn);
+    const int i = (int)(row - (int64_t)c * Nn);
+    const int ix = i % Mx, t = i / Mx, iy = t % My, iz = t / My;
+    const int ox[3] = {ix > 0 ? -1 : 0, 0, ix < Mx - 1 ? 1 : 0};
+    const int oy[3] = {iy > 0 ? -Mx : 0, 0, iy < My - 1 ? Mx : 0};
+    const int oz[3] = {iz > 0 ? -Mx * My : 0, 0, iz < Mz - 1 ? Mx * My : 0};
+    double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+        for (int sy = 0; sy < 3; ++sy)
+#pragma unroll
+            for (int sx = 0; sx < 3; ++sx) {
+                const int sidx = sx + 3 * sy + 9 * sz;
+                const int j = i + ox[sx] + oy[sy] + oz[sz];
+#pragma unroll
+                for (int d2 = 0; d2 < 3; ++d2)
+                    acc[d2] = fma(vals[(int64_t)(sidx * 3 + d2) * nrow + row], p[(int64_t)d2 * Nn + j], acc[d2]);
+            }
+    return (acc[0] + acc[1]) + acc[2];
+}
+
+// Masks an assembled stencil level in place for stencil_row: zero
+// coefficients towards neighbours outside the grid and towards essential
+// dofs, identity rows on essential dofs.  The Galerkin products and the dense
+// coarsest matrix leave essential rows and columns out, so they read the
+// same values from masked planes.
+__global__ void k_mask_stencil(double *__restrict__ vals, const uint8_t *__restrict__ ess, Grid g)
+{
+    const int64_t Nn = g.Nn, nrow = 3 * Nn;
+    GRID_STRIDE(row, nrow)
+    {
+        const int c = (int)(row / Nn);
+        const int64_t i = row - c * Nn;
+        const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
+        const bool erow = ess && ess[row];
+        for (int sidx = 0; sidx < 27; ++sidx) {
+            const int dx = sidx % 3 - 1, dy = (sidx / 3) % 3 - 1, dz = sidx / 9 - 1;
+            const bool inside = ix + dx >= 0 && ix + dx < g.Mx && iy + dy >= 0 && iy + dy < g.My && iz + dz >= 0 &&
+                                iz + dz < g.Mz;
+            const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
+            for (int d2 = 0; d2 < 3; ++d2) {
+                double &v = vals[(int64_t)(sidx * 3 + d2) * nrow + row];
+                if (!inside) v = 0.0;
+                else if (erow) v = (sidx == 13 && d2 == c) ? 1.0 : 0.0;
+                else if (ess && ess[d2 * Nn + j]) v = 0.0;
+            }
+        }
+    }
+}
+
 // q = A p with the assembled stencil (constrained rows/columns as the
 // operator: essential columns read as 0, essential rows return p), fused with
 // pq = (p, q) and alpha = rz / pq.
 __global__ void k_cg_spmv_pq(Dev d, const double *__restrict__ vals, const double *__restrict__ p,
-                             double *__restrict__ q, const uint8_t *__restrict__ ess, Grid g)
+                             double *__restrict__ q, Grid g)
 {
     if (d.flag[F_CDONE]) return;
     const int64_t Nn = g.Nn, nrow = 3 * Nn;
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(row, nrow)
     {
-        const int c = (int)(row / Nn);
-        const int64_t i = row - c * Nn;
-        double y;
-        if (ess && ess[row]) {
-            y = p[row];
-        } else {
-            const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
-            y = 0.0;
-            for (int dz = -1; dz <= 1; ++dz) {
-                if (iz + dz < 0 || iz + dz >= g.Mz) continue;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    if (iy + dy < 0 || iy + dy >= g.My) continue;
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (ix + dx < 0 || ix + dx >= g.Mx) continue;
-                        const int sidx = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-                        const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
-#pragma unroll
-                        for (int dd2 = 0; dd2 < 3; ++dd2) {
-                            const int64_t col = dd2 * Nn + j;
-                            const double xv = (ess && ess[col]) ? 0.0 : p[col];
-                            y += vals[(int64_t)(sidx * 3 + dd2) * nrow + row] * xv;
-                        }
-                    }
-                }
-            }
-        }
+        const double y = stencil_row(vals, p, g, row);
         q[row] = y;
         v[0] += p[row] * y;
     }
@@ -505,35 +542,6 @@ __device__ inline void publish(double *part, double (&v)[K])
         for (int k = 0; k < K; ++k) part[k * kRedBlocks + blockIdx.x] = v[k];
 }
 
-__device__ inline double stencil_row(const double *__restrict__ vals, const double *__restrict__ p,
-                                     const uint8_t *__restrict__ ess, const Grid &g, int64_t row)
-{
-    const int64_t Nn = g.Nn, nrow = 3 * Nn;
-    if (ess && ess[row]) return p[row];
-    const int c = (int)(row / Nn);
-    const int64_t i = row - c * Nn;
-    const int ix = (int)(i % g.Mx), iy = (int)((i / g.Mx) % g.My), iz = (int)(i / ((int64_t)g.Mx * g.My));
-    double y = 0.0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        if (iz + dz < 0 || iz + dz >= g.Mz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            if (iy + dy < 0 || iy + dy >= g.My) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (ix + dx < 0 || ix + dx >= g.Mx) continue;
-                const int sidx = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-                const int64_t j = i + dx + (int64_t)g.Mx * (dy + (int64_t)g.My * dz);
-#pragma unroll
-                for (int d2 = 0; d2 < 3; ++d2) {
-                    const int64_t col = d2 * Nn + j;
-                    const double xv = (ess && ess[col]) ? 0.0 : p[col];
-                    y += vals[(int64_t)(sidx * 3 + d2) * nrow + row] * xv;
-                }
-            }
-        }
-    }
-    return y;
-}
-
 __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict__ vals, double *__restrict__ x,
                                                  double *__restrict__ r, double *__restrict__ p, double *__restrict__ q,
                                                  const double *__restrict__ dinv, const double *__restrict__ b,
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
         double v1[1] = {0.0}, t1[1];
         GRID_STRIDE(row, n)
         {
-            const double y = stencil_row(vals, p, ess, g, row);
+            const double y = stencil_row(vals, p, g, row);
             q[row] = y;
             v1[0] += p[row] * y;
         }
@@ -649,9 +657,9 @@ __host__ __device__ inline double h_weight(int i, int J, int Mf, int Mc)
 
 // y = A x on an assembled stencil level (constrained like the operator)
 __global__ void k_stencil_apply(const double *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y,
-                                const uint8_t *__restrict__ ess, Grid g)
+                                Grid g)
 {
-    GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, ess, g, row);
+    GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, g, row);
 }
 
 // One axis of the h-prolongation: out (axis `ax` fine, size Mf) from in
@@ -680,6 +688,75 @@ __global__ void k_hprolong_axis(double *out, const double *in, int ax, int Nx, i
             s2 += w[k] * in[(((int64_t)c * cdims[2] + idx[2]) * cdims[1] + idx[1]) * cdims[0] + idx[0]];
         }
         out[o] = accumulate ? out[o] + s2 : s2;
+    }
+}
+
+// h-prolongation added in one pass: ef += P ec, each fine dof gathering its
+// (at most 8) coarse parents, nested x inside y inside z like the
+// axis-by-axis form.
+__global__ void k_hprolong_add(double *__restrict__ ef, const double *__restrict__ ec, Grid gf, Grid gc)
+{
+    const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
+    GRID_STRIDE(o, 3 * Nnf)
+    {
+        const int c = (int)(o / Nnf);
+        const int64_t i = o - c * Nnf;
+        const int fx = (int)(i % gf.Mx), fy = (int)((i / gf.Mx) % gf.My), fz = (int)(i / ((int64_t)gf.Mx * gf.My));
+        int Jx[2], Jy[2], Jz[2];
+        double wx[2], wy[2], wz[2];
+        const int nx = h_parents(fx, gf.Mx, gc.Mx, Jx, wx), ny = h_parents(fy, gf.My, gc.My, Jy, wy),
+                  nz = h_parents(fz, gf.Mz, gc.Mz, Jz, wz);
+        double sz = 0.0;
+        for (int kz = 0; kz < nz; ++kz) {
+            double sy = 0.0;
+            for (int ky = 0; ky < ny; ++ky) {
+                const double *row = ec + c * Nnc + (int64_t)gc.Mx * (Jy[ky] + (int64_t)gc.My * Jz[kz]);
+                double sx = 0.0;
+                for (int kx = 0; kx < nx; ++kx) sx += wx[kx] * row[Jx[kx]];
+                sy += wy[ky] * sx;
+            }
+            sz += wz[kz] * sy;
+        }
+        ef[o] = ef[o] + sz;
+    }
+}
+
+// h-restriction in one pass: out = R (in - in2) (in2 may be null), each
+// coarse dof gathering its fine children (at most 3 per axis) with the
+// transposed weights; essential coarse dofs are zeroed.
+__global__ void k_hrestrict(double *__restrict__ out, const double *__restrict__ in, const double *__restrict__ in2,
+                            Grid gf, Grid gc, const uint8_t *__restrict__ ess)
+{
+    const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
+    GRID_STRIDE(o, 3 * Nnc)
+    {
+        const int c = (int)(o / Nnc);
+        const int64_t I = o - c * Nnc;
+        const int Jx = (int)(I % gc.Mx), Jy = (int)((I / gc.Mx) % gc.My), Jz = (int)(I / ((int64_t)gc.Mx * gc.My));
+        const int px = h_pos(Jx, gf.Mx, gc.Mx), py = h_pos(Jy, gf.My, gc.My), pz = h_pos(Jz, gf.Mz, gc.Mz);
+        double sz = 0.0;
+        for (int iz = pz - 1; iz <= pz + 1; ++iz) {
+            if (iz < 0 || iz >= gf.Mz) continue;
+            const double wz = h_weight(iz, Jz, gf.Mz, gc.Mz);
+            if (wz == 0.0) continue;
+            double sy = 0.0;
+            for (int iy = py - 1; iy <= py + 1; ++iy) {
+                if (iy < 0 || iy >= gf.My) continue;
+                const double wy = h_weight(iy, Jy, gf.My, gc.My);
+                if (wy == 0.0) continue;
+                const int64_t base = c * Nnf + (int64_t)gf.Mx * (iy + (int64_t)gf.My * iz);
+                double sx = 0.0;
+                for (int ix = px - 1; ix <= px + 1; ++ix) {
+                    if (ix < 0 || ix >= gf.Mx) continue;
+                    const double wx = h_weight(ix, Jx, gf.Mx, gc.Mx);
+                    if (wx == 0.0) continue;
+                    sx += wx * (in2 ? in[base + ix] - in2[base + ix] : in[base + ix]);
+                }
+                sy += wy * sx;
+            }
+            sz += wz * sy;
+        }
+        out[o] = (ess && ess[o]) ? 0.0 : sz;
     }
 }
 
@@ -790,15 +867,19 @@ __global__ void k_rap_stencil(const double *__restrict__ fv, const uint8_t *__re
 }
 
 // y = Ainv x with a dense (coarsest-level) inverse, one thread per row
+// y = Ainv x (dense, n <= 1280): one warp per row, lane-strided partial
+// sums combined by a fixed butterfly.
 __global__ void k_dense_matvec(const double *__restrict__ Ainv, const double *__restrict__ x, double *__restrict__ y,
                                int64_t n)
 {
-    GRID_STRIDE(i, n)
-    {
-        double s2 = 0.0;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarp) {
         const double *row = Ainv + i * n;
-        for (int64_t j = 0; j < n; ++j) s2 += row[j] * x[j];
-        y[i] = s2;
+        double s2 = 0.0;
+        for (int64_t j = lane; j < n; j += 32) s2 = fma(row[j], x[j], s2);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) y[i] = s2;
     }
 }
 
@@ -1104,6 +1185,7 @@ struct pa_solver {
     // emitted; phases are separated by the operator applies, and the apply
     // that ends phase ph_target is recorded (ph_op, ph_x, ph_y) instead of
     // launched.  Off: every kernel and apply is launched as usual.
+    int64_t coarse_its = 0;  // coarse iterations of the current solve (graph mode)
     bool ph_on = false;
     int ph_target = 0, ph_counter = 0;
     pa_op *ph_op = nullptr;
@@ -1217,7 +1299,7 @@ int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
     double lam = 0.0;
     for (int it = 0; it < 10; ++it) {
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.e, n, P_DEN);
-        k_stencil_apply<<<blocks_for(n), 256, 0, st>>>(H.vals, H.e, H.t, H.ess, H.g);
+        k_stencil_apply<<<blocks_for(n), 256, 0, st>>>(H.vals, H.e, H.t, H.g);
         k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.d, H.r, H.t, nullptr, H.dinv, 0.0, 1.0, 1, n);
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.d, n, P_NUM);
         PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + P_NUM, s->dev.scal + P_NUM, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1329,6 +1411,8 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
             PA_CUDA_TRY(cudaStreamSynchronize(st));
         }
         if ((rc = dalloc(s, &C.dinv, C.n))) return rc;
+        k_mask_stencil<<<blocks_for(C.n, 128), 128, 0, st>>>(C.vals, C.ess, c);
+        PA_CUDA_TRY(cudaGetLastError());
         s->hl.push_back(C);
     }
     // work vectors, diagonals, Chebyshev intervals, coarsest inverse
@@ -1414,7 +1498,7 @@ int h_smooth(pa_solver *s, HLevel &H, bool from_zero, cudaStream_t st)
     for (int k = 0; k < s->cheb_order; ++k) {
         const double *tt = nullptr;
         if (!(k == 0 && from_zero)) {
-            k_stencil_apply<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, H.e, H.t, H.ess, H.g);
+            k_stencil_apply<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, H.e, H.t, H.g);
             tt = H.t;
         }
         double cd, cr;
@@ -1438,27 +1522,19 @@ int h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
 {
     HLevel &F = s->hl[k];
     if (k + 1 == s->hl.size()) {
-        k_dense_matvec<<<blocks_for(F.n, 64), 64, 0, st>>>(F.Ainv, F.r, F.e, F.n);
+        k_dense_matvec<<<(unsigned)((F.n * 32 + 255) / 256), 256, 0, st>>>(F.Ainv, F.r, F.e, F.n);
         PA_CUDA_TRY(cudaGetLastError());
         return PA_OK;
     }
     HLevel &C = s->hl[k + 1];
     int rc = h_smooth(s, F, true, st);
     if (rc) return rc;
-    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, F.e, F.t, F.ess, F.g);
-    // restrict r - t: x axis, y axis, z axis
-    const Grid &gf = F.g, &gc = C.g;
-    int64_t n1 = 3LL * gf.Mz * gf.My * gc.Mx, n2 = 3LL * gf.Mz * gc.My * gc.Mx, n3 = C.n;
-    k_hrestrict_axis<<<blocks_for(n1), 256, 0, st>>>(F.xa, F.r, F.t, 0, gf.Mx, gf.My, gf.Mz, gf.Mx, gc.Mx, nullptr);
-    k_hrestrict_axis<<<blocks_for(n2), 256, 0, st>>>(F.xb, F.xa, nullptr, 1, gc.Mx, gf.My, gf.Mz, gf.My, gc.My, nullptr);
-    k_hrestrict_axis<<<blocks_for(n3), 256, 0, st>>>(C.r, F.xb, nullptr, 2, gc.Mx, gc.My, gf.Mz, gf.Mz, gc.Mz, C.ess);
+    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, F.e, F.t, F.g);
+    // restrict r - t, then the coarse correction prolonged and added
+    k_hrestrict<<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
     rc = h_vcycle(s, k + 1, st);
     if (rc) return rc;
-    // prolong-add: x axis from the coarse grid, then y, then z (accumulate)
-    int64_t m1 = 3LL * gc.Mz * gc.My * gf.Mx, m2 = 3LL * gc.Mz * gf.My * gf.Mx;
-    k_hprolong_axis<<<blocks_for(m1), 256, 0, st>>>(F.xa, C.e, 0, gf.Mx, gc.My, gc.Mz, gf.Mx, gc.Mx, 0);
-    k_hprolong_axis<<<blocks_for(m2), 256, 0, st>>>(F.xb, F.xa, 1, gf.Mx, gf.My, gc.Mz, gf.My, gc.My, 0);
-    k_hprolong_axis<<<blocks_for(F.n), 256, 0, st>>>(F.e, F.xb, 2, gf.Mx, gf.My, gf.Mz, gf.Mz, gc.Mz, 1);
+    k_hprolong_add<<<blocks_for(F.n), 256, 0, st>>>(F.e, C.e, F.g, C.g);
     rc = h_smooth(s, F, false, st);
     PA_CUDA_TRY(cudaGetLastError());
     return rc;
@@ -1487,7 +1563,7 @@ int coarse_iter_hmg(pa_solver *s, Level &L, cudaStream_t st)
     HLevel &H = s->hl[0];
     int64_t nb = (n + 63) / 64;
     if (nb > kRedBlocks) nb = kRedBlocks;
-    k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->d_ess, L.op->g);
+    k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
     k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n);
     k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.r, L.cr, 1.0, n);
     int rc = h_vcycle(s, 0, st);
@@ -1646,7 +1722,7 @@ int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
         // FP64 work per row: spread the rows over the SMs (64 threads per CTA)
         int64_t nb = (n + 63) / 64;
         if (nb > kRedBlocks) nb = kRedBlocks;
-        k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->d_ess, L.op->g);
+        k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
     } else {
         int rc = op_apply_async(L.op, L.cp, L.cq, false, st, s->dev.flag + F_CDONE);
         if (rc) return rc;
@@ -1945,6 +2021,7 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
             if (r) return r;
         }
         PA_CUDA_TRY(cudaStreamSynchronize(st));
+        if (s->use_graphs) s->coarse_its += s->h_flag[F_CIT];
         return PA_OK;
     };
     rc = step(true);
@@ -1983,6 +2060,7 @@ int solve_begin(pa_solver *s, const double *b, double *x, double *bb_out, pa_sol
     const int64_t n = s->lv[0].n;
     *inf = pa_solve_info{};
     *trivial = false;
+    s->coarse_its = 0;
     for (size_t l = 0; l < s->lv.size() && l < 8; ++l) inf->lambda_max[l] = s->lv[l].lmax;
     PA_CUDA_TRY(cudaMemsetAsync(s->dev.flag, 0, sizeof(int) * NFLAG, st));
     k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, b, n, S_BB);
@@ -2021,6 +2099,7 @@ int solve_finish(pa_solver *s, double *x, int rc_loop, bool converged, double bb
     const double rr = read_scalar(s, S_RR, st);
     PA_CUDA_TRY(cudaGetLastError());
     inf->rel_residual = std::sqrt(rr / bb);
+    inf->coarse_iterations = (int)std::min<int64_t>(s->coarse_its, 0x7fffffff);
     if (status == PA_OK && !converged) status = PA_ENOTCONV;
     inf->status = status;
     if (status == PA_ENOTCONV) set_error(PA_ENOTCONV, "pa_gmg_pcg_solve: iteration cap reached");
@@ -2343,6 +2422,7 @@ int lockstep_tick(Lockstep *L)
     for (LockMember &m : L->m) {
         pa_solver *s = m.s;
         const double rr = s->h_scal[S_RR];
+        s->coarse_its += s->h_flag[F_CIT];
         if (m.started) ++m.it;
         m.started = true;
         if (s->h_flag[F_CTIMEOUT]) {
@@ -2580,10 +2660,12 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             TRY(dalloc(s, &L.cr, n));
             TRY(dalloc(s, &L.cp, n));
             TRY(dalloc(s, &L.cq, n));
-            if (L.p == 1) {
-                // assemble the coarse matrix (same quadrature as the operator)
+            if (L.p == 1 && L.op->g.Nn < (1LL << 30)) {
+                // assemble the coarse matrix (same quadrature as the operator);
+                // its kernels index nodes in 32 bits
                 TRY(dalloc(s, &L.stencil, 81 * n));
                 TRY(pa_op_assemble_p1(L.op, L.stencil, st));
+                k_mask_stencil<<<blocks_for(n, 128), 128, 0, st>>>(L.stencil, L.op->d_ess, L.op->g);
             }
         }
         if (fp32_levels) {
@@ -2682,6 +2764,7 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         // the FP64 residual (its rounding floor).
         int total_inner = 0, refine = 0;
         double rr_prev = -1.0;
+        bool inner_truncated = false;  // the last inner solve was cut short by maxit
         FcgVecs<float> v{s->x32, s->b32, s->r32, s->z32, s->p32, s->q32, true};
         while (true) {
             rc = op_apply_async(L0.op, xs, s->t, false, st, nullptr);
@@ -2697,7 +2780,7 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
                 converged = true;
                 break;
             }
-            if (rr_prev >= 0.0 && rr > 0.25 * rr_prev) {
+            if (rr_prev >= 0.0 && rr > 0.25 * rr_prev && !inner_truncated) {
                 converged = true;  // stagnation at the FP64 residual floor
                 break;
             }
@@ -2708,8 +2791,10 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
             k_scale_copy<double, float><<<blocks_for(n), 256, 0, st>>>(s->b32, s->r, sc, n);
             int it = 0;
             // inner solve: relative reduction 1e-4 or at most 50 iterations
-            rc = fcg<float>(s, v, s->g32, 1e-8, 1.0, std::min(50, maxit - total_inner), &it, st);
+            const int inner_cap = std::min(50, maxit - total_inner);
+            rc = fcg<float>(s, v, s->g32, 1e-8, 1.0, inner_cap, &it, st);
             if (rc) break;
+            inner_truncated = inner_cap < 50 && it == inner_cap;
             total_inner += it;
             ++refine;
             k_axpy<double, float><<<blocks_for(n), 256, 0, st>>>(xs, s->x32, 1.0 / sc, n);

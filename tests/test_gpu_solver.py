@@ -43,7 +43,9 @@ def test_small_beam_matches_direct_solve(pa, p, levels):
     lam, mu = syn.lame(1.0, 0.3)
     code, info, x, b, ess = _solve(pa, m, p, levels, lam, mu)
     assert code == pa.PA_OK, pa.lib.pa_last_error()
-    assert info.rel_residual <= 1e-10
+    # the stopping test is on the recursively updated residual (<= 1e-10);
+    # the true residual recomputed at exit differs from it by rounding
+    assert info.rel_residual <= 2e-10
     xo = oracle.solve_dense(p, m.nx, m.ny, m.nz, m.affine, lam, mu, b, ess)
     assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
     assert 1 <= info.iterations <= 60
