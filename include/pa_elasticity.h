@@ -132,9 +132,12 @@ int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void
 
 /* Launch shape of the fused element kernel: variant 0 (flattened
  * shared-memory sweeps, one output per thread step), 1 (register-tiled 1D
- * lines) or 2 (register-tiled lines whose X-sweep threads gather and whose
- * X^T-sweep threads store their own lines), elements per CTA, threads per
- * CTA (32..512, multiple of 32; variants 1 and 2 at most 256).
+ * lines), 2 (register-tiled lines whose X-sweep threads gather and whose
+ * X^T-sweep threads store their own lines) or 3 (as 2, with the fused Z
+ * stage run by three lanes per quadrature column, one per displacement
+ * component, exchanging gradient entries by warp shuffles: a third of the
+ * registers); elements per CTA; threads per CTA (32..512, multiple of 32;
+ * variants 1-3 at most 256; in FP64 variants 1 and 2 only for p <= 4).
  * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB. */
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);

@@ -1,14 +1,15 @@
 // Instantiations of the fused element kernels for float, p = 1..8 (q = p + 2):
 // variant 0 = flattened shared-memory sweeps, variant 1 = register-tiled lines,
-// variant 2 = register-tiled lines with the gather and store fused into the X sweeps.
+// variant 2 = register-tiled lines with the gather and store fused into the X sweeps,
+// variant 3 = variant 2 with the fused Z stage split over three lanes per column.
 #include "pa_apply.cuh"
 #include "pa_apply_line.cuh"
 
 namespace pa {
 namespace {
 
-// The register-tiled variant keeps 18 D values per thread in the fused Z
-// stage; in FP64 that fits the register file only up to D = 5.
+// Variants 1 and 2 keep 18 D values per thread in the fused Z stage; in FP64
+// that fits the register file only up to D = 5 (variant 3 keeps 6 D).
 template <int D>
 constexpr bool line_ok = sizeof(float) == 4 || D <= 5;
 
@@ -16,10 +17,8 @@ template <int D, int Q>
 size_t smem_for(const ApplyLaunch &c)
 {
     if (c.variant == 0) return flat_smem_bytes<float, D, Q>(c.epb);
-    if constexpr (line_ok<D>) {
-        if (c.threads > 256) return 0;
-        return line_smem_bytes<float, D, Q>(c.epb);
-    }
+    if (c.threads > 256) return 0;
+    if (c.variant == 3 || line_ok<D>) return line_smem_bytes<float, D, Q>(c.epb);
     return 0;
 }
 
@@ -27,18 +26,20 @@ template <int D, int Q>
 int launch_for(const ApplyArgs<float> &a, const Tables<float> &tab, const ApplyLaunch &c, cudaStream_t s)
 {
     if (c.variant == 0) return launch_flat<float, D, Q>(a, tab, c, s);
+    if (c.variant == 3) return launch_line<float, D, Q, true, true>(a, tab, c, s);
     if constexpr (line_ok<D>) return c.variant == 1 ? launch_line<float, D, Q, false>(a, tab, c, s)
                                                     : launch_line<float, D, Q, true>(a, tab, c, s);
-    return set_error(PA_EINVAL, "apply variant 1 is not instantiated for this degree and precision");
+    return set_error(PA_EINVAL, "apply variants 1 and 2 are not instantiated for this degree and precision");
 }
 
 template <int D, int Q>
 int launch_batch_for(const BatchArgs<float> &b, const Tables<float> &tab, const ApplyLaunch &c, cudaStream_t s)
 {
     if (c.variant == 0) return launch_flat_batch<float, D, Q>(b, tab, c, s);
+    if (c.variant == 3) return launch_line_batch<float, D, Q, true, true>(b, tab, c, s);
     if constexpr (line_ok<D>) return c.variant == 1 ? launch_line_batch<float, D, Q, false>(b, tab, c, s)
                                                     : launch_line_batch<float, D, Q, true>(b, tab, c, s);
-    return set_error(PA_EINVAL, "apply variant 1 is not instantiated for this degree and precision");
+    return set_error(PA_EINVAL, "apply variants 1 and 2 are not instantiated for this degree and precision");
 }
 
 }  // namespace

@@ -44,10 +44,100 @@ struct LineLayout {
     __host__ __device__ static size_t table_offset(int epb) { return (((size_t)epb * per_elem * sizeof(T)) + 15) & ~(size_t)15; }
 };
 
+__device__ __forceinline__ int sel3(int k, int x0, int x1, int x2) { return k == 0 ? x0 : (k == 1 ? x1 : x2); }
+template <typename T>
+__device__ __forceinline__ T sel3v(int k, T x0, T x1, T x2) { return k == 0 ? x0 : (k == 1 ? x1 : x2); }
+
+// The fused Z stage (Z sweep, pointwise stress of Eq. 7, Q reconstruction,
+// Z^T sweep) with one column (el, qx, qy) per three lanes: lane 10 c + k of
+// a warp holds the three channels of displacement component c of column
+// slot k (3 D inputs and 3 D accumulators instead of 9 D each), lanes 30
+// and 31 idle.  At each quadrature point the lanes of a column exchange by
+// shuffles the gradient entries the symmetric stress needs: du[c'][c] of
+// the other two components and their diagonal entries; lane c = 0 adds the
+// divergence in component order and broadcasts it.  Each lane keeps J^-1
+// with its columns rotated to the order c, c + 1, c + 2 (mod 3).
+template <typename T, int D, int Q>
+__device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int64_t e0,
+                                                int ne_blk, int tid, int nt)
+{
+    using L = LineLayout<T, D, Q>;
+    constexpr int CS = L::CS;
+    constexpr unsigned kMask = 0x3fffffffu;  // lanes 0..29
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    const int c = lane / 10, slot = lane - 10 * c;
+    if (c >= 3) return;
+    const int cn = c == 2 ? 0 : c + 1, cp = c == 0 ? 2 : c - 1;
+    const int ln = slot + 10 * cn, lp = slot + 10 * cp;
+    const int total = ne_blk * Q * Q;
+    for (int base = warp * 10; base < total; base += nwarp * 10) {
+        const int o = base + slot;
+        const bool act = o < total;
+        const int oo = act ? o : base;  // a lane past the end works on a valid column and writes nothing
+        const int el = oo / (Q * Q), col = oo - el * (Q * Q);
+        T *cpt = bufA + (size_t)el * L::A + col * CS + c * 3 * D;
+        T in[3][D];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < D; ++i) in[k][i] = cpt[k * D + i];
+        const T *geo = a.geo + (e0 + el) * kGeoStride;
+        T R[3][3];  // R[n][r] = Ji[n][(c + r) mod 3]
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            const T j0 = geo[n * 3 + 0], j1 = geo[n * 3 + 1], j2 = geo[n * 3 + 2];
+            R[n][0] = sel3v(c, j0, j1, j2);
+            R[n][1] = sel3v(cn, j0, j1, j2);
+            R[n][2] = sel3v(cp, j0, j1, j2);
+        }
+        const T cl = geo[9], cm = geo[10], m2 = cm + cm;
+        T acc[3][D];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[k][i] = T(0);
+#pragma unroll
+        for (int qz = 0; qz < Q; ++qz) {
+            T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                g0 = fma(in[0][i], tab.B[i * Q + qz], g0);
+                g1 = fma(in[1][i], tab.B[i * Q + qz], g1);
+                g2 = fma(in[2][i], tab.G[i * Q + qz], g2);
+            }
+            // du[c][(c + r) mod 3]
+            const T u0 = fma(R[0][0], g0, fma(R[1][0], g1, R[2][0] * g2));
+            const T u1 = fma(R[0][1], g0, fma(R[1][1], g1, R[2][1] * g2));
+            const T u2 = fma(R[0][2], g0, fma(R[1][2], g1, R[2][2] * g2));
+            const T from_n = __shfl_sync(kMask, u2, ln);  // du[cn][c]
+            const T from_p = __shfl_sync(kMask, u1, lp);  // du[cp][c]
+            const T dn = __shfl_sync(kMask, u0, ln), dp = __shfl_sync(kMask, u0, lp);
+            const T div = __shfl_sync(kMask, (u0 + dn) + dp, slot);  // (du00 + du11) + du22 from lane c = 0
+            const T ld = cl * div;
+            const T s0 = fma(m2, u0, ld);      // sigma[c][c]
+            const T s1 = cm * (u1 + from_n);   // sigma[c][cn]
+            const T s2 = cm * (u2 + from_p);   // sigma[c][cp]
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const T qv = fma(s0, R[m][0], fma(s1, R[m][1], s2 * R[m][2]));
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    acc[m][i] = fma(qv, (m == 2 ? tab.Gw[i * Q + qz] : tab.Bw[i * Q + qz]), acc[m][i]);
+            }
+        }
+        if (act)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int i = 0; i < D; ++i) cpt[k * D + i] = acc[k][i];
+    }
+}
+
 // FUSE: the gather is done by the X-sweep threads (one contiguous line of D
 // values each) and the X^T-sweep threads write their line of the E-vector
 // directly, instead of separate gather / store phases through shared memory.
-template <typename T, int D, int Q, bool FUSE>
+// SPLIT: the fused Z stage runs three lanes per column (z_columns_split).
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
 __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
     using L = LineLayout<T, D, Q>;
@@ -150,6 +240,8 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     __syncthreads();
 
     // ---- Z sweep + pointwise + Z^T sweep: column (el, qx, qy), in place
+    if constexpr (SPLIT) z_columns_split<T, D, Q>(a, tab, bufA, e0, ne_blk, tid, nt);
+    else
     for (int o = tid; o < ne_blk * Q * Q; o += nt) {
         int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
         T *cp = bufA + (size_t)el * L::A + col * CS;
@@ -280,20 +372,20 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     }
 }
 
-template <typename T, int D, int Q, bool FUSE>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
 __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
 {
-    line_body<T, D, Q, FUSE>(a, tab, epb, blockIdx.x);
+    line_body<T, D, Q, FUSE, SPLIT>(a, tab, epb, blockIdx.x);
 }
 
 // Several operators of the same degree and precision in one launch: CTA b
 // belongs to the operator k with cta_start[k] <= b < cta_start[k + 1].
-template <typename T, int D, int Q, bool FUSE>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
 __global__ void __launch_bounds__(256) pa_apply_line_batch_kernel(BatchArgs<T> bt, Tables<T> tab, int epb)
 {
     int k = 0;
     while (k + 1 < bt.count && (int64_t)blockIdx.x >= bt.cta_start[k + 1]) ++k;
-    line_body<T, D, Q, FUSE>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
+    line_body<T, D, Q, FUSE, SPLIT>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
 }
 
 template <typename T, int D, int Q>
@@ -302,12 +394,12 @@ size_t line_smem_bytes(int epb)
     return LineLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
 }
 
-template <typename T, int D, int Q, bool FUSE>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
 int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
     size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_line_kernel<T, D, Q, FUSE>;
+    auto kern = pa_apply_line_kernel<T, D, Q, FUSE, SPLIT>;
     static bool smem_set = false;
     if (!smem_set) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -320,11 +412,12 @@ int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
     return PA_OK;
 }
 
-template <typename T, int D, int Q, bool FUSE>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
 int launch_line_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
+    if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
     const size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE>;
+    auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE, SPLIT>;
     static bool smem_set = false;
     if (!smem_set) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

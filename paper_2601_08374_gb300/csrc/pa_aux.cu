@@ -77,6 +77,76 @@ __device__ __forceinline__ void assemble_node(const T *__restrict__ ye, T *__res
     }
 }
 
+// The same node sum specialised on the degree, with 32-bit node arithmetic
+// (grids of fewer than 2^31 nodes): the divisions by p and by the grid
+// extents are the costly part of a node's work.  Same additions in the same
+// order as assemble_node.
+template <typename T, int P>
+__device__ __forceinline__ void assemble_node_p(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
+                                                const uint8_t *__restrict__ ess, T ess_value, int accumulate,
+                                                const Grid &g, int gn)
+{
+    constexpr int D = P + 1, D3 = D * D * D;
+    const int t = gn / g.Mx;
+    const int gi[3] = {gn - t * g.Mx, t % g.My, t / g.My};
+    const int ne[3] = {g.nx, g.ny, g.nz};
+    int e[3][2], li[3][2], cnt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int k = gi[a] / P, r = gi[a] - k * P;
+        cnt[a] = 0;
+        if (r == 0) {
+            if (k - 1 >= 0) { e[a][cnt[a]] = k - 1; li[a][cnt[a]] = P; ++cnt[a]; }
+            if (k < ne[a]) { e[a][cnt[a]] = k; li[a][cnt[a]] = 0; ++cnt[a]; }
+        } else {
+            e[a][0] = k;
+            li[a][0] = r;
+            cnt[a] = 1;
+        }
+    }
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+    for (int c = 0; c < cnt[2]; ++c)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int a = 0; a < cnt[0]; ++a) {
+                const int el = e[0][a] + g.nx * (e[1][b] + g.ny * e[2][c]);
+                const int loc = li[0][a] + D * (li[1][b] + D * li[2][c]);
+                const T *base = ye + (int64_t)el * (3 * D3) + loc;
+                acc0 += base[0];
+                acc1 += base[D3];
+                acc2 += base[2 * D3];
+            }
+    T acc[3] = {acc0, acc1, acc2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int64_t k = c * g.Nn + gn;
+        T v = acc[c];
+        if (ess && ess[k]) v = xin ? xin[k] : ess_value;
+        y[k] = accumulate ? y[k] + v : v;
+    }
+}
+
+template <typename T, int P>
+__global__ void assemble_kernel_p(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
+                                  const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g,
+                                  const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const int n = (int)g.Nn;
+    for (int gn = blockIdx.x * blockDim.x + threadIdx.x; gn < n; gn += gridDim.x * blockDim.x)
+        assemble_node_p<T, P>(ye, y, xin, ess, ess_value, accumulate, g, gn);
+}
+
+template <typename T, int P>
+__global__ void assemble_batch_kernel_p(AssembleBatch<T> b)
+{
+    const int64_t total = b.node_start[b.count];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < b.count && t >= b.node_start[k + 1]) ++k;
+        assemble_node_p<T, P>(b.ye[k], b.y[k], b.x[k], b.ess[k], T(0), 0, b.g[k], (int)(t - b.node_start[k]));
+    }
+}
+
 template <typename T>
 __global__ void assemble_kernel(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
                                 const uint8_t *__restrict__ ess, T ess_value, int accumulate, Grid g,
@@ -100,11 +170,30 @@ __global__ void assemble_batch_kernel(AssembleBatch<T> b)
     }
 }
 
+constexpr int64_t kNode32 = (int64_t)1 << 31;
+
 template <typename T>
 int launch_assemble_batch(const AssembleBatch<T> &b, cudaStream_t s)
 {
     const int th = 256;
-    assemble_batch_kernel<T><<<grid_for(b.node_start[b.count], th), th, 0, s>>>(b);
+    const unsigned nb = grid_for(b.node_start[b.count], th);
+    bool same_p = true, small = true;
+    for (int k = 0; k < b.count; ++k) {
+        same_p = same_p && b.g[k].p == b.g[0].p;
+        small = small && b.g[k].Nn < kNode32;
+    }
+    if (b.count > 0 && same_p && small) {
+        switch (b.g[0].p) {
+#define PA_ASM_BATCH(P) \
+    case P: assemble_batch_kernel_p<T, P><<<nb, th, 0, s>>>(b); break;
+            PA_ASM_BATCH(1) PA_ASM_BATCH(2) PA_ASM_BATCH(3) PA_ASM_BATCH(4)
+            PA_ASM_BATCH(5) PA_ASM_BATCH(6) PA_ASM_BATCH(7) PA_ASM_BATCH(8)
+#undef PA_ASM_BATCH
+        default: assemble_batch_kernel<T><<<nb, th, 0, s>>>(b);
+        }
+    } else {
+        assemble_batch_kernel<T><<<nb, th, 0, s>>>(b);
+    }
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -116,7 +205,19 @@ int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_v
                     const Grid &g, cudaStream_t s, const int *skip)
 {
     const int th = 256;
-    assemble_kernel<T><<<grid_for(g.Nn, th), th, 0, s>>>(ye, y, xin, ess, ess_value, accumulate ? 1 : 0, g, skip);
+    const unsigned nb = grid_for(g.Nn, th);
+    const int acc = accumulate ? 1 : 0;
+    if (g.Nn < kNode32) {
+        switch (g.p) {
+#define PA_ASM(P) \
+    case P: assemble_kernel_p<T, P><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip); break;
+            PA_ASM(1) PA_ASM(2) PA_ASM(3) PA_ASM(4) PA_ASM(5) PA_ASM(6) PA_ASM(7) PA_ASM(8)
+#undef PA_ASM
+        default: assemble_kernel<T><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip);
+        }
+    } else {
+        assemble_kernel<T><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip);
+    }
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }

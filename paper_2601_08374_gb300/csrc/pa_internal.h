@@ -66,9 +66,10 @@ struct Grid {
 };
 
 // --------------------------------------------------------- apply launch --
-constexpr int kMaxVariant = 2;
+constexpr int kMaxVariant = 3;
 struct ApplyLaunch {
-    int variant = 0;  // 0: flattened smem sweeps, 1: register-tiled lines, 2: lines + fused gather/store
+    int variant = 0;  // 0: flattened smem sweeps, 1: register-tiled lines, 2: lines + fused gather/store,
+                      // 3: as 2 with the Z stage split over three lanes per column
     int epb = 1;      // elements per CTA
     int threads = 256;
 };

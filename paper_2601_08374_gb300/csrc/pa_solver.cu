@@ -31,7 +31,11 @@ namespace pa {
 namespace {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 2 * 152;
+// Reductions: up to 8 CTAs of 256 threads per SM, enough loads in flight to
+// stream HBM; the persistent coarse CG keeps to 2 CTAs per SM (its grid
+// barriers cost more with more CTAs).
+constexpr int kRedBlocks = 8 * 152;
+constexpr int kCoopBlocks = 2 * 152;
 
 // device scalar slots
 enum Slot {
@@ -2610,7 +2614,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_coop, 256, 0) == cudaSuccess)
-            s->coop_blocks = std::min(kRedBlocks, per_sm * nsm);
+            s->coop_blocks = std::min(kCoopBlocks, per_sm * nsm);
         cudaGetLastError();
     }
 
