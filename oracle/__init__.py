@@ -47,6 +47,12 @@ def _lib():
     lib.orc_apply.argtypes = common + [_dp, _dp, ctypes.c_int]
     lib.orc_apply_rows.argtypes = common + [_dp, ctypes.c_int64, _i64p, _dp, ctypes.c_int]
     lib.orc_diag.argtypes = common + [_dp, ctypes.c_int]
+    common_m = common[:7] + [_dp, _u8p]
+    lib.orc_apply_m.argtypes = common_m + [_dp, _dp, ctypes.c_int]
+    lib.orc_apply_rows_m.argtypes = common_m + [_dp, ctypes.c_int64, _i64p, _dp, ctypes.c_int]
+    lib.orc_diag_m.argtypes = common_m + [_dp, ctypes.c_int]
+    lib.orc_traction.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                 _u8p, _dp]
     lib.orc_load.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                              ctypes.c_int, _dp, _u8p, _dp, ctypes.c_int]
     lib.orc_prolong.argtypes = [ctypes.c_int] * 5 + [_dp, _dp]
@@ -162,8 +168,19 @@ def _check_mesh(nx, ny, nz, affine):
     return affine
 
 
-def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0):
-    """y = A x (constrained operator when ``ess`` is given)."""
+def _material(mat, ne):
+    """Per-element material [ne, 2] = (lambda_e, mu_e), or None."""
+    if mat is None:
+        return None
+    mat = _f64(mat)
+    if mat.shape != (ne, 2):
+        raise ValueError("material must be [ne, 2] (lambda_e, mu_e)")
+    return mat
+
+
+def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0, mat=None):
+    """y = A x (constrained operator when ``ess`` is given).  ``mat``: per
+    element (lambda_e, mu_e) [ne, 2] in place of the constants lam, mu."""
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
     x = _f64(x)
@@ -172,14 +189,15 @@ def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0):
         raise ValueError("x has wrong length")
     y = np.zeros(N)
     m = _mask(ess)
-    rc = _lib().orc_apply(r._h, nx, ny, nz, _d(affine), lam, mu,
-                          m.ctypes.data_as(_u8p) if m is not None else None, _d(x), _d(y), nthreads)
+    mt = _material(mat, nx * ny * nz)
+    rc = _lib().orc_apply_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+                            m.ctypes.data_as(_u8p) if m is not None else None, _d(x), _d(y), nthreads)
     if rc:
         raise RuntimeError(f"orc_apply failed ({rc})")
     return y
 
 
-def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=0):
+def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=0, mat=None):
     """Selected entries (L-vector indices ``rows``) of y = A x."""
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
@@ -187,21 +205,23 @@ def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.zeros(len(rows))
     m = _mask(ess)
-    rc = _lib().orc_apply_rows(r._h, nx, ny, nz, _d(affine), lam, mu,
-                               m.ctypes.data_as(_u8p) if m is not None else None, _d(x),
-                               len(rows), rows.ctypes.data_as(_i64p), _d(out), nthreads)
+    mt = _material(mat, nx * ny * nz)
+    rc = _lib().orc_apply_rows_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+                                 m.ctypes.data_as(_u8p) if m is not None else None, _d(x),
+                                 len(rows), rows.ctypes.data_as(_i64p), _d(out), nthreads)
     if rc:
         raise RuntimeError(f"orc_apply_rows failed ({rc})")
     return out
 
 
-def diag(p, nx, ny, nz, affine, lam, mu, ess=None, q=0, nthreads=0):
+def diag(p, nx, ny, nz, affine, lam, mu, ess=None, q=0, nthreads=0, mat=None):
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
     d = np.zeros(3 * n_nodes(nx, ny, nz, p))
     m = _mask(ess)
-    rc = _lib().orc_diag(r._h, nx, ny, nz, _d(affine), lam, mu,
-                         m.ctypes.data_as(_u8p) if m is not None else None, _d(d), nthreads)
+    mt = _material(mat, nx * ny * nz)
+    rc = _lib().orc_diag_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+                           m.ctypes.data_as(_u8p) if m is not None else None, _d(d), nthreads)
     if rc:
         raise RuntimeError(f"orc_diag failed ({rc})")
     return d
@@ -224,6 +244,20 @@ def load(p, nx, ny, nz, affine, f0=(0.0, 0.0, 0.0), modes=None, ess=None, q=0, n
                          m.ctypes.data_as(_u8p) if m is not None else None, _d(F), nthreads)
     if rc:
         raise RuntimeError(f"orc_load failed ({rc})")
+    return F
+
+
+def traction(p, nx, ny, nz, affine, face, t, ess=None, q=0):
+    """Load vector of a constant traction ``t`` (3,) on one face of the box:
+    face = 2 * axis + side (axis x/y/z = 0/1/2, side 0 = low, 1 = high)."""
+    r = ref(p, q)
+    affine = _check_mesh(nx, ny, nz, affine)
+    F = np.zeros(3 * n_nodes(nx, ny, nz, p))
+    m = _mask(ess)
+    rc = _lib().orc_traction(r._h, nx, ny, nz, _d(affine), int(face), _d(_f64(t).reshape(3)),
+                             m.ctypes.data_as(_u8p) if m is not None else None, _d(F))
+    if rc:
+        raise RuntimeError(f"orc_traction failed ({rc})")
     return F
 
 
@@ -261,9 +295,9 @@ def node_coords_box(nx, ny, nz, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
 
 
-def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0):
+def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0, mat=None):
     """Global (unconstrained) stiffness matrix of a small mesh, assembled
-    from the oracle's element matrices."""
+    from the oracle's element matrices (``mat``: per-element material)."""
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
     D = p + 1
@@ -277,7 +311,8 @@ def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0):
         ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
         gn = (ex * p + ix) + Mx * ((ey * p + iy) + My * (ez * p + iz))
         dofs = np.concatenate([c * Nn + gn for c in range(3)])
-        A[np.ix_(dofs, dofs)] += r.element_matrix(affine[e, :9], lam, mu)
+        le, me = (lam, mu) if mat is None else (float(mat[e][0]), float(mat[e][1]))
+        A[np.ix_(dofs, dofs)] += r.element_matrix(affine[e, :9], le, me)
     return A
 
 
@@ -291,7 +326,7 @@ def constrain_dense(A, ess):
     return Ac
 
 
-def solve_dense(p, nx, ny, nz, affine, lam, mu, b, ess, q=0):
+def solve_dense(p, nx, ny, nz, affine, lam, mu, b, ess, q=0, mat=None):
     """Direct FP64 solve of the constrained system (small meshes only)."""
-    A = constrain_dense(assemble_dense(p, nx, ny, nz, affine, lam, mu, q), ess)
+    A = constrain_dense(assemble_dense(p, nx, ny, nz, affine, lam, mu, q, mat=mat), ess)
     return np.linalg.solve(A, _f64(b))

@@ -142,14 +142,17 @@ def element_matrix(p, J, lam, mu):
 
 def global_matrix(p, nx, J_list, lam, mu):
     """Exact assembled matrix of an nx*1*1 row of elements (component-major
-    L-vector, node index x fastest), one exact J per element."""
+    L-vector, node index x fastest), one exact J per element; lam and mu are
+    numbers or one value per element."""
     D = p + 1
     D3 = D ** 3
     Mx, My = nx * p + 1, p + 1
     Nn = Mx * My * (p + 1)
     A = [[Fr(0)] * (3 * Nn) for _ in range(3 * Nn)]
     for e in range(nx):
-        Ke = element_matrix(p, J_list[e], lam, mu)
+        le = lam[e] if isinstance(lam, (list, tuple)) else lam
+        me = mu[e] if isinstance(mu, (list, tuple)) else mu
+        Ke = element_matrix(p, J_list[e], le, me)
         dofs = []
         for c in range(3):
             for a in range(D3):

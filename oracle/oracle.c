@@ -411,8 +411,23 @@ int orc_max_threads(void)
 /* y = A x for the whole mesh (constrained if ess != NULL).  Element results
  * are kept per element and summed node by node in a fixed order, so the
  * result does not depend on the thread count.                              */
+/* mat: per-element material, (lambda_e, mu_e) at mat[2e], mat[2e+1], or
+ * NULL for the constant (lambda, mu) -- the paper's PA data D holds the
+ * material per quadrature point, lambda(alpha, e) and mu(alpha, e)
+ * (Sec. 4.5); for material constant on each element that is this array.   */
+int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+                double lambda, double mu, const double *mat, const uint8_t *ess, const double *x, double *y,
+                int nthreads);
+
 int orc_apply(const orc_ref *r, int nx, int ny, int nz, const double *affine,
               double lambda, double mu, const uint8_t *ess, const double *x, double *y, int nthreads)
+{
+    return orc_apply_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, x, y, nthreads);
+}
+
+int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+                double lambda, double mu, const double *mat, const uint8_t *ess, const double *x, double *y,
+                int nthreads)
 {
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     grid_t g = make_grid(nx, ny, nz, r->p);
@@ -428,7 +443,8 @@ int orc_apply(const orc_ref *r, int nx, int ny, int nz, const double *affine,
         double C[81];
 #pragma omp for schedule(dynamic, 16)
         for (int64_t e = 0; e < g.ne; ++e) {
-            if (orc_element_coeff(affine + 12 * e, lambda, mu, C, NULL)) { bad = 1; continue; }
+            const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
+            if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
             for (int iz = 0; iz < D; ++iz)
                 for (int iy = 0; iy < D; ++iy)
                     for (int ix = 0; ix < D; ++ix) {
@@ -478,9 +494,20 @@ int orc_apply(const orc_ref *r, int nx, int ny, int nz, const double *affine,
 
 /* Selected entries of y = A x (rows are L-vector indices), computed one by
  * one from the rows of the contributing element matrices.                  */
+int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+                     double lambda, double mu, const double *mat, const uint8_t *ess, const double *x,
+                     int64_t nrows, const int64_t *rows, double *yrows, int nthreads);
+
 int orc_apply_rows(const orc_ref *r, int nx, int ny, int nz, const double *affine,
                    double lambda, double mu, const uint8_t *ess, const double *x,
                    int64_t nrows, const int64_t *rows, double *yrows, int nthreads)
+{
+    return orc_apply_rows_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, x, nrows, rows, yrows, nthreads);
+}
+
+int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+                     double lambda, double mu, const double *mat, const uint8_t *ess, const double *x,
+                     int64_t nrows, const int64_t *rows, double *yrows, int nthreads)
 {
     grid_t g = make_grid(nx, ny, nz, r->p);
     int D = g.D, D3 = r->D3, p = g.p;
@@ -505,7 +532,8 @@ int orc_apply_rows(const orc_ref *r, int nx, int ny, int nz, const double *affin
                     int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
                     int a = ix + D * (iy + D * iz);
                     double C[81];
-                    if (orc_element_coeff(affine + 12 * e, lambda, mu, C, NULL)) { bad = 1; continue; }
+                    const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
+                    if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
                     for (int bz = 0; bz < D; ++bz)
                         for (int by = 0; by < D; ++by)
                             for (int bx = 0; bx < D; ++bx) {
@@ -530,8 +558,17 @@ int orc_apply_rows(const orc_ref *r, int nx, int ny, int nz, const double *affin
 
 /* Diagonal of the (constrained) assembled matrix: sum over elements of the
  * element-matrix diagonal; essential entries are 1.                        */
+int orc_diag_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+               double lambda, double mu, const double *mat, const uint8_t *ess, double *dg, int nthreads);
+
 int orc_diag(const orc_ref *r, int nx, int ny, int nz, const double *affine,
              double lambda, double mu, const uint8_t *ess, double *dg, int nthreads)
+{
+    return orc_diag_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, dg, nthreads);
+}
+
+int orc_diag_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
+               double lambda, double mu, const double *mat, const uint8_t *ess, double *dg, int nthreads)
 {
     grid_t g = make_grid(nx, ny, nz, r->p);
     int D = g.D, D3 = r->D3, p = g.p;
@@ -551,7 +588,8 @@ int orc_diag(const orc_ref *r, int nx, int ny, int nz, const double *affine,
                     int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
                     int a = ix + D * (iy + D * iz);
                     double C[81];
-                    if (orc_element_coeff(affine + 12 * e, lambda, mu, C, NULL)) { bad = 1; continue; }
+                    const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
+                    if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
                     for (int c = 0; c < 3; ++c)
                         for (int mn = 0; mn < 9; ++mn)
                             acc[c] += r->S[((size_t)mn * D3 + a) * D3 + a] * C[(mn * 3 + c) * 3 + c];
@@ -645,6 +683,70 @@ int orc_load(const orc_ref *r, int nx, int ny, int nz, const double *affine, con
         }
     }
     free(fe_all);
+    return 0;
+}
+
+/* Neumann load of a constant traction t on one face of the box (Eq. 1: the
+ * boundary term integral over Gamma_N of t . v):
+ *   F_(i,c) += sum over the boundary faces of the elements on that face of
+ *              sum_(a,b) w_a w_b |dx/du x dx/dv| t_c Phi_i(face point),
+ * face = 2 * axis + side (axis 0/1/2 = x/y/z, side 0 = low, 1 = high); the
+ * face of an element is its reference face xi_axis = side, parametrised by
+ * the two other reference coordinates (u, v) in increasing axis order, and
+ * integrated with the q-point Gauss rule in each; the surface factor is the
+ * norm of the cross product of the two corresponding columns of J.  The
+ * basis is evaluated at the face points in full (no use of the nodal
+ * property).  Contributions are added element by element in increasing
+ * element order; essential entries are set to 0 afterwards.               */
+int orc_traction(const orc_ref *r, int nx, int ny, int nz, const double *affine, int face, const double *t,
+                 const uint8_t *ess, double *F)
+{
+    if (face < 0 || face > 5) return -1;
+    grid_t g = make_grid(nx, ny, nz, r->p);
+    const int D = g.D, Q = r->Q, D3 = r->D3;
+    const int ax = face / 2, side = face % 2;
+    const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;  /* the two tangential axes, increasing */
+    const int n3[3] = {nx, ny, nz};
+    double side_pt = (double)side, lv[64], ld_[64];
+    orc_lagrange(D, r->gll, 1, &side_pt, lv, ld_);      /* basis along the normal axis at the face */
+    double *fe = (double *)malloc(sizeof(double) * 3 * D3);
+    if (!fe) return -2;
+    for (int64_t e = 0; e < g.ne; ++e) {
+        const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+        const int64_t ei[3] = {ex, ey, ez};
+        if (ei[ax] != (side ? n3[ax] - 1 : 0)) continue;
+        const double *J = affine + 12 * e;
+        /* columns b and c of J: dx/du and dx/dv */
+        const double u[3] = {J[0 * 3 + bx], J[1 * 3 + bx], J[2 * 3 + bx]};
+        const double v[3] = {J[0 * 3 + cx], J[1 * 3 + cx], J[2 * 3 + cx]};
+        const double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        const double ds = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        memset(fe, 0, sizeof(double) * 3 * D3);
+        for (int iz = 0; iz < D; ++iz)
+            for (int iy = 0; iy < D; ++iy)
+                for (int ix = 0; ix < D; ++ix) {
+                    const int il[3] = {ix, iy, iz};
+                    double s = 0.0;
+                    for (int qb = 0; qb < Q; ++qb)
+                        for (int qa = 0; qa < Q; ++qa) {
+                            double phi = lv[il[ax]] * r->B[il[bx] * Q + qa] * r->B[il[cx] * Q + qb];
+                            s += r->gw[qa] * r->gw[qb] * ds * phi;
+                        }
+                    const int a = ix + D * (iy + D * iz);
+                    for (int c = 0; c < 3; ++c) fe[c * D3 + a] = t[c] * s;
+                }
+        for (int iz = 0; iz < D; ++iz)
+            for (int iy = 0; iy < D; ++iy)
+                for (int ix = 0; ix < D; ++ix) {
+                    const int a = ix + D * (iy + D * iz);
+                    const int64_t gn = node_of(&g, e, ix, iy, iz);
+                    for (int c = 0; c < 3; ++c) F[c * g.Nn + gn] += fe[c * D3 + a];
+                }
+    }
+    free(fe);
+    if (ess)
+        for (int64_t k = 0; k < 3 * g.Nn; ++k)
+            if (ess[k]) F[k] = 0.0;
     return 0;
 }
 

@@ -407,3 +407,81 @@ def test_dense_solve_residual():
     r = b - oracle.apply(p, 2, 1, 1, m.affine, lam, mu, x, ess=ess)
     assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(b)
     assert x[ess.astype(bool)].max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# Per-element material (the PA data D with lambda(alpha, e), mu(alpha, e),
+# Sec. 4.5, constant on each element) and the Neumann traction load (Eq. 1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("p", [1, 2])
+def test_per_element_material_exact(p):
+    """Two elements with contrasting materials (a 50:1 contrast as in the
+    paper's two-material beam) against the exact-rational brute force; pins
+    that element e takes material e."""
+    lam, mu = [Fr(50), Fr(1)], [Fr(50), Fr(1)]
+    Ax = np.array(exact.global_matrix(p, 2, [J_RAT, J_RAT2], lam, mu), dtype=float)
+    aff = np.zeros((2, 12))
+    aff[0, :9] = np.array(J_RAT, dtype=float).reshape(9)
+    aff[1, :9] = np.array(J_RAT2, dtype=float).reshape(9)
+    mat = np.array([[50.0, 50.0], [1.0, 1.0]])
+    x = np.random.default_rng(1).uniform(-1, 1, Ax.shape[0])
+    y = oracle.apply(p, 2, 1, 1, aff, 0.0, 0.0, x, mat=mat)
+    scale = np.abs(Ax).max()
+    assert np.max(np.abs(y - Ax @ x)) <= 1e-12 * scale
+    # the swapped assignment is a different operator
+    y2 = oracle.apply(p, 2, 1, 1, aff, 0.0, 0.0, x, mat=mat[::-1].copy())
+    assert np.max(np.abs(y2 - Ax @ x)) > 1e-3 * scale
+    # diagonal and selected rows with the same material
+    d = oracle.diag(p, 2, 1, 1, aff, 0.0, 0.0, mat=mat)
+    assert np.max(np.abs(d - np.diag(Ax))) <= 1e-12 * scale
+    rows = np.arange(0, Ax.shape[0], 5)
+    yr = oracle.apply_rows(p, 2, 1, 1, aff, 0.0, 0.0, x, rows, mat=mat)
+    assert np.max(np.abs(yr - (Ax @ x)[rows])) <= 1e-12 * scale
+
+
+def test_uniform_material_array_is_the_constant_material():
+    p, n = 3, 2
+    m = syn.random_affine_cube(n, seed=11)
+    x = syn.uniform_vector(m.n_dofs(p), seed=3)
+    mat = np.tile([1.7, 0.6], (m.ne, 1))
+    assert np.array_equal(oracle.apply(p, n, n, n, m.affine, 1.7, 0.6, x),
+                          oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, x, mat=mat))
+
+
+@pytest.mark.parametrize("p", [1, 3, 4])
+@pytest.mark.parametrize("face", [1, 4])
+def test_traction_totals_are_the_surface_integrals(p, face):
+    """Sum_i F_(i,c) = t_c |Gamma| (the basis sums to 1) and Sum_i F_(i,c)
+    y_i = t_c * integral of y over the face (linear fields are reproduced), on
+    a box [0,8] x [0,1] x [0,2] with uneven elements along the face."""
+    nx, ny, nz = 3, 2, 2
+    lo, hi = (0.0, 0.0, 0.0), (8.0, 1.0, 2.0)
+    aff = oracle.box_affine(nx, ny, nz, lo, hi)
+    t = np.array([0.3, -0.2, -1e-2])
+    F = oracle.traction(p, nx, ny, nz, aff, face, t)
+    X = oracle.node_coords_box(nx, ny, nz, p, lo, hi)
+    Nn = X.shape[0]
+    ax = face // 2
+    others = [a for a in range(3) if a != ax]
+    area = (hi[others[0]] - lo[others[0]]) * (hi[others[1]] - lo[others[1]])
+    for c in range(3):
+        Fc = F[c * Nn:(c + 1) * Nn]
+        assert abs(Fc.sum() - t[c] * area) <= 1e-13 * area
+        for a in others:  # first moments: centroid of the face along a
+            centroid = 0.5 * (lo[a] + hi[a])
+            assert abs((Fc * X[:, a]).sum() - t[c] * area * centroid) <= 1e-12 * area * hi[a]
+        # only nodes on the face are loaded
+        on_face = np.isclose(X[:, ax], hi[ax] if face % 2 else lo[ax])
+        assert np.all(Fc[~on_face] == 0.0)
+
+
+def test_traction_on_a_sheared_face_uses_the_surface_measure():
+    """One element whose x = 1 face is mapped to a parallelogram: the total
+    force is t times the parallelogram's area |u x v|."""
+    J = np.array([[2.0, 0.0, 0.0], [0.3, 1.5, 0.0], [0.0, 0.4, 0.8]])
+    aff = np.zeros((1, 12))
+    aff[0, :9] = J.reshape(9)
+    F = oracle.traction(2, 1, 1, 1, aff, 1, (0.0, 0.0, 1.0))
+    area = np.linalg.norm(np.cross(J[:, 1], J[:, 2]))
+    Nn = 27
+    assert abs(F[2 * Nn:].sum() - area) <= 1e-14 * area
