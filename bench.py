@@ -333,8 +333,13 @@ def run_solves(args, pa, torch):
     dofs, p = 6 and 8, FP64 and mixed).  Setup (operators, diagonals,
     eigenvalue estimates, graph capture on the first solve) is untimed."""
     out = []
-    cases = [dict(name="beam 32x4x4 p=4 (4->2->1) E=1 nu=0.3 f=(0,0,-1), x=0 clamped", mesh=syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0)),
-                  p=4, levels=[4, 2, 1], nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
+    beam = syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0))
+    cases = [dict(name="beam 32x4x4 p=4 (4->2->1) E=1 nu=0.3 f=(0,0,-1), x=0 clamped", mesh=beam,
+                  p=4, levels=[4, 2, 1], nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps),
+             dict(name="two-material beam 32x4x4 p=4 (4->2->1): lambda=mu=50 for x<4, lambda=mu=1 beyond; "
+                       "traction (0,0,-1e-2) on x=8, x=0 clamped (the paper's benchmark physics)", mesh=beam,
+                  p=4, levels=[4, 2, 1], nu=None, mat=syn.two_material(beam, 4.0), modes=None, f0=(0.0, 0.0, 0.0),
+                  traction=(1, (0.0, 0.0, -1e-2)), reps=args.solve_reps)]
     if not args.quick_solves:
         for p, n in ((6, syn.mixed_n(6)), (8, syn.mixed_n(8))):
             lv = [p, p // 2, 1] if p == 6 else [8, 4, 2, 1]
@@ -343,10 +348,10 @@ def run_solves(args, pa, torch):
                               modes=syn.smooth_force_modes(seed=3100 + p), f0=(0.0, 0.0, 0.0), reps=max(1, args.solve_reps // 2)))
     for c in cases:
         m, p = c["mesh"], c["p"]
-        lam, mu = syn.lame(1.0, c["nu"])
+        lam, mu = syn.lame(1.0, c["nu"]) if c["nu"] is not None else (0.0, 0.0)
         ess = syn.clamp_mask(m, p)
-        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
-        b = op.rhs(f0=c["f0"], modes=c["modes"])
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess, mat=c.get("mat"))
+        b = op.rhs(f0=c["f0"], modes=c["modes"], traction=c.get("traction"))
         row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "rtol": 1e-10}
         sols = {}
         for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):

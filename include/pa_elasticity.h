@@ -130,6 +130,24 @@ int pa_op_diag(pa_op *op, void *d, void *stream);
  * Essential entries are set to 0.  F: device L-vector of the op's precision. */
 int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void *F, void *stream);
 
+/* Per-element material (the PA data D of Sec. 4.5 with lambda(alpha, e),
+ * mu(alpha, e) constant on each element, e.g. the paper's two-material
+ * beam): lambda_mu = host double[ne][2] (lambda_e, mu_e), element order
+ * e = ex + nx (ey + ny ez); NULL restores the operator's constant (lambda,
+ * mu).  Rewrites the element geometry records (lambda_e detJ, mu_e detJ) on
+ * the device; solvers created afterwards build their coarse levels with the
+ * same material.  Synchronous.  PA_EINVAL on non-finite values. */
+int pa_op_set_material(pa_op *op, const double *lambda_mu);
+
+/* Adds the load of a constant traction t (host double[3]) on one face of
+ * the box to F (device L-vector of the op's precision): the Neumann term of
+ * the weak form, integral over the face of t . v (Eq. 1), with the op's
+ * Gauss rule on each element face and the surface measure of the element's
+ * affine map.  face = 2 * axis + side: 0 x = lo, 1 x = hi, 2 y = lo, 3 y = hi,
+ * 4 z = lo, 5 z = hi.  Essential entries of F are set to 0.  Asynchronous on
+ * `stream`. */
+int pa_op_traction(pa_op *op, int face, const double *t, void *F, void *stream);
+
 /* Launch shape of the fused element kernel: variant 0 (flattened
  * shared-memory sweeps, one output per thread step), 1 (register-tiled 1D
  * lines), 2 (register-tiled lines whose X-sweep threads gather and whose

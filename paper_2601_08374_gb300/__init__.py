@@ -82,6 +82,8 @@ _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp])
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
+_sig("pa_op_set_material", [_vp, _dp])
+_sig("pa_op_traction", [_vp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
 _sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_op_restrict", [_vp, _vp, _vp, _vp, _vp])
@@ -241,6 +243,21 @@ def pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, affine, x, y, ess_mask=N
                                 _stream_ptr(stream)), "pa_apply_noalloc")
 
 
+def pa_op_set_material(op, mat):
+    """Per-element material, [ne, 2] (lambda_e, mu_e); None restores the constant one."""
+    if mat is None:
+        _check(lib.pa_op_set_material(op, None), "pa_op_set_material")
+        return
+    m = np.ascontiguousarray(mat, dtype=np.float64)
+    _check(lib.pa_op_set_material(op, m.ctypes.data_as(_dp)), "pa_op_set_material")
+
+
+def pa_op_traction(op, face, t, F, stream=None):
+    tt = np.ascontiguousarray(t, dtype=np.float64).reshape(3)
+    _check(lib.pa_op_traction(op, int(face), tt.ctypes.data_as(_dp), _tptr(F), _stream_ptr(stream)),
+           "pa_op_traction")
+
+
 def pa_op_set_launch(op, variant, elems_per_block, threads):
     _check(lib.pa_op_set_launch(op, variant, elems_per_block, threads), "pa_op_set_launch")
 
@@ -382,7 +399,7 @@ def pa_server_destroy(srv):
 class Operator:
     """Owns a mesh + operator handle; vectors are torch CUDA tensors."""
 
-    def __init__(self, nx, ny, nz, affine, p, lam, mu, precision=PA_FP64, ess_mask=None, q=0):
+    def __init__(self, nx, ny, nz, affine, p, lam, mu, precision=PA_FP64, ess_mask=None, q=0, mat=None):
         import torch
         self._mesh = pa_mesh_create(nx, ny, nz, affine=affine)
         try:
@@ -392,6 +409,8 @@ class Operator:
             self._mesh = None
         self.ndofs, self.nelem, self.p, self.precision = pa_op_info(self.h)
         self.dtype = torch.float64 if precision == PA_FP64 else torch.float32
+        if mat is not None:
+            pa_op_set_material(self.h, mat)
 
     def close(self):
         if getattr(self, "h", None):
@@ -416,7 +435,11 @@ class Operator:
         pa_op_diag(self.h, d, stream)
         return d
 
-    def rhs(self, f0=(0.0, 0.0, 0.0), modes=None, stream=None):
+    def rhs(self, f0=(0.0, 0.0, 0.0), modes=None, stream=None, traction=None):
+        """Load vector of the body force; ``traction`` = (face, t) adds a
+        constant traction on one box face."""
         F = self.empty()
         pa_op_rhs(self.h, F, f0, modes, stream)
+        if traction is not None:
+            pa_op_traction(self.h, traction[0], traction[1], F, stream)
         return F

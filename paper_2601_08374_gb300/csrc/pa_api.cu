@@ -50,6 +50,37 @@ static void inverse3(const double *J, double det, double *Ji)
     Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
 }
 
+// Geometry records of every element from the host copies of the maps and
+// of the material: J^-1 (row-major), lambda_e detJ, mu_e detJ, detJ
+// (constant per affine element, Sec. 4.4; material constant per element,
+// the PA data D of Sec. 4.5), uploaded in the operator's precision.
+int upload_geometry(pa_op *op)
+{
+    const Grid &g = op->g;
+    const size_t geo_bytes = (size_t)g.ne * kGeoStride * op->elem;
+    std::vector<unsigned char> geo;
+    try {
+        geo.resize(geo_bytes);
+    } catch (...) {
+        return set_error(PA_ENOMEM, "geometry records: host allocation");
+    }
+    for (int64_t e = 0; e < g.ne; ++e) {
+        const double *J = op->h_affine.data() + 12 * e;
+        double det = det3(J), Ji[9];
+        inverse3(J, det, Ji);
+        const double lam = op->h_mat.empty() ? op->lambda : op->h_mat[2 * e];
+        const double mu = op->h_mat.empty() ? op->mu : op->h_mat[2 * e + 1];
+        double rec[kGeoStride] = {Ji[0], Ji[1], Ji[2], Ji[3], Ji[4], Ji[5], Ji[6], Ji[7], Ji[8],
+                                  lam * det, mu * det, det};
+        for (int k = 0; k < kGeoStride; ++k) {
+            if (op->precision == PA_FP64) reinterpret_cast<double *>(geo.data())[e * kGeoStride + k] = rec[k];
+            else reinterpret_cast<float *>(geo.data())[e * kGeoStride + k] = (float)rec[k];
+        }
+    }
+    PA_CUDA_TRY(cudaMemcpy(op->d_geo, geo.data(), geo_bytes, cudaMemcpyHostToDevice));
+    return PA_OK;
+}
+
 // Launch table per degree and precision: the shapes the autotuner picks for
 // the ~3M-dof operator sweep on GB300 (variant, elements per CTA, threads).
 ApplyLaunch default_apply_launch(int p, int precision)
@@ -276,18 +307,6 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
     const int D = p + 1;
     const size_t D3 = (size_t)D * D * D;
     const size_t geo_bytes = (size_t)g.ne * kGeoStride * op->elem;
-    std::vector<unsigned char> geo(geo_bytes);
-    for (int64_t e = 0; e < g.ne; ++e) {
-        const double *J = mesh->affine.data() + 12 * e;
-        double det = det3(J), Ji[9];
-        inverse3(J, det, Ji);
-        double rec[kGeoStride] = {Ji[0], Ji[1], Ji[2], Ji[3], Ji[4], Ji[5], Ji[6], Ji[7], Ji[8],
-                                  lambda * det, mu * det, det};
-        for (int k = 0; k < kGeoStride; ++k) {
-            if (precision == PA_FP64) reinterpret_cast<double *>(geo.data())[e * kGeoStride + k] = rec[k];
-            else reinterpret_cast<float *>(geo.data())[e * kGeoStride + k] = (float)rec[k];
-        }
-    }
     cudaError_t err;
     const size_t N = (size_t)3 * g.Nn;
     if ((err = cudaMalloc(&op->d_geo, geo_bytes)) != cudaSuccess ||
@@ -300,8 +319,7 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
         pa_op_destroy(op);
         return rc;
     }
-    if ((err = cudaMemcpy(op->d_geo, geo.data(), geo_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (err = cudaMemcpy(op->d_affine, mesh->affine.data(), sizeof(double) * 12 * (size_t)g.ne,
+    if ((err = cudaMemcpy(op->d_affine, mesh->affine.data(), sizeof(double) * 12 * (size_t)g.ne,
                           cudaMemcpyHostToDevice)) != cudaSuccess) {
         pa_op_destroy(op);
         return cuda_error(err, "pa_op_setup: cudaMemcpy");
@@ -312,6 +330,10 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
     } catch (...) {
         pa_op_destroy(op);
         return set_error(PA_ENOMEM, "pa_op_setup: host allocation");
+    }
+    if (int rc = upload_geometry(op)) {
+        pa_op_destroy(op);
+        return rc;
     }
     if (ess_mask) {
         if ((err = cudaMalloc((void **)&op->d_ess, N)) != cudaSuccess ||
@@ -439,6 +461,39 @@ int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void
                                         op->d_ess, 0.0f, false, op->g, s);
     }
     return rc;
+}
+
+int pa_op_set_material(pa_op *op, const double *lambda_mu)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_set_material: null op");
+    const int64_t ne = op->g.ne;
+    if (!lambda_mu) {
+        op->h_mat.clear();
+        return upload_geometry(op);
+    }
+    for (int64_t k = 0; k < 2 * ne; ++k)
+        if (!std::isfinite(lambda_mu[k])) return set_error(PA_EINVAL, "pa_op_set_material: non-finite material");
+    try {
+        op->h_mat.assign(lambda_mu, lambda_mu + 2 * ne);
+    } catch (...) {
+        return set_error(PA_ENOMEM, "pa_op_set_material: host allocation");
+    }
+    return upload_geometry(op);
+}
+
+int pa_op_traction(pa_op *op, int face, const double *t, void *F, void *stream)
+{
+    if (!op || !t || !F) return set_error(PA_EINVAL, "pa_op_traction: null argument");
+    if (face < 0 || face > 5) return set_error(PA_EINVAL, "pa_op_traction: face must be in 0..5");
+    // integrals of the 1D basis functions over [0,1] with the operator's rule
+    double m1[kMaxD] = {};
+    const Basis1D &b = op->basis;
+    for (int i = 0; i < b.D; ++i)
+        for (int q = 0; q < b.Q; ++q) m1[i] += b.qwts[q] * b.B[i * b.Q + q];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op->precision == PA_FP64)
+        return launch_traction<double>(op->d_affine, static_cast<double *>(F), op->d_ess, m1, face, t, op->g, s);
+    return launch_traction<float>(op->d_affine, static_cast<float *>(F), op->d_ess, m1, face, t, op->g, s);
 }
 
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads)

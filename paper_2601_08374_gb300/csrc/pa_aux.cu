@@ -226,6 +226,79 @@ template int launch_assemble<double>(const double *, double *, const double *, c
 template int launch_assemble<float>(const float *, float *, const float *, const uint8_t *, float, bool,
                                     const Grid &, cudaStream_t, const int *);
 
+// -------------------------------------------------------------- traction --
+// Neumann load of a constant traction t on one face of the box (the boundary
+// term of the weak form, Eq. 1), added to F node by node.  On an element's
+// face the basis is the product of the two tangential 1D bases (the nodal
+// basis along the normal is 1 at the face node and 0 elsewhere), so the
+// face integral of a node's basis function is dS_e m1[ib] m1[ic], with m1
+// the integrals of the 1D basis functions and dS_e = |dx/du x dx/dv| of the
+// element's affine map; a node sums the (at most 4) faces that hold it in
+// increasing element order.  Essential entries are set to 0.
+struct TractionArgs {
+    double m1[kMaxD];
+    double t[3];
+    int face;
+};
+
+template <typename T>
+__global__ void traction_kernel(const double *__restrict__ affine, T *__restrict__ F, const uint8_t *__restrict__ ess,
+                                TractionArgs ta, Grid g)
+{
+    const int ax = ta.face / 2, side = ta.face % 2;
+    const int bx = ax == 0 ? 1 : 0, cx = ax == 2 ? 1 : 2;
+    const int M[3] = {g.Mx, g.My, g.Mz}, ne[3] = {g.nx, g.ny, g.nz};
+    const int64_t nface = (int64_t)M[bx] * M[cx];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nface; k += (int64_t)gridDim.x * blockDim.x) {
+        int gi[3];
+        gi[ax] = side ? M[ax] - 1 : 0;
+        gi[bx] = (int)(k % M[bx]);
+        gi[cx] = (int)(k / M[bx]);
+        int eb[2], ib[2], ec[2], ic[2];
+        const int nb = axis_owners(gi[bx], ne[bx], g.p, eb, ib);
+        const int nc = axis_owners(gi[cx], ne[cx], g.p, ec, ic);
+        int ei[3];
+        ei[ax] = side ? ne[ax] - 1 : 0;
+        double acc = 0.0;
+        for (int kc = 0; kc < nc; ++kc)
+            for (int kb = 0; kb < nb; ++kb) {
+                ei[bx] = eb[kb];
+                ei[cx] = ec[kc];
+                const int64_t e = ei[0] + (int64_t)g.nx * (ei[1] + (int64_t)g.ny * ei[2]);
+                const double *J = affine + 12 * e;
+                const double u0 = J[0 * 3 + bx], u1 = J[1 * 3 + bx], u2 = J[2 * 3 + bx];
+                const double v0 = J[0 * 3 + cx], v1 = J[1 * 3 + cx], v2 = J[2 * 3 + cx];
+                const double c0 = u1 * v2 - u2 * v1, c1 = u2 * v0 - u0 * v2, c2 = u0 * v1 - u1 * v0;
+                acc += sqrt(c0 * c0 + c1 * c1 + c2 * c2) * ta.m1[ib[kb]] * ta.m1[ic[kc]];
+            }
+        const int64_t gn = gi[0] + (int64_t)g.Mx * (gi[1] + (int64_t)g.My * gi[2]);
+        for (int c = 0; c < 3; ++c) {
+            const int64_t kk = c * g.Nn + gn;
+            F[kk] = (ess && ess[kk]) ? T(0) : (T)((double)F[kk] + ta.t[c] * acc);
+        }
+    }
+}
+
+template <typename T>
+int launch_traction(const double *affine, T *F, const uint8_t *ess, const double *m1, int face, const double *t,
+                    const Grid &g, cudaStream_t s)
+{
+    TractionArgs ta{};
+    for (int i = 0; i <= g.p; ++i) ta.m1[i] = m1[i];
+    for (int c = 0; c < 3; ++c) ta.t[c] = t[c];
+    ta.face = face;
+    const int ax = face / 2;
+    const int64_t M[3] = {g.Mx, g.My, g.Mz};
+    const int64_t nface = M[ax == 0 ? 1 : 0] * M[ax == 2 ? 1 : 2];
+    traction_kernel<T><<<grid_for(nface, 256), 256, 0, s>>>(affine, F, ess, ta, g);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_traction<double>(const double *, double *, const uint8_t *, const double *, int, const double *,
+                                     const Grid &, cudaStream_t);
+template int launch_traction<float>(const double *, float *, const uint8_t *, const double *, int, const double *,
+                                    const Grid &, cudaStream_t);
+
 // -------------------------------------------------------------- diagonal --
 struct DiagTables {
     double M[kMaxD], C[kMaxD], K[kMaxD];  // sum_q w B^2, w B G, w G^2

@@ -121,6 +121,12 @@ template <typename T>
 int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_value, bool accumulate,
                     const Grid &g, cudaStream_t s, const int *skip = nullptr);
 
+// Neumann load of a constant traction on one box face, added to F
+// (face = 2 * axis + side); m1 = integrals of the 1D basis functions.
+template <typename T>
+int launch_traction(const double *affine, T *F, const uint8_t *ess, const double *m1, int face, const double *t,
+                    const Grid &g, cudaStream_t s);
+
 // Closed-form PA diagonal per element into the E-vector.
 template <typename T>
 int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s);
@@ -183,6 +189,7 @@ struct pa_op {
     void *d_xh = nullptr;        // device staging for apply_host
     void *d_yh = nullptr;
     std::vector<double> h_affine;  // host copy of the element maps (solver levels)
+    std::vector<double> h_mat;     // per-element (lambda_e, mu_e), empty for the constant material
     std::vector<uint8_t> h_ess;    // host copy of the essential mask (may be empty)
     // measurement: 3 events per recorded apply
     bool prof_on = false;

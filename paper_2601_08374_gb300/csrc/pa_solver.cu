@@ -1251,7 +1251,15 @@ int make_level_op(const pa_op *fine, int p, int precision, const std::vector<uin
     m.ny = fine->g.ny;
     m.nz = fine->g.nz;
     m.affine = fine->h_affine;
-    return pa_op_setup(&m, p, 0, fine->lambda, fine->mu, precision, mask.empty() ? nullptr : mask.data(), out);
+    int rc = pa_op_setup(&m, p, 0, fine->lambda, fine->mu, precision, mask.empty() ? nullptr : mask.data(), out);
+    if (rc == PA_OK && !fine->h_mat.empty()) {
+        rc = pa_op_set_material(*out, fine->h_mat.data());
+        if (rc) {
+            pa_op_destroy(*out);
+            *out = nullptr;
+        }
+    }
+    return rc;
 }
 
 // blocking read of one device scalar

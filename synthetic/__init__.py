@@ -126,3 +126,16 @@ def mixed_n(p: int, target_dofs: float = 8e6) -> int:
 
 
 SWEEP_P = (1, 2, 4, 6, 8)
+
+
+def two_material(mesh: Mesh, split_x: float, inner=(50.0, 50.0), outer=(1.0, 1.0)):
+    """Per-element material [ne, 2] (lambda_e, mu_e) of a two-material body:
+    elements whose centre lies at x < split_x take ``inner``, the others
+    ``outer`` (the paper's benchmark: lambda = mu = 50 and lambda = mu = 1, a
+    50:1 stiffness contrast)."""
+    A = mesh.affine
+    centre_x = A[:, 9] + 0.5 * (A[:, 0] + A[:, 1] + A[:, 2])
+    mat = np.empty((mesh.ne, 2))
+    mat[centre_x < split_x] = inner
+    mat[centre_x >= split_x] = outer
+    return mat

@@ -268,3 +268,43 @@ def test_batched_apply_matches_individual_applies(pa):
         pa.pa_op_apply_batch([ops[0].h, ops[0].h], [xs[0], xs[0]], [ys[0], ys[1]])
     for o in ops:
         o.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+def test_per_element_material_apply_and_diag(pa, p, prec):
+    """Per-element material (the PA data D with lambda(alpha, e), mu(alpha, e)
+    constant per element) against the oracle's apply and diagonal; None
+    restores the constant material."""
+    nx, ny, nz = 3, 2, 2
+    m = syn.random_affine_cube(nx, seed=600 + p, ny=ny, nz=nz)
+    rng = np.random.default_rng(p)
+    mat = rng.uniform(0.5, 50.0, (m.ne, 2))
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=61 + p)
+    op = pa.Operator(nx, ny, nz, m.affine, p, 1.0, 0.7, precision=prec, ess_mask=ess, mat=mat)
+    xt = torch.tensor(x, dtype=op.dtype, device="cuda")
+    yo = oracle.apply(p, nx, ny, nz, m.affine, 0.0, 0.0, x, ess=ess, mat=mat)
+    assert _relerr(op.apply(xt).double().cpu().numpy(), yo) <= TOL[prec]
+    do = oracle.diag(p, nx, ny, nz, m.affine, 0.0, 0.0, ess=ess, mat=mat)
+    assert _relerr(op.diag().double().cpu().numpy(), do) <= TOL[prec]
+    pa.pa_op_set_material(op.h, None)
+    yc = oracle.apply(p, nx, ny, nz, m.affine, 1.0, 0.7, x, ess=ess)
+    assert _relerr(op.apply(xt).double().cpu().numpy(), yc) <= TOL[prec]
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p,face", [(1, 1), (2, 0), (3, 3), (4, 5), (8, 1)])
+def test_traction_load_against_oracle(pa, p, face, prec):
+    """Body force plus a constant traction on one face (clamped at x = 0):
+    the load vector against the oracle's volume and surface integrals."""
+    m = syn.random_affine_cube(2, seed=700 + p, ny=2, nz=1)
+    ess = syn.clamp_mask(m, p)
+    t = (0.1, -0.3, -1e-2)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 1.0, precision=prec, ess_mask=ess)
+    F = op.rhs(f0=(0.0, 0.0, -1.0), traction=(face, t)).double().cpu().numpy()
+    Fo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess) + \
+        oracle.traction(p, m.nx, m.ny, m.nz, m.affine, face, t, ess=ess)
+    assert _relerr(F, Fo) <= TOL[prec]
+    op.close()

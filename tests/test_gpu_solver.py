@@ -220,3 +220,28 @@ def test_lockstep_batch_rejects_mixed_hierarchies_and_refinement_mode(pa):
         pa.pa_solver_destroy(s)
     for op in ops:
         op.close()
+
+
+@pytest.mark.parametrize("p,levels", [(2, [2, 1]), (4, [4, 2, 1])])
+def test_two_material_beam_with_traction_matches_direct_solve(pa, p, levels):
+    """The paper's benchmark physics on a small 8:1:1 beam: two materials
+    (lambda = mu = 50 for x < 4, 1 beyond, a 50:1 contrast), clamped at
+    x = 0, a constant traction (0, 0, -1e-2) on the x = 8 face; FP64 and the
+    FP32-V-cycle mode against a direct FP64 solve of the oracle's matrix."""
+    m = _beam(4, 1, 1)
+    mat = syn.two_material(m, 4.0)
+    ess = syn.clamp_mask(m, p)
+    t = (0.0, 0.0, -1e-2)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 1.0, ess_mask=ess, mat=mat)
+    b = op.rhs(traction=(1, t))
+    bo = oracle.traction(p, m.nx, m.ny, m.nz, m.affine, 1, t, ess=ess)
+    assert np.max(np.abs(b.cpu().numpy() - bo)) <= 1e-14 * np.max(np.abs(bo))
+    xo = oracle.solve_dense(p, m.nx, m.ny, m.nz, m.affine, 0.0, 0.0, bo, ess, mat=mat)
+    for mode in (pa.PA_SOLVE_FP64, pa.PA_SOLVE_MIXED_FCG, pa.PA_SOLVE_MIXED):
+        s = pa.pa_solver_create(op.h, levels, 2, 1e-2, 10, mode)
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 500)
+        pa.pa_solver_destroy(s)
+        assert code == pa.PA_OK, (mode, pa.lib.pa_last_error())
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo), mode
+    op.close()
