@@ -317,6 +317,8 @@ def run_ours(args):
         out["batched_apply"] = run_batched_apply(args, pa, torch)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, pa, torch)
+    if args.ablation_ps:
+        out["ablation"] = run_ablation(args, pa, torch)
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(ps, args)
     print(json.dumps(out), flush=True)
@@ -451,6 +453,43 @@ def serving_requests(pa, count, seed):
         out.append(pa.make_request(*dims, box, p, E, nu, modes=modes, rtol=1e-10, maxit=1000,
                                    mode=pa.PA_SOLVE_MIXED_FCG, keep_solution=False))
     return out
+
+
+def run_ablation(args, pa, torch):
+    """The paper's optimisation stack (Table 8) stage by stage on the GPU, FP64,
+    on the sweep's workloads: baseline (two kernels, Q values through HBM,
+    dense O(p^6) contractions, 81-term stress), + sum factorisation, + Voigt,
+    + fusion (the production kernel).  Median of CUDA-event-timed applies
+    (element kernels and assembly) per stage."""
+    out = []
+    for p in [int(v) for v in args.ablation_ps.split(",")]:
+        n, mesh, x = workload(p)
+        lam, mu = syn.lame(1.0, 0.3)
+        op = pa.Operator(n, n, n, mesh.affine, p, lam, mu)
+        xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(xt)
+        st = torch.cuda.current_stream()
+        row = {"p": p, "n": n, "ndofs": op.ndofs}
+        ms = {}
+        for stage in range(4):
+            pa.pa_op_apply_stage(op.h, stage, xt, y)  # first use allocates the stage's buffers
+            times = []
+            for _ in range(args.ablation_reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                pa.pa_op_apply_stage(op.h, stage, xt, y)
+                e1.record(st)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms[stage] = statistics.median(times)
+        names = ["baseline", "+sumfact", "+voigt", "+fusion"]
+        for stage in range(4):
+            row[names[stage]] = {"ms": round(ms[stage], 4), "gdofs": round(op.ndofs / (ms[stage] * 1e-3) / 1e9, 4),
+                                 "speedup_vs_baseline": round(ms[0] / ms[stage], 2)}
+        out.append(row)
+        op.close()
+    return {"dtype": "f64", "recipe": "sweep workloads (n^3 unit cube, random affine elements, E=1 nu=0.3), "
+            "unconstrained; each stage's time includes its element kernels and the assembly", "per_p": out}
 
 
 def small_requests(pa, count, seed):
@@ -636,6 +675,8 @@ def main(argv=None):
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
     ap.add_argument("--serve-calibration", type=int, default=16)
     ap.add_argument("--serve-small", type=int, default=64, help="small-solve burst served with and without batching")
+    ap.add_argument("--ablation-ps", default="2,4,8", help="degrees of the Table 8 stage ladder ('' skips it)")
+    ap.add_argument("--ablation-reps", type=int, default=5)
     ap.add_argument("--launch", default="", help="fixed element-kernel shape 'variant,elems_per_cta,threads' "
                                                  "(skips the autotuner)")
     args = ap.parse_args(argv)

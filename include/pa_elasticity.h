@@ -148,6 +148,21 @@ int pa_op_set_material(pa_op *op, const double *lambda_mu);
  * `stream`. */
 int pa_op_traction(pa_op *op, int face, const double *t, void *F, void *stream);
 
+/* The paper's optimisation stack measured stage by stage (Table 8), y = A x
+ * with the operator of pa_op_apply (same Dirichlet handling), FP64 only:
+ *   stage 0: baseline -- two kernels with the quadrature values in HBM
+ *            between them, dense O(p^6) contractions with the full 3D
+ *            basis-gradient tables, stress by the full 81-term C_ijkl
+ *            contraction;
+ *   stage 1: + sum factorisation (1D sweeps, still two kernels, full C);
+ *   stage 2: + Voigt notation (the structured stress of Eq. 7);
+ *   stage 3: + fusion: the production apply (pa_op_apply; any precision).
+ * Buffers of stages 0-2 (Q values, tensors, dense tables) are allocated on
+ * first use and kept by the operator.  Asynchronous on `stream` except for
+ * that first allocation.  PA_EINVAL for a stage outside 0..3 or stages 0-2
+ * on an FP32 operator. */
+int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream);
+
 /* Launch shape of the fused element kernel: variant 0 (flattened
  * shared-memory sweeps, one output per thread step), 1 (register-tiled 1D
  * lines), 2 (register-tiled lines whose X-sweep threads gather and whose

@@ -83,6 +83,7 @@ _sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POIN
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_set_material", [_vp, _dp])
+_sig("pa_op_apply_stage", [_vp, ctypes.c_int, _vp, _vp, _vp])
 _sig("pa_op_traction", [_vp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
 _sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
@@ -241,6 +242,12 @@ def pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, affine, x, y, ess_mask=N
     _check(lib.pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, _tptr(affine),
                                 _tptr(ess_mask) if ess_mask is not None else None, _tptr(x), _tptr(y),
                                 _stream_ptr(stream)), "pa_apply_noalloc")
+
+
+def pa_op_apply_stage(op, stage, x, y, stream=None):
+    """y = A x by one stage of the optimisation stack (0 baseline, 1 + sum
+    factorisation, 2 + Voigt, 3 + fusion = the production apply)."""
+    _check(lib.pa_op_apply_stage(op, int(stage), _tptr(x), _tptr(y), _stream_ptr(stream)), "pa_op_apply_stage")
 
 
 def pa_op_set_material(op, mat):

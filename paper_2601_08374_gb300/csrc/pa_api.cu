@@ -265,6 +265,7 @@ int pa_op_destroy(pa_op *op)
     cudaFree(op->d_ye);
     cudaFree(op->d_xh);
     cudaFree(op->d_yh);
+    for (void *q : op->d_abl) cudaFree(q);
     delete op;
     return PA_OK;
 }

@@ -47,7 +47,13 @@ struct FlatLayout {
     __host__ __device__ static size_t table_offset(int epb) { return (((size_t)tab + (size_t)epb * per_elem) * sizeof(T) + 15) & ~(size_t)15; }
 };
 
-template <typename T, int D, int Q>
+// PART 0: the whole fused dataflow.  PART 1 / 2 (ablation of Table 8 only):
+// the forward half up to the Q values, written to a.qvec, and the transposed
+// half from a.qvec -- the two-kernel form with the quadrature values making
+// a round trip through HBM.  FULLC (ablation only): the stress from the full
+// 81-term contraction sigma_ij = sum_kl C_ijkl du_kl with the element's
+// tensor read from a.ctensor, in place of the Voigt arithmetic of Eq. 7.
+template <typename T, int D, int Q, int PART = 0, bool FULLC = false>
 __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
     using L = FlatLayout<T, D, Q>;
@@ -84,6 +90,7 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
         gbase[el] = (int64_t)ex * p + Mx * ((int64_t)ey * p) + MxMy * ((int64_t)ez * p);
     }
     __syncthreads();
+    if (PART != 2) {
     // ---- P0: gather x_e[el][c][iz][iy][ix] into bufA
     {
         const int total = ne_blk * L::nX;
@@ -195,16 +202,31 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
-            // Voigt stress, order [00, 11, 22, 01, 02, 12]
-            const T div = du[0][0] + du[1][1] + du[2][2];
-            const T ld = cl * div, m2 = cm + cm;
             T s[3][3];
-            s[0][0] = fma(m2, du[0][0], ld);
-            s[1][1] = fma(m2, du[1][1], ld);
-            s[2][2] = fma(m2, du[2][2], ld);
-            s[0][1] = s[1][0] = cm * (du[0][1] + du[1][0]);
-            s[0][2] = s[2][0] = cm * (du[0][2] + du[2][0]);
-            s[1][2] = s[2][1] = cm * (du[1][2] + du[2][1]);
+            if constexpr (FULLC) {
+                const T *C = a.ctensor + (e0 + el) * 81;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+#pragma unroll
+                            for (int l = 0; l < 3; ++l) acc = fma(C[((i * 3 + j) * 3 + k) * 3 + l], du[k][l], acc);
+                        s[i][j] = acc;
+                    }
+            } else {
+                // Voigt stress, order [00, 11, 22, 01, 02, 12]
+                const T div = du[0][0] + du[1][1] + du[2][2];
+                const T ld = cl * div, m2 = cm + cm;
+                s[0][0] = fma(m2, du[0][0], ld);
+                s[1][1] = fma(m2, du[1][1], ld);
+                s[2][2] = fma(m2, du[2][2], ld);
+                s[0][1] = s[1][0] = cm * (du[0][1] + du[1][0]);
+                s[0][2] = s[2][0] = cm * (du[0][2] + du[2][0]);
+                s[1][2] = s[2][1] = cm * (du[1][2] + du[2][1]);
+            }
             T *s3 = bufB + (size_t)el * L::bufB + r;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -214,6 +236,24 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
         }
     }
     __syncthreads();
+    }  // PART != 2
+    if (PART == 1) {
+        // the Q values of the CTA's elements to HBM (contiguous block)
+        T *qv = a.qvec + e0 * L::n3;
+        for (int o = tid; o < ne_blk * L::n3; o += nt) {
+            const int el = o / L::n3;
+            qv[o] = bufB[(size_t)el * L::bufB + (o - el * L::n3)];
+        }
+        return;
+    }
+    if (PART == 2) {
+        const T *qv = a.qvec + e0 * L::n3;
+        for (int o = tid; o < ne_blk * L::n3; o += nt) {
+            const int el = o / L::n3;
+            bufB[(size_t)el * L::bufB + (o - el * L::n3)] = qv[o];
+        }
+        __syncthreads();
+    }
 
     // ---- P4: Z^T sweep.  out [el][c][m][iz][qy][qx] in bufA
     {
@@ -338,6 +378,13 @@ __global__ void __launch_bounds__(512) pa_apply_flat_batch_kernel(BatchArgs<T> b
     int k = 0;
     while (k + 1 < bt.count && (int64_t)blockIdx.x >= bt.cta_start[k + 1]) ++k;
     flat_body<T, D, Q>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
+}
+
+// The two halves of the fused kernel as separate launches (ablation).
+template <typename T, int D, int Q, int PART, bool FULLC>
+__global__ void __launch_bounds__(512) pa_apply_flat_part_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+{
+    flat_body<T, D, Q, PART, FULLC>(a, tab, epb, blockIdx.x);
 }
 
 template <typename T, int D, int Q>

@@ -82,6 +82,8 @@ struct ApplyArgs {
     const uint8_t *ess;  // [3*Nn] or nullptr
     const int *skip;     // device flag: when non-null and set, the launch does nothing
     Grid g;
+    T *qvec = nullptr;         // ablation stages only: quadrature values [ne][3][3][Q^3]
+    const T *ctensor = nullptr;  // ablation stages only: elasticity tensor per element [ne][81]
 };
 
 template <typename T>
@@ -190,6 +192,10 @@ struct pa_op {
     void *d_yh = nullptr;
     std::vector<double> h_affine;  // host copy of the element maps (solver levels)
     std::vector<double> h_mat;     // per-element (lambda_e, mu_e), empty for the constant material
+    // ablation stages (pa_op_apply_stage), allocated on first use:
+    // Q values [ne][9][Q^3], elasticity tensors [ne][81], dense basis-gradient
+    // tables [3][D^3][Q^3] and weighted transposed [3][Q^3][D^3]
+    void *d_abl[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<uint8_t> h_ess;    // host copy of the essential mask (may be empty)
     // measurement: 3 events per recorded apply
     bool prof_on = false;

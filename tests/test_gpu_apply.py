@@ -308,3 +308,37 @@ def test_traction_load_against_oracle(pa, p, face, prec):
         oracle.traction(p, m.nx, m.ny, m.nz, m.affine, face, t, ess=ess)
     assert _relerr(F, Fo) <= TOL[prec]
     op.close()
+
+
+@pytest.mark.parametrize("stage", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_optimisation_stack_stages_against_oracle(pa, p, stage):
+    """Every stage of the Table 8 ladder on the GPU (baseline with dense
+    contractions, full 81-term stress and the Q values through HBM; + sum
+    factorisation; + Voigt; + fusion) is the same operator: FP64 parity with
+    the oracle, constrained, on uneven elements with per-element material."""
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=800 + p, ny=ny, nz=nz)
+    mat = np.random.default_rng(p).uniform(0.5, 5.0, (m.ne, 2))
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=81 + p)
+    yo = oracle.apply(p, nx, ny, nz, m.affine, 0.0, 0.0, x, ess=ess, mat=mat)
+    op = pa.Operator(nx, ny, nz, m.affine, p, 1.0, 1.0, ess_mask=ess, mat=mat)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    y = torch.full_like(xt, float("nan"))
+    pa.pa_op_apply_stage(op.h, stage, xt, y)
+    assert _relerr(y.cpu().numpy(), yo) <= TOL[0]
+    op.close()
+
+
+def test_optimisation_stack_rejects_fp32_and_bad_stage(pa):
+    m = syn.random_affine_cube(2, seed=5)
+    op = pa.Operator(2, 2, 2, m.affine, 2, 1.0, 1.0, precision=pa.PA_FP32)
+    x = torch.zeros(op.ndofs, dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    pa.pa_op_apply_stage(op.h, 3, x, y)  # the production apply: any precision
+    for stage in (0, 4, -1):
+        with pytest.raises(pa.PAError) as ei:
+            pa.pa_op_apply_stage(op.h, stage, x, y)
+        assert ei.value.code == pa.PA_EINVAL
+    op.close()
