@@ -317,6 +317,8 @@ def run_ours(args):
         out["batched_apply"] = run_batched_apply(args, pa, torch)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, pa, torch)
+    if args.precision == "fp64" and not args.no_fp32:
+        out["fp32_sweep"] = run_fp32_sweep(args, pa, torch)
     if args.ablation_ps:
         out["ablation"] = run_ablation(args, pa, torch)
     if not args.no_cpu_baseline and ws == 1:
@@ -453,6 +455,53 @@ def serving_requests(pa, count, seed):
         out.append(pa.make_request(*dims, box, p, E, nu, modes=modes, rtol=1e-10, maxit=1000,
                                    mode=pa.PA_SOLVE_MIXED_FCG, keep_solution=False))
     return out
+
+
+def run_fp32_sweep(args, pa, torch):
+    """The same operator sweep in FP32 (the apply of the mixed-precision
+    solves): GDoF/s per p and over the sweep, with the element kernel's
+    algorithmic FP32 rate against the derived FP32 peak.  Same workloads,
+    timing and L2 rule as the FP64 line."""
+    lam, mu = syn.lame(1.0, 0.3)
+    stream = torch.cuda.current_stream()
+    cases = []
+    for p in [int(v) for v in args.ps.split(",")]:
+        n, mesh, x = workload(p)
+        op = pa.Operator(n, n, n, mesh.affine, p, lam, mu, precision=pa.PA_FP32)
+        if not args.no_autotune:
+            pa.pa_op_autotune(op.h, stream)
+        xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+        cases.append(dict(p=p, op=op, x=xt, y=torch.empty_like(xt), ndofs=op.ndofs, ne=op.nelem,
+                          launch=pa.pa_op_get_launch(op.h)))
+    for _ in range(args.warmup):
+        for c in cases:
+            pa.pa_op_apply(c["op"].h, c["x"], c["y"], stream)
+    for c in cases:
+        pa.pa_op_profile(c["op"].h, True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(3, args.steps)
+    e0.record(stream)
+    for _ in range(steps):
+        for c in cases:
+            pa.pa_op_apply(c["op"].h, c["x"], c["y"], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    peak = SM_COUNT * FLOP_PER_CLK_SM["f32"] * SM_MAX_MHZ * 1e6 / 1e12
+    per_p, fl_tot, el_tot = [], 0.0, 0.0
+    for c in cases:
+        te, ta, na = pa.pa_op_profile_read(c["op"].h)
+        pa.pa_op_profile(c["op"].h, False)
+        fl = flops_per_element(c["p"]) * c["ne"]
+        fl_tot += fl * na
+        el_tot += te
+        per_p.append({"p": c["p"], "gdofs": round(c["ndofs"] / ((te + ta) / na * 1e-3) / 1e9, 3),
+                      "frac_alu": round(fl / (te / na * 1e-3) / 1e12 / peak, 4), "launch": list(c["launch"])})
+        c["op"].close()
+    return {"value": round(sum(c["ndofs"] for c in cases) * steps / (ms * 1e-3) / 1e9, 4), "unit": "GDoF/s",
+            "dtype": "f32", "element_kernel_tflops_alg": round(fl_tot / (el_tot * 1e-3) / 1e12, 3),
+            "frac_of_derived_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / peak, 4), "per_p": per_p}
 
 
 def run_ablation(args, pa, torch):
@@ -677,6 +726,7 @@ def main(argv=None):
     ap.add_argument("--serve-small", type=int, default=64, help="small-solve burst served with and without batching")
     ap.add_argument("--ablation-ps", default="2,4,8", help="degrees of the Table 8 stage ladder ('' skips it)")
     ap.add_argument("--ablation-reps", type=int, default=5)
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 operator sweep of the FP64 line")
     ap.add_argument("--launch", default="", help="fixed element-kernel shape 'variant,elems_per_cta,threads' "
                                                  "(skips the autotuner)")
     args = ap.parse_args(argv)

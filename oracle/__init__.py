@@ -43,11 +43,12 @@ def _lib():
     lib.orc_ref_blocks.argtypes = [ctypes.c_void_p, _dp]
     lib.orc_element_coeff.argtypes = [_dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
     lib.orc_element_matrix.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, _dp]
+    lib.orc_element_matrix_t.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
     common = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _u8p]
     lib.orc_apply.argtypes = common + [_dp, _dp, ctypes.c_int]
     lib.orc_apply_rows.argtypes = common + [_dp, ctypes.c_int64, _i64p, _dp, ctypes.c_int]
     lib.orc_diag.argtypes = common + [_dp, ctypes.c_int]
-    common_m = common[:7] + [_dp, _u8p]
+    common_m = common[:7] + [_dp, _dp, _u8p]
     lib.orc_apply_m.argtypes = common_m + [_dp, _dp, ctypes.c_int]
     lib.orc_apply_rows_m.argtypes = common_m + [_dp, ctypes.c_int64, _i64p, _dp, ctypes.c_int]
     lib.orc_diag_m.argtypes = common_m + [_dp, ctypes.c_int]
@@ -144,6 +145,14 @@ class Ref:
             raise ValueError("detJ <= 0")
         return K
 
+    def element_matrix_t(self, J, C4):
+        """Element matrix of an anisotropic tensor C4 (81 values, C_cjdl)."""
+        D3 = self.D ** 3
+        K = np.zeros((3 * D3, 3 * D3))
+        if _lib().orc_element_matrix_t(self._h, _d(_f64(J).reshape(9)), _d(_f64(C4).reshape(81)), _d(K)):
+            raise ValueError("detJ <= 0")
+        return K
+
 
 @functools.lru_cache(maxsize=16)
 def ref(p: int, q: int = 0) -> Ref:
@@ -178,9 +187,33 @@ def _material(mat, ne):
     return mat
 
 
-def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0, mat=None):
+def _tensor(ctens, ne):
+    """Per-element anisotropic tensor [ne, 81] (C_cjdl), or None."""
+    if ctens is None:
+        return None
+    ctens = _f64(ctens).reshape(ne, 81)
+    return np.ascontiguousarray(ctens)
+
+
+def voigt_to_tensor(Cv):
+    """Full tensor C_ijkl (81, index ((i*3 + j)*3 + k)*3 + l) of a 6x6 Voigt
+    matrix in the order [00, 11, 22, 01, 02, 12] with engineering shear
+    strains (sigma_V = Cv eps_V, eps_V = [e00, e11, e22, 2 e01, 2 e02, 2 e12])."""
+    Cv = _f64(Cv).reshape(6, 6)
+    v = [[0, 3, 4], [3, 1, 5], [4, 5, 2]]
+    C = np.zeros(81)
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    C[((i * 3 + j) * 3 + k) * 3 + l] = Cv[v[i][j], v[k][l]]
+    return C
+
+
+def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0, mat=None, ctens=None):
     """y = A x (constrained operator when ``ess`` is given).  ``mat``: per
-    element (lambda_e, mu_e) [ne, 2] in place of the constants lam, mu."""
+    element (lambda_e, mu_e) [ne, 2] in place of the constants lam, mu;
+    ``ctens``: per-element anisotropic tensors [ne, 81] (takes precedence)."""
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
     x = _f64(x)
@@ -190,14 +223,15 @@ def apply(p, nx, ny, nz, affine, lam, mu, x, ess=None, q=0, nthreads=0, mat=None
     y = np.zeros(N)
     m = _mask(ess)
     mt = _material(mat, nx * ny * nz)
-    rc = _lib().orc_apply_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+    ct = _tensor(ctens, nx * ny * nz)
+    rc = _lib().orc_apply_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt), _d(ct),
                             m.ctypes.data_as(_u8p) if m is not None else None, _d(x), _d(y), nthreads)
     if rc:
         raise RuntimeError(f"orc_apply failed ({rc})")
     return y
 
 
-def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=0, mat=None):
+def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=0, mat=None, ctens=None):
     """Selected entries (L-vector indices ``rows``) of y = A x."""
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
@@ -206,7 +240,8 @@ def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=
     out = np.zeros(len(rows))
     m = _mask(ess)
     mt = _material(mat, nx * ny * nz)
-    rc = _lib().orc_apply_rows_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+    ct = _tensor(ctens, nx * ny * nz)
+    rc = _lib().orc_apply_rows_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt), _d(ct),
                                  m.ctypes.data_as(_u8p) if m is not None else None, _d(x),
                                  len(rows), rows.ctypes.data_as(_i64p), _d(out), nthreads)
     if rc:
@@ -214,13 +249,14 @@ def apply_rows(p, nx, ny, nz, affine, lam, mu, x, rows, ess=None, q=0, nthreads=
     return out
 
 
-def diag(p, nx, ny, nz, affine, lam, mu, ess=None, q=0, nthreads=0, mat=None):
+def diag(p, nx, ny, nz, affine, lam, mu, ess=None, q=0, nthreads=0, mat=None, ctens=None):
     r = ref(p, q)
     affine = _check_mesh(nx, ny, nz, affine)
     d = np.zeros(3 * n_nodes(nx, ny, nz, p))
     m = _mask(ess)
     mt = _material(mat, nx * ny * nz)
-    rc = _lib().orc_diag_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt),
+    ct = _tensor(ctens, nx * ny * nz)
+    rc = _lib().orc_diag_m(r._h, nx, ny, nz, _d(affine), lam, mu, _d(mt), _d(ct),
                            m.ctypes.data_as(_u8p) if m is not None else None, _d(d), nthreads)
     if rc:
         raise RuntimeError(f"orc_diag failed ({rc})")
@@ -295,7 +331,7 @@ def node_coords_box(nx, ny, nz, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
 
 
-def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0, mat=None):
+def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0, mat=None, ctens=None):
     """Global (unconstrained) stiffness matrix of a small mesh, assembled
     from the oracle's element matrices (``mat``: per-element material)."""
     r = ref(p, q)
@@ -311,6 +347,9 @@ def assemble_dense(p, nx, ny, nz, affine, lam, mu, q=0, mat=None):
         ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
         gn = (ex * p + ix) + Mx * ((ey * p + iy) + My * (ez * p + iz))
         dofs = np.concatenate([c * Nn + gn for c in range(3)])
+        if ctens is not None:
+            A[np.ix_(dofs, dofs)] += r.element_matrix_t(affine[e, :9], np.asarray(ctens, dtype=np.float64).reshape(-1, 81)[e])
+            continue
         le, me = (lam, mu) if mat is None else (float(mat[e][0]), float(mat[e][1]))
         A[np.ix_(dofs, dofs)] += r.element_matrix(affine[e, :9], le, me)
     return A
@@ -326,7 +365,7 @@ def constrain_dense(A, ess):
     return Ac
 
 
-def solve_dense(p, nx, ny, nz, affine, lam, mu, b, ess, q=0, mat=None):
+def solve_dense(p, nx, ny, nz, affine, lam, mu, b, ess, q=0, mat=None, ctens=None):
     """Direct FP64 solve of the constrained system (small meshes only)."""
-    A = constrain_dense(assemble_dense(p, nx, ny, nz, affine, lam, mu, q, mat=mat), ess)
+    A = constrain_dense(assemble_dense(p, nx, ny, nz, affine, lam, mu, q, mat=mat, ctens=ctens), ess)
     return np.linalg.solve(A, _f64(b))

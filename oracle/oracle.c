@@ -319,11 +319,60 @@ int orc_element_coeff(const double *J, double lambda, double mu, double *C, doub
     return 0;
 }
 
+/* The same coefficients for a general (anisotropic) elasticity tensor
+ * (Eq. 2), C4[((c*3 + j)*3 + d)*3 + l] = C_cjdl:
+ *   C[m][n][c][d] = detJ sum_jl Ji[m][j] C_cjdl Ji[n][l],
+ * i.e. sigma_cj = sum_dl C_cjdl du_d/dx_l tested with d phi_a / dx_j.       */
+int orc_element_coeff_t(const double *J, const double *C4, double *C, double *detJ_out)
+{
+    double Ji[9];
+    double det = inv3(J, Ji);
+    if (!(det > 0.0)) return -1;
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n)
+            for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) {
+                    double v = 0.0;
+                    for (int j = 0; j < 3; ++j)
+                        for (int l = 0; l < 3; ++l) v += Ji[m * 3 + j] * C4[((c * 3 + j) * 3 + d) * 3 + l] * Ji[n * 3 + l];
+                    C[((m * 3 + n) * 3 + c) * 3 + d] = det * v;
+                }
+    if (detJ_out) *detJ_out = det;
+    return 0;
+}
+
+/* Coefficients of element e: the per-element tensor (ctens[e], 81 values)
+ * when given, else the per-element isotropic material, else the constants. */
+static int element_coeff_of(int64_t e, const double *affine, double lambda, double mu, const double *mat,
+                            const double *ctens, double *C)
+{
+    if (ctens) return orc_element_coeff_t(affine + 12 * e, ctens + 81 * e, C, NULL);
+    const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
+    return orc_element_coeff(affine + 12 * e, le, me, C, NULL);
+}
+
 /* Dense element matrix, row (c,a) = c*D3 + a, column (d,b) = d*D3 + b.     */
+static void element_matrix_from(const orc_ref *r, const double *C, double *K);
+
 int orc_element_matrix(const orc_ref *r, const double *J, double lambda, double mu, double *K)
 {
     double C[81];
     if (orc_element_coeff(J, lambda, mu, C, NULL)) return -1;
+    element_matrix_from(r, C, K);
+    return 0;
+}
+
+/* Element matrix of an anisotropic tensor C4 (C_cjdl, 81 values).          */
+int orc_element_matrix_t(const orc_ref *r, const double *J, const double *C4, double *K)
+{
+    double C[81];
+    if (orc_element_coeff_t(J, C4, C, NULL)) return -1;
+    element_matrix_from(r, C, K);
+    return 0;
+}
+
+static void element_matrix_from(const orc_ref *r, const double *C, double *K)
+{
     int D3 = r->D3, N = 3 * D3;
     for (int c = 0; c < 3; ++c)
         for (int a = 0; a < D3; ++a)
@@ -334,7 +383,6 @@ int orc_element_matrix(const orc_ref *r, const double *J, double lambda, double 
                         s += r->S[((size_t)mn * D3 + a) * D3 + b] * C[(mn * 3 + c) * 3 + d];
                     K[(size_t)(c * D3 + a) * N + d * D3 + b] = s;
                 }
-    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -416,18 +464,19 @@ int orc_max_threads(void)
  * material per quadrature point, lambda(alpha, e) and mu(alpha, e)
  * (Sec. 4.5); for material constant on each element that is this array.   */
 int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-                double lambda, double mu, const double *mat, const uint8_t *ess, const double *x, double *y,
-                int nthreads);
+                double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess,
+                const double *x, double *y, int nthreads);
 
 int orc_apply(const orc_ref *r, int nx, int ny, int nz, const double *affine,
               double lambda, double mu, const uint8_t *ess, const double *x, double *y, int nthreads)
 {
-    return orc_apply_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, x, y, nthreads);
+    return orc_apply_m(r, nx, ny, nz, affine, lambda, mu, NULL, NULL, ess, x, y, nthreads);
 }
 
+/* ctens: per-element anisotropic tensor [ne][81] (C_cjdl), or NULL.        */
 int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-                double lambda, double mu, const double *mat, const uint8_t *ess, const double *x, double *y,
-                int nthreads)
+                double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess,
+                const double *x, double *y, int nthreads)
 {
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     grid_t g = make_grid(nx, ny, nz, r->p);
@@ -443,8 +492,7 @@ int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
         double C[81];
 #pragma omp for schedule(dynamic, 16)
         for (int64_t e = 0; e < g.ne; ++e) {
-            const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
-            if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
+            if (element_coeff_of(e, affine, lambda, mu, mat, ctens, C)) { bad = 1; continue; }
             for (int iz = 0; iz < D; ++iz)
                 for (int iy = 0; iy < D; ++iy)
                     for (int ix = 0; ix < D; ++ix) {
@@ -495,19 +543,19 @@ int orc_apply_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
 /* Selected entries of y = A x (rows are L-vector indices), computed one by
  * one from the rows of the contributing element matrices.                  */
 int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-                     double lambda, double mu, const double *mat, const uint8_t *ess, const double *x,
-                     int64_t nrows, const int64_t *rows, double *yrows, int nthreads);
+                     double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess,
+                     const double *x, int64_t nrows, const int64_t *rows, double *yrows, int nthreads);
 
 int orc_apply_rows(const orc_ref *r, int nx, int ny, int nz, const double *affine,
                    double lambda, double mu, const uint8_t *ess, const double *x,
                    int64_t nrows, const int64_t *rows, double *yrows, int nthreads)
 {
-    return orc_apply_rows_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, x, nrows, rows, yrows, nthreads);
+    return orc_apply_rows_m(r, nx, ny, nz, affine, lambda, mu, NULL, NULL, ess, x, nrows, rows, yrows, nthreads);
 }
 
 int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-                     double lambda, double mu, const double *mat, const uint8_t *ess, const double *x,
-                     int64_t nrows, const int64_t *rows, double *yrows, int nthreads)
+                     double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess,
+                     const double *x, int64_t nrows, const int64_t *rows, double *yrows, int nthreads)
 {
     grid_t g = make_grid(nx, ny, nz, r->p);
     int D = g.D, D3 = r->D3, p = g.p;
@@ -532,8 +580,7 @@ int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *aff
                     int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
                     int a = ix + D * (iy + D * iz);
                     double C[81];
-                    const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
-                    if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
+                    if (element_coeff_of(e, affine, lambda, mu, mat, ctens, C)) { bad = 1; continue; }
                     for (int bz = 0; bz < D; ++bz)
                         for (int by = 0; by < D; ++by)
                             for (int bx = 0; bx < D; ++bx) {
@@ -559,16 +606,18 @@ int orc_apply_rows_m(const orc_ref *r, int nx, int ny, int nz, const double *aff
 /* Diagonal of the (constrained) assembled matrix: sum over elements of the
  * element-matrix diagonal; essential entries are 1.                        */
 int orc_diag_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-               double lambda, double mu, const double *mat, const uint8_t *ess, double *dg, int nthreads);
+               double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess, double *dg,
+               int nthreads);
 
 int orc_diag(const orc_ref *r, int nx, int ny, int nz, const double *affine,
              double lambda, double mu, const uint8_t *ess, double *dg, int nthreads)
 {
-    return orc_diag_m(r, nx, ny, nz, affine, lambda, mu, NULL, ess, dg, nthreads);
+    return orc_diag_m(r, nx, ny, nz, affine, lambda, mu, NULL, NULL, ess, dg, nthreads);
 }
 
 int orc_diag_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
-               double lambda, double mu, const double *mat, const uint8_t *ess, double *dg, int nthreads)
+               double lambda, double mu, const double *mat, const double *ctens, const uint8_t *ess, double *dg,
+               int nthreads)
 {
     grid_t g = make_grid(nx, ny, nz, r->p);
     int D = g.D, D3 = r->D3, p = g.p;
@@ -588,8 +637,7 @@ int orc_diag_m(const orc_ref *r, int nx, int ny, int nz, const double *affine,
                     int64_t e = ex + (int64_t)g.nx * (ey + (int64_t)g.ny * ez);
                     int a = ix + D * (iy + D * iz);
                     double C[81];
-                    const double le = mat ? mat[2 * e] : lambda, me = mat ? mat[2 * e + 1] : mu;
-                    if (orc_element_coeff(affine + 12 * e, le, me, C, NULL)) { bad = 1; continue; }
+                    if (element_coeff_of(e, affine, lambda, mu, mat, ctens, C)) { bad = 1; continue; }
                     for (int c = 0; c < 3; ++c)
                         for (int mn = 0; mn < 9; ++mn)
                             acc[c] += r->S[((size_t)mn * D3 + a) * D3 + a] * C[(mn * 3 + c) * 3 + c];

@@ -485,3 +485,70 @@ def test_traction_on_a_sheared_face_uses_the_surface_measure():
     area = np.linalg.norm(np.cross(J[:, 1], J[:, 2]))
     Nn = 27
     assert abs(F[2 * Nn:].sum() - area) <= 1e-14 * area
+
+
+# --------------------------------------------------------------------------
+# Anisotropic material (Eq. 2 with a general C_ijkl; a 6x6 Voigt matrix)
+# --------------------------------------------------------------------------
+def _iso_voigt(lam, mu):
+    Cv = np.zeros((6, 6))
+    Cv[:3, :3] = lam
+    Cv[[0, 1, 2], [0, 1, 2]] = lam + 2 * mu
+    Cv[[3, 4, 5], [3, 4, 5]] = mu
+    return Cv
+
+
+def _spd_voigt(seed):
+    rng = np.random.default_rng(seed)
+    L = rng.uniform(-1, 1, (6, 6))
+    return L @ L.T + 2.0 * np.eye(6)
+
+
+def test_isotropic_voigt_tensor_is_the_lame_operator():
+    p, n = 2, 2
+    m = syn.random_affine_cube(n, seed=21)
+    x = syn.uniform_vector(m.n_dofs(p), seed=4)
+    lam, mu = 1.3, 0.45
+    ct = np.tile(oracle.voigt_to_tensor(_iso_voigt(lam, mu)), (m.ne, 1))
+    y1 = oracle.apply(p, n, n, n, m.affine, lam, mu, x)
+    y2 = oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, x, ctens=ct)
+    assert np.max(np.abs(y1 - y2)) <= 1e-13 * np.max(np.abs(y1))
+
+
+def test_anisotropic_operator_is_symmetric_and_kills_rigid_motions():
+    p, n = 3, 2
+    m = syn.globally_affine_mesh(n, n, n, M_GLOBAL, t=(0.3, -0.2, 0.5))
+    ct = np.stack([oracle.voigt_to_tensor(_spd_voigt(100 + e)) for e in range(m.ne)])
+    rng = np.random.default_rng(6)
+    x, z = rng.uniform(-1, 1, (2, m.n_dofs(p)))
+    Ax = oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, x, ctens=ct)
+    Az = oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, z, ctens=ct)
+    assert abs(z @ Ax - x @ Az) <= 1e-12 * np.abs(z) @ np.abs(Ax)
+    assert x @ Ax > 0
+    # translations and infinitesimal rotations u = w x X give zero strain
+    X = oracle.node_coords_box(n, n, n, p) @ M_GLOBAL.T + np.array([0.3, -0.2, 0.5])
+    Nn = X.shape[0]
+    for w in np.eye(3):
+        u = np.cross(w, X).T.reshape(-1)
+        Au = oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, u, ctens=ct)
+        assert np.max(np.abs(Au)) <= 1e-11 * np.max(np.abs(Ax))
+    t = np.concatenate([np.ones(Nn), np.zeros(2 * Nn)])
+    assert np.max(np.abs(oracle.apply(p, n, n, n, m.affine, 0.0, 0.0, t, ctens=ct))) <= 1e-11 * np.max(np.abs(Ax))
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_anisotropic_patch_test_energy(p):
+    """u = G X linear: u^T A u = |Omega| eps_V . (C_V eps_V), eps_V with
+    engineering shears, on a box [0,2] x [0,1] x [0,3]."""
+    nx, ny, nz = 2, 2, 3
+    lo, hi = (0.0, 0.0, 0.0), (2.0, 1.0, 3.0)
+    aff = oracle.box_affine(nx, ny, nz, lo, hi)
+    Cv = _spd_voigt(7)
+    ct = np.tile(oracle.voigt_to_tensor(Cv), (nx * ny * nz, 1))
+    G = np.random.default_rng(8).uniform(-1, 1, (3, 3))
+    X = oracle.node_coords_box(nx, ny, nz, p, lo, hi)
+    u = (X @ G.T).T.reshape(-1)
+    e = np.array([G[0, 0], G[1, 1], G[2, 2], G[0, 1] + G[1, 0], G[0, 2] + G[2, 0], G[1, 2] + G[2, 1]])
+    exact_energy = 6.0 * e @ Cv @ e
+    energy = u @ oracle.apply(p, nx, ny, nz, aff, 0.0, 0.0, u, ctens=ct)
+    assert abs(energy - exact_energy) <= 1e-12 * abs(exact_energy)
