@@ -139,6 +139,21 @@ int pa_op_rhs(pa_op *op, const double *f0, int nmodes, const double *modes, void
  * same material.  Synchronous.  PA_EINVAL on non-finite values. */
 int pa_op_set_material(pa_op *op, const double *lambda_mu);
 
+/* Anisotropic material (Eq. 2 with a general elasticity tensor): cvoigt =
+ * host double[ne][6][6], each a symmetric Voigt matrix in the order
+ * [00, 11, 22, 01, 02, 12] acting on engineering strains, sigma_V = C_V
+ * eps_V with eps_V = [e00, e11, e22, 2 e01, 2 e02, 2 e12]; it replaces the
+ * Lame material (isotropic C_V is lambda in the upper-left 3x3 block plus
+ * 2 mu on its diagonal and mu on the shear diagonal).  The element kernel
+ * then runs in the flattened variant with a 6x6 product per quadrature
+ * point; the diagonal, solver levels (coarse levels inherit the material;
+ * the coarsest p = 1 level is solved by Jacobi-CG with operator applies)
+ * and loads follow.  NULL restores the isotropic material.  Synchronous.
+ * PA_EINVAL for non-finite or non-symmetric matrices.  The batched apply,
+ * the ablation stages and the allocation-free apply take isotropic
+ * operators only (anisotropic ones are applied one by one in a batch). */
+int pa_op_set_anisotropic(pa_op *op, const double *cvoigt);
+
 /* Adds the load of a constant traction t (host double[3]) on one face of
  * the box to F (device L-vector of the op's precision): the Neumann term of
  * the weak form, integral over the face of t . v (Eq. 1), with the op's

@@ -83,6 +83,7 @@ _sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POIN
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_set_material", [_vp, _dp])
+_sig("pa_op_set_anisotropic", [_vp, _dp])
 _sig("pa_op_apply_stage", [_vp, ctypes.c_int, _vp, _vp, _vp])
 _sig("pa_op_traction", [_vp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
@@ -259,6 +260,15 @@ def pa_op_set_material(op, mat):
     _check(lib.pa_op_set_material(op, m.ctypes.data_as(_dp)), "pa_op_set_material")
 
 
+def pa_op_set_anisotropic(op, cvoigt):
+    """Per-element symmetric 6x6 Voigt matrices [ne, 6, 6]; None restores the isotropic material."""
+    if cvoigt is None:
+        _check(lib.pa_op_set_anisotropic(op, None), "pa_op_set_anisotropic")
+        return
+    c = np.ascontiguousarray(cvoigt, dtype=np.float64)
+    _check(lib.pa_op_set_anisotropic(op, c.ctypes.data_as(_dp)), "pa_op_set_anisotropic")
+
+
 def pa_op_traction(op, face, t, F, stream=None):
     tt = np.ascontiguousarray(t, dtype=np.float64).reshape(3)
     _check(lib.pa_op_traction(op, int(face), tt.ctypes.data_as(_dp), _tptr(F), _stream_ptr(stream)),
@@ -406,7 +416,7 @@ def pa_server_destroy(srv):
 class Operator:
     """Owns a mesh + operator handle; vectors are torch CUDA tensors."""
 
-    def __init__(self, nx, ny, nz, affine, p, lam, mu, precision=PA_FP64, ess_mask=None, q=0, mat=None):
+    def __init__(self, nx, ny, nz, affine, p, lam, mu, precision=PA_FP64, ess_mask=None, q=0, mat=None, cvoigt=None):
         import torch
         self._mesh = pa_mesh_create(nx, ny, nz, affine=affine)
         try:
@@ -418,6 +428,8 @@ class Operator:
         self.dtype = torch.float64 if precision == PA_FP64 else torch.float32
         if mat is not None:
             pa_op_set_material(self.h, mat)
+        if cvoigt is not None:
+            pa_op_set_anisotropic(self.h, cvoigt)
 
     def close(self):
         if getattr(self, "h", None):

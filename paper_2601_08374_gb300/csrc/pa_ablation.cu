@@ -199,6 +199,7 @@ extern "C" int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, v
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (stage == 3) return op_apply_async(op, x, y, false, s, nullptr);
     if (op->precision != PA_FP64) return set_error(PA_EINVAL, "pa_op_apply_stage: stages 0-2 are FP64 only");
+    if (op->d_cv) return set_error(PA_EINVAL, "pa_op_apply_stage: stages 0-2 take the isotropic material only");
     int rc = stage_buffers(op, stage, s);
     if (rc) return rc;
     ApplyArgs<double> a;

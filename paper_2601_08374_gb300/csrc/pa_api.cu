@@ -114,16 +114,20 @@ static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t
     a.ess = op->d_ess;
     a.skip = skip;
     a.g = op->g;
+    a.cvoigt = static_cast<const T *>(op->d_cv);
     const Tables<T> *tab;
     if constexpr (sizeof(T) == 8) tab = &op->tab64;
     else tab = &op->tab32;
+    // an anisotropic material runs in the flattened variant
+    const ApplyLaunch launch = (op->d_cv && op->launch.variant != 0) ? default_apply_launch(op->p, PA_FP64)
+                                                                      : op->launch;
     cudaEvent_t *ev = nullptr;
     if (op->prof_on && op->prof_count * 3 + 3 <= (int)op->prof_ev.size()) {
         ev = &op->prof_ev[op->prof_count * 3];
         ++op->prof_count;
         PA_CUDA_TRY(cudaEventRecord(ev[0], s));
     }
-    int rc = launch_apply_elements<T>(a, *tab, op->launch, s);
+    int rc = launch_apply_elements<T>(a, *tab, launch, s);
     if (rc) return rc;
     if (ev) PA_CUDA_TRY(cudaEventRecord(ev[1], s));
     rc = launch_assemble<T>(a.ye, y, x, op->d_ess, T(0), accumulate, op->g, s, skip);
@@ -266,6 +270,7 @@ int pa_op_destroy(pa_op *op)
     cudaFree(op->d_xh);
     cudaFree(op->d_yh);
     for (void *q : op->d_abl) cudaFree(q);
+    cudaFree(op->d_cv);
     delete op;
     return PA_OK;
 }
@@ -383,6 +388,27 @@ namespace pa {
 
 int apply_batch_async(pa_op *const *ops, const void *const *xs, void *const *ys, int count, cudaStream_t s)
 {
+    // anisotropic operators are applied one by one (the batched kernels take
+    // the isotropic material)
+    bool any_aniso = false;
+    for (int k = 0; k < count; ++k) any_aniso = any_aniso || ops[k]->d_cv;
+    if (any_aniso) {
+        std::vector<pa_op *> o2;
+        std::vector<const void *> x2;
+        std::vector<void *> y2;
+        for (int k = 0; k < count; ++k) {
+            if (ops[k]->d_cv) {
+                int rc = op_apply_async(ops[k], xs[k], ys[k], false, s, nullptr);
+                if (rc) return rc;
+            } else {
+                o2.push_back(ops[k]);
+                x2.push_back(xs[k]);
+                y2.push_back(ys[k]);
+            }
+        }
+        if (o2.empty()) return PA_OK;
+        return apply_batch_async(o2.data(), x2.data(), y2.data(), (int)o2.size(), s);
+    }
     // groups of equal (precision, degree), in first-appearance order
     std::vector<std::vector<int>> groups;
     std::vector<std::pair<int, int>> keys;
@@ -428,13 +454,13 @@ int pa_op_diag(pa_op *op, void *d, void *stream)
     int rc;
     if (op->precision == PA_FP64) {
         rc = launch_diag_elements<double>(static_cast<const double *>(op->d_geo), static_cast<double *>(op->d_ye),
-                                          op->basis, op->g, s);
+                                          op->basis, op->g, s, static_cast<const double *>(op->d_cv));
         if (!rc)
             rc = launch_assemble<double>(static_cast<const double *>(op->d_ye), static_cast<double *>(d), nullptr,
                                          op->d_ess, 1.0, false, op->g, s);
     } else {
         rc = launch_diag_elements<float>(static_cast<const float *>(op->d_geo), static_cast<float *>(op->d_ye),
-                                         op->basis, op->g, s);
+                                         op->basis, op->g, s, static_cast<const float *>(op->d_cv));
         if (!rc)
             rc = launch_assemble<float>(static_cast<const float *>(op->d_ye), static_cast<float *>(d), nullptr,
                                         op->d_ess, 1.0f, false, op->g, s);
@@ -480,6 +506,45 @@ int pa_op_set_material(pa_op *op, const double *lambda_mu)
         return set_error(PA_ENOMEM, "pa_op_set_material: host allocation");
     }
     return upload_geometry(op);
+}
+
+int pa_op_set_anisotropic(pa_op *op, const double *cvoigt)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_set_anisotropic: null op");
+    const int64_t ne = op->g.ne;
+    if (!cvoigt) {
+        op->h_cv.clear();
+        cudaFree(op->d_cv);
+        op->d_cv = nullptr;
+        return PA_OK;
+    }
+    for (int64_t e = 0; e < ne; ++e)
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                const double v = cvoigt[e * 36 + i * 6 + j];
+                if (!std::isfinite(v)) return set_error(PA_EINVAL, "pa_op_set_anisotropic: non-finite entry");
+                if (v != cvoigt[e * 36 + j * 6 + i]) return set_error(PA_EINVAL, "pa_op_set_anisotropic: matrix not symmetric");
+            }
+    std::vector<unsigned char> up;
+    try {
+        op->h_cv.assign(cvoigt, cvoigt + 36 * ne);
+        up.resize((size_t)ne * 21 * op->elem);
+    } catch (...) {
+        return set_error(PA_ENOMEM, "pa_op_set_anisotropic: host allocation");
+    }
+    for (int64_t e = 0; e < ne; ++e) {
+        const double det = det3(op->h_affine.data() + 12 * e);
+        int k = 0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i; j < 6; ++j, ++k) {
+                const double v = det * cvoigt[e * 36 + i * 6 + j];
+                if (op->precision == PA_FP64) reinterpret_cast<double *>(up.data())[e * 21 + k] = v;
+                else reinterpret_cast<float *>(up.data())[e * 21 + k] = (float)v;
+            }
+    }
+    if (!op->d_cv) PA_CUDA_TRY(cudaMalloc(&op->d_cv, up.size()));
+    PA_CUDA_TRY(cudaMemcpy(op->d_cv, up.data(), up.size(), cudaMemcpyHostToDevice));
+    return PA_OK;
 }
 
 int pa_op_traction(pa_op *op, int face, const double *t, void *F, void *stream)

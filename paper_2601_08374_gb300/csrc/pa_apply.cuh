@@ -53,7 +53,10 @@ struct FlatLayout {
 // a round trip through HBM.  FULLC (ablation only): the stress from the full
 // 81-term contraction sigma_ij = sum_kl C_ijkl du_kl with the element's
 // tensor read from a.ctensor, in place of the Voigt arithmetic of Eq. 7.
-template <typename T, int D, int Q, int PART = 0, bool FULLC = false>
+// ANISO: anisotropic material (Eq. 2): the Voigt stress sigma_V = C_V eps_V
+// with the element's symmetric 6x6 matrix (times detJ) from a.cvoigt,
+// eps_V = [du00, du11, du22, du01 + du10, du02 + du20, du12 + du21].
+template <typename T, int D, int Q, int PART = 0, bool FULLC = false, bool ANISO = false>
 __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
     using L = FlatLayout<T, D, Q>;
@@ -203,7 +206,28 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
                 for (int j = 0; j < 3; ++j)
                     du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
             T s[3][3];
-            if constexpr (FULLC) {
+            if constexpr (ANISO) {
+                const T *cv = a.cvoigt + (e0 + el) * 21;
+                const T ev[6] = {du[0][0], du[1][1], du[2][2], du[0][1] + du[1][0], du[0][2] + du[2][0],
+                                 du[1][2] + du[2][1]};
+                T sv[6];
+#pragma unroll
+                for (int I = 0; I < 6; ++I) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int J = 0; J < 6; ++J) {
+                        const int r = I < J ? I : J, c2 = I < J ? J : I;
+                        acc = fma(cv[r * 6 - r * (r - 1) / 2 + (c2 - r)], ev[J], acc);
+                    }
+                    sv[I] = acc;
+                }
+                s[0][0] = sv[0];
+                s[1][1] = sv[1];
+                s[2][2] = sv[2];
+                s[0][1] = s[1][0] = sv[3];
+                s[0][2] = s[2][0] = sv[4];
+                s[1][2] = s[2][1] = sv[5];
+            } else if constexpr (FULLC) {
                 const T *C = a.ctensor + (e0 + el) * 81;
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
@@ -380,6 +404,13 @@ __global__ void __launch_bounds__(512) pa_apply_flat_batch_kernel(BatchArgs<T> b
     flat_body<T, D, Q>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
 }
 
+// The fused kernel with an anisotropic material.
+template <typename T, int D, int Q>
+__global__ void __launch_bounds__(512) pa_apply_flat_aniso_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
+{
+    flat_body<T, D, Q, 0, false, true>(a, tab, epb, blockIdx.x);
+}
+
 // The two halves of the fused kernel as separate launches (ablation).
 template <typename T, int D, int Q, int PART, bool FULLC>
 __global__ void __launch_bounds__(512) pa_apply_flat_part_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
@@ -397,11 +428,11 @@ template <typename T, int D, int Q>
 int launch_flat(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
     size_t smem = flat_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_flat_kernel<T, D, Q>;
-    static size_t smem_set = 0;  // largest dynamic shared memory enabled so far for this instantiation
-    if (smem > smem_set) {
+    auto kern = a.cvoigt ? pa_apply_flat_aniso_kernel<T, D, Q> : pa_apply_flat_kernel<T, D, Q>;
+    static bool smem_set[2] = {false, false};
+    if (!smem_set[a.cvoigt ? 1 : 0]) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = 227 * 1024;
+        smem_set[a.cvoigt ? 1 : 0] = true;
     }
     int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
     if (nblk <= 0) return PA_OK;

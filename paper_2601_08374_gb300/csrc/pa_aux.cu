@@ -309,7 +309,8 @@ struct DiagTables {
 // where S^a_mn = sum_alpha w d_m Phi_a d_n Phi_a factorises into products of
 // the 1D sums M, C, K (tensor-product basis, Eq. 6).
 template <typename T>
-__global__ void diag_elements_kernel(const T *__restrict__ geo, T *__restrict__ ye, DiagTables t, Grid g)
+__global__ void diag_elements_kernel(const T *__restrict__ geo, T *__restrict__ ye, DiagTables t, Grid g,
+                                     const T *__restrict__ cv)
 {
     const int D = g.p + 1, D3 = D * D * D;
     const int64_t total = g.ne * D3;
@@ -336,6 +337,28 @@ __global__ void diag_elements_kernel(const T *__restrict__ geo, T *__restrict__ 
         for (int m = 0; m < 3; ++m)
             for (int n = 0; n < 3; ++n)
                 JJ[m][n] = Ji[m * 3 + 0] * Ji[n * 3 + 0] + Ji[m * 3 + 1] * Ji[n * 3 + 1] + Ji[m * 3 + 2] * Ji[n * 3 + 2];
+        if (cv) {
+            // anisotropic: sum_mn S_mn sum_jl Ji[m][j] C_cjcl Ji[n][l], C_cjcl the
+            // Voigt entry (v(c,j), v(c,l)) of the element's matrix (times detJ)
+            const int vi[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+            const T *ce = cv + e * 21;
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int m = 0; m < 3; ++m)
+                    for (int n = 0; n < 3; ++n) {
+                        double k2 = 0.0;
+                        for (int j = 0; j < 3; ++j)
+                            for (int l = 0; l < 3; ++l) {
+                                int r = vi[c][j], q = vi[c][l];
+                                if (r > q) { const int tmp = r; r = q; q = tmp; }
+                                k2 += Ji[m * 3 + j] * (double)ce[r * 6 - r * (r - 1) / 2 + (q - r)] * Ji[n * 3 + l];
+                            }
+                        s += k2 * S[m][n];
+                    }
+                ye[(e * 3 + c) * D3 + a] = (T)s;
+            }
+            continue;
+        }
         for (int c = 0; c < 3; ++c) {
             double s = 0.0;
             for (int m = 0; m < 3; ++m)
@@ -347,7 +370,7 @@ __global__ void diag_elements_kernel(const T *__restrict__ geo, T *__restrict__ 
 }
 
 template <typename T>
-int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s)
+int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s, const T *cv)
 {
     DiagTables t{};
     for (int i = 0; i < b.D; ++i) {
@@ -357,12 +380,14 @@ int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, c
     }
     const int th = 256;
     int64_t total = g.ne * b.D * b.D * b.D;
-    diag_elements_kernel<T><<<grid_for(total, th), th, 0, s>>>(geo, ye, t, g);
+    diag_elements_kernel<T><<<grid_for(total, th), th, 0, s>>>(geo, ye, t, g, cv);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
-template int launch_diag_elements<double>(const double *, double *, const Basis1D &, const Grid &, cudaStream_t);
-template int launch_diag_elements<float>(const float *, float *, const Basis1D &, const Grid &, cudaStream_t);
+template int launch_diag_elements<double>(const double *, double *, const Basis1D &, const Grid &, cudaStream_t,
+                                          const double *);
+template int launch_diag_elements<float>(const float *, float *, const Basis1D &, const Grid &, cudaStream_t,
+                                         const float *);
 
 // ----------------------------------------------------------- load vector --
 constexpr int kMaxModes = 16;

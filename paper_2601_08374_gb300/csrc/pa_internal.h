@@ -82,6 +82,7 @@ struct ApplyArgs {
     const uint8_t *ess;  // [3*Nn] or nullptr
     const int *skip;     // device flag: when non-null and set, the launch does nothing
     Grid g;
+    const T *cvoigt = nullptr;   // anisotropic material: 6x6 Voigt matrices times detJ, upper triangle [ne][21]
     T *qvec = nullptr;         // ablation stages only: quadrature values [ne][3][3][Q^3]
     const T *ctensor = nullptr;  // ablation stages only: elasticity tensor per element [ne][81]
 };
@@ -131,7 +132,7 @@ int launch_traction(const double *affine, T *F, const uint8_t *ess, const double
 
 // Closed-form PA diagonal per element into the E-vector.
 template <typename T>
-int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s);
+int launch_diag_elements(const T *geo, T *ye, const Basis1D &b, const Grid &g, cudaStream_t s, const T *cv = nullptr);
 
 // Load vector per element into the E-vector.
 template <typename T>
@@ -192,6 +193,8 @@ struct pa_op {
     void *d_yh = nullptr;
     std::vector<double> h_affine;  // host copy of the element maps (solver levels)
     std::vector<double> h_mat;     // per-element (lambda_e, mu_e), empty for the constant material
+    std::vector<double> h_cv;      // per-element anisotropic 6x6 Voigt matrices [ne][36], empty if isotropic
+    void *d_cv = nullptr;          // device copy: upper triangles times detJ [ne][21] in the op's precision
     // ablation stages (pa_op_apply_stage), allocated on first use:
     // Q values [ne][9][Q^3], elasticity tensors [ne][81], dense basis-gradient
     // tables [3][D^3][Q^3] and weighted transposed [3][Q^3][D^3]

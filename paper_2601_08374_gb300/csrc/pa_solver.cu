@@ -1252,12 +1252,11 @@ int make_level_op(const pa_op *fine, int p, int precision, const std::vector<uin
     m.nz = fine->g.nz;
     m.affine = fine->h_affine;
     int rc = pa_op_setup(&m, p, 0, fine->lambda, fine->mu, precision, mask.empty() ? nullptr : mask.data(), out);
-    if (rc == PA_OK && !fine->h_mat.empty()) {
-        rc = pa_op_set_material(*out, fine->h_mat.data());
-        if (rc) {
-            pa_op_destroy(*out);
-            *out = nullptr;
-        }
+    if (rc == PA_OK && !fine->h_mat.empty()) rc = pa_op_set_material(*out, fine->h_mat.data());
+    if (rc == PA_OK && !fine->h_cv.empty()) rc = pa_op_set_anisotropic(*out, fine->h_cv.data());
+    if (rc && *out) {
+        pa_op_destroy(*out);
+        *out = nullptr;
     }
     return rc;
 }
@@ -2672,7 +2671,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
             TRY(dalloc(s, &L.cr, n));
             TRY(dalloc(s, &L.cp, n));
             TRY(dalloc(s, &L.cq, n));
-            if (L.p == 1 && L.op->g.Nn < (1LL << 30)) {
+            if (L.p == 1 && L.op->g.Nn < (1LL << 30) && L.op->h_cv.empty()) {
                 // assemble the coarse matrix (same quadrature as the operator);
                 // its kernels index nodes in 32 bits
                 TRY(dalloc(s, &L.stencil, 81 * n));

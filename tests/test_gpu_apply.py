@@ -342,3 +342,40 @@ def test_optimisation_stack_rejects_fp32_and_bad_stage(pa):
             pa.pa_op_apply_stage(op.h, stage, x, y)
         assert ei.value.code == pa.PA_EINVAL
     op.close()
+
+
+def _spd_voigt_stack(ne, seed):
+    rng = np.random.default_rng(seed)
+    out = np.empty((ne, 6, 6))
+    for e in range(ne):
+        L = rng.uniform(-1, 1, (6, 6))
+        out[e] = L @ L.T + 2.0 * np.eye(6)
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 4, 7])
+def test_anisotropic_apply_and_diag(pa, p, prec):
+    """A general symmetric 6x6 Voigt matrix per element (Eq. 2) against the
+    oracle's full-tensor apply and diagonal, constrained; None restores the
+    isotropic material."""
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=900 + p, ny=ny, nz=nz)
+    Cv = _spd_voigt_stack(m.ne, p)
+    ct = np.stack([oracle.voigt_to_tensor(c) for c in Cv])
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=91 + p)
+    op = pa.Operator(nx, ny, nz, m.affine, p, 1.0, 0.7, precision=prec, ess_mask=ess, cvoigt=Cv)
+    xt = torch.tensor(x, dtype=op.dtype, device="cuda")
+    yo = oracle.apply(p, nx, ny, nz, m.affine, 0.0, 0.0, x, ess=ess, ctens=ct)
+    assert _relerr(op.apply(xt).double().cpu().numpy(), yo) <= TOL[prec]
+    do = oracle.diag(p, nx, ny, nz, m.affine, 0.0, 0.0, ess=ess, ctens=ct)
+    assert _relerr(op.diag().double().cpu().numpy(), do) <= TOL[prec]
+    pa.pa_op_set_anisotropic(op.h, None)
+    yc = oracle.apply(p, nx, ny, nz, m.affine, 1.0, 0.7, x, ess=ess)
+    assert _relerr(op.apply(xt).double().cpu().numpy(), yc) <= TOL[prec]
+    bad = Cv.copy()
+    bad[0, 0, 1] += 1.0
+    with pytest.raises(pa.PAError):
+        pa.pa_op_set_anisotropic(op.h, bad)
+    op.close()
