@@ -155,6 +155,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest x over all ranks (a timing: the job is as slow as its
+    slowest rank); the identity for a single process."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gdofs(ws: int, dofs_per_rank_step: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: the dofs every rank applied over the slowest
+    rank's time (replicas: each rank runs the same per-GPU workload)."""
+    return ws * dofs_per_rank_step * steps / seconds / 1e9
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -221,10 +239,7 @@ def run_ours(args):
         te, ta, na = pa.pa_op_profile_read(c["op"].h)
         pa.pa_op_profile(c["op"].h, False)
         c["elem_ms"], c["asm_ms"], c["napplies"] = te, ta, na
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
 
     # ---- end to end through the host-buffer C ABI call (pinned buffers)
     hosts = []
@@ -248,10 +263,7 @@ def run_ours(args):
         step_s.append(time.perf_counter() - t0)
     e2e_s = statistics.median(step_s) * e2e_steps
     e2e_mean_s = sum(step_s)
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
     bytes_step = sum(c["ndofs"] * elem for c in cases)
 
     if rank != 0:
@@ -259,7 +271,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return None
 
-    value = ws * total_dofs * args.steps / (ms * 1e-3) / 1e9
+    value = job_gdofs(ws, total_dofs, args.steps, ms * 1e-3)
     # roofline of the dominant kernel (the fused element kernel), aggregated
     # over the sweep: algorithmic flops of all its launches / their event time
     peak = SM_COUNT * FLOP_PER_CLK_SM[dtype_name] * SM_MAX_MHZ * 1e6 / 1e12
@@ -310,7 +322,7 @@ def run_ours(args):
                      "kernel": " + ".join(ELEMENT_KERNEL_NAMES[v] for v in sorted({c["launch"][0] for c in cases})),
                      "peak_source": (f"derived: {SM_COUNT} SMs x {FLOP_PER_CLK_SM[dtype_name]:.0f} {dtype_name} flop/clk/SM "
                                      f"x {SM_MAX_MHZ:.0f} MHz")},
-        "e2e": {"value": round(ws * total_dofs * e2e_steps / e2e_s / 1e9, 4), "unit": "GDoF/s",
+        "e2e": {"value": round(job_gdofs(ws, total_dofs, e2e_steps, e2e_s), 4), "unit": "GDoF/s",
                 "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
                 "api": "pa_op_apply_host (pinned host buffers)", "steps": e2e_steps,
                 "estimate": "median step time (host clock)",
