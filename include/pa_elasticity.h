@@ -181,14 +181,23 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
 /* Launch shape of the fused element kernel: variant 0 (flattened
  * shared-memory sweeps, one output per thread step), 1 (register-tiled 1D
  * lines), 2 (register-tiled lines whose X-sweep threads gather and whose
- * X^T-sweep threads store their own lines) or 3 (as 2, with the fused Z
+ * X^T-sweep threads store their own lines), 3 (as 2, with the fused Z
  * stage run by three lanes per quadrature column, one per displacement
  * component, exchanging gradient entries by warp shuffles: a third of the
- * registers); elements per CTA; threads per CTA (32..512, multiple of 32;
- * variants 1-3 at most 256; in FP64 variants 1 and 2 only for p <= 4).
+ * registers) or 4 (FP32, p <= 6: the six 1D contractions on the tensor
+ * cores, tcgen05.mma kind::tf32 with three TF32 products per contraction
+ * for FP32 accuracy, accumulators in TMEM; one shape: 128 threads and
+ * floor(128 / (p+2)^2) elements per CTA); elements per CTA; threads per CTA
+ * (32..512, multiple of 32; variants 1-3 at most 256; in FP64 variants 1
+ * and 2 only for p <= 4).
  * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB. */
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);
+
+/* Reports (and clears) a timeout of a bounded tensor-core wait in an apply
+ * of this operator since the last check (variant 4): PA_OK, or
+ * PA_ETIMEOUT when a result was not valid.  Synchronous. */
+int pa_op_check(pa_op *op);
 
 /* Autotuner: times every admissible (variant, elements per CTA, threads)
  * with CUDA events on `stream`, applying the operator to the op's own

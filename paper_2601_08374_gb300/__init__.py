@@ -84,6 +84,7 @@ _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_set_material", [_vp, _dp])
 _sig("pa_op_set_anisotropic", [_vp, _dp])
+_sig("pa_op_check", [_vp])
 _sig("pa_op_apply_stage", [_vp, ctypes.c_int, _vp, _vp, _vp])
 _sig("pa_op_traction", [_vp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
@@ -258,6 +259,11 @@ def pa_op_set_material(op, mat):
         return
     m = np.ascontiguousarray(mat, dtype=np.float64)
     _check(lib.pa_op_set_material(op, m.ctypes.data_as(_dp)), "pa_op_set_material")
+
+
+def pa_op_check(op):
+    """Raises PAError(PA_ETIMEOUT) when a bounded tensor-core wait of an apply timed out."""
+    _check(lib.pa_op_check(op), "pa_op_check")
 
 
 def pa_op_set_anisotropic(op, cvoigt):

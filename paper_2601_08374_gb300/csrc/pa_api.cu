@@ -115,6 +115,7 @@ static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t
     a.skip = skip;
     a.g = op->g;
     a.cvoigt = static_cast<const T *>(op->d_cv);
+    a.err = op->d_err;
     const Tables<T> *tab;
     if constexpr (sizeof(T) == 8) tab = &op->tab64;
     else tab = &op->tab32;
@@ -271,6 +272,7 @@ int pa_op_destroy(pa_op *op)
     cudaFree(op->d_yh);
     for (void *q : op->d_abl) cudaFree(q);
     cudaFree(op->d_cv);
+    cudaFree(op->d_err);
     delete op;
     return PA_OK;
 }
@@ -319,7 +321,9 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
         (err = cudaMalloc((void **)&op->d_affine, sizeof(double) * 12 * (size_t)g.ne)) != cudaSuccess ||
         (err = cudaMalloc(&op->d_ye, (size_t)g.ne * 3 * D3 * op->elem)) != cudaSuccess ||
         (err = cudaMalloc(&op->d_xh, N * op->elem)) != cudaSuccess ||
-        (err = cudaMalloc(&op->d_yh, N * op->elem)) != cudaSuccess) {
+        (err = cudaMalloc(&op->d_yh, N * op->elem)) != cudaSuccess ||
+        (err = cudaMalloc((void **)&op->d_err, sizeof(int))) != cudaSuccess ||
+        (err = cudaMemset(op->d_err, 0, sizeof(int))) != cudaSuccess) {
         int rc = err == cudaErrorMemoryAllocation ? set_error(PA_ENOMEM, "pa_op_setup: device allocation failed")
                                                   : cuda_error(err, "pa_op_setup: cudaMalloc");
         pa_op_destroy(op);
@@ -508,6 +512,16 @@ int pa_op_set_material(pa_op *op, const double *lambda_mu)
     return upload_geometry(op);
 }
 
+int pa_op_check(pa_op *op)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_check: null op");
+    int flag = 0;
+    PA_CUDA_TRY(cudaMemcpy(&flag, op->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return PA_OK;
+    PA_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
+    return set_error(PA_ETIMEOUT, "pa_op_check: a tensor-core wait of an apply timed out (its result is not valid)");
+}
+
 int pa_op_set_anisotropic(pa_op *op, const double *cvoigt)
 {
     if (!op) return set_error(PA_EINVAL, "pa_op_set_anisotropic: null op");
@@ -604,6 +618,12 @@ int pa_op_autotune(pa_op *op, void *stream)
     for (int v = 0; v <= kMaxVariant && rc == PA_OK; ++v)
         for (int ep : epbs)
             for (int th : thrs) {
+                if (v == 4) {
+                    // the tensor-core variant has one shape: floor(128 / Q^2) elements, 128 threads
+                    if (ep != epbs[0] || th != thrs[0]) continue;
+                    ep = 128 / (op->q * op->q);
+                    th = 128;
+                }
                 if (pa_op_set_launch(op, v, ep, th) != PA_OK) continue;
                 if ((int64_t)ep > op->g.ne) continue;
                 float best_here = 1e30f;

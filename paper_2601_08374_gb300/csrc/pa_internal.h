@@ -66,10 +66,11 @@ struct Grid {
 };
 
 // --------------------------------------------------------- apply launch --
-constexpr int kMaxVariant = 3;
+constexpr int kMaxVariant = 4;
 struct ApplyLaunch {
     int variant = 0;  // 0: flattened smem sweeps, 1: register-tiled lines, 2: lines + fused gather/store,
-                      // 3: as 2 with the Z stage split over three lanes per column
+                      // 3: as 2 with the Z stage split over three lanes per column,
+                      // 4: tensor-core contractions (FP32, p <= 6)
     int epb = 1;      // elements per CTA
     int threads = 256;
 };
@@ -83,6 +84,7 @@ struct ApplyArgs {
     const int *skip;     // device flag: when non-null and set, the launch does nothing
     Grid g;
     const T *cvoigt = nullptr;   // anisotropic material: 6x6 Voigt matrices times detJ, upper triangle [ne][21]
+    int *err = nullptr;          // device flag set by a kernel whose bounded wait on the tensor core ran out
     T *qvec = nullptr;         // ablation stages only: quadrature values [ne][3][3][Q^3]
     const T *ctensor = nullptr;  // ablation stages only: elasticity tensor per element [ne][81]
 };
@@ -195,6 +197,7 @@ struct pa_op {
     std::vector<double> h_mat;     // per-element (lambda_e, mu_e), empty for the constant material
     std::vector<double> h_cv;      // per-element anisotropic 6x6 Voigt matrices [ne][36], empty if isotropic
     void *d_cv = nullptr;          // device copy: upper triangles times detJ [ne][21] in the op's precision
+    int *d_err = nullptr;          // set when a tensor-core wait timed out (pa_op_check)
     // ablation stages (pa_op_apply_stage), allocated on first use:
     // Q values [ne][9][Q^3], elasticity tensors [ne][81], dense basis-gradient
     // tables [3][D^3][Q^3] and weighted transposed [3][Q^3][D^3]

@@ -379,3 +379,40 @@ def test_anisotropic_apply_and_diag(pa, p, prec):
     with pytest.raises(pa.PAError):
         pa.pa_op_set_anisotropic(op.h, bad)
     op.close()
+
+
+@pytest.mark.parametrize("p", range(1, 7))
+def test_tensor_core_variant_against_oracle(pa, p):
+    """Variant 4 (FP32): the six 1D contractions on the tensor cores
+    (tcgen05.mma kind::tf32, three TF32 products per contraction), against
+    the oracle at the FP32 tolerance, constrained, on a mesh whose element
+    count leaves a ragged last batch; no tensor-core wait timed out."""
+    nx, ny, nz = {1: (5, 4, 3), 2: (5, 3, 2), 3: (3, 3, 2), 4: (5, 2, 1), 5: (3, 1, 1), 6: (3, 1, 1)}[p]
+    m = syn.random_affine_cube(nx, seed=950 + p, ny=ny, nz=nz)
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=95 + p)
+    yo = oracle.apply(p, nx, ny, nz, m.affine, 1.0, 0.7, x, ess=ess)
+    op = pa.Operator(nx, ny, nz, m.affine, p, 1.0, 0.7, precision=pa.PA_FP32, ess_mask=ess)
+    E = 128 // (p + 2) ** 2
+    assert op.nelem % E != 0
+    pa.pa_op_set_launch(op.h, 4, E, 128)
+    with pytest.raises(pa.PAError):
+        pa.pa_op_set_launch(op.h, 4, E + 1, 128)  # the one admissible shape
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    y = op.apply(xt)
+    torch.cuda.synchronize()
+    pa.pa_op_check(op.h)
+    assert _relerr(y.double().cpu().numpy(), yo) <= TOL[1]
+    op.close()
+
+
+def test_tensor_core_variant_is_fp32_and_low_degree_only(pa):
+    m = syn.random_affine_cube(2, seed=3)
+    op64 = pa.Operator(2, 2, 2, m.affine, 2, 1.0, 1.0)
+    with pytest.raises(pa.PAError):
+        pa.pa_op_set_launch(op64.h, 4, 8, 128)
+    op64.close()
+    op = pa.Operator(2, 1, 1, m.affine[:2], 7, 1.0, 1.0, precision=pa.PA_FP32)
+    with pytest.raises(pa.PAError):
+        pa.pa_op_set_launch(op.h, 4, 1, 128)
+    op.close()
