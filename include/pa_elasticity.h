@@ -186,7 +186,7 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
  * component, exchanging gradient entries by warp shuffles: a third of the
  * registers) or 4 (FP32, p <= 6: the six 1D contractions on the tensor
  * cores, tcgen05.mma kind::tf32 with three TF32 products per contraction
- * for FP32 accuracy, accumulators in TMEM; one shape: 128 threads and
+ * for FP32 accuracy, accumulators in TMEM; one shape: 384 threads and
  * floor(128 / (p+2)^2) elements per CTA); elements per CTA; threads per CTA
  * (32..512, multiple of 32; variants 1-3 at most 256; in FP64 variants 1
  * and 2 only for p <= 4).

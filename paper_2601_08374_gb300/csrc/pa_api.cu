@@ -619,10 +619,10 @@ int pa_op_autotune(pa_op *op, void *stream)
         for (int ep : epbs)
             for (int th : thrs) {
                 if (v == 4) {
-                    // the tensor-core variant has one shape: floor(128 / Q^2) elements, 128 threads
+                    // the tensor-core variant has one shape: floor(128 / Q^2) elements, 384 threads
                     if (ep != epbs[0] || th != thrs[0]) continue;
                     ep = 128 / (op->q * op->q);
-                    th = 128;
+                    th = 384;
                 }
                 if (pa_op_set_launch(op, v, ep, th) != PA_OK) continue;
                 if ((int64_t)ep > op->g.ne) continue;

@@ -22,8 +22,8 @@ size_t smem_for(const ApplyLaunch &c)
 {
     if (c.variant == 0) return flat_smem_bytes<float, D, Q>(c.epb);
     if (c.variant == 4) {
-        // one shape: 128 threads, floor(128 / Q^2) elements per CTA
-        if (tc_elems(D, Q) == 0 || c.threads != 128 || c.epb != tc_elems(D, Q)) return 0;
+        // one shape: 384 threads, floor(128 / Q^2) elements per CTA
+        if (tc_elems(D, Q) == 0 || c.threads != kTcThreads || c.epb != tc_elems(D, Q)) return 0;
         return tc_smem_bytes();
     }
     if (c.threads > 256) return 0;

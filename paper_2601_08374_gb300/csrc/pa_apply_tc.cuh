@@ -22,10 +22,12 @@
 //   Y^T  rows (el, iz, qx)   slices (c, m)        K = qy   U0 = T0 Bw, U12 = T1 Gw + T2 Bw
 //   X^T  rows (el, iz, iy)   slices (c, U0/U12)   K = qx   y = U0 Gw + U12 Bw
 //
-// One thread per TMEM lane (128 threads); after each sweep a thread reads
-// its line's accumulators and writes the values, split into TF32 hi / lo,
-// to the rows of the next sweep's A operand (a transpose through shared
-// memory).  Operands are K-major without swizzle: core matrices of 8 rows x
+// Three threads per TMEM lane (384 threads; warps w, w + 4, w + 8 read the
+// same lane quarter): thread part c handles displacement component c of its
+// line (the pointwise stage: every third quadrature point).  After each
+// sweep a thread reads its line's accumulators and writes the values, split
+// into TF32 hi / lo, to the rows of the next sweep's A operand (a transpose
+// through shared memory).  Operands are K-major without swizzle: core matrices of 8 rows x
 // 16 bytes, LBO 128 B along K, SBO (K / 4) * 128 B along M.  Every wait on
 // the tensor core is bounded; on timeout the kernel flags a.err, frees its
 // TMEM and returns.
@@ -178,8 +180,10 @@ __device__ __forceinline__ void tc_issue(int sweep, uint32_t tmem, const unsigne
     }
 }
 
+constexpr int kTcThreads = 384;
+
 template <int D, int Q>
-__global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, TcTables tt, int64_t nbatch)
+__global__ void __launch_bounds__(kTcThreads, 2) pa_apply_tc_kernel(ApplyArgs<float> a, TcTables tt, int64_t nbatch)
 {
     using namespace tc;
     constexpr int E = kRows / (Q * Q);
@@ -190,18 +194,20 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
     uint64_t *mbar = reinterpret_cast<uint64_t *>(Tlo + kNumTab * kTab * 4);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, part = tid >> 7;  // line (TMEM lane) and component
     const Grid &g = a.g;
     const int p = D - 1;
     const int64_t Nn = g.Nn, Mx = g.Mx, MxMy = (int64_t)g.Mx * g.My;
 
     // tables to their canonical layout; the A buffers zeroed (padding entries
     // must be finite: they meet zero table entries)
-    for (int i = tid; i < kNumTab * 16 * 8; i += 128) {
+    for (int i = tid; i < kNumTab * 16 * 8; i += kTcThreads) {
         const int t = i / 128, r = (i / 8) % 16, k = i % 8;
         *reinterpret_cast<float *>(Thi + t * kTab * 4 + off(r, k, 256)) = tt.hi[t][r][k];
         *reinterpret_cast<float *>(Tlo + t * kTab * 4 + off(r, k, 256)) = tt.lo[t][r][k];
     }
-    for (int i = tid; i < 2 * kAbytes / 16; i += 128) reinterpret_cast<float4 *>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < 2 * kAbytes / 16; i += kTcThreads)
+        reinterpret_cast<float4 *>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool ok = true;
 
@@ -243,76 +249,71 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
         const int ne = (int)((g.ne - e0) < E ? (g.ne - e0) : E);
         float v[16];
 
-        // ---- gather: row (el, iz, iy), slice c, K = ix
-        if (tid < ne * D * D) {
-            const int el = tid / (D * D), iz = (tid / D) % D, iy = tid % D;
+        // ---- gather: row (el, iz, iy), slice c = part, K = ix
+        if (row < ne * D * D) {
+            const int el = row / (D * D), iz = (row / D) % D, iy = row % D;
             const int64_t e = e0 + el, t = e / g.nx;
             const int ex = (int)(e - t * g.nx), ey = (int)(t % g.ny), ez = (int)(t / g.ny);
             const int64_t base = (int64_t)ex * p + Mx * ((int64_t)ey * p + iy) + MxMy * ((int64_t)ez * p + iz);
+            const int c = part;
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int ix = 0; ix < D; ++ix) {
-                    const int64_t k = c * Nn + base + ix;
-                    float xv = a.x[k];
-                    if (a.ess && a.ess[k]) xv = 0.f;
-                    put(Ahi, Alo, tid, 8 * c + ix, xv);
-                }
+            for (int ix = 0; ix < D; ++ix) {
+                const int64_t k = c * Nn + base + ix;
+                float xv = a.x[k];
+                if (a.ess && a.ess[k]) xv = 0.f;
+                put(Ahi, Alo, row, 8 * c + ix, xv);
+            }
         }
         if (!(ok = run(0))) break;
         // ---- X out: row (el, iz, iy); blocks c: u[qx] cols < Q, v[qx] cols Q..2Q-1
         //      -> Y rows (el, iz, qx), slices (c, u/v), K = iy
         {
-            const bool act = tid < ne * D * D;
-            const int el = tid / (D * D), iz = (tid / D) % D, iy = tid % D;
+            const bool act = row < ne * D * D;
+            const int el = row / (D * D), iz = (row / D) % D, iy = row % D;
+            const int c = part;
+            ld16(lane_base + 16 * c, v);
+            ld_wait();
+            if (act)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ld16(lane_base + 16 * c, v);
-                ld_wait();
-                if (act)
-#pragma unroll
-                    for (int qx = 0; qx < Q; ++qx) {
-                        const int r = (el * D + iz) * Q + qx;
-                        put(Ahi, Alo, r, 8 * (2 * c) + iy, v[qx]);
-                        put(Ahi, Alo, r, 8 * (2 * c + 1) + iy, v[Q + qx]);
-                    }
-            }
+                for (int qx = 0; qx < Q; ++qx) {
+                    const int r = (el * D + iz) * Q + qx;
+                    put(Ahi, Alo, r, 8 * (2 * c) + iy, v[qx]);
+                    put(Ahi, Alo, r, 8 * (2 * c + 1) + iy, v[Q + qx]);
+                }
         }
         if (!(ok = run(1))) break;
         // ---- Y out: row (el, iz, qx); block 2c: d2[qy] cols < Q, d1[qy] cols Q..; block 2c+1: d0[qy]
         //      -> Z rows (el, qy, qx), slices (c, k), K = iz
         {
-            const bool act = tid < ne * D * Q;
-            const int el = tid / (D * Q), iz = (tid / Q) % D, qx = tid % Q;
+            const bool act = row < ne * D * Q;
+            const int el = row / (D * Q), iz = (row / Q) % D, qx = row % Q;
+            const int c = part;
+            float w[16];
+            ld16(lane_base + 16 * (2 * c), v);
+            ld16(lane_base + 16 * (2 * c + 1), w);
+            ld_wait();
+            if (act)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float w[16];
-                ld16(lane_base + 16 * (2 * c), v);
-                ld16(lane_base + 16 * (2 * c + 1), w);
-                ld_wait();
-                if (act)
-#pragma unroll
-                    for (int qy = 0; qy < Q; ++qy) {
-                        const int r = (el * Q + qy) * Q + qx;
-                        put(Ahi, Alo, r, 8 * (3 * c + 0) + iz, w[qy]);      // d0: d/dxi
-                        put(Ahi, Alo, r, 8 * (3 * c + 1) + iz, v[Q + qy]);  // d1: d/deta
-                        put(Ahi, Alo, r, 8 * (3 * c + 2) + iz, v[qy]);      // d2: interpolated
-                    }
-            }
+                for (int qy = 0; qy < Q; ++qy) {
+                    const int r = (el * Q + qy) * Q + qx;
+                    put(Ahi, Alo, r, 8 * (3 * c + 0) + iz, w[qy]);      // d0: d/dxi
+                    put(Ahi, Alo, r, 8 * (3 * c + 1) + iz, v[Q + qy]);  // d1: d/deta
+                    put(Ahi, Alo, r, 8 * (3 * c + 2) + iz, v[qy]);      // d2: interpolated
+                }
         }
         if (!(ok = run(2))) break;
         // ---- Z out + pointwise: row (el, qy, qx); block 3c+k: gr[c][k] at qz (cols < Q)
         //      -> Z^T rows (el, qy, qx) (the same), slices (c, m), K = qz
         {
-            const bool act = tid < ne * Q * Q;
-            const int el = act ? tid / (Q * Q) : 0;
+            const bool act = row < ne * Q * Q;
+            const int el = act ? row / (Q * Q) : 0;
             const float *geo = a.geo + (e0 + el) * kGeoStride;
             float Ji[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) Ji[i] = act ? geo[i] : 0.f;
             const float cl = act ? geo[9] : 0.f, cm = act ? geo[10] : 0.f, m2 = cm + cm;
 #pragma unroll 1
-            for (int qz = 0; qz < Q; ++qz) {
+            for (int qz = part; qz < Q; qz += 3) {
                 // the nine reference-gradient entries at this point (column qz of blocks 0..8)
                 float gq[9];
 #pragma unroll
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
                     for (int c = 0; c < 3; ++c)
 #pragma unroll
                         for (int m = 0; m < 3; ++m)
-                            put(Ahi, Alo, tid, 8 * (3 * c + m) + qz,
+                            put(Ahi, Alo, row, 8 * (3 * c + m) + qz,
                                 fmaf(s3[c][0], Ji[m * 3 + 0], fmaf(s3[c][1], Ji[m * 3 + 1], s3[c][2] * Ji[m * 3 + 2])));
                 }
             }
@@ -347,10 +348,10 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
         // ---- Z^T out: row (el, qy, qx); block 3c+m: T[c][m][iz] (cols < D)
         //      -> Y^T rows (el, iz, qx), slices (c, m), K = qy
         {
-            const bool act = tid < ne * Q * Q;
-            const int el = tid / (Q * Q), qy = (tid / Q) % Q, qx = tid % Q;
+            const bool act = row < ne * Q * Q;
+            const int el = row / (Q * Q), qy = (row / Q) % Q, qx = row % Q;
 #pragma unroll
-            for (int s = 0; s < 9; ++s) {
+            for (int s = 3 * part; s < 3 * part + 3; ++s) {
                 ld16(lane_base + 16 * s, v);
                 ld_wait();
                 if (act)
@@ -362,10 +363,10 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
         // ---- Y^T out: row (el, iz, qx); block 2c: U0[iy], block 2c+1: U12[iy]
         //      -> X^T rows (el, iz, iy), slices (c, U0/U12), K = qx
         {
-            const bool act = tid < ne * D * Q;
-            const int el = tid / (D * Q), iz = (tid / Q) % D, qx = tid % Q;
+            const bool act = row < ne * D * Q;
+            const int el = row / (D * Q), iz = (row / Q) % D, qx = row % Q;
 #pragma unroll
-            for (int s = 0; s < 6; ++s) {
+            for (int s = 2 * part; s < 2 * part + 2; ++s) {
                 ld16(lane_base + 16 * s, v);
                 ld_wait();
                 if (act)
@@ -376,17 +377,15 @@ __global__ void __launch_bounds__(128) pa_apply_tc_kernel(ApplyArgs<float> a, Tc
         if (!(ok = run(5))) break;
         // ---- X^T out: row (el, iz, iy); block c: y[c][ix] -> E-vector
         {
-            const bool act = tid < ne * D * D;
-            const int el = tid / (D * D), iz = (tid / D) % D, iy = tid % D;
+            const bool act = row < ne * D * D;
+            const int el = row / (D * D), iz = (row / D) % D, iy = row % D;
+            const int c = part;
+            ld16(lane_base + 16 * c, v);
+            ld_wait();
+            if (act) {
+                float *out = a.ye + ((e0 + el) * 3 + c) * D3 + (iz * D + iy) * D;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ld16(lane_base + 16 * c, v);
-                ld_wait();
-                if (act) {
-                    float *out = a.ye + ((e0 + el) * 3 + c) * D3 + (iz * D + iy) * D;
-#pragma unroll
-                    for (int ix = 0; ix < D; ++ix) out[ix] = v[ix];
-                }
+                for (int ix = 0; ix < D; ++ix) out[ix] = v[ix];
             }
         }
     }
@@ -418,7 +417,7 @@ int launch_tc(const ApplyArgs<float> &a, const TcTables &tt, cudaStream_t s)
         smem_set = true;
     }
     const int64_t grid = nbatch < 2 * 152 ? nbatch : 2 * 152;
-    kern<<<(unsigned)grid, 128, tc_smem_bytes(), s>>>(a, tt, nbatch);
+    kern<<<(unsigned)grid, kTcThreads, tc_smem_bytes(), s>>>(a, tt, nbatch);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }

@@ -395,9 +395,9 @@ def test_tensor_core_variant_against_oracle(pa, p):
     op = pa.Operator(nx, ny, nz, m.affine, p, 1.0, 0.7, precision=pa.PA_FP32, ess_mask=ess)
     E = 128 // (p + 2) ** 2
     assert op.nelem % E != 0
-    pa.pa_op_set_launch(op.h, 4, E, 128)
+    pa.pa_op_set_launch(op.h, 4, E, 384)
     with pytest.raises(pa.PAError):
-        pa.pa_op_set_launch(op.h, 4, E + 1, 128)  # the one admissible shape
+        pa.pa_op_set_launch(op.h, 4, E + 1, 384)  # the one admissible shape
     xt = torch.tensor(x, dtype=torch.float32, device="cuda")
     y = op.apply(xt)
     torch.cuda.synchronize()
@@ -410,9 +410,9 @@ def test_tensor_core_variant_is_fp32_and_low_degree_only(pa):
     m = syn.random_affine_cube(2, seed=3)
     op64 = pa.Operator(2, 2, 2, m.affine, 2, 1.0, 1.0)
     with pytest.raises(pa.PAError):
-        pa.pa_op_set_launch(op64.h, 4, 8, 128)
+        pa.pa_op_set_launch(op64.h, 4, 8, 384)
     op64.close()
     op = pa.Operator(2, 1, 1, m.affine[:2], 7, 1.0, 1.0, precision=pa.PA_FP32)
     with pytest.raises(pa.PAError):
-        pa.pa_op_set_launch(op.h, 4, 1, 128)
+        pa.pa_op_set_launch(op.h, 4, 1, 384)
     op.close()
