@@ -85,12 +85,12 @@ def kernel_source_hash() -> str:
 # and launch table with this hash.  The E-vector writes mostly stay in L2
 # and reach DRAM during the assembly kernel, so for p >= 4 the figure is
 # essentially the reads of x and of the geometry records.
-TRAFFIC_HASH = "1dea2309d720e077"
+TRAFFIC_HASH = "1e62abf3e5d7bfad"
 ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>",
-                        3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>"}
+                        3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)"}
 TRAFFIC_BYTES: dict = {
-    ("f64", 1): 249046528, ("f64", 2): 60151168, ("f64", 4): 26915712, ("f64", 6): 22379264, ("f64", 8): 22179328,
-    ("f32", 1): 96714752, ("f32", 2): 18397056, ("f32", 4): 13158144, ("f32", 6): 11214848, ("f32", 8): 11122688,
+    ("f64", 1): 249766016, ("f64", 2): 59984512, ("f64", 4): 26843776, ("f64", 6): 22366848, ("f64", 8): 22146432,
+    ("f32", 1): 96612224, ("f32", 2): 18396416, ("f32", 4): 13157504, ("f32", 6): 11214336, ("f32", 8): 11102848,
 }
 
 
