@@ -352,8 +352,10 @@ def run_ours(args):
 
 def run_solves(args, pa, torch):
     """GMG-PCG solves/s: the cantilever beam (32x4x4 elements, p = 4 -> 2 -> 1,
-    FP64 and mixed) and the near-incompressible random-affine cubes (~8M
-    dofs, p = 6 and 8, FP64 and mixed).  Setup (operators, diagonals,
+    FP64 and mixed; also with two h-levels under the p-levels), the beam
+    refined once more (64x8x8) with and without three h-levels, and the
+    near-incompressible random-affine cubes (~8M dofs, p = 6 and 8, FP64
+    and mixed).  Setup (operators, diagonals,
     eigenvalue estimates, graph capture on the first solve) is untimed."""
     out = []
     beam = syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0))
@@ -362,7 +364,15 @@ def run_solves(args, pa, torch):
              dict(name="two-material beam 32x4x4 p=4 (4->2->1): lambda=mu=50 for x<4, lambda=mu=1 beyond; "
                        "traction (0,0,-1e-2) on x=8, x=0 clamped (the paper's benchmark physics)", mesh=beam,
                   p=4, levels=[4, 2, 1], nu=None, mat=syn.two_material(beam, 4.0), modes=None, f0=(0.0, 0.0, 0.0),
-                  traction=(1, (0.0, 0.0, -1e-2)), reps=args.solve_reps)]
+                  traction=(1, (0.0, 0.0, -1e-2)), reps=args.solve_reps),
+             dict(name="beam 32x4x4 p=4 (4->2->1, then h-levels 16x2x2 and 8x1x1 at p=1) E=1 nu=0.3 f=(0,0,-1), "
+                       "x=0 clamped", mesh=beam, p=4, levels=[4, 2, 1], h=2, nu=0.3, modes=None,
+                  f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
+    beam2 = syn.box_mesh(64, 8, 8, hi=(8.0, 1.0, 1.0))
+    for h in (0, 3):
+        cases.append(dict(name=f"beam 64x8x8 p=4 (4->2->1{', then 3 h-levels to 8x1x1' if h else ''}) E=1 nu=0.3 "
+                               "f=(0,0,-1), x=0 clamped", mesh=beam2, p=4, levels=[4, 2, 1], h=h, nu=0.3, modes=None,
+                          f0=(0.0, 0.0, -1.0), reps=args.solve_reps, solve_modes=("fp64", "mixed_fcg")))
     if not args.quick_solves:
         for p, n in ((6, syn.mixed_n(6)), (8, syn.mixed_n(8))):
             lv = [p, p // 2, 1] if p == 6 else [8, 4, 2, 1]
@@ -375,10 +385,13 @@ def run_solves(args, pa, torch):
         ess = syn.clamp_mask(m, p)
         op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess, mat=c.get("mat"))
         b = op.rhs(f0=c["f0"], modes=c["modes"], traction=c.get("traction"))
-        row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "rtol": 1e-10}
+        h = c.get("h", 0)
+        row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "h_levels": h, "rtol": 1e-10}
         sols = {}
         for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):
-            s = pa.pa_solver_create(op.h, c["levels"], 2, COARSE_RTOL, COARSE_MAXIT, mode)
+            if key not in c.get("solve_modes", ("fp64", "mixed_ir", "mixed_fcg")):
+                continue
+            s = pa.pa_solver_create_hp(op.h, c["levels"], h, 2, COARSE_RTOL, COARSE_MAXIT, mode)
             x = torch.zeros_like(b)
             code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)  # warm-up (captures the graphs)
             times = []
@@ -397,6 +410,8 @@ def run_solves(args, pa, torch):
                 row[key]["refinements"] = info.refinements
             pa.pa_solver_destroy(s)
         for key in ("mixed_ir", "mixed_fcg"):
+            if key not in sols:
+                continue
             d = (sols[key] - sols["fp64"]).norm() / sols["fp64"].norm()
             row[key]["rel_diff_vs_fp64"] = float(f"{float(d):.3e}")
             row[key]["speedup_over_fp64"] = round(row[key]["solves_per_s"] / row["fp64"]["solves_per_s"], 3)

@@ -220,7 +220,11 @@ int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64
  * GLL spaces of p-levels).  prolong: xf = P xc evaluates the coarse field at
  * the fine nodes; restrict: rc = P^T rf (exact transpose).  FP64 device
  * L-vectors; no essential-dof masking is applied.  Both operators must be
- * FP64. */
+ * FP64.  The same calls give the h-transfer when both operators are p = 1
+ * and the fine mesh has twice the coarse element count in x, y and z (the
+ * natural injection of the trilinear space under one uniform refinement:
+ * fine node 2I takes coarse node I, an odd fine node the mean of its two
+ * coarse neighbours along each axis). */
 int pa_op_prolong(const pa_op *coarse, const pa_op *fine, const double *xc, double *xf, void *stream);
 int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, double *rc, void *stream);
 
@@ -292,6 +296,25 @@ enum pa_solve_mode { PA_SOLVE_FP64 = 0, PA_SOLVE_MIXED = 1, PA_SOLVE_MIXED_FCG =
  * outer loop.  `fine` must be FP64 and must outlive the solver. */
 int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order, double coarse_rtol,
                      int coarse_maxit, int mode, pa_solver **out);
+
+/* As pa_solver_create, with h_levels geometric levels appended below the
+ * p-levels (Sec. 3: the hierarchy of r uniform refinements at p = 1, then
+ * p-refinements).  Requires p_levels[nlev-1] = 1 when h_levels > 0 and
+ * nlev + h_levels <= 8.  Each h-level is the p = 1 operator (matrix-free PA,
+ * Chebyshev-Jacobi smoothed like the p-levels) on the mesh whose uniform
+ * refinement is the level above: coarse element (I,J,K) merges fine elements
+ * (2I+a, 2J+b, 2K+c), a, b, c in {0,1}, with x0 of child (0,0,0) and twice its
+ * J.  Transfers between h-levels are the natural injection of the trilinear
+ * space (prolongation) and its exact transpose (restriction).  A coarse dof
+ * is essential when its interpolation reaches an essential fine dof.  The
+ * coarsest level is solved as in pa_solver_create (assembled p = 1 matrix,
+ * CG preconditioned by a Galerkin multigrid on that matrix).
+ * Fails with PA_EINVAL if some h-level has an odd element count in any
+ * direction, if some coarse element's eight children are not the eighths of
+ * one affine map (to 1e-12 relative), or if the per-element material
+ * (pa_op_set_material / pa_op_set_anisotropic) differs among them. */
+int pa_solver_create_hp(pa_op *fine, int nlev, const int *p_levels, int h_levels, int cheb_order,
+                        double coarse_rtol, int coarse_maxit, int mode, pa_solver **out);
 int pa_solver_destroy(pa_solver *s);
 
 /* Solver options:

@@ -313,6 +313,36 @@ def restrict(pc, pf, nx, ny, nz, rf):
     return rc
 
 
+def _h_matrix_1d(n):
+    """[2n+1, n+1] matrix of one uniform refinement of n linear elements:
+    row i holds the coarse nodal basis (GLL p = 1, barycentric Lagrange)
+    evaluated at fine node i, which lies at reference coordinate
+    (i - 2E) / 2 of coarse element E = min(i // 2, n - 1)."""
+    nodes = gll01(1)
+    P = np.zeros((2 * n + 1, n + 1))
+    for i in range(2 * n + 1):
+        E = min(i // 2, n - 1)
+        val, _ = lagrange(nodes, [(i - 2 * E) / 2.0])
+        P[i, E:E + 2] = val[:, 0]
+    return P
+
+
+def prolong_h(nx, ny, nz, xc):
+    """h-prolongation (Sec. 3, natural injection for h-refined levels): the
+    p = 1 field on the nx*ny*nz coarse mesh evaluated at the nodes of its
+    uniform refinement (2nx*2ny*2nz elements).  Component-major L-vectors."""
+    Px, Py, Pz = _h_matrix_1d(nx), _h_matrix_1d(ny), _h_matrix_1d(nz)
+    xc = _f64(xc).reshape(3, nz + 1, ny + 1, nx + 1)
+    return np.einsum("ia,jb,kc,dcba->dkji", Px, Py, Pz, xc).reshape(-1)
+
+
+def restrict_h(nx, ny, nz, rf):
+    """Transpose of ``prolong_h`` (nx, ny, nz: the coarse element counts)."""
+    Px, Py, Pz = _h_matrix_1d(nx), _h_matrix_1d(ny), _h_matrix_1d(nz)
+    rf = _f64(rf).reshape(3, 2 * nz + 1, 2 * ny + 1, 2 * nx + 1)
+    return np.einsum("ia,jb,kc,dkji->dcba", Px, Py, Pz, rf).reshape(-1)
+
+
 def box_affine(nx, ny, nz, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     A = np.zeros((nx * ny * nz, 12))
     _lib().orc_box_affine(nx, ny, nz, _d(_f64(lo)), _d(_f64(hi)), _d(A))

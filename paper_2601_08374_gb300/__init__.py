@@ -108,6 +108,8 @@ _sig("pa_server_set_option", [_vp, ctypes.c_int, ctypes.c_double])
 if hasattr(lib, "pa_solver_create"):
     _sig("pa_solver_create", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.POINTER(_vp)])
+    _sig("pa_solver_create_hp", [_vp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_int, ctypes.POINTER(_vp)])
     _sig("pa_solver_destroy", [_vp])
     _sig("pa_solver_set_option", [_vp, ctypes.c_int, ctypes.c_double])
     _sig("pa_gmg_pcg_solve", [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(pa_solve_info), _vp])
@@ -312,6 +314,17 @@ def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=
     lv = (ctypes.c_int * len(p_levels))(*p_levels)
     _check(lib.pa_solver_create(op, len(p_levels), lv, cheb_order, coarse_rtol, coarse_maxit, mode,
                                 ctypes.byref(h)), "pa_solver_create")
+    return h
+
+
+def pa_solver_create_hp(op, p_levels, h_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=300,
+                        mode=PA_SOLVE_FP64):
+    """p-levels on the operator's mesh, then `h_levels` p = 1 levels on meshes
+    coarsened by two per direction (uniform refinement undone)."""
+    h = _vp()
+    lv = (ctypes.c_int * len(p_levels))(*p_levels)
+    _check(lib.pa_solver_create_hp(op, len(p_levels), lv, h_levels, cheb_order, coarse_rtol, coarse_maxit, mode,
+                                   ctypes.byref(h)), "pa_solver_create_hp")
     return h
 
 

@@ -666,39 +666,11 @@ __global__ void k_stencil_apply(const double *__restrict__ vals, const double *_
     GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, g, row);
 }
 
-// One axis of the h-prolongation: out (axis `ax` fine, size Mf) from in
-// (axis coarse, size Mc); dims of out given in Nx, Ny, Nz.
-__global__ void k_hprolong_axis(double *out, const double *in, int ax, int Nx, int Ny, int Nz, int Mf, int Mc,
-                                int accumulate)
-{
-    const int dims[3] = {Nx, Ny, Nz};
-    int cdims[3] = {Nx, Ny, Nz};
-    cdims[ax] = Mc;
-    const int64_t total = 3LL * Nx * Ny * Nz;
-    GRID_STRIDE(o, total)
-    {
-        int64_t t = o;
-        int idx[3];
-        idx[0] = (int)(t % dims[0]); t /= dims[0];
-        idx[1] = (int)(t % dims[1]); t /= dims[1];
-        idx[2] = (int)(t % dims[2]);
-        const int c = (int)(t / dims[2]);
-        int J[2];
-        double w[2];
-        const int np = h_parents(idx[ax], Mf, Mc, J, w);
-        double s2 = 0.0;
-        for (int k = 0; k < np; ++k) {
-            idx[ax] = J[k];
-            s2 += w[k] * in[(((int64_t)c * cdims[2] + idx[2]) * cdims[1] + idx[1]) * cdims[0] + idx[0]];
-        }
-        out[o] = accumulate ? out[o] + s2 : s2;
-    }
-}
-
-// h-prolongation added in one pass: ef += P ec, each fine dof gathering its
-// (at most 8) coarse parents, nested x inside y inside z like the
-// axis-by-axis form.
-__global__ void k_hprolong_add(double *__restrict__ ef, const double *__restrict__ ec, Grid gf, Grid gc)
+// h-prolongation (natural injection of the trilinear space, Sec. 3) in one
+// pass: ef += P ec, each fine dof gathering its (at most 8) coarse parents,
+// summed x inside y inside z.
+template <typename T>
+__global__ void k_hprolong_add(T *__restrict__ ef, const T *__restrict__ ec, Grid gf, Grid gc)
 {
     const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
     GRID_STRIDE(o, 3 * Nnf)
@@ -710,16 +682,16 @@ __global__ void k_hprolong_add(double *__restrict__ ef, const double *__restrict
         double wx[2], wy[2], wz[2];
         const int nx = h_parents(fx, gf.Mx, gc.Mx, Jx, wx), ny = h_parents(fy, gf.My, gc.My, Jy, wy),
                   nz = h_parents(fz, gf.Mz, gc.Mz, Jz, wz);
-        double sz = 0.0;
+        T sz = 0;
         for (int kz = 0; kz < nz; ++kz) {
-            double sy = 0.0;
+            T sy = 0;
             for (int ky = 0; ky < ny; ++ky) {
-                const double *row = ec + c * Nnc + (int64_t)gc.Mx * (Jy[ky] + (int64_t)gc.My * Jz[kz]);
-                double sx = 0.0;
-                for (int kx = 0; kx < nx; ++kx) sx += wx[kx] * row[Jx[kx]];
-                sy += wy[ky] * sx;
+                const T *row = ec + c * Nnc + (int64_t)gc.Mx * (Jy[ky] + (int64_t)gc.My * Jz[kz]);
+                T sx = 0;
+                for (int kx = 0; kx < nx; ++kx) sx += (T)wx[kx] * row[Jx[kx]];
+                sy += (T)wy[ky] * sx;
             }
-            sz += wz[kz] * sy;
+            sz += (T)wz[kz] * sy;
         }
         ef[o] = ef[o] + sz;
     }
@@ -728,8 +700,9 @@ __global__ void k_hprolong_add(double *__restrict__ ef, const double *__restrict
 // h-restriction in one pass: out = R (in - in2) (in2 may be null), each
 // coarse dof gathering its fine children (at most 3 per axis) with the
 // transposed weights; essential coarse dofs are zeroed.
-__global__ void k_hrestrict(double *__restrict__ out, const double *__restrict__ in, const double *__restrict__ in2,
-                            Grid gf, Grid gc, const uint8_t *__restrict__ ess)
+template <typename T>
+__global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ in2, Grid gf, Grid gc,
+                            const uint8_t *__restrict__ ess)
 {
     const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
     GRID_STRIDE(o, 3 * Nnc)
@@ -738,61 +711,29 @@ __global__ void k_hrestrict(double *__restrict__ out, const double *__restrict__
         const int64_t I = o - c * Nnc;
         const int Jx = (int)(I % gc.Mx), Jy = (int)((I / gc.Mx) % gc.My), Jz = (int)(I / ((int64_t)gc.Mx * gc.My));
         const int px = h_pos(Jx, gf.Mx, gc.Mx), py = h_pos(Jy, gf.My, gc.My), pz = h_pos(Jz, gf.Mz, gc.Mz);
-        double sz = 0.0;
+        T sz = 0;
         for (int iz = pz - 1; iz <= pz + 1; ++iz) {
             if (iz < 0 || iz >= gf.Mz) continue;
-            const double wz = h_weight(iz, Jz, gf.Mz, gc.Mz);
-            if (wz == 0.0) continue;
-            double sy = 0.0;
+            const T wz = (T)h_weight(iz, Jz, gf.Mz, gc.Mz);
+            if (wz == (T)0) continue;
+            T sy = 0;
             for (int iy = py - 1; iy <= py + 1; ++iy) {
                 if (iy < 0 || iy >= gf.My) continue;
-                const double wy = h_weight(iy, Jy, gf.My, gc.My);
-                if (wy == 0.0) continue;
+                const T wy = (T)h_weight(iy, Jy, gf.My, gc.My);
+                if (wy == (T)0) continue;
                 const int64_t base = c * Nnf + (int64_t)gf.Mx * (iy + (int64_t)gf.My * iz);
-                double sx = 0.0;
+                T sx = 0;
                 for (int ix = px - 1; ix <= px + 1; ++ix) {
                     if (ix < 0 || ix >= gf.Mx) continue;
-                    const double wx = h_weight(ix, Jx, gf.Mx, gc.Mx);
-                    if (wx == 0.0) continue;
+                    const T wx = (T)h_weight(ix, Jx, gf.Mx, gc.Mx);
+                    if (wx == (T)0) continue;
                     sx += wx * (in2 ? in[base + ix] - in2[base + ix] : in[base + ix]);
                 }
                 sy += wy * sx;
             }
             sz += wz * sy;
         }
-        out[o] = (ess && ess[o]) ? 0.0 : sz;
-    }
-}
-
-// Exact transpose of k_hprolong_axis: out (axis coarse, size Mc) from in
-// (axis fine, size Mf); optional in2 subtracted on the fly; optional ess mask
-// (on the output L-vector) zeroes essential entries.
-__global__ void k_hrestrict_axis(double *out, const double *in, const double *in2, int ax, int Nx, int Ny, int Nz,
-                                 int Mf, int Mc, const uint8_t *ess)
-{
-    int odims[3] = {Nx, Ny, Nz}, fdims[3] = {Nx, Ny, Nz};
-    odims[ax] = Mc;
-    fdims[ax] = Mf;
-    const int64_t total = 3LL * odims[0] * odims[1] * odims[2];
-    GRID_STRIDE(o, total)
-    {
-        int64_t t = o;
-        int idx[3];
-        idx[0] = (int)(t % odims[0]); t /= odims[0];
-        idx[1] = (int)(t % odims[1]); t /= odims[1];
-        idx[2] = (int)(t % odims[2]);
-        const int c = (int)(t / odims[2]);
-        const int J = idx[ax], pj = h_pos(J, Mf, Mc);
-        double s2 = 0.0;
-        for (int i = pj - 1; i <= pj + 1; ++i) {
-            if (i < 0 || i >= Mf) continue;
-            const double w = h_weight(i, J, Mf, Mc);
-            if (w == 0.0) continue;
-            idx[ax] = i;
-            const int64_t fi = (((int64_t)c * fdims[2] + idx[2]) * fdims[1] + idx[1]) * fdims[0] + idx[0];
-            s2 += w * (in2 ? in[fi] - in2[fi] : in[fi]);
-        }
-        out[o] = (ess && ess[o]) ? 0.0 : s2;
+        out[o] = (ess && ess[o]) ? (T)0 : sz;
     }
 }
 
@@ -1132,6 +1073,7 @@ struct Level {
     double *xa = nullptr, *xb = nullptr;  // transfer temporaries (fine size of this level)
     float *xa32 = nullptr, *xb32 = nullptr;
     XferTab xt{};  // coarse (next level) basis at this level's nodes
+    bool hdown = false;  // the next level is this mesh coarsened once (p = 1 both), not a lower degree
     double lmax = 0.0;
     double theta = 0.0, delta = 0.0;
     // coarse CG vectors
@@ -1244,16 +1186,109 @@ std::vector<uint8_t> coarse_mask(const std::vector<uint8_t> &fine, const Grid &g
     return out;
 }
 
-int make_level_op(const pa_op *fine, int p, int precision, const std::vector<uint8_t> &mask, pa_op **out)
+// Element data of one level's mesh: the fine operator's, or the mesh whose
+// uniform refinement is the level above (Sec. 3: the h-levels of the
+// hierarchy come from r uniform refinements of a coarse mesh).
+struct LevelMesh {
+    int nx = 0, ny = 0, nz = 0;
+    std::vector<double> affine;  // [ne][12]: J row-major, x0
+    std::vector<double> mat;     // [ne][2] (lambda_e, mu_e), or empty
+    std::vector<double> cv;      // [ne][36] Voigt matrices, or empty
+    double lambda = 0.0, mu = 0.0;
+};
+
+LevelMesh mesh_of(const pa_op *op)
+{
+    LevelMesh m;
+    m.nx = op->g.nx;
+    m.ny = op->g.ny;
+    m.nz = op->g.nz;
+    m.affine = op->h_affine;
+    m.mat = op->h_mat;
+    m.cv = op->h_cv;
+    m.lambda = op->lambda;
+    m.mu = op->mu;
+    return m;
+}
+
+// Undo one uniform refinement: coarse element (I, J, K) is the union of the
+// fine elements (2I + a, 2J + b, 2K + c), a, b, c in {0, 1}.  Its map is
+// x0 = x0 of child (0,0,0), J = 2 J of that child.  Fails unless every
+// dimension is even, every child's map is the matching eighth of that map
+// (to rounding) and the children share one material.
+int coarsen_mesh(const LevelMesh &f, LevelMesh &c)
+{
+    if ((f.nx & 1) || (f.ny & 1) || (f.nz & 1))
+        return set_error(PA_EINVAL, "solver: h-coarsening needs even element counts in x, y and z");
+    c = LevelMesh();
+    c.nx = f.nx / 2;
+    c.ny = f.ny / 2;
+    c.nz = f.nz / 2;
+    c.lambda = f.lambda;
+    c.mu = f.mu;
+    const int64_t nec = (int64_t)c.nx * c.ny * c.nz;
+    c.affine.assign((size_t)nec * 12, 0.0);
+    if (!f.mat.empty()) c.mat.assign((size_t)nec * 2, 0.0);
+    if (!f.cv.empty()) c.cv.assign((size_t)nec * 36, 0.0);
+    auto fe = [&](int ix, int iy, int iz) { return (int64_t)ix + (int64_t)f.nx * (iy + (int64_t)f.ny * iz); };
+    for (int K = 0; K < c.nz; ++K)
+        for (int J = 0; J < c.ny; ++J)
+            for (int I = 0; I < c.nx; ++I) {
+                const int64_t E = (int64_t)I + (int64_t)c.nx * (J + (int64_t)c.ny * K);
+                const double *a0 = f.affine.data() + 12 * fe(2 * I, 2 * J, 2 * K);
+                double *A = c.affine.data() + 12 * E;
+                double scale = 0.0;
+                for (int k = 0; k < 9; ++k) {
+                    A[k] = 2.0 * a0[k];
+                    scale = std::max(scale, std::fabs(A[k]));
+                }
+                for (int k = 0; k < 3; ++k) A[9 + k] = a0[9 + k];
+                const double tol = 1e-12 * scale;
+                for (int cc = 0; cc < 2; ++cc)
+                    for (int bb = 0; bb < 2; ++bb)
+                        for (int aa = 0; aa < 2; ++aa) {
+                            const int64_t e = fe(2 * I + aa, 2 * J + bb, 2 * K + cc);
+                            const double *ae = f.affine.data() + 12 * e;
+                            const double off[3] = {0.5 * aa, 0.5 * bb, 0.5 * cc};
+                            bool ok = true;
+                            for (int k = 0; k < 9; ++k) ok = ok && std::fabs(ae[k] - 0.5 * A[k]) <= tol;
+                            for (int i = 0; i < 3; ++i) {
+                                const double x0 = A[9 + i] + A[3 * i] * off[0] + A[3 * i + 1] * off[1] + A[3 * i + 2] * off[2];
+                                ok = ok && std::fabs(ae[9 + i] - x0) <= tol + 1e-12 * std::fabs(x0);
+                            }
+                            if (!ok) return set_error(PA_EINVAL, "solver: mesh is not a uniform refinement (h-coarsening)");
+                            if (!f.mat.empty()) {
+                                if (f.mat[2 * e] != f.mat[2 * fe(2 * I, 2 * J, 2 * K)] ||
+                                    f.mat[2 * e + 1] != f.mat[2 * fe(2 * I, 2 * J, 2 * K) + 1])
+                                    return set_error(PA_EINVAL, "solver: material varies inside a coarse element");
+                            }
+                            if (!f.cv.empty()) {
+                                for (int k = 0; k < 36; ++k)
+                                    if (f.cv[36 * e + k] != f.cv[36 * fe(2 * I, 2 * J, 2 * K) + k])
+                                        return set_error(PA_EINVAL, "solver: material varies inside a coarse element");
+                            }
+                        }
+                if (!f.mat.empty()) {
+                    c.mat[2 * E] = f.mat[2 * fe(2 * I, 2 * J, 2 * K)];
+                    c.mat[2 * E + 1] = f.mat[2 * fe(2 * I, 2 * J, 2 * K) + 1];
+                }
+                if (!f.cv.empty())
+                    std::copy(f.cv.begin() + 36 * fe(2 * I, 2 * J, 2 * K), f.cv.begin() + 36 * fe(2 * I, 2 * J, 2 * K) + 36,
+                              c.cv.begin() + 36 * E);
+            }
+    return PA_OK;
+}
+
+int make_level_op(const LevelMesh &lm, int p, int precision, const std::vector<uint8_t> &mask, pa_op **out)
 {
     pa_mesh m;
-    m.nx = fine->g.nx;
-    m.ny = fine->g.ny;
-    m.nz = fine->g.nz;
-    m.affine = fine->h_affine;
-    int rc = pa_op_setup(&m, p, 0, fine->lambda, fine->mu, precision, mask.empty() ? nullptr : mask.data(), out);
-    if (rc == PA_OK && !fine->h_mat.empty()) rc = pa_op_set_material(*out, fine->h_mat.data());
-    if (rc == PA_OK && !fine->h_cv.empty()) rc = pa_op_set_anisotropic(*out, fine->h_cv.data());
+    m.nx = lm.nx;
+    m.ny = lm.ny;
+    m.nz = lm.nz;
+    m.affine = lm.affine;
+    int rc = pa_op_setup(&m, p, 0, lm.lambda, lm.mu, precision, mask.empty() ? nullptr : mask.data(), out);
+    if (rc == PA_OK && !lm.mat.empty()) rc = pa_op_set_material(*out, lm.mat.data());
+    if (rc == PA_OK && !lm.cv.empty()) rc = pa_op_set_anisotropic(*out, lm.cv.data());
     if (rc && *out) {
         pa_op_destroy(*out);
         *out = nullptr;
@@ -1364,6 +1399,28 @@ bool spd_inverse(std::vector<double> &A, int n)
 
 // Builds the h-hierarchy under the p = 1 level: Galerkin stencils, masks,
 // diagonals, Chebyshev intervals, and a dense inverse on the coarsest level.
+// h-coarse essential mask: coarse dof j is essential when its interpolation
+// reaches an essential fine dof (the 0/1 fine mask restricted); exact for
+// essential sets made of whole faces.
+std::vector<uint8_t> h_coarse_mask(const std::vector<uint8_t> &fm, const Grid &gf, const Grid &gc)
+{
+    std::vector<uint8_t> cm((size_t)3 * gc.Nn, 0);
+    const int Mf[3] = {gf.Mx, gf.My, gf.Mz}, Mc[3] = {gc.Mx, gc.My, gc.Mz};
+    for (int comp = 0; comp < 3; ++comp)
+        for (int64_t i = 0; i < gf.Nn; ++i) {
+            if (!fm[(size_t)(comp * gf.Nn + i)]) continue;
+            const int f[3] = {(int)(i % gf.Mx), (int)((i / gf.Mx) % gf.My), (int)(i / ((int64_t)gf.Mx * gf.My))};
+            int J[3][2], nJ[3];
+            double w[3][2];
+            for (int a = 0; a < 3; ++a) nJ[a] = h_parents(f[a], Mf[a], Mc[a], J[a], w[a]);
+            for (int kz = 0; kz < nJ[2]; ++kz)
+                for (int ky = 0; ky < nJ[1]; ++ky)
+                    for (int kx = 0; kx < nJ[0]; ++kx)
+                        cm[(size_t)(comp * gc.Nn + J[0][kx] + (int64_t)gc.Mx * (J[1][ky] + (int64_t)gc.My * J[2][kz]))] = 1;
+        }
+    return cm;
+}
+
 int build_h_levels(pa_solver *s, cudaStream_t st)
 {
     Level &L = s->lv.back();
@@ -1403,20 +1460,7 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
             std::vector<uint8_t> fm((size_t)F.n);
             PA_CUDA_TRY(cudaMemcpyAsync(fm.data(), F.ess, F.n, cudaMemcpyDeviceToHost, st));
             PA_CUDA_TRY(cudaStreamSynchronize(st));
-            std::vector<uint8_t> cm((size_t)C.n, 0);
-            const int Mf[3] = {F.g.Mx, F.g.My, F.g.Mz}, Mc[3] = {c.Mx, c.My, c.Mz};
-            for (int comp = 0; comp < 3; ++comp)
-                for (int64_t i = 0; i < F.g.Nn; ++i) {
-                    if (!fm[(size_t)(comp * F.g.Nn + i)]) continue;
-                    const int f[3] = {(int)(i % F.g.Mx), (int)((i / F.g.Mx) % F.g.My), (int)(i / ((int64_t)F.g.Mx * F.g.My))};
-                    int J[3][2], nJ[3];
-                    double w[3][2];
-                    for (int a = 0; a < 3; ++a) nJ[a] = h_parents(f[a], Mf[a], Mc[a], J[a], w[a]);
-                    for (int kz = 0; kz < nJ[2]; ++kz)
-                        for (int ky = 0; ky < nJ[1]; ++ky)
-                            for (int kx = 0; kx < nJ[0]; ++kx)
-                                cm[(size_t)(comp * c.Nn + J[0][kx] + (int64_t)c.Mx * (J[1][ky] + (int64_t)c.My * J[2][kz]))] = 1;
-                }
+            std::vector<uint8_t> cm = h_coarse_mask(fm, F.g, c);
             if ((rc = dalloc(s, &C.ess, C.n))) return rc;
             PA_CUDA_TRY(cudaMemcpyAsync(C.ess, cm.data(), C.n, cudaMemcpyHostToDevice, st));
             PA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1542,16 +1586,18 @@ int h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
     if (rc) return rc;
     k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, F.e, F.t, F.g);
     // restrict r - t, then the coarse correction prolonged and added
-    k_hrestrict<<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
+    k_hrestrict<double><<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
     rc = h_vcycle(s, k + 1, st);
     if (rc) return rc;
-    k_hprolong_add<<<blocks_for(F.n), 256, 0, st>>>(F.e, C.e, F.g, C.g);
+    k_hprolong_add<double><<<blocks_for(F.n), 256, 0, st>>>(F.e, C.e, F.g, C.g);
     rc = h_smooth(s, F, false, st);
     PA_CUDA_TRY(cudaGetLastError());
     return rc;
 }
 
-bool use_hmg(pa_solver *s) { return s->use_hmg && s->hl.size() > 1; }
+// h-multigrid preconditioned coarse CG: on a ladder of h-levels, or (a
+// coarse level small enough for it) on the dense inverse alone
+bool use_hmg(pa_solver *s) { return s->use_hmg && !s->hl.empty() && s->hl.back().Ainv != nullptr; }
 
 // start of the h-multigrid preconditioned coarse CG: x = 0, r = b, z = M r, p = z
 int coarse_start_hmg(pa_solver *s, Level &L, cudaStream_t st)
@@ -1677,6 +1723,10 @@ int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
 template <typename T>
 void restrict_to(Level &F, Level &C, const T *r, const T *t, T *out, cudaStream_t st)
 {
+    if (F.hdown) {
+        k_hrestrict<T><<<blocks_for(3 * C.op->g.Nn), 256, 0, st>>>(out, r, t, F.op->g, C.op->g, C.op->d_ess);
+        return;
+    }
     const Grid &g = F.op->g;
     const int n_[3] = {g.nx, g.ny, g.nz};
     const int pf = F.p, pc = C.p;
@@ -1698,6 +1748,10 @@ void restrict_to(Level &F, Level &C, const T *r, const T *t, T *out, cudaStream_
 template <typename T>
 void prolong_add(Level &F, Level &C, const T *ec, T *ef, cudaStream_t st)
 {
+    if (F.hdown) {
+        k_hprolong_add<T><<<blocks_for(3 * F.op->g.Nn), 256, 0, st>>>(ef, ec, F.op->g, C.op->g);
+        return;
+    }
     const Grid &g = F.op->g;
     const int n_[3] = {g.nx, g.ny, g.nz};
     const int pf = F.p, pc = C.p;
@@ -2486,10 +2540,18 @@ int pa_op_assemble_p1(const pa_op *op, double *vals, void *stream)
     return PA_OK;
 }
 
+// p = 1 on both sides and the fine mesh twice as fine in every direction:
+// the h-transfer (natural injection of the trilinear space)
+static bool h_pair(const pa_op *c, const pa_op *f)
+{
+    return c->p == 1 && f->p == 1 && f->g.nx == 2 * c->g.nx && f->g.ny == 2 * c->g.ny && f->g.nz == 2 * c->g.nz;
+}
+
 static int transfer_check(const pa_op *c, const pa_op *f)
 {
     if (!c || !f) return set_error(PA_EINVAL, "transfer: null operator");
     if (c->precision != PA_FP64 || f->precision != PA_FP64) return set_error(PA_EINVAL, "transfer: FP64 operators only");
+    if (h_pair(c, f)) return PA_OK;
     if (c->g.nx != f->g.nx || c->g.ny != f->g.ny || c->g.nz != f->g.nz)
         return set_error(PA_EINVAL, "transfer: operators live on different meshes");
     if (!(c->p < f->p)) return set_error(PA_EINVAL, "transfer: coarse degree must be below fine degree");
@@ -2511,6 +2573,12 @@ int pa_op_prolong(const pa_op *coarse, const pa_op *fine, const double *xc, doub
     if (rc) return rc;
     if (!xc || !xf) return set_error(PA_EINVAL, "pa_op_prolong: null vector");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (h_pair(coarse, fine)) {
+        PA_CUDA_TRY(cudaMemsetAsync(xf, 0, sizeof(double) * (size_t)fine->ndofs(), st));
+        k_hprolong_add<double><<<blocks_for(fine->ndofs()), 256, 0, st>>>(xf, xc, fine->g, coarse->g);
+        PA_CUDA_TRY(cudaGetLastError());
+        return PA_OK;
+    }
     Level F, C;
     F.op = const_cast<pa_op *>(fine);
     F.p = fine->p;
@@ -2532,6 +2600,11 @@ int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, dou
     if (rc) return rc;
     if (!rf || !rc_out) return set_error(PA_EINVAL, "pa_op_restrict: null vector");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (h_pair(coarse, fine)) {
+        k_hrestrict<double><<<blocks_for(coarse->ndofs()), 256, 0, st>>>(rc_out, rf, nullptr, fine->g, coarse->g, nullptr);
+        PA_CUDA_TRY(cudaGetLastError());
+        return PA_OK;
+    }
     Level F, C;
     F.op = const_cast<pa_op *>(fine);
     F.p = fine->p;
@@ -2573,9 +2646,18 @@ int pa_solver_destroy(pa_solver *s)
 int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order, double coarse_rtol, int coarse_maxit,
                      int mode, pa_solver **out)
 {
+    return pa_solver_create_hp(fine, nlev, p_levels, 0, cheb_order, coarse_rtol, coarse_maxit, mode, out);
+}
+
+int pa_solver_create_hp(pa_op *fine, int nlev, const int *p_levels, int h_levels, int cheb_order, double coarse_rtol,
+                        int coarse_maxit, int mode, pa_solver **out)
+{
     if (!out) return set_error(PA_EINVAL, "pa_solver_create: null output");
     *out = nullptr;
     if (!fine || !p_levels || nlev < 1 || nlev > 8) return set_error(PA_EINVAL, "pa_solver_create: bad levels");
+    if (h_levels < 0 || nlev + h_levels > 8) return set_error(PA_EINVAL, "pa_solver_create: at most 8 levels in all");
+    if (h_levels > 0 && p_levels[nlev - 1] != 1)
+        return set_error(PA_EINVAL, "pa_solver_create: h-levels need the last degree to be 1");
     if (fine->precision != PA_FP64) return set_error(PA_EINVAL, "pa_solver_create: fine operator must be FP64");
     if (p_levels[0] != fine->p) return set_error(PA_EINVAL, "pa_solver_create: p_levels[0] must be the fine degree");
     for (int l = 1; l < nlev; ++l)
@@ -2625,28 +2707,54 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
         cudaGetLastError();
     }
 
-    s->lv.resize(nlev);
+    const int ntot = nlev + h_levels;
+    s->lv.resize(ntot);
     std::vector<uint8_t> mask = fine->h_ess;
-    for (int l = 0; l < nlev; ++l) {
+    LevelMesh cur = mesh_of(fine);  // mesh of the level being built
+    for (int l = 0; l < ntot; ++l) {
         Level &L = s->lv[l];
-        L.p = p_levels[l];
+        L.p = l < nlev ? p_levels[l] : 1;
         if (l == 0) {
             L.op = fine;
-        } else {
+        } else if (l < nlev) {
+            // p-coarsening: same mesh, lower degree
             const pa_op *F = s->lv[l - 1].op;
             if (!mask.empty()) {
                 Basis1D bc;
                 bc.build(L.p, L.p + 2);
                 mask = coarse_mask(mask, F->g, L.p, bc, F->basis);
             }
-            TRY(make_level_op(fine, L.p, PA_FP64, mask, &L.op));
+            TRY(make_level_op(cur, L.p, PA_FP64, mask, &L.op));
             L.own_op = true;
+        } else {
+            // h-coarsening: p = 1 on the mesh whose uniform refinement is the level above
+            const pa_op *F = s->lv[l - 1].op;
+            LevelMesh c;
+            TRY(coarsen_mesh(cur, c));
+            if (!mask.empty()) {
+                Grid gc{};
+                gc.nx = c.nx;
+                gc.ny = c.ny;
+                gc.nz = c.nz;
+                gc.p = 1;
+                gc.Mx = c.nx + 1;
+                gc.My = c.ny + 1;
+                gc.Mz = c.nz + 1;
+                gc.ne = (int64_t)c.nx * c.ny * c.nz;
+                gc.Nn = (int64_t)gc.Mx * gc.My * gc.Mz;
+                mask = h_coarse_mask(mask, F->g, gc);
+            }
+            cur = std::move(c);
+            TRY(make_level_op(cur, 1, PA_FP64, mask, &L.op));
+            L.own_op = true;
+            s->lv[l - 1].hdown = true;
         }
         L.n = L.op->ndofs();
-        if (fp32_levels) TRY(make_level_op(fine, L.p, PA_FP32, L.op->h_ess, &L.op32));
+        if (fp32_levels) TRY(make_level_op(cur, L.p, PA_FP32, L.op->h_ess, &L.op32));
     }
+    const int nlev_all = ntot;
     cudaStream_t st = s->stream;
-    for (int l = 0; l < nlev; ++l) {
+    for (int l = 0; l < nlev_all; ++l) {
         Level &L = s->lv[l];
         const int64_t n = L.n;
         TRY(dalloc(s, &L.dinv, n));
@@ -2656,15 +2764,17 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
         TRY(dalloc(s, &L.d, n));
         TRY(pa_op_diag(L.op, L.t, st));
         k_recip<double><<<blocks_for(n), 256, 0, st>>>(L.dinv, L.t, n);
-        if (l < nlev - 1) {
+        if (l < nlev_all - 1) {
             TRY(dalloc(s, &L.xa, n));
             TRY(dalloc(s, &L.xb, n));
-            const int pc = p_levels[l + 1];
-            Basis1D bc;
-            bc.build(pc, pc + 2);
-            std::vector<double> val((size_t)(pc + 1) * (L.p + 1)), der(val.size());
-            lagrange_product(pc + 1, bc.nodes.data(), L.p + 1, L.op->basis.nodes.data(), val.data(), der.data());
-            for (size_t i = 0; i < val.size(); ++i) L.xt.L[i] = std::fabs(val[i]) < 1e-15 ? 0.0 : val[i];
+            if (!L.hdown) {
+                const int pc = p_levels[l + 1];
+                Basis1D bc;
+                bc.build(pc, pc + 2);
+                std::vector<double> val((size_t)(pc + 1) * (L.p + 1)), der(val.size());
+                lagrange_product(pc + 1, bc.nodes.data(), L.p + 1, L.op->basis.nodes.data(), val.data(), der.data());
+                for (size_t i = 0; i < val.size(); ++i) L.xt.L[i] = std::fabs(val[i]) < 1e-15 ? 0.0 : val[i];
+            }
             TRY(estimate_lmax(s, L, st));
         } else {
             TRY(dalloc(s, &L.cx, n));
@@ -2791,8 +2901,12 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
                 converged = true;
                 break;
             }
-            if (rr_prev >= 0.0 && rr > 0.25 * rr_prev && !inner_truncated) {
-                converged = true;  // stagnation at the FP64 residual floor
+            if (rr_prev >= 0.0 && rr > 0.25 * rr_prev && !inner_truncated && rr <= 1e6 * tol2 * bb) {
+                // stagnation within 1e3 of the tolerance: the FP64 residual
+                // floor.  Farther away, a refinement step that gained less
+                // than 2x (the FP32 inner residual drifted from the true one)
+                // is followed by another until the iteration cap.
+                converged = true;
                 break;
             }
             if (total_inner >= maxit) break;

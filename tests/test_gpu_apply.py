@@ -214,6 +214,55 @@ def test_transfers_against_oracle(pa, pc, pf):
     opf.close()
 
 
+@pytest.mark.parametrize("nx,ny,nz", [(1, 1, 1), (3, 2, 1), (8, 2, 2)])
+def test_h_transfers_against_oracle(pa, nx, ny, nz):
+    """p = 1 prolongation to the uniformly refined mesh and its transpose
+    (the h-level transfers) against the oracle's evaluation of the coarse
+    trilinear field at the fine nodes."""
+    mc = syn.box_mesh(nx, ny, nz, hi=(2.0, 1.0, 1.5))
+    mf = syn.box_mesh(2 * nx, 2 * ny, 2 * nz, hi=(2.0, 1.0, 1.5))
+    opc = pa.Operator(mc.nx, mc.ny, mc.nz, mc.affine, 1, 1.0, 1.0)
+    opf = pa.Operator(mf.nx, mf.ny, mf.nz, mf.affine, 1, 1.0, 1.0)
+    rng = np.random.default_rng(nx + 5 * ny + 25 * nz)
+    u = rng.normal(size=opc.ndofs)
+    v = rng.normal(size=opf.ndofs)
+    xf = torch.empty(opf.ndofs, dtype=torch.float64, device="cuda")
+    rc = torch.empty(opc.ndofs, dtype=torch.float64, device="cuda")
+    pa.pa_op_prolong(opc.h, opf.h, torch.tensor(u, device="cuda"), xf)
+    pa.pa_op_restrict(opc.h, opf.h, torch.tensor(v, device="cuda"), rc)
+    assert _relerr(xf.cpu().numpy(), oracle.prolong_h(nx, ny, nz, u)) <= 1e-15
+    assert _relerr(rc.cpu().numpy(), oracle.restrict_h(nx, ny, nz, v)) <= 1e-14
+    opc.close()
+    opf.close()
+
+
+def test_h_coarse_operator_is_galerkin_product_on_gpu(pa):
+    """The p = 1 operator on the coarse mesh equals R A_fine P (nested
+    spaces, exact quadrature, material constant per coarse element), all
+    three factors applied by the library: a property that holds at any
+    size, checked here on a sheared domain with two materials."""
+    M = np.array([[1.3, 0.2, -0.1], [0.1, 0.9, 0.3], [-0.2, 0.15, 1.1]])
+    mc = syn.globally_affine_mesh(6, 4, 2, M, t=(0.3, -0.2, 0.5))
+    mf = syn.globally_affine_mesh(12, 8, 4, M, t=(0.3, -0.2, 0.5))
+    rng = np.random.default_rng(4)
+    mat_c = rng.uniform(0.5, 3.0, size=(mc.ne, 2))
+    ef = np.arange(mf.ne)
+    ex, ey, ez = ef % 12, (ef // 12) % 8, ef // 96
+    mat_f = mat_c[ex // 2 + 6 * (ey // 2 + 4 * (ez // 2))]
+    opc = pa.Operator(mc.nx, mc.ny, mc.nz, mc.affine, 1, 1.0, 1.0, mat=mat_c)
+    opf = pa.Operator(mf.nx, mf.ny, mf.nz, mf.affine, 1, 1.0, 1.0, mat=mat_f)
+    x = torch.tensor(rng.uniform(-1, 1, size=opc.ndofs), device="cuda")
+    y = opc.apply(x)
+    xf = torch.empty(opf.ndofs, dtype=torch.float64, device="cuda")
+    pa.pa_op_prolong(opc.h, opf.h, x, xf)
+    yf = opf.apply(xf)
+    g = torch.empty_like(y)
+    pa.pa_op_restrict(opc.h, opf.h, yf, g)
+    assert _relerr(g.cpu().numpy(), y.cpu().numpy()) <= 1e-12
+    opc.close()
+    opf.close()
+
+
 def test_assembled_p1_stencil_against_oracle_matrix(pa):
     """The assembled coarse matrix (27-point stencil) against the oracle's
     assembled global matrix, entry by entry."""

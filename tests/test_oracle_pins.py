@@ -397,6 +397,57 @@ def test_transfer_adjoint_and_polynomial_exactness(pc, pf):
     np.testing.assert_allclose(oracle.prolong(pc, pf, n, n, n, field(Xc)), field(Xf), atol=1e-13)
 
 
+@pytest.mark.parametrize("nx,ny,nz", [(1, 1, 1), (2, 1, 3)])
+def test_h_transfer_adjoint_and_trilinear_exactness(nx, ny, nz):
+    """One uniform refinement at p = 1 (Sec. 3, h-levels): restriction is the
+    exact transpose of prolongation, and a trilinear field on the coarse
+    mesh is reproduced exactly at the fine nodes."""
+    rng = np.random.default_rng(nx + 10 * ny + 100 * nz)
+    u = rng.normal(size=3 * oracle.n_nodes(nx, ny, nz, 1))
+    v = rng.normal(size=3 * oracle.n_nodes(2 * nx, 2 * ny, 2 * nz, 1))
+    Pu = oracle.prolong_h(nx, ny, nz, u)
+    Rv = oracle.restrict_h(nx, ny, nz, v)
+    assert abs(Pu @ v - u @ Rv) <= 1e-13 * np.linalg.norm(Pu) * np.linalg.norm(v)
+    hi = (2.0, 1.0, 3.0)
+    Xc = oracle.node_coords_box(nx, ny, nz, 1, hi=hi)
+    Xf = oracle.node_coords_box(2 * nx, 2 * ny, 2 * nz, 1, hi=hi)
+
+    def field(X):
+        x, y, z = X.T
+        return np.stack([1 + x - 2 * y + 0.5 * x * y * z, x * y - z, 0.3 + y * z + x * z]).reshape(-1)
+
+    np.testing.assert_allclose(oracle.prolong_h(nx, ny, nz, field(Xc)), field(Xf), atol=1e-14)
+    # a field quadratic along x is not in the coarse space: interpolation
+    # misses it at the odd fine nodes (the check above has teeth)
+    q = np.concatenate([Xc[:, 0] ** 2] * 3)
+    assert np.max(np.abs(oracle.prolong_h(nx, ny, nz, q) - np.concatenate([Xf[:, 0] ** 2] * 3))) > 1e-3
+
+
+def test_h_coarse_operator_is_galerkin_product():
+    """Nested trilinear spaces, exact Gauss quadrature and a material that
+    is constant on each coarse element make the operator rediscretised on
+    the coarse mesh equal to P^T A_fine P (the Galerkin product), on a
+    globally affine (sheared) domain with two materials."""
+    t = (0.3, -0.2, 0.5)
+    mc = syn.globally_affine_mesh(2, 1, 2, M_GLOBAL, t=t)
+    mf = syn.globally_affine_mesh(4, 2, 4, M_GLOBAL, t=t)
+    mat_c = np.array([[3.0, 2.0], [0.5, 0.25], [1.0, 4.0], [2.0, 1.5]])
+    ef = np.arange(mf.ne)
+    parent = (ef % 4) // 2 + 2 * ((ef // 8) // 2)
+    mat_f = mat_c[parent]
+    Ac = oracle.assemble_dense(1, 2, 1, 2, mc.affine, 0.0, 0.0, mat=mat_c)
+    Af = oracle.assemble_dense(1, 4, 2, 4, mf.affine, 0.0, 0.0, mat=mat_f)
+    nc = Ac.shape[0]
+    P = np.stack([oracle.prolong_h(2, 1, 2, np.eye(nc)[j]) for j in range(nc)], axis=1)
+    G = P.T @ Af @ P
+    assert np.max(np.abs(G - Ac)) <= 1e-12 * np.max(np.abs(Ac))
+    # a material that is not constant per coarse element breaks the identity
+    mat_bad = mat_f.copy()
+    mat_bad[0] = [9.0, 9.0]
+    Gb = P.T @ oracle.assemble_dense(1, 4, 2, 4, mf.affine, 0.0, 0.0, mat=mat_bad) @ P
+    assert np.max(np.abs(Gb - Ac)) > 1e-3 * np.max(np.abs(Ac))
+
+
 def test_dense_solve_residual():
     p = 2
     m = syn.box_mesh(2, 1, 1, hi=(2.0, 1.0, 1.0))
