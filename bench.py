@@ -599,16 +599,18 @@ def run_serving(args, pa, torch):
     served form (mixed precision, several slots, small solves in the lockstep
     batch lane).  The Poisson arrival rate is a fraction of the served
     capacity.  Reports p50/p99 latency (submit to completion) and completed
-    solves/s, and a burst of small solves served with and without the batch
+    solves/s, the calibration burst again with h-levels off (p-levels
+    only), and a burst of small solves served with and without the batch
     lane."""
     import threading
     reqs = serving_requests(pa, args.serve_requests, seed=4242)
     budget = int(args.serve_budget_gb * (1 << 30))
     ncal = min(len(reqs), args.serve_calibration)
 
-    def burst(rs, slots, batch=1):
+    def burst(rs, slots, batch=1, h_levels=1):
         srv = pa.pa_server_create(budget, slots)
         pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_BATCH, batch)
+        pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_H_LEVELS, h_levels)
         t0 = time.perf_counter()
         ts = [pa.pa_server_submit(srv, r) for r in rs]
         res = [pa.pa_server_wait(srv, t) for t in ts]
@@ -626,6 +628,7 @@ def run_serving(args, pa, torch):
         fp64_reqs.append(r2)
     fp64_cap, fp64_ok, _ = burst(fp64_reqs, 1, batch=0)
     cap, cal_ok, _ = burst(reqs[:ncal], args.serve_slots)
+    cap_noh, noh_ok, _ = burst(reqs[:ncal], args.serve_slots, h_levels=0)
     small = small_requests(pa, args.serve_small, seed=99)
     small_off, small_off_ok, st_off = burst(small, args.serve_slots, batch=0)
     small_on, small_on_ok, st_small = burst(small, args.serve_slots, batch=1)
@@ -644,7 +647,7 @@ def run_serving(args, pa, torch):
 
     th = threading.Thread(target=submitter)
     th.start()
-    lat, statuses, iters, solve_s = [], [], [], []
+    lat, statuses, iters, solve_s, hlev = [], [], [], [], []
     for i in range(len(reqs)):
         while tickets[i] is None:
             time.sleep(0.001)
@@ -653,6 +656,7 @@ def run_serving(args, pa, torch):
         lat.append(tm.latency_s)
         iters.append(info.iterations)
         solve_s.append(tm.solve_s)
+        hlev.append(tm.h_levels)
     th.join()
     wall = time.perf_counter() - start
     st = pa.pa_server_stats(srv)
@@ -663,13 +667,16 @@ def run_serving(args, pa, torch):
             "fp64_alone_solves_per_s": round(fp64_cap, 3),
             "served_burst_solves_per_s": round(cap, 3),
             "served_over_fp64_alone": round(cap / fp64_cap, 3),
+            "served_burst_solves_per_s_h_levels_off": round(cap_noh, 3),
+            "h_levels_speedup": round(cap / cap_noh, 3),
             "arrival_rate_per_s": round(rate, 3), "load_fraction": args.serve_load,
             "solves_per_s": round(len(reqs) / wall, 3),
             "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
             "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
             "mean_solve_s": round(float(np.mean(solve_s)), 4), "mean_iterations": round(float(np.mean(iters)), 1),
+            "requests_with_h_levels": int(sum(1 for h in hlev if h > 0)),
             "ok": int(sum(1 for c in statuses if c == pa.PA_OK)),
-            "calibration_ok": [fp64_ok, cal_ok],
+            "calibration_ok": [fp64_ok, cal_ok, noh_ok],
             "batch_lane": {"batched": int(st.batched), "ticks": int(st.batch_ticks),
                            "mean_members_per_tick": round(st.batch_member_ticks / max(st.batch_ticks, 1), 2),
                            "max_members": int(st.batch_max_members)},

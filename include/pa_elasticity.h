@@ -416,6 +416,8 @@ typedef struct pa_request_timing {
     double solve_s;          /* the solve (in either lane)                */
     int64_t footprint_bytes; /* admission estimate of device memory       */
     int batched;             /* 1: solved in the lockstep batch lane      */
+    int levels;              /* multigrid levels of its solver, all told  */
+    int h_levels;            /* of which h-levels (PA_SERVER_OPT_H_LEVELS) */
 } pa_request_timing;
 
 typedef struct pa_server_stats_t {
@@ -432,11 +434,16 @@ typedef struct pa_server_stats_t {
  *  PA_SERVER_OPT_BATCH_MAX_DOFS (default 2,000,000): largest fine-level dof
  *    count that joins the batch lane (larger solves fill the GPU alone).
  *  PA_SERVER_OPT_BATCH_MAX_MEMBERS (default 64, at most 256): members per
- *    lockstep batch; further requests wait for a member to leave. */
+ *    lockstep batch; further requests wait for a member to leave.
+ *  PA_SERVER_OPT_H_LEVELS (default 1): each request's hierarchy gets h-levels
+ *    below its p-levels (pa_solver_create_hp): the element counts are halved
+ *    while all three are even, the p = 1 level above has more than 320
+ *    dofs, and the hierarchy has at most 8 levels; 0: p-levels only. */
 enum pa_server_option {
     PA_SERVER_OPT_BATCH = 1,
     PA_SERVER_OPT_BATCH_MAX_DOFS = 2,
-    PA_SERVER_OPT_BATCH_MAX_MEMBERS = 3
+    PA_SERVER_OPT_BATCH_MAX_MEMBERS = 3,
+    PA_SERVER_OPT_H_LEVELS = 4
 };
 int pa_server_set_option(pa_server *s, int option, double value);
 

@@ -51,7 +51,8 @@ class pa_request(ctypes.Structure):
 
 class pa_request_timing(ctypes.Structure):
     _fields_ = [("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double), ("setup_s", ctypes.c_double),
-                ("solve_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64), ("batched", ctypes.c_int)]
+                ("solve_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64), ("batched", ctypes.c_int),
+                ("levels", ctypes.c_int), ("h_levels", ctypes.c_int)]
 
 
 class pa_server_stats_t(ctypes.Structure):
@@ -415,6 +416,7 @@ def pa_server_wait(srv, ticket, x_len=0):
 PA_SERVER_OPT_BATCH = 1
 PA_SERVER_OPT_BATCH_MAX_DOFS = 2
 PA_SERVER_OPT_BATCH_MAX_MEMBERS = 3
+PA_SERVER_OPT_H_LEVELS = 4
 
 
 def pa_server_set_option(srv, option, value):

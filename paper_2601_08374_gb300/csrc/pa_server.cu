@@ -37,6 +37,7 @@ struct Ticket {
     int64_t id = 0;
     pa_request req{};
     std::vector<int> levels;
+    int hlev = 0;  // h-levels below the p-levels
     size_t footprint = 0;
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = PA_OK;
@@ -79,20 +80,39 @@ std::vector<int> p_levels_for(int p)
     return lv;
 }
 
+// h-levels under the p-hierarchy of a box mesh: halve the element counts
+// while all three are even, the hierarchy has at most 8 levels, and the
+// p = 1 level above still has more than 320 dofs (the size whose assembled
+// matrix the solver inverts densely).
+int h_levels_for(const pa_request &r, int np)
+{
+    int nx = r.nx, ny = r.ny, nz = r.nz, h = 0;
+    while (np + h < 8 && !(nx & 1) && !(ny & 1) && !(nz & 1) && 3LL * (nx + 1) * (ny + 1) * (nz + 1) > 320) {
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        ++h;
+    }
+    return h;
+}
+
 // Device bytes that pa_op_setup + pa_solver_create + the request's own
 // vectors allocate (sum of the documented allocations).
-size_t footprint_bytes(const pa_request &r, const std::vector<int> &levels)
+size_t footprint_bytes(const pa_request &r, const std::vector<int> &levels, int hlev)
 {
-    const size_t ne = (size_t)r.nx * r.ny * r.nz;
     size_t total = 0, n0 = 0;
-    for (size_t l = 0; l < levels.size(); ++l) {
-        const int p = levels[l], D = p + 1;
-        const size_t N = 3 * (size_t)(r.nx * p + 1) * (r.ny * p + 1) * (r.nz * p + 1);
+    const size_t nlev = levels.size() + (size_t)hlev;
+    for (size_t l = 0; l < nlev; ++l) {
+        const int p = l < levels.size() ? levels[l] : 1, D = p + 1;
+        const int sh = l < levels.size() ? 0 : (int)(l + 1 - levels.size());  // halvings of the mesh
+        const size_t nx = (size_t)(r.nx >> sh), ny = (size_t)(r.ny >> sh), nz = (size_t)(r.nz >> sh);
+        const size_t ne = nx * ny * nz;
+        const size_t N = 3 * (nx * p + 1) * (ny * p + 1) * (nz * p + 1);
         if (l == 0) n0 = N;
         auto op_bytes = [&](size_t elem) {
             return ne * 12 * elem + ne * 96 + ne * 3 * (size_t)D * D * D * elem + 2 * N * elem + N;
         };
-        total += op_bytes(8) + 5 * N * 8 + (l + 1 < levels.size() ? 2 : 4) * N * 8;
+        total += op_bytes(8) + 5 * N * 8 + (l + 1 < nlev ? 2 : 4) * N * 8;
         if (r.mode != PA_SOLVE_FP64) total += op_bytes(4) + 7 * N * 4;
     }
     total += 7 * n0 * 8 + (r.mode == PA_SOLVE_MIXED ? 6 * n0 * 4 : 0);
@@ -114,6 +134,7 @@ struct pa_server {
     bool stop = false;
     // batch lane
     bool batch = true;
+    bool h_levels = true;  // h-levels under the p-levels where the mesh allows
     int64_t batch_max_dofs = 2000000;
     int batch_max_members = 64;
     int64_t in_lane = 0;  // handed to a stepper, not finished
@@ -162,7 +183,8 @@ int setup_request(pa_server *srv, Ticket &t, Res &res)
         if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &res.op))) break;
         pa_mesh_destroy(mesh);
         mesh = nullptr;
-        if ((rc = pa_solver_create(res.op, (int)t.levels.size(), t.levels.data(), 2, 1e-2, 10, r.mode, &res.sol)))
+        if ((rc = pa_solver_create_hp(res.op, (int)t.levels.size(), t.levels.data(), t.hlev, 2, 1e-2, 10, r.mode,
+                                      &res.sol)))
             break;
         // concurrent solvers must not each hold a grid-wide barrier
         pa_solver_set_option(res.sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);
@@ -427,10 +449,11 @@ int pa_server_submit(pa_server *s, const pa_request *req, int64_t *ticket)
     auto t = std::make_shared<Ticket>();
     t->req = *req;
     t->levels = p_levels_for(req->p);
-    t->footprint = footprint_bytes(*req, t->levels);
     t->t_submit = clk::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        t->hlev = s->h_levels ? h_levels_for(*req, (int)t->levels.size()) : 0;
+        t->footprint = footprint_bytes(*req, t->levels, t->hlev);
         t->id = s->next_id++;
         s->tickets[t->id] = t;
         s->queue.push_back(t);
@@ -466,6 +489,8 @@ int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, 
     if (info) *info = t->info;
     if (timing) {
         timing->batched = t->batched;
+        timing->levels = (int)t->levels.size() + t->hlev;
+        timing->h_levels = t->hlev;
         timing->latency_s = std::chrono::duration<double>(t->t_end - t->t_submit).count();
         timing->queue_s = std::chrono::duration<double>(t->t_start - t->t_submit).count();
         timing->setup_s = t->setup_s;
@@ -511,6 +536,7 @@ int pa_server_set_option(pa_server *s, int option, double value)
         if (!(value >= 1.0 && value <= 256.0)) return set_error(PA_EINVAL, "pa_server_set_option: members in 1..256");
         s->batch_max_members = (int)value;
         return PA_OK;
+    case PA_SERVER_OPT_H_LEVELS: s->h_levels = value != 0.0; return PA_OK;
     default: return set_error(PA_EINVAL, "pa_server_set_option: unknown option");
     }
 }

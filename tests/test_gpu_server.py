@@ -127,3 +127,25 @@ def test_served_solution_matches_direct_solve(pa):
     xo = oracle.solve_dense(2, 4, 1, 1, m.affine, lam, mu, b, ess)
     assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
     assert tm.latency_s >= tm.solve_s > 0
+
+
+def test_served_h_levels_match_direct_solve_and_the_p_only_hierarchy(pa):
+    """A 16x2x2 beam request gets one h-level by default (its p = 1 level
+    has 459 dofs); the served solution matches a direct solve, and so does
+    the same request served with h-levels off."""
+    E, nu = 1.0, 0.3
+    m = syn.box_mesh(16, 2, 2, hi=(8.0, 1.0, 1.0))
+    lam, mu = syn.lame(E, nu)
+    ess = syn.clamp_mask(m, 2)
+    b = oracle.load(2, 16, 2, 2, m.affine, f0=(0, 0, -1.0), ess=ess)
+    xo = oracle.solve_dense(2, 16, 2, 2, m.affine, lam, mu, b, ess)
+    for h_on in (1, 0):
+        r = pa.make_request(16, 2, 2, (0, 0, 0, 8.0, 1.0, 1.0), 2, E, nu, f0=(0, 0, -1.0), rtol=1e-10, maxit=300,
+                            mode=pa.PA_SOLVE_MIXED_FCG, keep_solution=True)
+        srv = pa.pa_server_create(8 << 30, 2)
+        pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_H_LEVELS, h_on)
+        code, info, tm, x = pa.pa_server_wait(srv, pa.pa_server_submit(srv, r), _ndofs(r))
+        pa.pa_server_destroy(srv)
+        assert code == pa.PA_OK, pa.lib.pa_last_error()
+        assert (tm.h_levels, tm.levels) == ((1, 3) if h_on else (0, 2))
+        assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
