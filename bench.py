@@ -85,12 +85,12 @@ def kernel_source_hash() -> str:
 # and launch table with this hash.  The E-vector writes mostly stay in L2
 # and reach DRAM during the assembly kernel, so for p >= 4 the figure is
 # essentially the reads of x and of the geometry records.
-TRAFFIC_HASH = "1e62abf3e5d7bfad"
+TRAFFIC_HASH = "4402b46b78d7f92e"
 ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>",
                         3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)"}
 TRAFFIC_BYTES: dict = {
-    ("f64", 1): 249766016, ("f64", 2): 59984512, ("f64", 4): 26843776, ("f64", 6): 22366848, ("f64", 8): 22146432,
-    ("f32", 1): 96612224, ("f32", 2): 18396416, ("f32", 4): 13157504, ("f32", 6): 11214336, ("f32", 8): 11102848,
+    ("f64", 1): 249711232, ("f64", 2): 60165248, ("f64", 4): 26777344, ("f64", 6): 22379648, ("f64", 8): 22142336,
+    ("f32", 1): 96614528, ("f32", 2): 18396288, ("f32", 4): 13157504, ("f32", 6): 11213952, ("f32", 8): 11102208,
 }
 
 
@@ -632,6 +632,8 @@ def run_serving(args, pa, torch):
     small = small_requests(pa, args.serve_small, seed=99)
     small_off, small_off_ok, st_off = burst(small, args.serve_slots, batch=0)
     small_on, small_on_ok, st_small = burst(small, args.serve_slots, batch=1)
+    small_off_noh, _, _ = burst(small, args.serve_slots, batch=0, h_levels=0)
+    small_on_noh, _, st_small_noh = burst(small, args.serve_slots, batch=1, h_levels=0)
     rate = args.serve_load * cap
     arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
     srv = pa.pa_server_create(budget, args.serve_slots)
@@ -683,6 +685,11 @@ def run_serving(args, pa, torch):
             "small_burst": {"requests": len(small), "recipe": "p U{2,4,6,8}; cube n^3, n ~ U{3..8}; mixed precision",
                             "solves_per_s_lane_off": round(small_off, 3), "solves_per_s_lane_on": round(small_on, 3),
                             "lane_speedup": round(small_on / small_off, 3), "ok": [small_off_ok, small_on_ok],
+                            "h_levels_off": {"solves_per_s_lane_off": round(small_off_noh, 3),
+                                             "solves_per_s_lane_on": round(small_on_noh, 3),
+                                             "lane_speedup": round(small_on_noh / small_off_noh, 3),
+                                             "mean_members_per_tick": round(st_small_noh.batch_member_ticks
+                                                                            / max(st_small_noh.batch_ticks, 1), 2)},
                             "mean_setup_s_off_on": [round(st_off.mean_setup_s, 4), round(st_small.mean_setup_s, 4)],
                             "mean_solve_s_off_on": [round(st_off.mean_solve_s, 4), round(st_small.mean_solve_s, 4)],
                             "mean_members_per_tick": round(st_small.batch_member_ticks / max(st_small.batch_ticks, 1), 2),

@@ -45,6 +45,8 @@ struct FlatLayout {
     static constexpr int per_elem = bufA + bufB;
     // byte offset of the per-CTA element table (global base node per element)
     __host__ __device__ static size_t table_offset(int epb) { return (((size_t)tab + (size_t)epb * per_elem) * sizeof(T) + 15) & ~(size_t)15; }
+    // byte offset of the per-CTA coefficient table (10 values per element)
+    __host__ __device__ static size_t coef_offset(int epb) { return (table_offset(epb) + sizeof(int64_t) * (size_t)epb + 15) & ~(size_t)15; }
 };
 
 // PART 0: the whole fused dataflow.  PART 1 / 2 (ablation of Table 8 only):
@@ -86,11 +88,21 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
     const int64_t Nn = a.g.Nn;
     const int64_t Mx = a.g.Mx, MxMy = (int64_t)a.g.Mx * a.g.My;
     int64_t *gbase = reinterpret_cast<int64_t *>(smem_raw + L::table_offset(epb));
+    // isotropic pointwise stage: per element mu detJ J^-1 (9) and 2 mu detJ
+    constexpr bool kIso = !ANISO && !FULLC;
+    T *coef = reinterpret_cast<T *>(smem_raw + L::coef_offset(epb));
     for (int el = tid; el < ne_blk; el += nt) {
         const int64_t e = e0 + el;
         const int64_t t = e / a.g.nx;
         const int ex = (int)(e - t * a.g.nx), ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
         gbase[el] = (int64_t)ex * p + Mx * ((int64_t)ey * p) + MxMy * ((int64_t)ez * p);
+        if (kIso && PART != 2) {
+            const T *geo = a.geo + e * kGeoStride;
+            const T cm = geo[10];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) coef[el * 10 + k] = cm * geo[k];
+            coef[el * 10 + 9] = cm + cm;
+        }
     }
     __syncthreads();
     if (PART != 2) {
@@ -197,14 +209,16 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
             T Ji[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
-            const T cl = geo[9], cm = geo[10];
+            const T cl = geo[9];
             // physical gradient du[c][j] = sum_n Ji[n][j] gr[c][n]
             T du[3][3];
+            if constexpr (!kIso) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
+                    for (int j = 0; j < 3; ++j)
+                        du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
+            }
             T s[3][3];
             if constexpr (ANISO) {
                 const T *cv = a.cvoigt + (e0 + el) * 21;
@@ -241,15 +255,26 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
                         s[i][j] = acc;
                     }
             } else {
-                // Voigt stress, order [00, 11, 22, 01, 02, 12]
-                const T div = du[0][0] + du[1][1] + du[2][2];
-                const T ld = cl * div, m2 = cm + cm;
-                s[0][0] = fma(m2, du[0][0], ld);
-                s[1][1] = fma(m2, du[1][1], ld);
-                s[2][2] = fma(m2, du[2][2], ld);
-                s[0][1] = s[1][0] = cm * (du[0][1] + du[1][0]);
-                s[0][2] = s[2][0] = cm * (du[0][2] + du[2][0]);
-                s[1][2] = s[2][1] = cm * (du[1][2] + du[2][1]);
+                // Voigt stress (Eq. 7), order [00, 11, 22, 01, 02, 12]: only
+                // the diagonal of grad u is formed; each shear stress
+                // mu detJ (du_ab + du_ba) is one 6-term dot of the reference
+                // gradient with the element's mu detJ J^-1 (two FP64
+                // instructions fewer per pair than forming du_ab and du_ba)
+                const T *cj = coef + el * 10;
+                T dg[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dg[c] = fma(Ji[c], gr[c][0], fma(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
+                const T ld = cl * (dg[0] + dg[1] + dg[2]), m2 = cj[9];
+                s[0][0] = fma(m2, dg[0], ld);
+                s[1][1] = fma(m2, dg[1], ld);
+                s[2][2] = fma(m2, dg[2], ld);
+                auto shear = [&](int ia, int ib) {
+                    return fma(cj[ib], gr[ia][0], fma(cj[3 + ib], gr[ia][1], fma(cj[6 + ib], gr[ia][2],
+                           fma(cj[ia], gr[ib][0], fma(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
+                };
+                s[0][1] = s[1][0] = shear(0, 1);
+                s[0][2] = s[2][0] = shear(0, 2);
+                s[1][2] = s[2][1] = shear(1, 2);
             }
             T *s3 = bufB + (size_t)el * L::bufB + r;
 #pragma unroll
@@ -421,7 +446,7 @@ __global__ void __launch_bounds__(512) pa_apply_flat_part_kernel(ApplyArgs<T> a,
 template <typename T, int D, int Q>
 size_t flat_smem_bytes(int epb)
 {
-    return FlatLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
+    return FlatLayout<T, D, Q>::coef_offset(epb) + sizeof(T) * 10 * (size_t)epb;
 }
 
 template <typename T, int D, int Q>

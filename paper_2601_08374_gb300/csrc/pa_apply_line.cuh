@@ -251,10 +251,13 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
 #pragma unroll
             for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
         const T *geo = a.geo + (e0 + el) * kGeoStride;
-        T Ji[9];
+        T Ji[9], cj[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
         const T cl = geo[9], cm = geo[10], m2 = cm + cm;
+        // mu detJ J^-1: each shear stress is one 6-term dot with it
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
         T acc[9][D];
 #pragma unroll
         for (int ch = 0; ch < 9; ++ch)
@@ -276,20 +279,23 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
                 gr[c][1] = g1;
                 gr[c][2] = g2;
             }
-            T du[3][3];
+            // Voigt stress (Eq. 7): the diagonal of grad u, then each shear
+            // stress mu detJ (du_ab + du_ba) as one 6-term dot
+            T dg[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    du[c][j] = fma(Ji[0 * 3 + j], gr[c][0], fma(Ji[1 * 3 + j], gr[c][1], Ji[2 * 3 + j] * gr[c][2]));
-            const T ld = cl * (du[0][0] + du[1][1] + du[2][2]);
+            for (int c = 0; c < 3; ++c) dg[c] = fma(Ji[c], gr[c][0], fma(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
+            const T ld = cl * (dg[0] + dg[1] + dg[2]);
             T s[3][3];
-            s[0][0] = fma(m2, du[0][0], ld);
-            s[1][1] = fma(m2, du[1][1], ld);
-            s[2][2] = fma(m2, du[2][2], ld);
-            s[0][1] = s[1][0] = cm * (du[0][1] + du[1][0]);
-            s[0][2] = s[2][0] = cm * (du[0][2] + du[2][0]);
-            s[1][2] = s[2][1] = cm * (du[1][2] + du[2][1]);
+            s[0][0] = fma(m2, dg[0], ld);
+            s[1][1] = fma(m2, dg[1], ld);
+            s[2][2] = fma(m2, dg[2], ld);
+            auto shear = [&](int ia, int ib) {
+                return fma(cj[ib], gr[ia][0], fma(cj[3 + ib], gr[ia][1], fma(cj[6 + ib], gr[ia][2],
+                       fma(cj[ia], gr[ib][0], fma(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
+            };
+            s[0][1] = s[1][0] = shear(0, 1);
+            s[0][2] = s[2][0] = shear(0, 2);
+            s[1][2] = s[2][1] = shear(1, 2);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
