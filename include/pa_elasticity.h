@@ -118,6 +118,18 @@ int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys,
  * buffers should be pinned for full copy bandwidth. */
 int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream);
 
+/* Several operators applied from host buffers in one call, with the copies
+ * overlapped with the applies: y_host[k] = A_k x_host[k] for k < count.
+ * The inputs are copied to the device back to back on an internal stream;
+ * operator k is applied on `stream` as soon as its input has landed, and its
+ * result is copied back on a second internal stream while the following
+ * operators compute.  Returns after every y_host[k] is on the host.  Each
+ * operator may appear once (its staging vectors carry the copies); host
+ * buffers should be pinned, otherwise the copies do not overlap.  Fails with
+ * PA_EINVAL for null entries or a repeated operator. */
+int pa_op_apply_host_batch(pa_op *const *ops, const void *const *x_host, void *const *y_host, int count,
+                           void *stream);
+
 /* d = diag(A) of the constrained operator (essential entries = 1), from the
  * closed form built on 1D sums of w B^2, w B G, w G^2 (Sec. 3.1: the
  * diagonal feeding the Chebyshev-Jacobi smoother).  d: device L-vector. */

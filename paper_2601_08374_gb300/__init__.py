@@ -80,6 +80,7 @@ _sig("pa_op_destroy", [_vp])
 _sig("pa_op_info", [_vp, _i64p, _i64p, _ip, _ip])
 _sig("pa_op_apply", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
+_sig("pa_op_apply_host_batch", [_vp, _vp, _vp, ctypes.c_int, _vp])
 _sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp])
 _sig("pa_op_diag", [_vp, _vp, _vp])
 _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
@@ -214,6 +215,19 @@ def pa_op_apply_host(op, x_host, y_host, stream=None):
     xp = ctypes.c_void_p(x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data)
     yp = ctypes.c_void_p(y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data)
     _check(lib.pa_op_apply_host(op, xp, yp, _stream_ptr(stream)), "pa_op_apply_host")
+
+
+def _host_ptr(a):
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+def pa_op_apply_host_batch(ops, xs_host, ys_host, stream=None):
+    """Several operators from host buffers, copies overlapped with the applies."""
+    n = len(ops)
+    ha = (_vp * n)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops])
+    xa = (_vp * n)(*[_host_ptr(x) for x in xs_host])
+    ya = (_vp * n)(*[_host_ptr(y) for y in ys_host])
+    _check(lib.pa_op_apply_host_batch(ha, xa, ya, n, _stream_ptr(stream)), "pa_op_apply_host_batch")
 
 
 def pa_op_diag(op, d, stream=None):

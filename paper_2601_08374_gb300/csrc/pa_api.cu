@@ -451,6 +451,60 @@ int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream)
     return PA_OK;
 }
 
+int pa_op_apply_host_batch(pa_op *const *ops, const void *const *x_host, void *const *y_host, int count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!ops || !x_host || !y_host)))
+        return set_error(PA_EINVAL, "pa_op_apply_host_batch: bad arguments");
+    for (int k = 0; k < count; ++k) {
+        if (!ops[k] || !x_host[k] || !y_host[k]) return set_error(PA_EINVAL, "pa_op_apply_host_batch: null entry");
+        for (int j = 0; j < k; ++j)
+            if (ops[j] == ops[k]) return set_error(PA_EINVAL, "pa_op_apply_host_batch: an operator appears twice");
+    }
+    if (count == 0) return PA_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t up = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)2 * count + 1, nullptr);
+    int rc = PA_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking);
+    for (size_t i = 0; e == cudaSuccess && i < ev.size(); ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_error(e, "pa_op_apply_host_batch: stream or event creation");
+    // the copies start after the caller's earlier work on `stream`
+    if (!rc && (e = cudaEventRecord(ev[2 * count], s)) == cudaSuccess) e = cudaStreamWaitEvent(up, ev[2 * count], 0);
+    if (!rc && e != cudaSuccess) rc = cuda_error(e, "pa_op_apply_host_batch: ordering");
+    // every input goes up back to back on one stream ...
+    for (int k = 0; !rc && k < count; ++k) {
+        const size_t bytes = (size_t)ops[k]->ndofs() * ops[k]->elem;
+        e = cudaMemcpyAsync(ops[k]->d_xh, x_host[k], bytes, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k], up);
+        if (e != cudaSuccess) rc = cuda_error(e, "pa_op_apply_host_batch: host-to-device copy");
+    }
+    // ... each apply starts when its input has landed, and its result goes
+    // down on a third stream while the next operators compute
+    for (int k = 0; !rc && k < count; ++k) {
+        if ((e = cudaStreamWaitEvent(s, ev[k], 0)) != cudaSuccess) {
+            rc = cuda_error(e, "pa_op_apply_host_batch: ordering");
+            break;
+        }
+        rc = pa_op_apply(ops[k], ops[k]->d_xh, ops[k]->d_yh, stream);
+        if (rc) break;
+        const size_t bytes = (size_t)ops[k]->ndofs() * ops[k]->elem;
+        e = cudaEventRecord(ev[count + k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(down, ev[count + k], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(y_host[k], ops[k]->d_yh, bytes, cudaMemcpyDeviceToHost, down);
+        if (e != cudaSuccess) rc = cuda_error(e, "pa_op_apply_host_batch: device-to-host copy");
+    }
+    // all three streams drained before the resources go
+    if (up) cudaStreamSynchronize(up);
+    if (down && (e = cudaStreamSynchronize(down)) != cudaSuccess && !rc) rc = cuda_error(e, "pa_op_apply_host_batch: sync");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess && !rc) rc = cuda_error(e, "pa_op_apply_host_batch: sync");
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
+    return rc;
+}
+
 int pa_op_diag(pa_op *op, void *d, void *stream)
 {
     if (!op || !d) return set_error(PA_EINVAL, "pa_op_diag: null argument");

@@ -119,6 +119,32 @@ def test_apply_is_deterministic_and_host_path(pa):
     op.close()
 
 
+def test_host_batch_apply_equals_device_applies(pa):
+    """Several operators (both precisions, several degrees) applied from
+    pinned host buffers with the copies overlapped: the same bits as one
+    device apply each; a repeated operator is refused."""
+    ops, xs, ys_dev = [], [], []
+    for k, (p, prec) in enumerate([(2, pa.PA_FP64), (4, pa.PA_FP32), (1, pa.PA_FP64), (3, pa.PA_FP32)]):
+        m = syn.random_affine_cube(3 + k, seed=60 + k)
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 0.5, precision=prec)
+        dt = torch.float64 if prec == pa.PA_FP64 else torch.float32
+        x = torch.tensor(syn.uniform_vector(op.ndofs, seed=k), dtype=dt, device="cuda")
+        ops.append(op)
+        xs.append(x)
+        ys_dev.append(op.apply(x))
+    torch.cuda.synchronize()
+    xh = [x.cpu().pin_memory() for x in xs]
+    yh = [torch.full_like(h, float("nan")).pin_memory() for h in xh]
+    pa.pa_op_apply_host_batch([o.h for o in ops], xh, yh)
+    for a, b in zip(yh, ys_dev):
+        assert torch.equal(a, b.cpu())
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_op_apply_host_batch([ops[0].h, ops[0].h], xh[:1] * 2, yh[:1] * 2)
+    assert ei.value.code == pa.PA_EINVAL
+    for op in ops:
+        op.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("p", [1, 2, 4, 8])
 def test_diag(pa, p, prec):
