@@ -361,26 +361,32 @@ def run_solves(args, pa, torch):
     eigenvalue estimates, graph capture on the first solve) is untimed."""
     out = []
     beam = syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0))
-    cases = [dict(name="beam 32x4x4 p=4 (4->2->1) E=1 nu=0.3 f=(0,0,-1), x=0 clamped", mesh=beam,
+    cases = [dict(key="beam", name="beam 32x4x4 p=4 (4->2->1) E=1 nu=0.3 f=(0,0,-1), x=0 clamped", mesh=beam,
                   p=4, levels=[4, 2, 1], nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps),
-             dict(name="two-material beam 32x4x4 p=4 (4->2->1): lambda=mu=50 for x<4, lambda=mu=1 beyond; "
+             dict(key="beam2mat", name="two-material beam 32x4x4 p=4 (4->2->1): lambda=mu=50 for x<4, lambda=mu=1 beyond; "
                        "traction (0,0,-1e-2) on x=8, x=0 clamped (the paper's benchmark physics)", mesh=beam,
                   p=4, levels=[4, 2, 1], nu=None, mat=syn.two_material(beam, 4.0), modes=None, f0=(0.0, 0.0, 0.0),
                   traction=(1, (0.0, 0.0, -1e-2)), reps=args.solve_reps),
-             dict(name="beam 32x4x4 p=4 (4->2->1, then h-levels 16x2x2 and 8x1x1 at p=1) E=1 nu=0.3 f=(0,0,-1), "
+             dict(key="beamh", name="beam 32x4x4 p=4 (4->2->1, then h-levels 16x2x2 and 8x1x1 at p=1) E=1 nu=0.3 f=(0,0,-1), "
                        "x=0 clamped", mesh=beam, p=4, levels=[4, 2, 1], h=2, nu=0.3, modes=None,
                   f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
     beam2 = syn.box_mesh(64, 8, 8, hi=(8.0, 1.0, 1.0))
     for h in (0, 3):
-        cases.append(dict(name=f"beam 64x8x8 p=4 (4->2->1{', then 3 h-levels to 8x1x1' if h else ''}) E=1 nu=0.3 "
+        cases.append(dict(key="beam64h" if h else "beam64",
+                          name=f"beam 64x8x8 p=4 (4->2->1{', then 3 h-levels to 8x1x1' if h else ''}) E=1 nu=0.3 "
                                "f=(0,0,-1), x=0 clamped", mesh=beam2, p=4, levels=[4, 2, 1], h=h, nu=0.3, modes=None,
                           f0=(0.0, 0.0, -1.0), reps=args.solve_reps, solve_modes=("fp64", "mixed_fcg")))
     if not args.quick_solves:
         for p, n in ((6, syn.mixed_n(6)), (8, syn.mixed_n(8))):
             lv = [p, p // 2, 1] if p == 6 else [8, 4, 2, 1]
-            cases.append(dict(name=f"cube {n}^3 p={p} random affine maps nu=0.45 smooth force, x=0 clamped",
+            cases.append(dict(key=f"cube{p}", name=f"cube {n}^3 p={p} random affine maps nu=0.45 smooth force, x=0 clamped",
                               mesh=syn.random_affine_cube(n, seed=3000 + p), p=p, levels=lv, nu=0.45,
                               modes=syn.smooth_force_modes(seed=3100 + p), f0=(0.0, 0.0, 0.0), reps=max(1, args.solve_reps // 2)))
+    if args.solve_cases:
+        keep = set(args.solve_cases.split(","))
+        cases = [c for c in cases if c["key"] in keep]
+    eager = args.solve_eager_maxit > 0
+    cap = args.solve_eager_maxit if eager else 1000
     for c in cases:
         m, p = c["mesh"], c["p"]
         lam, mu = syn.lame(1.0, c["nu"]) if c["nu"] is not None else (0.0, 0.0)
@@ -393,15 +399,19 @@ def run_solves(args, pa, torch):
         for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):
             if key not in c.get("solve_modes", ("fp64", "mixed_ir", "mixed_fcg")):
                 continue
+            if args.solve_modes and key not in args.solve_modes.split(","):
+                continue
             s = pa.pa_solver_create_hp(op.h, c["levels"], h, 2, COARSE_RTOL, COARSE_MAXIT, mode)
+            if eager:
+                pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, 0)
             x = torch.zeros_like(b)
-            code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)  # warm-up (captures the graphs)
+            code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, cap)  # warm-up (captures the graphs)
             times = []
             for _ in range(c["reps"]):
                 x.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+                code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, cap)
                 times.append(time.perf_counter() - t0)
             sols[key] = x.clone()
             row[key] = {"status": int(code), "solves_per_s": round(1.0 / statistics.median(times), 3),
@@ -412,7 +422,7 @@ def run_solves(args, pa, torch):
                 row[key]["refinements"] = info.refinements
             pa.pa_solver_destroy(s)
         for key in ("mixed_ir", "mixed_fcg"):
-            if key not in sols:
+            if key not in sols or "fp64" not in sols:
                 continue
             d = (sols[key] - sols["fp64"]).norm() / sols["fp64"].norm()
             row[key]["rel_diff_vs_fp64"] = float(f"{float(d):.3e}")
@@ -766,6 +776,11 @@ def main(argv=None):
     ap.add_argument("--no-solve", action="store_true", help="skip the GMG-PCG solve measurements")
     ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")
     ap.add_argument("--solve-reps", type=int, default=4)
+    ap.add_argument("--solve-cases", default="", help="comma list of solve-case keys to run (default: all): "
+                    "beam, beam2mat, beamh, beam64, beam64h, cube6, cube8")
+    ap.add_argument("--solve-modes", default="", help="comma list of fp64, mixed_ir, mixed_fcg (default: each case's)")
+    ap.add_argument("--solve-eager-maxit", type=int, default=0,
+                    help="profiling aid: graphs off and this iteration cap for every solve (0: graphs, cap 1000)")
     ap.add_argument("--batch-ops", type=int, default=96, help="0 skips the batched-apply measurement")
     ap.add_argument("--batch-reps", type=int, default=20)
     ap.add_argument("--serve-requests", type=int, default=256, help="0 skips the serving measurement")

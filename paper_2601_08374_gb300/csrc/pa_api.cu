@@ -90,7 +90,7 @@ ApplyLaunch default_apply_launch(int p, int precision)
     static const int thr64[kMaxP + 1] = {0, 384, 128, 256, 256, 256, 128, 256, 512};
     static const int v32[kMaxP + 1] = {0, 2, 2, 2, 2, 2, 2, 2, 3};
     static const int epb32[kMaxP + 1] = {0, 24, 8, 4, 3, 2, 2, 2, 1};
-    static const int thr32[kMaxP + 1] = {0, 128, 128, 128, 128, 128, 128, 128, 128};
+    static const int thr32[kMaxP + 1] = {0, 128, 64, 128, 128, 128, 128, 128, 96};
     ApplyLaunch c;
     if (precision == PA_FP64) {
         c.variant = v64[p];
@@ -667,7 +667,7 @@ int pa_op_autotune(pa_op *op, void *stream)
     ApplyLaunch best = keep;
     float best_ms = 1e30f;
     static const int epbs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
-    static const int thrs[] = {128, 256, 384, 512};
+    static const int thrs[] = {64, 96, 128, 160, 192, 256, 384, 512};
     int rc = PA_OK;
     for (int v = 0; v <= kMaxVariant && rc == PA_OK; ++v)
         for (int ep : epbs)

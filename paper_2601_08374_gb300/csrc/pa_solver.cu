@@ -666,14 +666,33 @@ __global__ void k_stencil_apply(const double *__restrict__ vals, const double *_
     GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, g, row);
 }
 
+// One Chebyshev step on a stencil level fused with its operator apply:
+// d = cd d + cr Dinv (r - A e_in); e_out = e_in + d (e_in and e_out distinct)
+__device__ inline void stencil_cheb_row(const double *__restrict__ vals, const double *__restrict__ ein,
+                                        double *__restrict__ eout, double *__restrict__ dv,
+                                        const double *__restrict__ r, const double *__restrict__ dinv, double cd,
+                                        double cr, const Grid &g, int64_t row)
+{
+    const double rk = r[row] - stencil_row(vals, ein, g, row);
+    const double di = (cd != 0.0 ? cd * dv[row] : 0.0) + cr * dinv[row] * rk;
+    dv[row] = di;
+    eout[row] = ein[row] + di;
+}
+
+__global__ void k_stencil_cheb(const double *__restrict__ vals, const double *__restrict__ ein,
+                               double *__restrict__ eout, double *__restrict__ dv, const double *__restrict__ r,
+                               const double *__restrict__ dinv, double cd, double cr, Grid g)
+{
+    GRID_STRIDE(row, 3 * g.Nn) stencil_cheb_row(vals, ein, eout, dv, r, dinv, cd, cr, g, row);
+}
+
 // h-prolongation (natural injection of the trilinear space, Sec. 3) in one
 // pass: ef += P ec, each fine dof gathering its (at most 8) coarse parents,
 // summed x inside y inside z.
 template <typename T>
-__global__ void k_hprolong_add(T *__restrict__ ef, const T *__restrict__ ec, Grid gf, Grid gc)
+__device__ inline T hprolong_val(const T *__restrict__ ec, const Grid &gf, const Grid &gc, int64_t o)
 {
     const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
-    GRID_STRIDE(o, 3 * Nnf)
     {
         const int c = (int)(o / Nnf);
         const int64_t i = o - c * Nnf;
@@ -693,19 +712,24 @@ __global__ void k_hprolong_add(T *__restrict__ ef, const T *__restrict__ ec, Gri
             }
             sz += (T)wz[kz] * sy;
         }
-        ef[o] = ef[o] + sz;
+        return sz;
     }
+}
+
+template <typename T>
+__global__ void k_hprolong_add(T *__restrict__ ef, const T *__restrict__ ec, Grid gf, Grid gc)
+{
+    GRID_STRIDE(o, 3 * gf.Nn) ef[o] = ef[o] + hprolong_val(ec, gf, gc, o);
 }
 
 // h-restriction in one pass: out = R (in - in2) (in2 may be null), each
 // coarse dof gathering its fine children (at most 3 per axis) with the
 // transposed weights; essential coarse dofs are zeroed.
 template <typename T>
-__global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ in2, Grid gf, Grid gc,
-                            const uint8_t *__restrict__ ess)
+__device__ inline T hrestrict_val(const T *__restrict__ in, const T *__restrict__ in2, const Grid &gf, const Grid &gc,
+                                  int64_t o)
 {
     const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
-    GRID_STRIDE(o, 3 * Nnc)
     {
         const int c = (int)(o / Nnc);
         const int64_t I = o - c * Nnc;
@@ -733,8 +757,15 @@ __global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const
             }
             sz += wz * sy;
         }
-        out[o] = (ess && ess[o]) ? (T)0 : sz;
+        return sz;
     }
+}
+
+template <typename T>
+__global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ in2, Grid gf, Grid gc,
+                            const uint8_t *__restrict__ ess)
+{
+    GRID_STRIDE(o, 3 * gc.Nn) out[o] = (ess && ess[o]) ? (T)0 : hrestrict_val(in, in2, gf, gc, o);
 }
 
 // Galerkin coarse stencil: one thread per coarse row (c, I); essential fine
@@ -844,21 +875,10 @@ __global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64
         d.scal[C_BB] = tot[0];
         d.scal[C_RR] = tot[0];
         d.scal[C_TOL2] = tol2;
+        d.scal[C_RZ] = 0.0;  // no previous direction: the first one is z
         d.flag[F_CDONE] = (tot[0] == 0.0 || !isfinite(tot[0])) ? 1 : 0;
         d.flag[F_CIT] = 0;
     }
-}
-
-// start 2: p = z, rz = (r, z)
-__global__ void k_pcg_start2(Dev d, double *p, const double *z, const double *r, int64_t n)
-{
-    double v[1] = {0.0}, tot[1];
-    GRID_STRIDE(i, n)
-    {
-        p[i] = z[i];
-        v[0] += r[i] * z[i];
-    }
-    if (grid_sum<1>(d, v, tot)) d.scal[C_RZ] = tot[0];
 }
 
 // x += alpha p; r -= alpha q; rr = (r, r); done when rr <= tol2 bb
@@ -880,24 +900,26 @@ __global__ void k_pcg_update(Dev d, double *x, double *r, const double *p, const
     }
 }
 
-// rz_new = (r, z); beta = rz_new / rz; rz = rz_new
+// rz_new = (r, z); beta = rz_new / rz (0 when there is no previous
+// direction, rz = 0); rz = rz_new
 __global__ void k_pcg_beta(Dev d, const double *r, const double *z, int64_t n)
 {
     if (d.flag[F_CDONE]) return;
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n) v[0] += r[i] * z[i];
     if (grid_sum<1>(d, v, tot)) {
-        d.scal[C_BETA] = tot[0] / d.scal[C_RZ];
+        const double rz = d.scal[C_RZ];
+        d.scal[C_BETA] = rz != 0.0 ? tot[0] / rz : 0.0;
         d.scal[C_RZ] = tot[0];
     }
 }
 
-// p = z + beta p
+// p = z + beta p (p = z when beta = 0: the old p is not read)
 __global__ void k_pcg_p(Dev d, double *p, const double *z, int64_t n)
 {
     if (d.flag[F_CDONE]) return;
     const double beta = d.scal[C_BETA];
-    GRID_STRIDE(i, n) p[i] = z[i] + beta * p[i];
+    GRID_STRIDE(i, n) p[i] = beta != 0.0 ? z[i] + beta * p[i] : z[i];
 }
 
 // Loop condition of the graph's coarse WHILE node: continue while the coarse
@@ -1088,7 +1110,8 @@ struct HLevel {
     double *vals = nullptr;     // stencil (81 planes of n); level 0 borrows the p = 1 stencil
     uint8_t *ess = nullptr;     // essential mask (level 0 borrows the operator's)
     double *dinv = nullptr;     // 1 / diag
-    double *r = nullptr, *e = nullptr, *t = nullptr, *d = nullptr;
+    double *r = nullptr, *e = nullptr, *t = nullptr, *d = nullptr;  // level 0: r is the coarse CG residual
+    double *e2 = nullptr;       // second iterate buffer of the fused smoothing steps
     double *xa = nullptr, *xb = nullptr;  // transfer temporaries (size of this level)
     double theta = 0.0, delta = 0.0, lmax = 0.0;
     double *Ainv = nullptr;     // dense inverse on the coarsest level
@@ -1397,8 +1420,6 @@ bool spd_inverse(std::vector<double> &A, int n)
     return true;
 }
 
-// Builds the h-hierarchy under the p = 1 level: Galerkin stencils, masks,
-// diagonals, Chebyshev intervals, and a dense inverse on the coarsest level.
 // h-coarse essential mask: coarse dof j is essential when its interpolation
 // reaches an essential fine dof (the 0/1 fine mask restricted); exact for
 // essential sets made of whole faces.
@@ -1421,6 +1442,8 @@ std::vector<uint8_t> h_coarse_mask(const std::vector<uint8_t> &fm, const Grid &g
     return cm;
 }
 
+// Builds the h-hierarchy under the p = 1 level: Galerkin stencils, masks,
+// diagonals, Chebyshev intervals, and a dense inverse on the coarsest level.
 int build_h_levels(pa_solver *s, cudaStream_t st)
 {
     Level &L = s->lv.back();
@@ -1474,7 +1497,10 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
     for (size_t k = 0; k < s->hl.size(); ++k) {
         HLevel &H = s->hl[k];
         int rc;
-        if ((rc = dalloc(s, &H.r, H.n)) || (rc = dalloc(s, &H.e, H.n)) || (rc = dalloc(s, &H.t, H.n)) ||
+        // level 0 reads its right-hand side from the coarse CG residual in place
+        if (k == 0) H.r = L.cr;
+        else if ((rc = dalloc(s, &H.r, H.n))) return rc;
+        if ((rc = dalloc(s, &H.e, H.n)) || (rc = dalloc(s, &H.e2, H.n)) || (rc = dalloc(s, &H.t, H.n)) ||
             (rc = dalloc(s, &H.d, H.n)) || (rc = dalloc(s, &H.xa, H.n)) || (rc = dalloc(s, &H.xb, H.n)))
             return rc;
         if (k > 0) {
@@ -1544,18 +1570,18 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
     return PA_OK;
 }
 
-// Chebyshev smoothing on an h-level (stencil operator), e <- S(r)
-int h_smooth(pa_solver *s, HLevel &H, bool from_zero, cudaStream_t st)
+// Chebyshev smoothing on an h-level (stencil operator) of the iterate in
+// buffer e.  A step from a zero iterate needs no operator apply (k_cheb);
+// every other step is one fused kernel (stencil apply and update) from one
+// iterate buffer into the other (H.e / H.e2).  Returns the buffer with the
+// result.
+double *h_smooth(pa_solver *s, HLevel &H, double *e, bool from_zero, cudaStream_t st)
 {
     const int64_t n = H.n;
     const double sigma = H.theta / H.delta;
     double rho_prev = 1.0 / sigma;
+    double *cur = e;
     for (int k = 0; k < s->cheb_order; ++k) {
-        const double *tt = nullptr;
-        if (!(k == 0 && from_zero)) {
-            k_stencil_apply<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, H.e, H.t, H.g);
-            tt = H.t;
-        }
         double cd, cr;
         if (k == 0) {
             cd = 0.0;
@@ -1566,67 +1592,64 @@ int h_smooth(pa_solver *s, HLevel &H, bool from_zero, cudaStream_t st)
             cr = 2.0 * rho / H.delta;
             rho_prev = rho;
         }
-        k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.e, H.d, H.r, tt, H.dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
+        if (k == 0 && from_zero) {
+            k_cheb<double><<<blocks_for(n), 256, 0, st>>>(cur, H.d, H.r, nullptr, H.dinv, cd, cr, 1, n);
+        } else {
+            double *nxt = cur == H.e ? H.e2 : H.e;
+            k_stencil_cheb<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, cur, nxt, H.d, H.r, H.dinv, cd, cr, H.g);
+            cur = nxt;
+        }
     }
-    PA_CUDA_TRY(cudaGetLastError());
-    return PA_OK;
+    return cur;
 }
 
-// h-V(1,1) cycle from h-level k: e_k ~ A_k^-1 r_k
-int h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
+// h-V(1,1) cycle from h-level k: e_k ~ A_k^-1 r_k; returns the buffer of
+// level k holding e_k.  Launch errors are left for the caller's check.
+double *h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
 {
     HLevel &F = s->hl[k];
     if (k + 1 == s->hl.size()) {
         k_dense_matvec<<<(unsigned)((F.n * 32 + 255) / 256), 256, 0, st>>>(F.Ainv, F.r, F.e, F.n);
-        PA_CUDA_TRY(cudaGetLastError());
-        return PA_OK;
+        return F.e;
     }
     HLevel &C = s->hl[k + 1];
-    int rc = h_smooth(s, F, true, st);
-    if (rc) return rc;
-    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, F.e, F.t, F.g);
+    double *e = h_smooth(s, F, F.e, true, st);
+    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, e, F.t, F.g);
     // restrict r - t, then the coarse correction prolonged and added
     k_hrestrict<double><<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
-    rc = h_vcycle(s, k + 1, st);
-    if (rc) return rc;
-    k_hprolong_add<double><<<blocks_for(F.n), 256, 0, st>>>(F.e, C.e, F.g, C.g);
-    rc = h_smooth(s, F, false, st);
-    PA_CUDA_TRY(cudaGetLastError());
-    return rc;
+    const double *ec = h_vcycle(s, k + 1, st);
+    k_hprolong_add<double><<<blocks_for(F.n), 256, 0, st>>>(e, ec, F.g, C.g);
+    return h_smooth(s, F, e, false, st);
 }
 
 // h-multigrid preconditioned coarse CG: on a ladder of h-levels, or (a
 // coarse level small enough for it) on the dense inverse alone
 bool use_hmg(pa_solver *s) { return s->use_hmg && !s->hl.empty() && s->hl.back().Ainv != nullptr; }
 
-// start of the h-multigrid preconditioned coarse CG: x = 0, r = b, z = M r, p = z
+// h-multigrid preconditioned coarse CG, with the loop rotated so that each
+// iteration applies the preconditioner once and the last one applies none
+// after convergence:
+//   start:     x = 0, r = b, rz = 0 (the first direction is z itself)
+//   iteration: z = M r; beta = (r, z) / rz (0 at first); p = z + beta p;
+//              q = A p, alpha = rz / (p, q); x += alpha p; r -= alpha q;
+//              stop when (r, r) <= tol^2 (b, b)
 int coarse_start_hmg(pa_solver *s, Level &L, cudaStream_t st)
 {
-    const int64_t n = L.n;
-    HLevel &H = s->hl[0];
-    k_pcg_start1<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.r, n, s->coarse_rtol * s->coarse_rtol);
-    k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.r, L.cr, 1.0, n);
-    int rc = h_vcycle(s, 0, st);
-    if (rc) return rc;
-    k_pcg_start2<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cp, H.e, L.cr, n);
+    k_pcg_start1<<<red_blocks(L.n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.r, L.n, s->coarse_rtol * s->coarse_rtol);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
 
-// one iteration: q = A p, alpha, x, r, rr; z = M r; beta; p = z + beta p
 int coarse_iter_hmg(pa_solver *s, Level &L, cudaStream_t st)
 {
     const int64_t n = L.n;
-    HLevel &H = s->hl[0];
+    const double *z = h_vcycle(s, 0, st);  // reads L.cr in place
+    k_pcg_beta<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cr, z, n);
+    k_pcg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, z, n);
     int64_t nb = (n + 63) / 64;
     if (nb > kRedBlocks) nb = kRedBlocks;
     k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
     k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n);
-    k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.r, L.cr, 1.0, n);
-    int rc = h_vcycle(s, 0, st);
-    if (rc) return rc;
-    k_pcg_beta<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cr, H.e, n);
-    k_pcg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, H.e, n);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -1800,7 +1823,10 @@ int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
 }
 
 // The persistent cooperative coarse CG applies when the coarse level is
-// assembled and co-resident CTAs are available.
+// assembled, Jacobi-preconditioned (h-multigrid off) and co-resident CTAs
+// are available.  (The h-multigrid PCG as one cooperative launch, with a
+// grid barrier between its ~26 dependent stages per iteration, measured
+// slower than the launched kernels in the step graph at every CTA count.)
 bool use_coop(pa_solver *s)
 {
     return !use_hmg(s) && s->allow_coop && s->coop_blocks > 0 && s->lv.back().stencil != nullptr;
