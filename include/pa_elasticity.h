@@ -104,6 +104,12 @@ int pa_op_info(const pa_op *op, int64_t *ndofs, int64_t *nelem, int *p, int *pre
  * precision; they must not alias.  y is overwritten. */
 int pa_op_apply(pa_op *op, const void *x, void *y, void *stream);
 
+/* y += A x (the accumulating form of the apply, MFEM's AddMult): the same
+ * computation as pa_op_apply with each node sum added to y instead of
+ * stored; on essential dofs y += x (the constrained operator's identity
+ * rows).  Same argument rules as pa_op_apply. */
+int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream);
+
 /* y_k = A_k x_k for k < count in few launches: operators of equal degree and
  * precision are applied together, one launch of the element kernel over all
  * their elements (uneven sizes allowed) and one launch of the node

@@ -79,6 +79,7 @@ _sig("pa_op_setup", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_
 _sig("pa_op_destroy", [_vp])
 _sig("pa_op_info", [_vp, _i64p, _i64p, _ip, _ip])
 _sig("pa_op_apply", [_vp, _vp, _vp, _vp])
+_sig("pa_op_apply_add", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host", [_vp, _vp, _vp, _vp])
 _sig("pa_op_apply_host_batch", [_vp, _vp, _vp, ctypes.c_int, _vp])
 _sig("pa_op_apply_batch", [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp])
@@ -199,6 +200,11 @@ def pa_op_info(op):
 
 def pa_op_apply(op, x, y, stream=None):
     _check(lib.pa_op_apply(op, _tptr(x), _tptr(y), _stream_ptr(stream)), "pa_op_apply")
+
+
+def pa_op_apply_add(op, x, y, stream=None):
+    """y += A x."""
+    _check(lib.pa_op_apply_add(op, _tptr(x), _tptr(y), _stream_ptr(stream)), "pa_op_apply_add")
 
 
 def pa_op_apply_batch(ops, xs, ys, stream=None):

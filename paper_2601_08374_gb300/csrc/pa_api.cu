@@ -374,6 +374,13 @@ int pa_op_apply(pa_op *op, const void *x, void *y, void *stream)
     return op_apply_async(op, x, y, false, static_cast<cudaStream_t>(stream), nullptr);
 }
 
+int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream)
+{
+    if (!op || !x || !y) return set_error(PA_EINVAL, "pa_op_apply_add: null argument");
+    if (x == y) return set_error(PA_EINVAL, "pa_op_apply_add: x and y must not alias");
+    return op_apply_async(op, x, y, true, static_cast<cudaStream_t>(stream), nullptr);
+}
+
 int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream)
 {
     if (count < 0 || (count > 0 && (!ops || !xs || !ys))) return set_error(PA_EINVAL, "pa_op_apply_batch: bad arguments");

@@ -131,9 +131,10 @@ __global__ void assemble_kernel_p(const T *__restrict__ ye, T *__restrict__ y, c
                                   const int *__restrict__ skip)
 {
     if (skip && *skip) return;
-    const int n = (int)g.Nn;
-    for (int gn = blockIdx.x * blockDim.x + threadIdx.x; gn < n; gn += gridDim.x * blockDim.x)
-        assemble_node_p<T, P>(ye, y, xin, ess, ess_value, accumulate, g, gn);
+    // the loop counter is 64-bit: near 2^31 nodes a 32-bit counter plus the
+    // grid stride would overflow; the node arithmetic inside stays 32-bit
+    for (int64_t gn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gn < g.Nn; gn += (int64_t)gridDim.x * blockDim.x)
+        assemble_node_p<T, P>(ye, y, xin, ess, ess_value, accumulate, g, (int)gn);
 }
 
 template <typename T, int P>

@@ -491,3 +491,60 @@ def test_tensor_core_variant_is_fp32_and_low_degree_only(pa):
     with pytest.raises(pa.PAError):
         pa.pa_op_set_launch(op.h, 4, 1, 384)
     op.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [1, 3, 8])
+def test_degenerate_inputs(pa, p, prec):
+    """Degenerate cases of the method: zero input gives exactly zero; every
+    dof essential gives the identity; rigid translations (any geometry) and,
+    on a globally affine mesh, rigid rotations lie in the kernel of the
+    unconstrained operator to rounding of the operator's scale."""
+    dt = torch.float64 if prec == 0 else torch.float32
+    m = syn.random_affine_cube(3, seed=90 + p, ny=2, nz=2)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 0.7, precision=prec)
+    N = op.ndofs
+    z = torch.zeros(N, dtype=dt, device="cuda")
+    assert torch.count_nonzero(op.apply(z)) == 0
+    xr = torch.tensor(syn.uniform_vector(N, seed=5), dtype=dt, device="cuda")
+    scale = float(op.apply(xr).abs().max())
+    Nn = N // 3
+    for c in range(3):
+        t = torch.zeros(N, dtype=dt, device="cuda")
+        t[c * Nn:(c + 1) * Nn] = 1.0
+        assert float(op.apply(t).abs().max()) <= TOL[prec] * scale
+    op.close()
+    allm = np.ones(N, dtype=np.uint8)
+    opc = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 0.7, precision=prec, ess_mask=allm)
+    assert torch.equal(opc.apply(xr), xr)
+    opc.close()
+    M = np.array([[1.3, 0.2, -0.1], [0.1, 0.9, 0.3], [-0.2, 0.15, 1.1]])
+    mg = syn.globally_affine_mesh(3, 2, 2, M, t=(0.3, -0.2, 0.5))
+    opg = pa.Operator(mg.nx, mg.ny, mg.nz, mg.affine, p, 1.0, 0.7, precision=prec)
+    X = oracle.node_coords_box(3, 2, 2, p) @ M.T + np.array([0.3, -0.2, 0.5])
+    sg = float(opg.apply(torch.tensor(syn.uniform_vector(N, seed=6), dtype=dt, device="cuda")).abs().max())
+    for w in np.eye(3):
+        u = np.cross(w, X)  # rotation field w x X
+        y = opg.apply(torch.tensor(u.T.reshape(-1), dtype=dt, device="cuda"))
+        assert float(y.abs().max()) <= 10 * TOL[prec] * sg * np.abs(X).max()
+    opg.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 5])
+def test_apply_add_accumulates(pa, p, prec):
+    """pa_op_apply_add: y0 + A x against the oracle (constrained rows add x)."""
+    dt = torch.float64 if prec == 0 else torch.float32
+    m = syn.random_affine_cube(3, seed=70 + p, ny=2, nz=2)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, precision=prec, ess_mask=ess)
+    x = syn.uniform_vector(op.ndofs, seed=1)
+    y0 = syn.uniform_vector(op.ndofs, seed=2)
+    y = torch.tensor(y0, dtype=dt, device="cuda")
+    pa.pa_op_apply_add(op.h, torch.tensor(x, dtype=dt, device="cuda"), y)
+    yo = y0 + oracle.apply(p, m.nx, m.ny, m.nz, m.affine, lam, mu, x, ess=ess)
+    assert _relerr(y.cpu().double().numpy(), yo) <= TOL[prec]
+    with pytest.raises(pa.PAError):
+        pa.pa_op_apply_add(op.h, y, y)
+    op.close()
