@@ -548,3 +548,22 @@ def test_apply_add_accumulates(pa, p, prec):
     with pytest.raises(pa.PAError):
         pa.pa_op_apply_add(op.h, y, y)
     op.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_largest_served_size_sampled(pa, prec):
+    """The largest request of the served stream (32^3 elements at p = 8,
+    50.9M dofs), clamped at x = 0: sampled rows (both faces, edges, the
+    interior) against the oracle's element-matrix rows."""
+    n, p = 32, 8
+    m = syn.box_mesh(n, n, n)
+    lam, mu = syn.lame(3.0, 0.4)
+    ess = syn.clamp_mask(m, p)
+    N = m.n_dofs(p)
+    assert N == 3 * 257 ** 3
+    x = syn.uniform_vector(N, seed=11)
+    y = _run_apply(pa, m, p, lam, mu, x, prec, ess)
+    rng = np.random.default_rng(12)
+    rows = np.concatenate([rng.choice(N, 2000, replace=False), [0, 1, 256, 257, N // 3, N - 1]])
+    yo = oracle.apply_rows(p, n, n, n, m.affine, lam, mu, x, rows, ess=ess)
+    assert np.max(np.abs(y[rows] - yo)) <= TOL[prec] * np.max(np.abs(yo))

@@ -375,3 +375,36 @@ def test_h_levels_lockstep_equals_solo(pa):
         pa.pa_solver_destroy(s)
     for op in ops:
         op.close()
+
+
+def test_mixed_precision_cube_at_full_size(pa):
+    """The mixed-precision configuration at its full size (23^3 elements,
+    p = 6, 8.06M dofs, nu = 0.45, random affine maps): both mixed forms
+    reach the FP64 solution within 1e-8, and the FP64 solution's residual,
+    recomputed with the oracle's operator on sampled rows, is at the solver
+    tolerance's scale."""
+    p = 6
+    n = syn.mixed_n(p)
+    m = syn.random_affine_cube(n, seed=3000 + p)
+    lam, mu = syn.lame(1.0, 0.45)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(modes=syn.smooth_force_modes(seed=3100 + p))
+    xs = {}
+    for mode in (pa.PA_SOLVE_FP64, pa.PA_SOLVE_MIXED, pa.PA_SOLVE_MIXED_FCG):
+        s = pa.pa_solver_create(op.h, [6, 3, 1], 2, 1e-2, 10, mode)
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+        pa.pa_solver_destroy(s)
+        assert code == pa.PA_OK, (mode, pa.lib.pa_last_error())
+        assert info.rel_residual <= 2e-10
+        xs[mode] = x
+    x64 = xs[pa.PA_SOLVE_FP64]
+    for mode in (pa.PA_SOLVE_MIXED, pa.PA_SOLVE_MIXED_FCG):
+        assert float((xs[mode] - x64).norm() / x64.norm()) <= 1e-8
+    bh, xh = b.cpu().numpy(), x64.cpu().numpy()
+    N = len(bh)
+    rows = np.random.default_rng(13).choice(N, 1500, replace=False)
+    r = bh[rows] - oracle.apply_rows(p, n, n, n, m.affine, lam, mu, xh, rows, ess=ess)
+    assert np.max(np.abs(r)) <= 1e-8 * np.max(np.abs(bh))
+    op.close()
