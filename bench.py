@@ -370,6 +370,10 @@ def run_solves(args, pa, torch):
              dict(key="beamh", name="beam 32x4x4 p=4 (4->2->1, then h-levels 16x2x2 and 8x1x1 at p=1) E=1 nu=0.3 f=(0,0,-1), "
                        "x=0 clamped", mesh=beam, p=4, levels=[4, 2, 1], h=2, nu=0.3, modes=None,
                   f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
+    cases.append(dict(key="beam_c1", name="beam 32x4x4 p=4 (4->2->1) as above, coarse solve capped at one PCG "
+                           "iteration (instead of the paper's 1e-2 / at most 10)", mesh=beam, p=4, levels=[4, 2, 1],
+                      nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps, coarse=(COARSE_RTOL, 1),
+                      solve_modes=("fp64", "mixed_fcg")))
     beam2 = syn.box_mesh(64, 8, 8, hi=(8.0, 1.0, 1.0))
     for h in (0, 3):
         cases.append(dict(key="beam64h" if h else "beam64",
@@ -382,6 +386,11 @@ def run_solves(args, pa, torch):
             cases.append(dict(key=f"cube{p}", name=f"cube {n}^3 p={p} random affine maps nu=0.45 smooth force, x=0 clamped",
                               mesh=syn.random_affine_cube(n, seed=3000 + p), p=p, levels=lv, nu=0.45,
                               modes=syn.smooth_force_modes(seed=3100 + p), f0=(0.0, 0.0, 0.0), reps=max(1, args.solve_reps // 2)))
+        if p == 6:
+            cases.append(dict(key="cube6_c1", name=f"cube {syn.mixed_n(6)}^3 p=6 as above, coarse solve capped at one PCG "
+                                   "iteration", mesh=syn.random_affine_cube(syn.mixed_n(6), seed=3006), p=6, levels=[6, 3, 1],
+                              nu=0.45, modes=syn.smooth_force_modes(seed=3106), f0=(0.0, 0.0, 0.0),
+                              reps=max(1, args.solve_reps // 2), coarse=(COARSE_RTOL, 1), solve_modes=("mixed_ir",)))
     if args.solve_cases:
         keep = set(args.solve_cases.split(","))
         cases = [c for c in cases if c["key"] in keep]
@@ -394,14 +403,16 @@ def run_solves(args, pa, torch):
         op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess, mat=c.get("mat"))
         b = op.rhs(f0=c["f0"], modes=c["modes"], traction=c.get("traction"))
         h = c.get("h", 0)
-        row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "h_levels": h, "rtol": 1e-10}
+        row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "h_levels": h, "rtol": 1e-10,
+               "coarse_rtol_maxit": list(c.get("coarse", (COARSE_RTOL, COARSE_MAXIT)))}
         sols = {}
         for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):
             if key not in c.get("solve_modes", ("fp64", "mixed_ir", "mixed_fcg")):
                 continue
             if args.solve_modes and key not in args.solve_modes.split(","):
                 continue
-            s = pa.pa_solver_create_hp(op.h, c["levels"], h, 2, COARSE_RTOL, COARSE_MAXIT, mode)
+            crtol, cmax = c.get("coarse", (COARSE_RTOL, COARSE_MAXIT))
+            s = pa.pa_solver_create_hp(op.h, c["levels"], h, 2, crtol, cmax, mode)
             if eager:
                 pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, 0)
             x = torch.zeros_like(b)
@@ -777,7 +788,7 @@ def main(argv=None):
     ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")
     ap.add_argument("--solve-reps", type=int, default=4)
     ap.add_argument("--solve-cases", default="", help="comma list of solve-case keys to run (default: all): "
-                    "beam, beam2mat, beamh, beam64, beam64h, cube6, cube8")
+                    "beam, beam2mat, beamh, beam_c1, beam64, beam64h, cube6, cube8, cube6_c1")
     ap.add_argument("--solve-modes", default="", help="comma list of fp64, mixed_ir, mixed_fcg (default: each case's)")
     ap.add_argument("--solve-eager-maxit", type=int, default=0,
                     help="profiling aid: graphs off and this iteration cap for every solve (0: graphs, cap 1000)")
