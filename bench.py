@@ -386,11 +386,10 @@ def run_solves(args, pa, torch):
             cases.append(dict(key=f"cube{p}", name=f"cube {n}^3 p={p} random affine maps nu=0.45 smooth force, x=0 clamped",
                               mesh=syn.random_affine_cube(n, seed=3000 + p), p=p, levels=lv, nu=0.45,
                               modes=syn.smooth_force_modes(seed=3100 + p), f0=(0.0, 0.0, 0.0), reps=max(1, args.solve_reps // 2)))
-        if p == 6:
-            cases.append(dict(key="cube6_c1", name=f"cube {syn.mixed_n(6)}^3 p=6 as above, coarse solve capped at one PCG "
-                                   "iteration", mesh=syn.random_affine_cube(syn.mixed_n(6), seed=3006), p=6, levels=[6, 3, 1],
-                              nu=0.45, modes=syn.smooth_force_modes(seed=3106), f0=(0.0, 0.0, 0.0),
-                              reps=max(1, args.solve_reps // 2), coarse=(COARSE_RTOL, 1), solve_modes=("mixed_ir",)))
+        cases.append(dict(key="cube6_c1", name=f"cube {syn.mixed_n(6)}^3 p=6 as above, coarse solve capped at one PCG "
+                               "iteration", mesh=syn.random_affine_cube(syn.mixed_n(6), seed=3006), p=6, levels=[6, 3, 1],
+                          nu=0.45, modes=syn.smooth_force_modes(seed=3106), f0=(0.0, 0.0, 0.0),
+                          reps=max(1, args.solve_reps // 2), coarse=(COARSE_RTOL, 1), solve_modes=("mixed_ir",)))
     if args.solve_cases:
         keep = set(args.solve_cases.split(","))
         cases = [c for c in cases if c["key"] in keep]
