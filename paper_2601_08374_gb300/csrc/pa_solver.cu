@@ -761,11 +761,43 @@ __device__ inline T hrestrict_val(const T *__restrict__ in, const T *__restrict_
     }
 }
 
+// First Chebyshev step from a zero iterate of an h-level, taken by the
+// kernel that produces the level's right-hand side: e = d = cr Dinv r
+// (the step needs no operator apply, so it costs no dependent stage).
+struct FirstStep {
+    double *e = nullptr, *d = nullptr;  // null: no fused step
+    const double *dinv = nullptr;
+    double cr = 0.0;
+};
+
+__device__ inline void first_step(const FirstStep &f, int64_t i, double r)
+{
+    if (f.e) {
+        const double di = 0.0 + f.cr * f.dinv[i] * r;
+        f.d[i] = di;
+        f.e[i] = di;
+    }
+}
+
 template <typename T>
 __global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ in2, Grid gf, Grid gc,
                             const uint8_t *__restrict__ ess)
 {
     GRID_STRIDE(o, 3 * gc.Nn) out[o] = (ess && ess[o]) ? (T)0 : hrestrict_val(in, in2, gf, gc, o);
+}
+
+// The same restriction followed by the coarse level's first Chebyshev step
+// from a zero iterate (e = d = cr Dinv r), which needs no operator apply.
+__global__ void k_hrestrict_first(double *__restrict__ out, const double *__restrict__ in,
+                                  const double *__restrict__ in2, Grid gf, Grid gc, const uint8_t *__restrict__ ess,
+                                  FirstStep f)
+{
+    GRID_STRIDE(o, 3 * gc.Nn)
+    {
+        const double v = (ess && ess[o]) ? 0.0 : hrestrict_val(in, in2, gf, gc, o);
+        out[o] = v;
+        first_step(f, o, v);
+    }
 }
 
 // Galerkin coarse stencil: one thread per coarse row (c, I); essential fine
@@ -861,7 +893,7 @@ __global__ void k_dense_matvec(const double *__restrict__ Ainv, const double *__
 
 // preconditioned coarse CG (z = M r from the h-cycle)
 // start 1: x = 0, r = b, bb = (b, b), done = bb == 0
-__global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64_t n, double tol2)
+__global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64_t n, double tol2, FirstStep f)
 {
     double v[1] = {0.0}, tot[1];
     GRID_STRIDE(i, n)
@@ -870,6 +902,7 @@ __global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64
         x[i] = 0.0;
         r[i] = bi;
         v[0] += bi * bi;
+        first_step(f, i, bi);
     }
     if (grid_sum<1>(d, v, tot)) {
         d.scal[C_BB] = tot[0];
@@ -882,7 +915,7 @@ __global__ void k_pcg_start1(Dev d, double *x, double *r, const double *b, int64
 }
 
 // x += alpha p; r -= alpha q; rr = (r, r); done when rr <= tol2 bb
-__global__ void k_pcg_update(Dev d, double *x, double *r, const double *p, const double *q, int64_t n)
+__global__ void k_pcg_update(Dev d, double *x, double *r, const double *p, const double *q, int64_t n, FirstStep f)
 {
     if (d.flag[F_CDONE]) return;
     const double alpha = d.scal[C_ALPHA];
@@ -893,6 +926,7 @@ __global__ void k_pcg_update(Dev d, double *x, double *r, const double *p, const
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
         v[0] += ri * ri;
+        first_step(f, i, ri);
     }
     if (grid_sum<1>(d, v, tot)) {
         d.scal[C_RR] = tot[0];
@@ -1570,11 +1604,28 @@ int build_h_levels(pa_solver *s, cudaStream_t st)
     return PA_OK;
 }
 
+// The first-step arguments of h-level H (cr of the first Chebyshev step)
+FirstStep h_first_step(const HLevel &H)
+{
+    FirstStep f;
+    f.e = H.e;
+    f.d = H.d;
+    f.dinv = H.dinv;
+    f.cr = 1.0 / H.theta;
+    return f;
+}
+
+// ... of the first h-level, which the coarse CG's start and update kernels
+// take (none when the first level is the dense bottom)
+FirstStep coarse_first_step(pa_solver *s) { return s->hl.size() > 1 ? h_first_step(s->hl[0]) : FirstStep{}; }
+
 // Chebyshev smoothing on an h-level (stencil operator) of the iterate in
-// buffer e.  A step from a zero iterate needs no operator apply (k_cheb);
-// every other step is one fused kernel (stencil apply and update) from one
-// iterate buffer into the other (H.e / H.e2).  Returns the buffer with the
-// result.
+// buffer e.  The step from a zero iterate needs no operator apply: the
+// kernel that produced the level's right-hand side has already taken it
+// into H.e and H.d (first_step), so pre-smoothing starts at the second
+// step.  Every other step is one fused kernel (stencil apply and update)
+// from one iterate buffer into the other (H.e / H.e2).  Returns the buffer
+// with the result.
 double *h_smooth(pa_solver *s, HLevel &H, double *e, bool from_zero, cudaStream_t st)
 {
     const int64_t n = H.n;
@@ -1593,7 +1644,7 @@ double *h_smooth(pa_solver *s, HLevel &H, double *e, bool from_zero, cudaStream_
             rho_prev = rho;
         }
         if (k == 0 && from_zero) {
-            k_cheb<double><<<blocks_for(n), 256, 0, st>>>(cur, H.d, H.r, nullptr, H.dinv, cd, cr, 1, n);
+            continue;  // taken by the producer of H.r
         } else {
             double *nxt = cur == H.e ? H.e2 : H.e;
             k_stencil_cheb<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, cur, nxt, H.d, H.r, H.dinv, cd, cr, H.g);
@@ -1615,8 +1666,12 @@ double *h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
     HLevel &C = s->hl[k + 1];
     double *e = h_smooth(s, F, F.e, true, st);
     k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, e, F.t, F.g);
-    // restrict r - t, then the coarse correction prolonged and added
-    k_hrestrict<double><<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
+    // restrict r - t (with the coarse level's first smoothing step unless it
+    // is the dense bottom), then the coarse correction prolonged and added
+    if (k + 2 < s->hl.size())
+        k_hrestrict_first<<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess, h_first_step(C));
+    else
+        k_hrestrict<double><<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
     const double *ec = h_vcycle(s, k + 1, st);
     k_hprolong_add<double><<<blocks_for(F.n), 256, 0, st>>>(e, ec, F.g, C.g);
     return h_smooth(s, F, e, false, st);
@@ -1635,7 +1690,8 @@ bool use_hmg(pa_solver *s) { return s->use_hmg && !s->hl.empty() && s->hl.back()
 //              stop when (r, r) <= tol^2 (b, b)
 int coarse_start_hmg(pa_solver *s, Level &L, cudaStream_t st)
 {
-    k_pcg_start1<<<red_blocks(L.n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.r, L.n, s->coarse_rtol * s->coarse_rtol);
+    k_pcg_start1<<<red_blocks(L.n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.r, L.n, s->coarse_rtol * s->coarse_rtol,
+                                                          coarse_first_step(s));
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -1649,7 +1705,7 @@ int coarse_iter_hmg(pa_solver *s, Level &L, cudaStream_t st)
     int64_t nb = (n + 63) / 64;
     if (nb > kRedBlocks) nb = kRedBlocks;
     k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
-    k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n);
+    k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n, coarse_first_step(s));
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
