@@ -420,6 +420,73 @@ __device__ inline double stencil_row(const double *__restrict__ vals, const doub
     return (acc[0] + acc[1]) + acc[2];
 }
 
+// Three lanes per stencil row: lanes 3r, 3r + 1, 3r + 2 of a warp take row
+// base + r (r = 0..9; lanes 30, 31 idle), lane d2 summing the 27 products
+// with the neighbours' component d2 in stencil_row's order, and the row's
+// first lane adding the three sums as stencil_row does (same bits).  On a
+// small level one thread per row leaves most SMs idle while each active SM
+// works through 81 FP64 products per thread; three lanes spread them over
+// three times the SMs.
+__device__ inline double stencil_part(const double *__restrict__ vals, const double *__restrict__ p, const Grid &g,
+                                      int64_t row, int d2)
+{
+    const int Nn = (int)g.Nn, Mx = g.Mx, My = g.My, Mz = g.Mz;
+    const int64_t nrow = 3 * (int64_t)Nn;
+    const int c = (int)(row / Nn);
+    const int i = (int)(row - (int64_t)c * Nn);
+    const int ix = i % Mx, t = i / Mx, iy = t % My, iz = t / My;
+    const int ox[3] = {ix > 0 ? -1 : 0, 0, ix < Mx - 1 ? 1 : 0};
+    const int oy[3] = {iy > 0 ? -Mx : 0, 0, iy < My - 1 ? Mx : 0};
+    const int oz[3] = {iz > 0 ? -Mx * My : 0, 0, iz < Mz - 1 ? Mx * My : 0};
+    const double *pd = p + (int64_t)d2 * Nn;
+    double acc = 0.0;
+#pragma unroll
+    for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+        for (int sy = 0; sy < 3; ++sy)
+#pragma unroll
+            for (int sx = 0; sx < 3; ++sx) {
+                const int sidx = sx + 3 * sy + 9 * sz;
+                acc = fma(vals[(int64_t)(sidx * 3 + d2) * nrow + row], pd[i + ox[sx] + oy[sy] + oz[sz]], acc);
+            }
+    return acc;
+}
+
+// The row sum on the row's first lane (all 32 lanes must call it together).
+__device__ inline double stencil_row3(const double *__restrict__ vals, const double *__restrict__ p, const Grid &g,
+                                      int64_t row, int d2, bool valid)
+{
+    const double part = valid ? stencil_part(vals, p, g, row, d2) : 0.0;
+    const double p1 = __shfl_down_sync(0xffffffffu, part, 1);
+    const double p2 = __shfl_down_sync(0xffffffffu, part, 2);
+    return (part + p1) + p2;
+}
+
+// Warp-strided loop over groups of ten rows: row, d2 and valid (the lane
+// has a row and the row exists) for each lane; the loop bounds are uniform
+// over the warp, so the shuffles see every lane.
+#define ROW3_LOOP(nrow_expr, BODY)                                                                       \
+    {                                                                                                    \
+        const int64_t nrow_ = (nrow_expr);                                                               \
+        const int lane_ = threadIdx.x & 31, r_ = lane_ / 3, d2 = lane_ - 3 * r_;                        \
+        const int64_t w0_ = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                     \
+        const int64_t nw_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                                      \
+        for (int64_t base_ = w0_ * 10; base_ < nrow_; base_ += nw_ * 10) {                               \
+            const int64_t row = base_ + r_;                                                              \
+            const bool valid = lane_ < 30 && row < nrow_;                                                \
+            BODY                                                                                         \
+        }                                                                                                \
+    }
+
+// CTAs of 128 threads (4 warps, 40 rows) for a three-lanes-per-row kernel
+unsigned row3_blocks(int64_t nrow, int64_t cap = 152 * 16)
+{
+    int64_t b = ((nrow + 9) / 10 + 3) / 4;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
 // Masks an assembled stencil level in place for stencil_row: zero
 // coefficients towards neighbours outside the grid and towards essential
 // dofs, identity rows on essential dofs.  The Galerkin products and the dense
@@ -456,14 +523,14 @@ __global__ void k_cg_spmv_pq(Dev d, const double *__restrict__ vals, const doubl
                              double *__restrict__ q, Grid g)
 {
     if (d.flag[F_CDONE]) return;
-    const int64_t Nn = g.Nn, nrow = 3 * Nn;
     double v[1] = {0.0}, tot[1];
-    GRID_STRIDE(row, nrow)
-    {
-        const double y = stencil_row(vals, p, g, row);
-        q[row] = y;
-        v[0] += p[row] * y;
-    }
+    ROW3_LOOP(3 * g.Nn, {
+        const double y = stencil_row3(vals, p, g, row, d2, valid);
+        if (valid && d2 == 0) {
+            q[row] = y;
+            v[0] += p[row] * y;
+        }
+    })
     if (grid_sum<1>(d, v, tot)) {
         double pq = tot[0];
         if (!(pq > 0.0) || !isfinite(pq)) {
@@ -663,27 +730,27 @@ __host__ __device__ inline double h_weight(int i, int J, int Mf, int Mc)
 __global__ void k_stencil_apply(const double *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y,
                                 Grid g)
 {
-    GRID_STRIDE(row, 3 * g.Nn) y[row] = stencil_row(vals, x, g, row);
+    ROW3_LOOP(3 * g.Nn, {
+        const double v = stencil_row3(vals, x, g, row, d2, valid);
+        if (valid && d2 == 0) y[row] = v;
+    })
 }
 
 // One Chebyshev step on a stencil level fused with its operator apply:
 // d = cd d + cr Dinv (r - A e_in); e_out = e_in + d (e_in and e_out distinct)
-__device__ inline void stencil_cheb_row(const double *__restrict__ vals, const double *__restrict__ ein,
-                                        double *__restrict__ eout, double *__restrict__ dv,
-                                        const double *__restrict__ r, const double *__restrict__ dinv, double cd,
-                                        double cr, const Grid &g, int64_t row)
-{
-    const double rk = r[row] - stencil_row(vals, ein, g, row);
-    const double di = (cd != 0.0 ? cd * dv[row] : 0.0) + cr * dinv[row] * rk;
-    dv[row] = di;
-    eout[row] = ein[row] + di;
-}
-
 __global__ void k_stencil_cheb(const double *__restrict__ vals, const double *__restrict__ ein,
                                double *__restrict__ eout, double *__restrict__ dv, const double *__restrict__ r,
                                const double *__restrict__ dinv, double cd, double cr, Grid g)
 {
-    GRID_STRIDE(row, 3 * g.Nn) stencil_cheb_row(vals, ein, eout, dv, r, dinv, cd, cr, g, row);
+    ROW3_LOOP(3 * g.Nn, {
+        const double ae = stencil_row3(vals, ein, g, row, d2, valid);
+        if (valid && d2 == 0) {
+            const double rk = r[row] - ae;
+            const double di = (cd != 0.0 ? cd * dv[row] : 0.0) + cr * dinv[row] * rk;
+            dv[row] = di;
+            eout[row] = ein[row] + di;
+        }
+    })
 }
 
 // h-prolongation (natural injection of the trilinear space, Sec. 3) in one
@@ -1402,7 +1469,7 @@ int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
     double lam = 0.0;
     for (int it = 0; it < 10; ++it) {
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.e, n, P_DEN);
-        k_stencil_apply<<<blocks_for(n), 256, 0, st>>>(H.vals, H.e, H.t, H.g);
+        k_stencil_apply<<<row3_blocks(n), 128, 0, st>>>(H.vals, H.e, H.t, H.g);
         k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.d, H.r, H.t, nullptr, H.dinv, 0.0, 1.0, 1, n);
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.d, n, P_NUM);
         PA_CUDA_TRY(cudaMemcpyAsync(s->h_scal + P_NUM, s->dev.scal + P_NUM, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1647,7 +1714,7 @@ double *h_smooth(pa_solver *s, HLevel &H, double *e, bool from_zero, cudaStream_
             continue;  // taken by the producer of H.r
         } else {
             double *nxt = cur == H.e ? H.e2 : H.e;
-            k_stencil_cheb<<<blocks_for(n, 128), 128, 0, st>>>(H.vals, cur, nxt, H.d, H.r, H.dinv, cd, cr, H.g);
+            k_stencil_cheb<<<row3_blocks(n), 128, 0, st>>>(H.vals, cur, nxt, H.d, H.r, H.dinv, cd, cr, H.g);
             cur = nxt;
         }
     }
@@ -1665,7 +1732,7 @@ double *h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
     }
     HLevel &C = s->hl[k + 1];
     double *e = h_smooth(s, F, F.e, true, st);
-    k_stencil_apply<<<blocks_for(F.n, 128), 128, 0, st>>>(F.vals, e, F.t, F.g);
+    k_stencil_apply<<<row3_blocks(F.n), 128, 0, st>>>(F.vals, e, F.t, F.g);
     // restrict r - t (with the coarse level's first smoothing step unless it
     // is the dense bottom), then the coarse correction prolonged and added
     if (k + 2 < s->hl.size())
@@ -1702,9 +1769,7 @@ int coarse_iter_hmg(pa_solver *s, Level &L, cudaStream_t st)
     const double *z = h_vcycle(s, 0, st);  // reads L.cr in place
     k_pcg_beta<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cr, z, n);
     k_pcg_p<<<blocks_for(n), 256, 0, st>>>(s->dev, L.cp, z, n);
-    int64_t nb = (n + 63) / 64;
-    if (nb > kRedBlocks) nb = kRedBlocks;
-    k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
+    k_cg_spmv_pq<<<row3_blocks(n, kRedBlocks), 128, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
     k_pcg_update<<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.cx, L.cr, L.cp, L.cq, n, coarse_first_step(s));
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
@@ -1863,10 +1928,8 @@ int coarse_iter(pa_solver *s, Level &L, cudaStream_t st)
     if (use_hmg(s)) return coarse_iter_hmg(s, L, st);
     const int64_t n = L.n;
     if (L.stencil) {
-        // FP64 work per row: spread the rows over the SMs (64 threads per CTA)
-        int64_t nb = (n + 63) / 64;
-        if (nb > kRedBlocks) nb = kRedBlocks;
-        k_cg_spmv_pq<<<(unsigned)nb, 64, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
+        // FP64 work per row: three lanes per row spread it over the SMs
+        k_cg_spmv_pq<<<row3_blocks(n, kRedBlocks), 128, 0, st>>>(s->dev, L.stencil, L.cp, L.cq, L.op->g);
     } else {
         int rc = op_apply_async(L.op, L.cp, L.cq, false, st, s->dev.flag + F_CDONE);
         if (rc) return rc;
