@@ -1163,9 +1163,11 @@ __global__ void k_restrict_axis(T *out, const T *in, const T *in2, int ax, int N
 }
 
 // Grid of a reduction kernel: about 4 elements per thread, at most kRedBlocks.
+// one element per thread up to the cap: small vectors (coarse levels) spread
+// over many SMs instead of waiting on a few
 unsigned red_blocks(int64_t n)
 {
-    int64_t b = (n + 4 * kRedThreads - 1) / (4 * kRedThreads);
+    int64_t b = (n + kRedThreads - 1) / kRedThreads;
     if (b > kRedBlocks) b = kRedBlocks;
     if (b < 1) b = 1;
     return (unsigned)b;
@@ -1736,11 +1738,11 @@ double *h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
     // restrict r - t (with the coarse level's first smoothing step unless it
     // is the dense bottom), then the coarse correction prolonged and added
     if (k + 2 < s->hl.size())
-        k_hrestrict_first<<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess, h_first_step(C));
+        k_hrestrict_first<<<blocks_for(C.n, 64), 64, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess, h_first_step(C));
     else
-        k_hrestrict<double><<<blocks_for(C.n), 256, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
+        k_hrestrict<double><<<blocks_for(C.n, 64), 64, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
     const double *ec = h_vcycle(s, k + 1, st);
-    k_hprolong_add<double><<<blocks_for(F.n), 256, 0, st>>>(e, ec, F.g, C.g);
+    k_hprolong_add<double><<<blocks_for(F.n, 64), 64, 0, st>>>(e, ec, F.g, C.g);
     return h_smooth(s, F, e, false, st);
 }
 
