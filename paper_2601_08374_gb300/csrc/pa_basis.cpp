@@ -63,7 +63,7 @@ void legendre_and_derivative(int n, double t, double &P, double &dP)
 
 void gauss_legendre_01(int q, double *x, double *w)
 {
-    double b[kMaxQ + 8], t[kMaxQ + 8];
+    double b[kMaxQ + 8] = {}, t[kMaxQ + 8] = {};
     for (int k = 1; k < q; ++k) b[k - 1] = k / std::sqrt(4.0 * k * k - 1.0);
     tridiag_eigs(q, b, t);
     for (int k = 0; k < q; ++k) {
@@ -83,7 +83,7 @@ void gll_nodes_01(int p, double *x)
     x[p] = 1.0;
     int n = p - 1;
     if (n <= 0) return;
-    double b[kMaxD + 8], t[kMaxD + 8];
+    double b[kMaxD + 8] = {}, t[kMaxD + 8] = {};
     // Jacobi(1,1) recurrence: b_k^2 = k (k + 2) / ((2k + 1)(2k + 3))
     for (int k = 1; k < n; ++k) b[k - 1] = std::sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
     tridiag_eigs(n, b, t);
