@@ -789,43 +789,55 @@ __global__ void k_hprolong_add(T *__restrict__ ef, const T *__restrict__ ec, Gri
     GRID_STRIDE(o, 3 * gf.Nn) ef[o] = ef[o] + hprolong_val(ec, gf, gc, o);
 }
 
-// h-restriction in one pass: out = R (in - in2) (in2 may be null), each
-// coarse dof gathering its fine children (at most 3 per axis) with the
-// transposed weights; essential coarse dofs are zeroed.
+// h-restriction out = R (in - in2) (in2 may be null): each coarse dof
+// gathers its fine children (at most 3 per axis) with the transposed
+// weights, summed x inside y inside z.  One z-plane (iz = pz - 1 + k): the
+// plane's weight (0 when the plane is outside the grid or has no weight)
+// and its y/x sum.
 template <typename T>
-__device__ inline T hrestrict_val(const T *__restrict__ in, const T *__restrict__ in2, const Grid &gf, const Grid &gc,
-                                  int64_t o)
+__device__ inline T hrestrict_plane(const T *__restrict__ in, const T *__restrict__ in2, const Grid &gf,
+                                    const Grid &gc, int64_t o, int k, T &wz)
 {
     const int64_t Nnf = gf.Nn, Nnc = gc.Nn;
-    {
-        const int c = (int)(o / Nnc);
-        const int64_t I = o - c * Nnc;
-        const int Jx = (int)(I % gc.Mx), Jy = (int)((I / gc.Mx) % gc.My), Jz = (int)(I / ((int64_t)gc.Mx * gc.My));
-        const int px = h_pos(Jx, gf.Mx, gc.Mx), py = h_pos(Jy, gf.My, gc.My), pz = h_pos(Jz, gf.Mz, gc.Mz);
-        T sz = 0;
-        for (int iz = pz - 1; iz <= pz + 1; ++iz) {
-            if (iz < 0 || iz >= gf.Mz) continue;
-            const T wz = (T)h_weight(iz, Jz, gf.Mz, gc.Mz);
-            if (wz == (T)0) continue;
-            T sy = 0;
-            for (int iy = py - 1; iy <= py + 1; ++iy) {
-                if (iy < 0 || iy >= gf.My) continue;
-                const T wy = (T)h_weight(iy, Jy, gf.My, gc.My);
-                if (wy == (T)0) continue;
-                const int64_t base = c * Nnf + (int64_t)gf.Mx * (iy + (int64_t)gf.My * iz);
-                T sx = 0;
-                for (int ix = px - 1; ix <= px + 1; ++ix) {
-                    if (ix < 0 || ix >= gf.Mx) continue;
-                    const T wx = (T)h_weight(ix, Jx, gf.Mx, gc.Mx);
-                    if (wx == (T)0) continue;
-                    sx += wx * (in2 ? in[base + ix] - in2[base + ix] : in[base + ix]);
-                }
-                sy += wy * sx;
-            }
-            sz += wz * sy;
+    const int c = (int)(o / Nnc);
+    const int64_t I = o - c * Nnc;
+    const int Jx = (int)(I % gc.Mx), Jy = (int)((I / gc.Mx) % gc.My), Jz = (int)(I / ((int64_t)gc.Mx * gc.My));
+    const int px = h_pos(Jx, gf.Mx, gc.Mx), py = h_pos(Jy, gf.My, gc.My), iz = h_pos(Jz, gf.Mz, gc.Mz) - 1 + k;
+    wz = (iz < 0 || iz >= gf.Mz) ? (T)0 : (T)h_weight(iz, Jz, gf.Mz, gc.Mz);
+    T sy = 0;
+    if (wz == (T)0) return sy;
+    for (int iy = py - 1; iy <= py + 1; ++iy) {
+        if (iy < 0 || iy >= gf.My) continue;
+        const T wy = (T)h_weight(iy, Jy, gf.My, gc.My);
+        if (wy == (T)0) continue;
+        const int64_t base = c * Nnf + (int64_t)gf.Mx * (iy + (int64_t)gf.My * iz);
+        T sx = 0;
+        for (int ix = px - 1; ix <= px + 1; ++ix) {
+            if (ix < 0 || ix >= gf.Mx) continue;
+            const T wx = (T)h_weight(ix, Jx, gf.Mx, gc.Mx);
+            if (wx == (T)0) continue;
+            sx += wx * (in2 ? in[base + ix] - in2[base + ix] : in[base + ix]);
         }
-        return sz;
+        sy += wy * sx;
     }
+    return sy;
+}
+
+// The three z-planes on three lanes (ROW3_LOOP's lane layout); the row's
+// first lane adds them in plane order.  All 32 lanes must call it together.
+template <typename T>
+__device__ inline T hrestrict_val3(const T *__restrict__ in, const T *__restrict__ in2, const Grid &gf, const Grid &gc,
+                                   int64_t o, int k, bool valid)
+{
+    T wz = 0;
+    const T sy = valid ? hrestrict_plane(in, in2, gf, gc, o, k, wz) : (T)0;
+    const T w1 = __shfl_down_sync(0xffffffffu, wz, 1), s1 = __shfl_down_sync(0xffffffffu, sy, 1);
+    const T w2 = __shfl_down_sync(0xffffffffu, wz, 2), s2 = __shfl_down_sync(0xffffffffu, sy, 2);
+    T sz = 0;
+    if (wz != (T)0) sz += wz * sy;
+    if (w1 != (T)0) sz += w1 * s1;
+    if (w2 != (T)0) sz += w2 * s2;
+    return sz;
 }
 
 // First Chebyshev step from a zero iterate of an h-level, taken by the
@@ -846,11 +858,15 @@ __device__ inline void first_step(const FirstStep &f, int64_t i, double r)
     }
 }
 
+// (three lanes per coarse dof, row3_blocks CTAs of 128 threads)
 template <typename T>
 __global__ void k_hrestrict(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ in2, Grid gf, Grid gc,
                             const uint8_t *__restrict__ ess)
 {
-    GRID_STRIDE(o, 3 * gc.Nn) out[o] = (ess && ess[o]) ? (T)0 : hrestrict_val(in, in2, gf, gc, o);
+    ROW3_LOOP(3 * gc.Nn, {
+        const T v = hrestrict_val3(in, in2, gf, gc, row, d2, valid);
+        if (valid && d2 == 0) out[row] = (ess && ess[row]) ? (T)0 : v;
+    })
 }
 
 // The same restriction followed by the coarse level's first Chebyshev step
@@ -859,12 +875,14 @@ __global__ void k_hrestrict_first(double *__restrict__ out, const double *__rest
                                   const double *__restrict__ in2, Grid gf, Grid gc, const uint8_t *__restrict__ ess,
                                   FirstStep f)
 {
-    GRID_STRIDE(o, 3 * gc.Nn)
-    {
-        const double v = (ess && ess[o]) ? 0.0 : hrestrict_val(in, in2, gf, gc, o);
-        out[o] = v;
-        first_step(f, o, v);
-    }
+    ROW3_LOOP(3 * gc.Nn, {
+        const double r3 = hrestrict_val3(in, in2, gf, gc, row, d2, valid);
+        if (valid && d2 == 0) {
+            const double v = (ess && ess[row]) ? 0.0 : r3;
+            out[row] = v;
+            first_step(f, row, v);
+        }
+    })
 }
 
 // Galerkin coarse stencil: one thread per coarse row (c, I); essential fine
@@ -1738,9 +1756,9 @@ double *h_vcycle(pa_solver *s, size_t k, cudaStream_t st)
     // restrict r - t (with the coarse level's first smoothing step unless it
     // is the dense bottom), then the coarse correction prolonged and added
     if (k + 2 < s->hl.size())
-        k_hrestrict_first<<<blocks_for(C.n, 64), 64, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess, h_first_step(C));
+        k_hrestrict_first<<<row3_blocks(C.n), 128, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess, h_first_step(C));
     else
-        k_hrestrict<double><<<blocks_for(C.n, 64), 64, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
+        k_hrestrict<double><<<row3_blocks(C.n), 128, 0, st>>>(C.r, F.r, F.t, F.g, C.g, C.ess);
     const double *ec = h_vcycle(s, k + 1, st);
     k_hprolong_add<double><<<blocks_for(F.n, 64), 64, 0, st>>>(e, ec, F.g, C.g);
     return h_smooth(s, F, e, false, st);
@@ -1870,7 +1888,7 @@ template <typename T>
 void restrict_to(Level &F, Level &C, const T *r, const T *t, T *out, cudaStream_t st)
 {
     if (F.hdown) {
-        k_hrestrict<T><<<blocks_for(3 * C.op->g.Nn), 256, 0, st>>>(out, r, t, F.op->g, C.op->g, C.op->d_ess);
+        k_hrestrict<T><<<row3_blocks(3 * C.op->g.Nn), 128, 0, st>>>(out, r, t, F.op->g, C.op->g, C.op->d_ess);
         return;
     }
     const Grid &g = F.op->g;
@@ -2748,7 +2766,7 @@ int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, dou
     if (!rf || !rc_out) return set_error(PA_EINVAL, "pa_op_restrict: null vector");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (h_pair(coarse, fine)) {
-        k_hrestrict<double><<<blocks_for(coarse->ndofs()), 256, 0, st>>>(rc_out, rf, nullptr, fine->g, coarse->g, nullptr);
+        k_hrestrict<double><<<row3_blocks(coarse->ndofs()), 128, 0, st>>>(rc_out, rf, nullptr, fine->g, coarse->g, nullptr);
         PA_CUDA_TRY(cudaGetLastError());
         return PA_OK;
     }
