@@ -208,7 +208,10 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
  * floor(128 / (p+2)^2) elements per CTA); elements per CTA; threads per CTA
  * (32..512, multiple of 32; variants 1-3 at most 256; in FP64 variants 1
  * and 2 only for p <= 4).
- * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB. */
+ * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB.
+ * pa_op_setup starts from a per-degree default shape; on a mesh with fewer
+ * than 2 x 152 x (its elements per CTA) elements the elements per CTA drop
+ * to max(1, n_e / 304), so that every SM gets two CTAs where it can. */
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);
 

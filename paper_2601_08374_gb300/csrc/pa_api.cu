@@ -311,6 +311,15 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
     fill_tables(op->basis, op->tab64);
     fill_tables(op->basis, op->tab32);
     op->launch = default_apply_launch(p, precision);
+    {
+        // a mesh too small to give every SM two CTAs of the default shape
+        // gets fewer elements per CTA (the default shapes come from meshes
+        // of ~3M dofs; a solver's coarse p-levels and small requests are
+        // far smaller)
+        const int64_t two_per_sm = 2 * 152;
+        if (g.ne < two_per_sm * op->launch.epb)
+            op->launch.epb = (int)std::max<int64_t>(1, g.ne / two_per_sm);
+    }
 
     const int D = p + 1;
     const size_t D3 = (size_t)D * D * D;
