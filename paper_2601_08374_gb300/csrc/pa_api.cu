@@ -151,7 +151,12 @@ int apply_batch_group(pa_op *const *ops, const void *const *xs, void *const *ys,
     for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxBatch) {
         const size_t m = std::min(idx.size() - c0, (size_t)kMaxBatch);
         pa_op *first = ops[idx[c0]];
-        const ApplyLaunch cfg = first->launch;
+        ApplyLaunch cfg = first->launch;
+        // a shape fitted to one small mesh (fewer elements per CTA than the
+        // default) is undone: the batch as a whole has the elements to fill
+        // the SMs
+        const ApplyLaunch dflt = default_apply_launch(first->p, first->precision);
+        if (cfg.variant == dflt.variant && cfg.threads == dflt.threads && cfg.epb < dflt.epb) cfg = dflt;
         BatchArgs<T> b{};
         AssembleBatch<T> ab{};
         b.count = ab.count = (int)m;
