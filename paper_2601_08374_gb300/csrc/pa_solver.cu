@@ -1,8 +1,11 @@
-// GMG-preconditioned CG solver on the p-hierarchy (Sec. 3): V(1,1) cycle with
-// Chebyshev-Jacobi smoothing on every level but the coarsest (Sec. 3.1),
-// interpolation prolongation and its exact transpose as restriction between
-// GLL spaces (Sec. 3), an FP64 Jacobi-preconditioned CG coarse solve
-// (Sec. 3.2, with CG in place of AMG), and an outer flexible CG.
+// GMG-preconditioned CG solver (Sec. 3): p-levels on the fine mesh, then
+// optional h-levels at p = 1 on uniformly coarsened meshes; V(1,1) cycle
+// with Chebyshev-Jacobi smoothing on every level but the coarsest (Sec. 3.1),
+// interpolation prolongation and its exact transpose as restriction (GLL
+// spaces between p-levels, natural injection between h-levels, Sec. 3); on
+// the coarsest level an assembled 27-point stencil solved inexactly by FP64
+// CG preconditioned by a geometric multigrid of Galerkin stencils (Sec. 3.2,
+// in place of AMG; Jacobi-CG selectable); an outer flexible CG.
 //
 // All vectors and scalars stay on the device.  Dot products are
 // deterministic two-level reductions (fixed block partition, last block sums
