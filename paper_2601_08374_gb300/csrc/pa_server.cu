@@ -11,9 +11,12 @@
 // (continuous batching).  Other requests are solved by their worker on the
 // solver's own stream, overlapping with everything else.  When a request
 // finishes its memory is released and the next queued requests are
-// admitted.  Every solve is deterministic (fixed-order reductions, no
-// atomics in the arithmetic, batched applies with the arithmetic of single
-// ones), so a request gives the same bits alone or in any mix.
+// admitted.  A request's hierarchy is its p-levels (halving to 1) and,
+// where its box mesh is a uniform refinement, h-levels below them
+// (PA_SERVER_OPT_H_LEVELS).  Every solve is deterministic (fixed-order
+// reductions, no atomics in the arithmetic, batched applies with the
+// arithmetic of single ones), so a request gives the same bits alone or in
+// any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
