@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -104,10 +105,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, out_dir: str = ""):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples: a directory given on the command line, else a
+        # temporary file (the JSON line carries their summary either way)
+        d = out_dir or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_rank{device_index}.csv")
 
     def __enter__(self):
         try:
@@ -225,7 +229,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(torch.cuda.current_device(), args.clocks_dir) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             step()
@@ -786,6 +790,8 @@ def main(argv=None):
     ap.add_argument("--no-solve", action="store_true", help="skip the GMG-PCG solve measurements")
     ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")
     ap.add_argument("--solve-reps", type=int, default=4)
+    ap.add_argument("--clocks-dir", default="", help="directory for the raw nvidia-smi clock samples "
+                    "(default: a temporary directory)")
     ap.add_argument("--solve-cases", default="", help="comma list of solve-case keys to run (default: all): "
                     "beam, beam2mat, beamh, beam_c1, beam64, beam64h, cube6, cube8, cube6_c1")
     ap.add_argument("--solve-modes", default="", help="comma list of fp64, mixed_ir, mixed_fcg (default: each case's)")
