@@ -566,6 +566,26 @@ def test_isotropic_voigt_tensor_is_the_lame_operator():
     assert np.max(np.abs(y1 - y2)) <= 1e-13 * np.max(np.abs(y1))
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_anisotropic_diagonal_is_the_dense_matrix_diagonal(p):
+    """The anisotropic diagonal (closed form from 1D sums, per element
+    tensor) equals the diagonal of the matrix assembled densely from the
+    element matrices, constrained rows giving 1; with a Lame tensor it is
+    the isotropic diagonal."""
+    nx, ny, nz = 2, 1, 2
+    m = syn.random_affine_cube(nx, seed=30 + p, ny=ny, nz=nz)
+    ct = np.stack([oracle.voigt_to_tensor(_spd_voigt(200 + e)) for e in range(m.ne)])
+    ess = syn.clamp_mask(m, p)
+    d = oracle.diag(p, nx, ny, nz, m.affine, 0.0, 0.0, ess=ess, ctens=ct)
+    A = oracle.constrain_dense(oracle.assemble_dense(p, nx, ny, nz, m.affine, 0.0, 0.0, ctens=ct), ess)
+    assert np.max(np.abs(d - np.diag(A))) <= 1e-12 * np.max(np.abs(np.diag(A)))
+    lam, mu = 0.9, 0.6
+    ci = np.tile(oracle.voigt_to_tensor(_iso_voigt(lam, mu)), (m.ne, 1))
+    di = oracle.diag(p, nx, ny, nz, m.affine, 0.0, 0.0, ctens=ci)
+    dl = oracle.diag(p, nx, ny, nz, m.affine, lam, mu)
+    assert np.max(np.abs(di - dl)) <= 1e-13 * np.max(np.abs(dl))
+
+
 def test_anisotropic_operator_is_symmetric_and_kills_rigid_motions():
     p, n = 3, 2
     m = syn.globally_affine_mesh(n, n, n, M_GLOBAL, t=(0.3, -0.2, 0.5))
