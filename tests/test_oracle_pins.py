@@ -377,6 +377,38 @@ def test_load_partition_of_unity():
         assert abs(F[c * Nn:(c + 1) * Nn].sum() - f0[c] * vol) <= 1e-13 * abs(f0[c] * vol)
 
 
+def test_load_of_sine_modes_integrates_the_force():
+    """A body force of sine modes f_c = amp sin(k . x + phi): the summed load
+    of component c (the basis is a partition of unity) is the integral of
+    f_c over the box, Im(amp e^{i phi} prod_d (e^{i k_d} - 1) / (i k_d)) on
+    [0,1]^3, to the Gauss rule's error (q = 5 points per 0.25-wide
+    element, |k| <= 2: far below the tolerance)."""
+    p, n = 3, 4
+    aff = oracle.box_affine(n, n, n)
+    rng = np.random.default_rng(31)
+    modes = np.zeros((3, 2, 5))
+    modes[..., 0] = rng.uniform(-1, 1, (3, 2))
+    modes[..., 1:4] = rng.uniform(0.5, 2.0, (3, 2, 3)) * rng.choice([-1.0, 1.0], (3, 2, 3))
+    modes[..., 4] = rng.uniform(0, 2 * np.pi, (3, 2))
+    F = oracle.load(p, n, n, n, aff, modes=modes)
+    Nn = oracle.n_nodes(n, n, n, p)
+
+    def integral(amp, kx, ky, kz, ph):
+        prod = np.exp(1j * ph)
+        for k in (kx, ky, kz):
+            prod *= (np.exp(1j * k) - 1.0) / (1j * k)
+        return amp * prod.imag
+
+    for c in range(3):
+        exact = sum(integral(*md) for md in modes[c])
+        total = F[c * Nn:(c + 1) * Nn].sum()
+        assert abs(total - exact) <= 1e-9 * max(1.0, abs(exact))
+        # the check has teeth: a flipped phase or a dropped mode misses it
+        flipped = sum(integral(md[0], md[1], md[2], md[3], -md[4]) for md in modes[c])
+        assert abs(total - flipped) > 1e-2
+        assert abs(total - integral(*modes[c][0])) > 1e-2
+
+
 @pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (4, 8), (1, 3)])
 def test_transfer_adjoint_and_polynomial_exactness(pc, pf):
     n = 2
