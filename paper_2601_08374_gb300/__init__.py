@@ -477,8 +477,19 @@ class Operator:
             pa_op_destroy(self.h)
             self.h = None
 
-    def __del__(self):
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
         self.close()
+        return False
+
+    def __del__(self):
+        # at interpreter exit the module's globals may already be gone
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def empty(self):
         import torch
