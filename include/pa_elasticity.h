@@ -104,8 +104,8 @@ int pa_op_info(const pa_op *op, int64_t *ndofs, int64_t *nelem, int *p, int *pre
  * precision; they must not alias.  y is overwritten. */
 int pa_op_apply(pa_op *op, const void *x, void *y, void *stream);
 
-/* y += A x (the accumulating form of the apply, MFEM's AddMult): the same
- * computation as pa_op_apply with each node sum added to y instead of
+/* y += A x (the accumulating form of the apply, MFEM's AddMult; Sec.
+ * 4.2-4.5 as pa_op_apply): the same computation as pa_op_apply with each node sum added to y instead of
  * stored; on essential dofs y += x (the constrained operator's identity
  * rows).  Same argument rules as pa_op_apply. */
 int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream);
@@ -119,7 +119,8 @@ int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream);
  * appear only once; x_k and y_k must not alias. */
 int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream);
 
-/* Same computation with host buffers: copies x to the device, applies, and
+/* Same computation with host buffers (no counterpart in the paper, whose
+ * operator works in host memory): copies x to the device, applies, and
  * copies y back, all on `stream`; returns after y is on the host.  Host
  * buffers should be pinned for full copy bandwidth. */
 int pa_op_apply_host(pa_op *op, const void *x_host, void *y_host, void *stream);
@@ -360,18 +361,22 @@ enum pa_solver_option {
 };
 int pa_solver_set_option(pa_solver *s, int option, double value);
 
-/* Solve A x = b (x: in = initial guess, out = solution; device double
- * L-vectors).  FP64 mode: flexible CG stops when its recursively updated
- * residual satisfies ||r||_2 <= rtol ||b||_2.  Mixed mode: iterative
- * refinement stops when the FP64 residual b - A x satisfies the same test,
- * or when a refinement step no longer halves it (the FP64 rounding floor,
- * of order eps ||A|| ||x|| / ||b||, which for stiff bending problems can lie
- * above 1e-10).  info->rel_residual is always the true FP64 residual
+/* Solve A x = b with the GMG-preconditioned CG of Sec. 3 (x: in = initial
+ * guess, out = solution; device double L-vectors).  PA_SOLVE_FP64 and
+ * PA_SOLVE_MIXED_FCG: the flexible CG stops when its recursively updated
+ * residual satisfies ||r||_2 <= rtol ||b||_2 (the paper tests the
+ * preconditioned norm; the relative residual is this library's reading).
+ * PA_SOLVE_MIXED: iterative refinement stops when the FP64 residual b - A x
+ * satisfies the same test, or when, within a factor 1e3 of the tolerance, a
+ * refinement step no longer halves it (the FP64 rounding floor, of order
+ * eps ||A|| ||x|| / ||b||, which for stiff bending problems can lie above
+ * 1e-10).  info->rel_residual is always the true FP64 residual
  * ||b - A x|| / ||b|| recomputed at exit.  maxit caps the outer CG
- * iterations (FP64) or the total inner iterations (mixed).  Waits for
- * `stream`, runs on the solver's own stream and returns when x is written;
- * returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every case when
- * non-NULL), PA_EINVAL for a non-finite b. */
+ * iterations (flexible-CG modes) or the total inner iterations (mixed).
+ * Waits for `stream`, runs on the solver's own stream and returns when x is
+ * written; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every
+ * case when non-NULL), PA_ETIMEOUT if a persistent coarse kernel's bounded
+ * barrier gave up, PA_EINVAL for a non-finite b. */
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream);
 
