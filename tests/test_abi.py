@@ -63,6 +63,25 @@ def test_host_only_entry_points(pa):
     pa.pa_mesh_destroy(h)
 
 
+def test_argument_checks_before_any_device_call(pa):
+    """Null handles, negative counts and bad level lists are refused with
+    PA_EINVAL and a message before any CUDA call (so without a GPU)."""
+    import ctypes
+    lib = pa.lib
+    assert lib.pa_op_apply_add(None, None, None, None) == pa.PA_EINVAL
+    assert lib.pa_op_apply_host_batch(None, None, None, -1, None) == pa.PA_EINVAL
+    assert lib.pa_op_apply_host_batch(None, None, None, 0, None) == pa.PA_OK
+    assert lib.pa_gmg_pcg_solve_batch(None, None, None, -1, 1e-10, 10, None, None) == pa.PA_EINVAL
+    assert lib.pa_op_prolong(None, None, None, None, None) == pa.PA_EINVAL
+    assert lib.pa_op_restrict(None, None, None, None, None) == pa.PA_EINVAL
+    out = ctypes.c_void_p()
+    lv = (ctypes.c_int * 3)(4, 2, 1)
+    assert lib.pa_solver_create_hp(None, 3, lv, 1, 2, 1e-2, 10, 0, ctypes.byref(out)) == pa.PA_EINVAL
+    assert not out.value
+    assert lib.pa_solver_create_hp(None, 3, lv, 1, 2, 1e-2, 10, 0, None) == pa.PA_EINVAL
+    assert b"null" in lib.pa_last_error()
+
+
 def test_flop_model_reproduces_table6():
     """bench.flops_per_element against the per-element counts printed in
     Table 6 of the paper (tests/golden/table6_flops.txt)."""
