@@ -297,6 +297,11 @@ typedef struct pa_solve_info {
     double lambda_max[8];  /* per level: power-iteration estimate of max eig(D^-1 A) */
     int coarse_iterations; /* coarse-level CG iterations summed over all V-cycles
                               (counted with graphs on, the default; 0 otherwise) */
+    int tolerance_met;     /* 1 when the true residual rel_residual <= rtol, else 0.
+                              PA_OK means the solver's own stopping test passed
+                              (see pa_gmg_pcg_solve); near the FP64 rounding floor
+                              that test can pass while the true residual is above
+                              rtol, and this flag tells the two apart */
 } pa_solve_info;
 
 /* PA_SOLVE_FP64: everything in FP64.
@@ -371,7 +376,8 @@ int pa_solver_set_option(pa_solver *s, int option, double value);
  * refinement step no longer halves it (the FP64 rounding floor, of order
  * eps ||A|| ||x|| / ||b||, which for stiff bending problems can lie above
  * 1e-10).  info->rel_residual is always the true FP64 residual
- * ||b - A x|| / ||b|| recomputed at exit.  maxit caps the outer CG
+ * ||b - A x|| / ||b|| recomputed at exit, and info->tolerance_met says
+ * whether that true residual is within rtol (PA_OK alone does not).  maxit caps the outer CG
  * iterations (flexible-CG modes) or the total inner iterations (mixed).
  * Waits for `stream`, runs on the solver's own stream and returns when x is
  * written; returns PA_OK, PA_ENOTCONV or PA_EBREAKDOWN (info filled in every

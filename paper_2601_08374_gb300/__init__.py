@@ -35,7 +35,8 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 class pa_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("b_norm", ctypes.c_double), ("inner_iterations", ctypes.c_int), ("refinements", ctypes.c_int),
-                ("lambda_max", ctypes.c_double * 8), ("coarse_iterations", ctypes.c_int)]
+                ("lambda_max", ctypes.c_double * 8), ("coarse_iterations", ctypes.c_int),
+                ("tolerance_met", ctypes.c_int)]
 
 
 PA_REQUEST_MAX_MODES = 16
@@ -262,8 +263,44 @@ def pa_op_restrict(coarse, fine, rf, rc, stream=None):
     _check(lib.pa_op_restrict(coarse, fine, _tptr(rf), _tptr(rc), _stream_ptr(stream)), "pa_op_restrict")
 
 
+def _noalloc_arg(name, t, dtype, numel, shape=None):
+    """Checks one tensor argument of pa_apply_noalloc (the C side has no
+    handle to compare sizes against, so a wrong tensor would be read or
+    written out of bounds on the device)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"pa_apply_noalloc: {name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"pa_apply_noalloc: {name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != shape:
+        raise ValueError(f"pa_apply_noalloc: {name} must have shape {shape}, got {tuple(t.shape)}")
+    if t.numel() != numel:
+        raise ValueError(f"pa_apply_noalloc: {name} must have {numel} entries, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"pa_apply_noalloc: {name} must be contiguous")
+
+
 def pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, affine, x, y, ess_mask=None, stream=None):
-    """Allocation-free apply; affine, x, y (and ess_mask) are CUDA tensors."""
+    """Allocation-free apply; affine [nx*ny*nz, 12] float64, x, y (L-vectors
+    of ``precision``) and ess_mask (uint8, one entry per dof) are contiguous
+    CUDA tensors.  Raises ValueError for a tensor of the wrong dtype, shape,
+    layout or device before calling the library."""
+    import torch
+    if precision not in (PA_FP64, PA_FP32):
+        raise ValueError("pa_apply_noalloc: precision must be PA_FP64 or PA_FP32")
+    if min(nx, ny, nz) < 1 or not 1 <= p <= 8:
+        raise ValueError("pa_apply_noalloc: need nx, ny, nz >= 1 and 1 <= p <= 8")
+    ne = nx * ny * nz
+    ndofs = 3 * (nx * p + 1) * (ny * p + 1) * (nz * p + 1)
+    vt = torch.float64 if precision == PA_FP64 else torch.float32
+    _noalloc_arg("affine", affine, torch.float64, 12 * ne, (ne, 12))
+    _noalloc_arg("x", x, vt, ndofs)
+    _noalloc_arg("y", y, vt, ndofs)
+    if ess_mask is not None:
+        _noalloc_arg("ess_mask", ess_mask, torch.uint8, ndofs)
+    for name, t in (("affine", affine), ("x", x), ("y", y), ("ess_mask", ess_mask)):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"pa_apply_noalloc: {name} must be on a CUDA device")
     _check(lib.pa_apply_noalloc(nx, ny, nz, p, lam, mu, precision, _tptr(affine),
                                 _tptr(ess_mask) if ess_mask is not None else None, _tptr(x), _tptr(y),
                                 _stream_ptr(stream)), "pa_apply_noalloc")

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <climits>
 #include <new>
 #include <string>
 #include <utility>
@@ -188,6 +189,34 @@ int apply_batch_group(pa_op *const *ops, const void *const *xs, void *const *ys,
     }
     return PA_OK;
 }
+
+int make_grid(int nx, int ny, int nz, int p, Grid &g, const char *who)
+{
+    const std::string w(who);
+    if (nx < 1 || ny < 1 || nz < 1) return set_error(PA_EINVAL, w + ": dimensions must be >= 1");
+    if (p < 1 || p > kMaxP) return set_error(PA_EINVAL, w + ": p must be in 1..8");
+    // every factor is below 2^31, so each product below is formed only when
+    // it cannot leave int64
+    const int64_t kMaxElems = (int64_t)1 << 31, kMaxNodes = (int64_t)1 << 36;
+    const int64_t nxy = (int64_t)nx * ny;
+    if (nxy > kMaxElems || nz > kMaxElems / nxy) return set_error(PA_EINVAL, w + ": too many elements (more than 2^31)");
+    const int64_t ne = nxy * nz;
+    const int64_t mx = (int64_t)nx * p + 1, my = (int64_t)ny * p + 1, mz = (int64_t)nz * p + 1;
+    if (mx > INT32_MAX || my > INT32_MAX || mz > INT32_MAX)
+        return set_error(PA_EINVAL, w + ": nodes per direction (n p + 1) exceed 2^31 - 1");
+    const int64_t mxy = mx * my;
+    if (mxy > kMaxNodes || mz > kMaxNodes / mxy) return set_error(PA_EINVAL, w + ": too many nodes (more than 2^36)");
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.p = p;
+    g.Mx = (int)mx;
+    g.My = (int)my;
+    g.Mz = (int)mz;
+    g.ne = ne;
+    g.Nn = mx * my * mz;
+    return PA_OK;
+}
 }  // namespace pa
 
 using namespace pa;
@@ -206,6 +235,7 @@ int pa_lame(double E, double nu, double *lambda, double *mu)
     *mu = E / (2.0 * (1.0 + nu));
     return PA_OK;
 }
+
 
 int pa_mesh_create(int nx, int ny, int nz, const double *box, const double *affine, pa_mesh **out)
 {
@@ -303,15 +333,10 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
     op->mu = mu;
     op->elem = precision == PA_FP64 ? 8 : 4;
     Grid &g = op->g;
-    g.nx = mesh->nx;
-    g.ny = mesh->ny;
-    g.nz = mesh->nz;
-    g.p = p;
-    g.Mx = mesh->nx * p + 1;
-    g.My = mesh->ny * p + 1;
-    g.Mz = mesh->nz * p + 1;
-    g.ne = (int64_t)mesh->nx * mesh->ny * mesh->nz;
-    g.Nn = (int64_t)g.Mx * g.My * g.Mz;
+    if (int rc = make_grid(mesh->nx, mesh->ny, mesh->nz, p, g, "pa_op_setup")) {
+        delete op;
+        return rc;
+    }
     op->basis.build(p, q);
     fill_tables(op->basis, op->tab64);
     fill_tables(op->basis, op->tab32);

@@ -65,6 +65,13 @@ struct Grid {
     int64_t ne, Nn;
 };
 
+// Fills g for an nx*ny*nz mesh of degree p after checking every size the
+// kernels index with: dimensions >= 1, at most 2^31 elements, node counts
+// per direction (n p + 1) that fit an int, and at most 2^36 nodes (so byte
+// counts of L-vectors, E-vectors and geometry records stay far from 64-bit
+// overflow).  PA_EINVAL with a message naming `who` otherwise.
+int make_grid(int nx, int ny, int nz, int p, Grid &g, const char *who);
+
 // --------------------------------------------------------- apply launch --
 constexpr int kMaxVariant = 4;
 struct ApplyLaunch {

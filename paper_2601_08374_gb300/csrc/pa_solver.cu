@@ -2304,6 +2304,7 @@ int solve_begin(pa_solver *s, const double *b, double *x, double *bb_out, pa_sol
         PA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
         PA_CUDA_TRY(cudaStreamSynchronize(st));
         inf->rel_residual = 0.0;
+        inf->tolerance_met = 1;
         *trivial = true;
         return PA_OK;
     }
@@ -2316,7 +2317,7 @@ int solve_begin(pa_solver *s, const double *b, double *x, double *bb_out, pa_sol
 // End of a solve: the true FP64 residual of the solver's iterate, which is
 // copied to x.  rc_loop is the iteration loop's return code (breakdown is
 // reported as a status with the residual; other errors are returned as is).
-int solve_finish(pa_solver *s, double *x, int rc_loop, bool converged, double bb, pa_solve_info *inf)
+int solve_finish(pa_solver *s, double *x, int rc_loop, bool converged, double bb, double tol2, pa_solve_info *inf)
 {
     cudaStream_t st = s->stream;
     Level &L0 = s->lv[0];
@@ -2332,6 +2333,7 @@ int solve_finish(pa_solver *s, double *x, int rc_loop, bool converged, double bb
     const double rr = read_scalar(s, S_RR, st);
     PA_CUDA_TRY(cudaGetLastError());
     inf->rel_residual = std::sqrt(rr / bb);
+    inf->tolerance_met = rr <= tol2 * bb ? 1 : 0;
     inf->coarse_iterations = (int)std::min<int64_t>(s->coarse_its, 0x7fffffff);
     if (status == PA_OK && !converged) status = PA_ENOTCONV;
     inf->status = status;
@@ -2517,7 +2519,7 @@ void retire(Lockstep &L, LockMember &m, int rc_loop, bool converged)
     LockstepDone d;
     d.tag = m.tag;
     m.info.iterations = m.it;
-    int st = solve_finish(m.s, m.x_out, rc_loop, converged, m.bb, &m.info);
+    int st = solve_finish(m.s, m.x_out, rc_loop, converged, m.bb, m.tol2, &m.info);
     d.status = st;
     if (st != PA_OK) d.error = pa_last_error();
     d.info = m.info;
@@ -3097,7 +3099,7 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
         inf.inner_iterations = total_inner;
         inf.refinements = refine;
     }
-    const int status = solve_finish(s, x, rc, converged, bb, &inf);
+    const int status = solve_finish(s, x, rc, converged, bb, tol2, &inf);
     if (info) *info = inf;
     return status;
 }

@@ -142,26 +142,33 @@ size_t noalloc_scratch_bytes(int p, int64_t ne, size_t elem)
 
 using namespace pa;
 
+namespace {
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t pa_ = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+    return pa_ < pb + nb && pb < pa_ + na;
+}
+}  // namespace
+
 extern "C" int pa_apply_noalloc(int nx, int ny, int nz, int p, double lambda, double mu, int precision,
                                 const double *affine, const uint8_t *ess_mask, const void *x, void *y, void *stream)
 {
-    if (nx < 1 || ny < 1 || nz < 1) return set_error(PA_EINVAL, "pa_apply_noalloc: dimensions must be >= 1");
-    if (p < 1 || p > kMaxP) return set_error(PA_EINVAL, "pa_apply_noalloc: p must be in 1..8");
     if (precision != PA_FP64 && precision != PA_FP32) return set_error(PA_EINVAL, "pa_apply_noalloc: bad precision");
     if (!affine || !x || !y) return set_error(PA_EINVAL, "pa_apply_noalloc: null argument");
-    if (x == y) return set_error(PA_EINVAL, "pa_apply_noalloc: x and y must not alias");
     if (!std::isfinite(lambda) || !std::isfinite(mu)) return set_error(PA_EINVAL, "pa_apply_noalloc: non-finite Lame parameters");
     Grid g;
-    g.nx = nx;
-    g.ny = ny;
-    g.nz = nz;
-    g.p = p;
-    g.Mx = nx * p + 1;
-    g.My = ny * p + 1;
-    g.Mz = nz * p + 1;
-    g.ne = (int64_t)nx * ny * nz;
-    g.Nn = (int64_t)g.Mx * g.My * g.Mz;
+    // the same size limits as pa_op_setup: every product below stays far
+    // inside 64 bits (at most 2^31 elements, 2^36 nodes, 729 nodes per element)
+    if (int rc = make_grid(nx, ny, nz, p, g, "pa_apply_noalloc")) return rc;
     const size_t elem = precision == PA_FP64 ? 8 : 4;
+    const size_t vec_bytes = (size_t)(3 * g.Nn) * elem;
+    if (ranges_overlap(x, vec_bytes, y, vec_bytes))
+        return set_error(PA_EINVAL, "pa_apply_noalloc: x and y overlap");
+    if (ranges_overlap(affine, (size_t)g.ne * 12 * sizeof(double), y, vec_bytes))
+        return set_error(PA_EINVAL, "pa_apply_noalloc: affine and y overlap");
+    if (ess_mask && ranges_overlap(ess_mask, (size_t)(3 * g.Nn), y, vec_bytes))
+        return set_error(PA_EINVAL, "pa_apply_noalloc: ess_mask and y overlap");
     const size_t need = noalloc_scratch_bytes(p, g.ne, elem);
     if (need > kStaticScratchBytes)
         return set_error(PA_EINVAL, "pa_apply_noalloc: mesh needs " + std::to_string(need) +

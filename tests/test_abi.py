@@ -92,3 +92,71 @@ def test_flop_model_reproduces_table6():
         p = int(p)
         assert bench.flops_per_element(p) == int(fe)
         assert round(bench.flops_per_element(p) / (3 * p ** 3)) == int(fd)
+
+
+def test_noalloc_refuses_overflowing_sizes_and_overlaps(pa):
+    """pa_apply_noalloc checks the mesh sizes with overflow-safe products and
+    refuses overlapping x / y / mask / affine ranges, all before any device
+    call (the pointers below are never dereferenced)."""
+    lib = pa.lib
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 30), ctypes.c_void_p(1 << 40)]
+    big = 1 << 21  # 2^63 elements as a product: must not wrap past the limits
+    for dims in [(big, big, big), (1 << 30, 1 << 30, 1), ((1 << 31) - 1, 1, 1), (1 << 16, 1 << 16, 2)]:
+        rc = lib.pa_apply_noalloc(*dims, 8, 1.0, 1.0, pa.PA_FP64, fake[0], None, fake[1], fake[2], None)
+        assert rc == pa.PA_EINVAL, dims
+        assert b"too many" in lib.pa_last_error() or b"exceed" in lib.pa_last_error()
+    # x and y overlapping by one entry (2 x 2 x 2 elements, p = 1: 81 dofs)
+    x = ctypes.c_void_p(1 << 20)
+    y = ctypes.c_void_p((1 << 20) + 80 * 8)
+    rc = lib.pa_apply_noalloc(2, 2, 2, 1, 1.0, 1.0, pa.PA_FP64, ctypes.c_void_p(1 << 30), None, x, y, None)
+    assert rc == pa.PA_EINVAL and b"x and y overlap" in lib.pa_last_error()
+    rc = lib.pa_apply_noalloc(2, 2, 2, 1, 1.0, 1.0, pa.PA_FP64, ctypes.c_void_p((1 << 20) + 8), None,
+                              ctypes.c_void_p(1 << 30), ctypes.c_void_p(1 << 20), None)
+    assert rc == pa.PA_EINVAL and b"affine and y overlap" in lib.pa_last_error()
+    rc = lib.pa_apply_noalloc(2, 2, 2, 1, 1.0, 1.0, pa.PA_FP64, ctypes.c_void_p(1 << 30),
+                              ctypes.c_void_p((1 << 20) + 640), ctypes.c_void_p(1 << 40), ctypes.c_void_p(1 << 20), None)
+    assert rc == pa.PA_EINVAL and b"ess_mask and y overlap" in lib.pa_last_error()
+
+
+def test_noalloc_binding_checks_tensors(pa):
+    """The Python wrapper of pa_apply_noalloc refuses tensors of the wrong
+    dtype, shape, length, layout or device with ValueError (CPU tensors
+    reach the device check last)."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, p = 2, 1, 1, 2
+    ne, nd = 2, 3 * 5 * 3 * 3
+    good = dict(affine=torch.zeros(ne, 12, dtype=torch.float64), x=torch.zeros(nd, dtype=torch.float64),
+                y=torch.zeros(nd, dtype=torch.float64), ess_mask=torch.zeros(nd, dtype=torch.uint8))
+    bad_cases = [
+        ("affine", torch.zeros(ne, 12, dtype=torch.float32), "float64"),
+        ("affine", torch.zeros(ne * 12, dtype=torch.float64), "shape"),
+        ("affine", torch.zeros(12, ne, dtype=torch.float64).t(), "contiguous"),
+        ("x", torch.zeros(nd, dtype=torch.float32), "float64"),
+        ("x", torch.zeros(nd + 1, dtype=torch.float64), "entries"),
+        ("y", torch.zeros(nd - 3, dtype=torch.float64), "entries"),
+        ("y", torch.zeros(2 * nd, dtype=torch.float64)[::2], "contiguous"),
+        ("ess_mask", torch.zeros(nd, dtype=torch.bool), "uint8"),
+        ("ess_mask", torch.zeros(nd - 1, dtype=torch.uint8), "entries"),
+        ("x", None, "CUDA"),  # every tensor right but on the CPU
+    ]
+    for name, t, word in bad_cases:
+        args = dict(good)
+        if t is not None:
+            args[name] = t
+        with pytest.raises(ValueError) as ei:
+            pa.pa_apply_noalloc(nx, ny, nz, p, 1.0, 1.0, pa.PA_FP64, args["affine"], args["x"], args["y"],
+                                ess_mask=args["ess_mask"])
+        assert word in str(ei.value), (name, word, str(ei.value))
+    with pytest.raises(ValueError):
+        pa.pa_apply_noalloc(nx, ny, nz, p, 1.0, 1.0, 7, good["affine"], good["x"], good["y"])
+
+
+def test_noalloc_rejects_meshes_beyond_the_scratch(pa):
+    """A mesh whose scratch exceeds the fixed 64 MiB array is refused with
+    PA_EINVAL and the required size, before any device call (the pointers
+    are placeholders that are never dereferenced)."""
+    lib = pa.lib
+    n = 40  # p = 8: 64000 elements x 2199 doubles each, far above 64 MiB
+    rc = lib.pa_apply_noalloc(n, n, n, 8, 1.0, 1.0, pa.PA_FP64, ctypes.c_void_p(1 << 44), None,
+                              ctypes.c_void_p(1 << 40), ctypes.c_void_p(1 << 42), None)
+    assert rc == pa.PA_EINVAL and b"64 MiB" in lib.pa_last_error()
