@@ -123,7 +123,7 @@ def test_host_batch_apply_equals_device_applies(pa):
     """Several operators (both precisions, several degrees) applied from
     pinned host buffers with the copies overlapped: the same bits as one
     device apply each; a repeated operator is refused."""
-    ops, xs, ys_dev = [], [], []
+    ops, xs, ys_dev, probs = [], [], [], []
     for k, (p, prec) in enumerate([(2, pa.PA_FP64), (4, pa.PA_FP32), (1, pa.PA_FP64), (3, pa.PA_FP32)]):
         m = syn.random_affine_cube(3 + k, seed=60 + k)
         op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, 1.0, 0.5, precision=prec)
@@ -132,12 +132,17 @@ def test_host_batch_apply_equals_device_applies(pa):
         ops.append(op)
         xs.append(x)
         ys_dev.append(op.apply(x))
+        probs.append((p, prec, m))
     torch.cuda.synchronize()
     xh = [x.cpu().pin_memory() for x in xs]
     yh = [torch.full_like(h, float("nan")).pin_memory() for h in xh]
     pa.pa_op_apply_host_batch([o.h for o in ops], xh, yh)
     for a, b in zip(yh, ys_dev):
         assert torch.equal(a, b.cpu())
+    # each member against the oracle's apply
+    for a, x, (p, prec, m) in zip(yh, xh, probs):
+        yo = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, 1.0, 0.5, x.double().numpy())
+        assert _relerr(a.double().numpy(), yo) <= TOL[prec], (p, prec)
     with pytest.raises(pa.PAError) as ei:
         pa.pa_op_apply_host_batch([ops[0].h, ops[0].h], xh[:1] * 2, yh[:1] * 2)
     assert ei.value.code == pa.PA_EINVAL
@@ -320,9 +325,10 @@ def test_assembled_p1_stencil_against_oracle_matrix(pa):
 
 def test_batched_apply_matches_individual_applies(pa):
     """One batched launch over operators of uneven sizes, degrees and
-    precisions (more than 24 in one group) equals the one-by-one applies."""
+    precisions (more than 24 in one group) equals the one-by-one applies,
+    and every member matches the oracle's apply at the operator tolerance."""
     rng = np.random.default_rng(31)
-    ops, xs, refs = [], [], []
+    ops, xs, refs, probs = [], [], [], []
     specs = [(int(rng.choice([2, 4, 8])), int(rng.integers(0, 2)), tuple(int(v) for v in rng.integers(1, 4, 3)))
              for _ in range(12)]
     specs += [(2, 0, (2, 1, 1))] * 26  # one group larger than a launch
@@ -334,11 +340,15 @@ def test_batched_apply_matches_individual_applies(pa):
         ops.append(op)
         xs.append(x)
         refs.append(op.apply(x).clone())
+        probs.append((p, prec, m, ess))
     ys = [torch.full_like(x, float("nan")) for x in xs]
     pa.pa_op_apply_batch([o.h for o in ops], xs, ys)
     torch.cuda.synchronize()
     for y, r in zip(ys, refs):
         assert torch.equal(y, r)
+    for y, x, (p, prec, m, ess) in zip(ys, xs, probs):
+        yo = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, 1.0, 0.7, x.double().cpu().numpy(), ess=ess)
+        assert _relerr(y.double().cpu().numpy(), yo) <= TOL[prec], (p, prec, m.nx, m.ny, m.nz)
     with pytest.raises(pa.PAError):
         pa.pa_op_apply_batch([ops[0].h, ops[0].h], [xs[0], xs[0]], [ys[0], ys[1]])
     for o in ops:

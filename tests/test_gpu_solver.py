@@ -189,6 +189,14 @@ def test_lockstep_batch_equals_solo_solves(pa, mode):
         assert infos[k].rel_residual == solo[k][2]
         assert torch.equal(xs[k], solo[k][3]), k
     assert infos[3].b_norm == 0.0 and torch.count_nonzero(xs[3]) == 0
+    # the batched solutions against the oracle's direct solve of each system
+    for k in (0, 1, 2):
+        m, p, _ = specs[k]
+        ess = syn.clamp_mask(m, p)
+        bo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+        xo, _ = oracle.solve_sparse(p, m.nx, m.ny, m.nz, m.affine, lam, mu, bo, ess)
+        xk = xs[k].cpu().numpy()
+        assert np.linalg.norm(xk - xo) <= 1e-8 * np.linalg.norm(xo), k
     # an iteration cap ends the solves of a batch at the same step as solo
     xs2 = [torch.zeros_like(b) for b in bs]
     code, infos2 = pa.pa_gmg_pcg_solve_batch([sols[0], sols[4]], [bs[0], bs[4]], [xs2[0], xs2[4]], 1e-10, 3)
@@ -405,6 +413,105 @@ def test_mixed_precision_cube_at_full_size(pa):
     bh, xh = b.cpu().numpy(), x64.cpu().numpy()
     N = len(bh)
     rows = np.random.default_rng(13).choice(N, 1500, replace=False)
+    r = bh[rows] - oracle.apply_rows(p, n, n, n, m.affine, lam, mu, xh, rows, ess=ess)
+    assert np.max(np.abs(r)) <= 1e-8 * np.max(np.abs(bh))
+    op.close()
+
+
+@pytest.fixture(scope="module")
+def beam_config3_oracle():
+    """The cantilever-beam system at its configured size (32 x 4 x 4
+    elements on [0,8] x [0,1]^2, p = 4, E = 1, nu = 0.3, f = (0, 0, -1),
+    x = 0 clamped; 111,843 dofs) solved by the oracle: sparse LU of its
+    assembled matrix plus one refinement step with its element-by-element
+    apply (about a minute of host time)."""
+    m = _beam(32, 4, 4)
+    p = 4
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    bo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+    xo, res = oracle.solve_sparse(p, m.nx, m.ny, m.nz, m.affine, lam, mu, bo, ess)
+    assert res <= 2e-9  # the FP64 residual floor of this system lies near 1e-9
+    return m, p, lam, mu, ess, bo, xo
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("h_levels", [0, 2])
+def test_beam_config3_solution_against_oracle_solve(pa, beam_config3_oracle, mode, h_levels):
+    """GMG-PCG on the configured beam (p = 4 -> 2 -> 1, with and without
+    two h-levels below, the paper's inexact coarse solve 1e-2 / 10) in FP64,
+    mixed iterative refinement and mixed flexible CG: the solution within
+    1e-8 relative error of the oracle's direct solve."""
+    m, p, lam, mu, ess, bo, xo = beam_config3_oracle
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+    b = torch.tensor(bo, device="cuda")
+    x = torch.zeros_like(b)
+    s = pa.pa_solver_create_hp(op.h, [4, 2, 1], h_levels, 2, 1e-2, 10, mode)
+    code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+    pa.pa_solver_destroy(s)
+    op.close()
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    xh = x.cpu().numpy()
+    err = np.linalg.norm(xh - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, (mode, h_levels, err, info.rel_residual)
+    assert info.rel_residual <= 2e-9
+    assert info.tolerance_met == (1 if info.rel_residual <= 1e-10 else 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_p8_cube_hierarchy_against_oracle_solve(pa, mode):
+    """The p = 8 hierarchy of the mixed-precision configuration (8 -> 4 ->
+    2 -> 1, nu = 0.45, random affine maps, smooth sine-mode force, x = 0
+    clamped) on a 2^3 cube the host can factor (14,739 dofs): every mode
+    within 1e-8 of the oracle's direct solve."""
+    p, n = 8, 2
+    m = syn.random_affine_cube(n, seed=3000 + p)
+    lam, mu = syn.lame(1.0, 0.45)
+    ess = syn.clamp_mask(m, p)
+    modes = syn.smooth_force_modes(seed=3100 + p)
+    bo = oracle.load(p, n, n, n, m.affine, modes=modes, ess=ess)
+    xo, res = oracle.solve_sparse(p, n, n, n, m.affine, lam, mu, bo, ess)
+    assert res <= 1e-12
+    op = pa.Operator(n, n, n, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(modes=modes)
+    assert np.max(np.abs(b.cpu().numpy() - bo)) <= 1e-12 * np.max(np.abs(bo))
+    x = torch.zeros_like(b)
+    s = pa.pa_solver_create(op.h, [8, 4, 2, 1], 2, 1e-2, 10, mode)
+    code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+    pa.pa_solver_destroy(s)
+    op.close()
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, (mode, err)
+
+
+def test_mixed_precision_cube_p8_at_full_size(pa):
+    """The p = 8 mixed-precision configuration at its full size (17^3
+    elements, 7.71M dofs, levels 8 -> 4 -> 2 -> 1, nu = 0.45): both mixed
+    forms reach the FP64 solution within 1e-8, and the FP64 solution's
+    residual with the oracle's operator on sampled rows is at the solver
+    tolerance's scale."""
+    p = 8
+    n = syn.mixed_n(p)
+    m = syn.random_affine_cube(n, seed=3000 + p)
+    lam, mu = syn.lame(1.0, 0.45)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(modes=syn.smooth_force_modes(seed=3100 + p))
+    xs = {}
+    for mode in (pa.PA_SOLVE_FP64, pa.PA_SOLVE_MIXED, pa.PA_SOLVE_MIXED_FCG):
+        s = pa.pa_solver_create(op.h, [8, 4, 2, 1], 2, 1e-2, 10, mode)
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 2000)
+        pa.pa_solver_destroy(s)
+        assert code == pa.PA_OK, (mode, pa.lib.pa_last_error())
+        assert info.rel_residual <= 2e-10
+        xs[mode] = x
+    x64 = xs[pa.PA_SOLVE_FP64]
+    for mode in (pa.PA_SOLVE_MIXED, pa.PA_SOLVE_MIXED_FCG):
+        assert float((xs[mode] - x64).norm() / x64.norm()) <= 1e-8
+    bh, xh = b.cpu().numpy(), x64.cpu().numpy()
+    rows = np.random.default_rng(17).choice(len(bh), 1500, replace=False)
     r = bh[rows] - oracle.apply_rows(p, n, n, n, m.affine, lam, mu, xh, rows, ess=ess)
     assert np.max(np.abs(r)) <= 1e-8 * np.max(np.abs(bh))
     op.close()

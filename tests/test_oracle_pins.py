@@ -655,3 +655,49 @@ def test_anisotropic_patch_test_energy(p):
     exact_energy = 6.0 * e @ Cv @ e
     energy = u @ oracle.apply(p, nx, ny, nz, aff, 0.0, 0.0, u, ctens=ct)
     assert abs(energy - exact_energy) <= 1e-12 * abs(exact_energy)
+
+
+# --------------------------------------------------------------------------
+# sparse assembly and the direct solve used to gate the GPU solves
+# --------------------------------------------------------------------------
+def test_sparse_assembly_equals_matrix_free_apply_and_dense_assembly():
+    """The scipy assembly of the element matrices applied to a vector equals
+    the element-by-element apply of oracle.c (a separate code path), and the
+    dense assembly entry by entry, with per-element material."""
+    p, (nx, ny, nz) = 3, (3, 2, 2)
+    m = syn.random_affine_cube(nx, seed=41, ny=ny, nz=nz)
+    mat = np.random.default_rng(4).uniform(0.5, 5.0, (m.ne, 2))
+    A = oracle.assemble_sparse(p, nx, ny, nz, m.affine, 0.0, 0.0, mat=mat)
+    x = syn.uniform_vector(m.n_dofs(p), seed=42)
+    y = oracle.apply(p, nx, ny, nz, m.affine, 0.0, 0.0, x, mat=mat)
+    assert np.max(np.abs(A @ x - y)) <= 1e-13 * np.max(np.abs(y))
+    Ad = oracle.assemble_dense(p, nx, ny, nz, m.affine, 0.0, 0.0, mat=mat)
+    assert np.max(np.abs(A.toarray() - Ad)) <= 1e-14 * np.max(np.abs(Ad))
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_direct_solve_recovers_a_linear_displacement(p):
+    """Closed form: on a beam clamped at x = 0, the displacement u = (a x,
+    b x, c x) has the uniform strain e_xx = a, e_xy = b/2, e_xz = c/2 and the
+    constant stress s = lambda tr(e) I + 2 mu e; its load is the traction
+    s n on the five free faces.  It lies in the finite-element space, so the
+    solve of the constrained system with that load must return its nodal
+    values (a dropped traction face, a wrong sign or a transposed stress
+    index misses them by O(1))."""
+    nx, ny, nz, hi = 4, 2, 1, (8.0, 1.0, 0.5)
+    m = syn.box_mesh(nx, ny, nz, hi=hi)
+    lam, mu = syn.lame(1.0, 0.3)
+    a, b, c = 1e-2, -2e-2, 3e-2
+    sxx, syy, szz, sxy, sxz = (lam + 2 * mu) * a, lam * a, lam * a, mu * b, mu * c
+    faces = {1: (sxx, sxy, sxz), 2: (-sxy, -syy, 0.0), 3: (sxy, syy, 0.0), 4: (-sxz, 0.0, -szz),
+             5: (sxz, 0.0, szz)}
+    ess = syn.clamp_mask(m, p)
+    F = sum(oracle.traction(p, nx, ny, nz, m.affine, f, t, ess=ess) for f, t in faces.items())
+    x, res = oracle.solve_sparse(p, nx, ny, nz, m.affine, lam, mu, F, ess)
+    X = oracle.node_coords_box(nx, ny, nz, p, hi=hi)[:, 0]
+    u = np.concatenate([a * X, b * X, c * X])
+    # residual at the FP64 floor; the nodal error grows along the clamped
+    # beam with its condition number (2e-9 relative at p = 4), far below
+    # the O(1) miss of a wrong load or operator
+    assert res <= 1e-12
+    assert np.max(np.abs(x - u)) <= 1e-8 * np.max(np.abs(u))
