@@ -38,10 +38,21 @@ import synthetic as syn  # noqa: E402
 
 METRIC = "Op GDoF/s vs p (FP64 vs FP32-refined); GMG-PCG solves/s, p50/p99 latency"
 SWEEP = (1, 2, 4, 6, 8)
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
 # FP64: 2 FMA / clk / SM (4 flop); FP32: 128 FMA / clk / SM (256 flop)
 FLOP_PER_CLK_SM = {"f64": 4.0, "f32": 256.0}
+SM_MAX_MHZ_NOMINAL = 2070.0  # used only when no clock sample was taken
+
+
+def derived_peak_tflops(dtype_name: str, sms: int, mhz: float) -> float:
+    """FMA-unit peak from unit counts and a clock: SMs x flop/clk/SM x MHz."""
+    return sms * FLOP_PER_CLK_SM[dtype_name] * mhz * 1e6 / 1e12
+
+
+def peak_clock_mhz(clocks: dict) -> float:
+    """The SM clock of the derived peak: the median sampled during the timed
+    region (nominal maximum when nvidia-smi gave no sample)."""
+    v = clocks.get("sm_mhz") if clocks else None
+    return float(v) if v else SM_MAX_MHZ_NOMINAL
 
 
 def flops_per_element(p: int) -> int:
@@ -58,6 +69,16 @@ def algorithmic_bytes(p: int, n: int, elem: int) -> int:
     return 2 * ndofs * elem + n ** 3 * 12 * elem
 
 
+def sweep_workload_name(precision: str, ps) -> str:
+    """The operator sweep's description (the same for both arms)."""
+    ns = [syn.sweep_n(p) for p in ps]
+    dofs = sum(3 * (n * p + 1) ** 3 for n, p in zip(ns, ps))
+    return (f"{precision.upper()} op_apply sweep p in {{{','.join(map(str, ps))}}}, n^3 unit cube "
+            f"(n = {', '.join(map(str, ns))}; {dofs / 1e6:.2f}M dofs per step), "
+            "per-element random affine maps (scales U[0.5,2], shear U[-0.3,0.3]), "
+            "E=1 nu=0.3, x ~ U[-1,1], unconstrained")
+
+
 def workload(p: int, scale: float = 1.0):
     n = max(1, int(round(syn.sweep_n(p) * scale)))
     mesh = syn.random_affine_cube(n, seed=1000 + p)
@@ -70,7 +91,7 @@ def kernel_source_hash() -> str:
     (the shapes the sweep runs), so stored ncu traffic goes stale with them."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_08374_gb300", "csrc")
-    for f in ("pa_apply.cuh", "pa_apply_line.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
+    for f in ("pa_apply.cuh", "pa_apply_line.cuh", "pa_apply_plane.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "pa_api.cu"), "rb") as fh:
@@ -81,14 +102,14 @@ def kernel_source_hash() -> str:
 
 
 # ncu DRAM bytes (read + write) per launch of the element kernel, keyed by
-# (precision, p): the median over the launches of the sweep's launch list
-# (profiles/pa_apply_sweep_launches.md), valid only for the kernel source
-# and launch table with this hash.  The E-vector writes mostly stay in L2
+# (precision, p): one-kernel captures of the sweep's element launches,
+# valid only for the kernel source and launch table with this hash.  The E-vector writes mostly stay in L2
 # and reach DRAM during the assembly kernel, so for p >= 4 the figure is
 # essentially the reads of x and of the geometry records.
 TRAFFIC_HASH = "9284aacec0bdd2a7"
 ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>",
-                        3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)"}
+                        3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)",
+                        5: "pa_apply_plane_kernel<SPLIT=0>", 6: "pa_apply_plane_kernel<SPLIT=1>"}
 TRAFFIC_BYTES: dict = {
     ("f64", 1): 249449344, ("f64", 2): 59693824, ("f64", 4): 26705920, ("f64", 6): 22366976, ("f64", 8): 22142208,
     ("f32", 1): 96642688, ("f32", 2): 18397696, ("f32", 4): 13158144, ("f32", 6): 11214976, ("f32", 8): 11102720,
@@ -245,6 +266,23 @@ def run_ours(args):
         c["elem_ms"], c["asm_ms"], c["napplies"] = te, ta, na
     ms = max_over_ranks(ms, ws, "cuda")
 
+    # ---- single pair: each operator applied back to back to one x / y
+    # (its vectors stay in L2 where they fit), beside the rotating figure
+    for c in cases:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        pa.pa_op_apply(c["op"].h, c["x"], c["y"], stream)
+        e0.record(stream)
+        for _ in range(reps):
+            pa.pa_op_apply(c["op"].h, c["x"], c["y"], stream)
+        e1.record(stream)
+        e1.synchronize()
+        c["single_pair_ms"] = e0.elapsed_time(e1) / reps
+
+    # ---- measured FMA rate of the CUDA cores (the ceiling beside the derived one)
+    fma_measured = pa.pa_measure_fma_rate(prec, stream)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
     # ---- end to end through the host-buffer C ABI call (pinned buffers)
     hosts = []
     for c in cases:
@@ -278,8 +316,11 @@ def run_ours(args):
 
     value = job_gdofs(ws, total_dofs, args.steps, ms * 1e-3)
     # roofline of the dominant kernel (the fused element kernel), aggregated
-    # over the sweep: algorithmic flops of all its launches / their event time
-    peak = SM_COUNT * FLOP_PER_CLK_SM[dtype_name] * SM_MAX_MHZ * 1e6 / 1e12
+    # over the sweep: algorithmic flops of all its launches / their event
+    # time, against the FMA-unit peak at the clock sampled during the run
+    clocks = clk.summary()
+    mhz = peak_clock_mhz(clocks)
+    peak = derived_peak_tflops(dtype_name, sms, mhz)
     fl_total = sum(flops_per_element(c["p"]) * c["ne"] * c["napplies"] for c in cases)
     el_ms = sum(c["elem_ms"] for c in cases)
     achieved = fl_total / (el_ms * 1e-3) / 1e12
@@ -298,6 +339,7 @@ def run_ours(args):
                          "tflops_alg": round(fl / (t_el * 1e-3) / 1e12, 4),
                          "frac_alu": round(fl / (t_el * 1e-3) / 1e12 / peak, 4),
                          "hbm_gbs_alg": round(algorithmic_bytes(c["p"], c["n"], elem) / (t_all * 1e-3) / 1e9, 1),
+                         "single_pair_gdofs": round(c["ndofs"] / (c["single_pair_ms"] * 1e-3) / 1e9, 4),
                          "launch": list(c["launch"])})
     out = {
         "metric": METRIC,
@@ -313,10 +355,7 @@ def run_ours(args):
         "dtype": dtype_name,
         "data": "synthetic",
         "config": {
-            "workload": (f"{args.precision.upper()} op_apply sweep p in {{{','.join(map(str, ps))}}}, n^3 unit cube "
-                         f"(n = {', '.join(str(c['n']) for c in cases)}; {total_dofs / 1e6:.2f}M dofs per step), "
-                         "per-element random affine maps (scales U[0.5,2], shear U[-0.3,0.3]), "
-                         "E=1 nu=0.3, x ~ U[-1,1], unconstrained"),
+            "workload": sweep_workload_name(args.precision, ps),
             "l2": ("inputs larger than L2: each step applies 5 operators in turn; one step touches "
                    f"{sum(c['ndofs'] * elem * 2 + c['ne'] * 12 * elem + c['ne'] * 3 * (c['p'] + 1) ** 3 * elem for c in cases) / 1e9:.2f} GB"),
             "parallelism": f"replicas x{ws}",
@@ -325,8 +364,11 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": " + ".join(ELEMENT_KERNEL_NAMES[v] for v in sorted({c["launch"][0] for c in cases})),
-                     "peak_source": (f"derived: {SM_COUNT} SMs x {FLOP_PER_CLK_SM[dtype_name]:.0f} {dtype_name} flop/clk/SM "
-                                     f"x {SM_MAX_MHZ:.0f} MHz")},
+                     "peak_source": (f"derived: {sms} SMs x {FLOP_PER_CLK_SM[dtype_name]:.0f} {dtype_name} flop/clk/SM "
+                                     f"x {mhz:.0f} MHz (median SM clock sampled during the timed region)"),
+                     "measured_fma_peak": round(fma_measured, 4),
+                     "frac_of_measured_fma_peak": round(achieved / fma_measured, 4),
+                     "measured_peak_source": "pa_measure_fma_rate: independent FMA chains on every SM, best of 5"},
         "e2e": {"value": round(job_gdofs(ws, total_dofs, e2e_steps, e2e_s), 4), "unit": "GDoF/s",
                 "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
                 "api": "pa_op_apply_host_batch (the step's operators from pinned host buffers, copies "
@@ -334,7 +376,7 @@ def run_ours(args):
                 "estimate": "median step time (host clock)",
                 "mean_steps_value": round(ws * total_dofs * e2e_steps / e2e_mean_s / 1e9, 4)},
         "gpu_launches": 2 * len(cases) * args.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if not args.no_solve:
         out["solve"] = run_solves(args, pa, torch)
@@ -343,7 +385,7 @@ def run_ours(args):
     if args.serve_requests > 0:
         out["serving"] = run_serving(args, pa, torch)
     if args.precision == "fp64" and not args.no_fp32:
-        out["fp32_sweep"] = run_fp32_sweep(args, pa, torch)
+        out["fp32_sweep"] = run_fp32_sweep(args, pa, torch, sms, mhz)
     if args.ablation_ps:
         out["ablation"] = run_ablation(args, pa, torch)
     if not args.no_cpu_baseline and ws == 1:
@@ -517,7 +559,7 @@ def serving_requests(pa, count, seed):
     return out
 
 
-def run_fp32_sweep(args, pa, torch):
+def run_fp32_sweep(args, pa, torch, sms, mhz):
     """The same operator sweep in FP32 (the apply of the mixed-precision
     solves): GDoF/s per p and over the sweep, with the element kernel's
     algorithmic FP32 rate against the derived FP32 peak.  Same workloads,
@@ -548,7 +590,8 @@ def run_fp32_sweep(args, pa, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    peak = SM_COUNT * FLOP_PER_CLK_SM["f32"] * SM_MAX_MHZ * 1e6 / 1e12
+    peak = derived_peak_tflops("f32", sms, mhz)
+    fma_measured = pa.pa_measure_fma_rate(pa.PA_FP32, stream)
     per_p, fl_tot, el_tot = [], 0.0, 0.0
     for c in cases:
         te, ta, na = pa.pa_op_profile_read(c["op"].h)
@@ -561,7 +604,9 @@ def run_fp32_sweep(args, pa, torch):
         c["op"].close()
     return {"value": round(sum(c["ndofs"] for c in cases) * steps / (ms * 1e-3) / 1e9, 4), "unit": "GDoF/s",
             "dtype": "f32", "element_kernel_tflops_alg": round(fl_tot / (el_tot * 1e-3) / 1e12, 3),
-            "frac_of_derived_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / peak, 4), "per_p": per_p}
+            "frac_of_derived_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / peak, 4),
+            "derived_fp32_peak_tflops": round(peak, 3), "measured_fp32_fma_peak_tflops": round(fma_measured, 3),
+            "frac_of_measured_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / fma_measured, 4), "per_p": per_p}
 
 
 def run_ablation(args, pa, torch):
@@ -726,7 +771,7 @@ def run_serving(args, pa, torch):
                       "FP32 V-cycle (mixed precision), rtol 1e-10"}
 
 
-def _oracle_sweep(ps, scale):
+def _oracle_sweep(ps, scale, per_p=None):
     import oracle
     lam, mu = syn.lame(1.0, 0.3)
     dofs, secs = 0, 0.0
@@ -735,17 +780,52 @@ def _oracle_sweep(ps, scale):
         oracle.ref(p)  # reference blocks built outside the timing
         t0 = time.perf_counter()
         oracle.apply(p, n, n, n, mesh.affine, lam, mu, x)
-        secs += time.perf_counter() - t0
+        dt = time.perf_counter() - t0
+        secs += dt
         dofs += mesh.n_dofs(p)
+        if per_p is not None:
+            per_p.append({"p": p, "n": n, "ndofs": mesh.n_dofs(p), "s": round(dt, 4),
+                          "gdofs": round(mesh.n_dofs(p) / dt / 1e9, 6)})
     return dofs, secs
 
 
 def cpu_baseline(ps, args):
+    """The plain FP64 oracle timed on the host cores: the operator sweep at
+    full size (one step, per degree as well), the 4^3 p = 2 clamped cube of
+    the small apply configuration, and the direct solve of the cantilever
+    beam (32x4x4, p = 4: sparse LU of the assembled matrix plus one
+    refinement step) that the GPU solves are gated against."""
     import oracle
-    dofs, secs = _oracle_sweep(ps, 1.0)
-    return {"value": round(dofs / secs / 1e9, 6), "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "one full step: the oracle's element-matrix apply for every p of the sweep at full size, "
-                      "FP64, OpenMP over elements"}
+    per_p = []
+    dofs, secs = _oracle_sweep(ps, 1.0, per_p)
+    out = {"value": round(dofs / secs / 1e9, 6), "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": "one full step: the oracle's element-matrix apply for every p of the sweep at full size, "
+                     "FP64, OpenMP over elements", "per_p": per_p}
+    # the small apply configuration (4^3 unit cube, p = 2, x = 0 clamped)
+    m = syn.box_mesh(4, 4, 4)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, 2)
+    x = syn.uniform_vector(m.n_dofs(2), seed=0)
+    oracle.apply(2, 4, 4, 4, m.affine, lam, mu, x, ess=ess)
+    reps, t0 = 0, time.perf_counter()
+    while reps < 10 or time.perf_counter() - t0 < 0.5:
+        oracle.apply(2, 4, 4, 4, m.affine, lam, mu, x, ess=ess)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    out["config_small_cube_apply"] = {"ndofs": m.n_dofs(2), "s_per_apply": round(dt, 6),
+                                      "gdofs": round(m.n_dofs(2) / dt / 1e9, 6), "reps": reps}
+    if not args.no_oracle_solve:
+        beam = syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0))
+        ess = syn.clamp_mask(beam, 4)
+        b = oracle.load(4, 32, 4, 4, beam.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+        t0 = time.perf_counter()
+        _, res = oracle.solve_sparse(4, 32, 4, 4, beam.affine, lam, mu, b, ess)
+        dt = time.perf_counter() - t0
+        out["beam_solve"] = {"ndofs": len(b), "s": round(dt, 3), "solves_per_s": round(1.0 / dt, 5),
+                             "rel_residual": float(f"{res:.3e}"),
+                             "method": "assembly of the element matrices, sparse LU (scipy SuperLU, one thread), "
+                                       "one refinement step with the element-by-element apply"}
+    return out
 
 
 def run_reference(args):
@@ -754,21 +834,20 @@ def run_reference(args):
         return None
     import oracle
     ps = [int(s) for s in args.ps.split(",")]
-    scale = 1.0 / 3.0
     for _ in range(args.warmup):
-        _oracle_sweep(ps, scale)
+        _oracle_sweep(ps, 1.0)
     dofs, secs = 0, 0.0
     for _ in range(args.steps):
-        d, s = _oracle_sweep(ps, scale)
+        d, s = _oracle_sweep(ps, 1.0)
         dofs += d
         secs += s
     v = dofs / secs / 1e9
-    sample = ("each step: the oracle's element-matrix apply for every p of the sweep on the same recipe at "
-              "(n/3)^3 elements, FP64, OpenMP over elements")
+    sample = ("each step: the oracle's element-matrix apply for every p of the sweep at full size (the GPU "
+              "arm's step), FP64, OpenMP over elements")
     out = {"metric": METRIC, "value": round(v, 6), "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"FP64 op_apply sweep p in {{{args.ps}}} (oracle sample, see cpu_baseline)",
+           "config": {"workload": sweep_workload_name("fp64", ps),
                       "parallelism": "host cores"},
            "cpu_baseline": {"value": round(v, 6), "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
                             "sample": sample},
@@ -786,6 +865,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--ps", default=",".join(map(str, SWEEP)))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-solve", action="store_true", help="skip the oracle's beam solve in cpu_baseline")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the GMG-PCG solve measurements")
     ap.add_argument("--quick-solves", action="store_true", help="only the beam solve")

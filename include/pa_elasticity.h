@@ -237,6 +237,16 @@ int pa_op_autotune(pa_op *op, void *stream);
 int pa_op_profile(pa_op *op, int enable);
 int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64_t *applies);
 
+/* Measured multiply-add rate of the CUDA cores in TFLOP/s (2 flops per
+ * FMA) for PA_FP64 or PA_FP32 arithmetic: the ceiling of the element
+ * kernels, which are bound by those units (Sec. 4: the operator's flops are
+ * FMAs of the sum-factorised contractions).  Runs a probe kernel of
+ * independent FMA chains over every SM on `stream` (best of five timed
+ * launches after one warm-up), allocates and frees a small output buffer,
+ * synchronises.  No counterpart in the paper, which takes its CPUs' peaks
+ * from a benchmark tool. */
+int pa_measure_fma_rate(int precision, double *tflops, void *stream);
+
 /* p-transfer between two operators on the same mesh with degrees
  * pc = coarse->p < pf = fine->p (Sec. 3: polynomial interpolation between the
  * GLL spaces of p-levels).  prolong: xf = P xc evaluates the coarse field at

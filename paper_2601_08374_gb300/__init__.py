@@ -96,6 +96,7 @@ _sig("pa_op_prolong", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_op_restrict", [_vp, _vp, _vp, _vp, _vp])
 _sig("pa_apply_noalloc", [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                           ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
+_sig("pa_measure_fma_rate", [ctypes.c_int, _dp, _vp])
 _sig("pa_op_set_launch", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int])
 _sig("pa_op_get_launch", [_vp, _ip, _ip, _ip])
 _sig("pa_op_autotune", [_vp, _vp])
@@ -339,6 +340,13 @@ def pa_op_traction(op, face, t, F, stream=None):
     tt = np.ascontiguousarray(t, dtype=np.float64).reshape(3)
     _check(lib.pa_op_traction(op, int(face), tt.ctypes.data_as(_dp), _tptr(F), _stream_ptr(stream)),
            "pa_op_traction")
+
+
+def pa_measure_fma_rate(precision, stream=None):
+    """Measured FMA rate of the CUDA cores (TFLOP/s) for PA_FP64 / PA_FP32."""
+    t = ctypes.c_double()
+    _check(lib.pa_measure_fma_rate(precision, ctypes.byref(t), _stream_ptr(stream)), "pa_measure_fma_rate")
+    return t.value
 
 
 def pa_op_set_launch(op, variant, elems_per_block, threads):

@@ -2,11 +2,14 @@
 // variant 0 = flattened shared-memory sweeps, variant 1 = register-tiled lines,
 // variant 2 = register-tiled lines with the gather and store fused into the X sweeps,
 // variant 3 = variant 2 with the fused Z stage split over three lanes per column,
-// variant 4 = the contractions on the tensor cores (tcgen05, three-pass TF32; p <= 6).
+// variant 4 = the contractions on the tensor cores (tcgen05, three-pass TF32; p <= 6),
+// variant 5 = plane-fused sweeps (X+Y and Y^T+X^T per plane in registers, p <= 6),
+// variant 6 = variant 5 with the fused Z stage split over three lanes per column.
 #include <cstring>
 
 #include "pa_apply.cuh"
 #include "pa_apply_line.cuh"
+#include "pa_apply_plane.cuh"
 #include "pa_apply_tc.cuh"
 
 namespace pa {
@@ -27,6 +30,9 @@ size_t smem_for(const ApplyLaunch &c)
         return tc_smem_bytes();
     }
     if (c.threads > 256) return 0;
+    // variant 5 keeps 18 D column values per thread: up to D = 7
+    if (c.variant == 5) return D <= 7 ? plane_smem_bytes<float, D, Q>(c.epb) : 0;
+    if (c.variant == 6) return plane_smem_bytes<float, D, Q>(c.epb);
     if (c.variant == 3 || line_ok<D>) return line_smem_bytes<float, D, Q>(c.epb);
     return 0;
 }
@@ -36,6 +42,11 @@ int launch_for(const ApplyArgs<float> &a, const Tables<float> &tab, const ApplyL
 {
     if (c.variant == 0) return launch_flat<float, D, Q>(a, tab, c, s);
     if (c.variant == 3) return launch_line<float, D, Q, true, true>(a, tab, c, s);
+    if (c.variant == 6) return launch_plane<float, D, Q, true>(a, tab, c, s);
+    if (c.variant == 5) {
+        if constexpr (D <= 7) return launch_plane<float, D, Q, false>(a, tab, c, s);
+        return set_error(PA_EINVAL, "apply variant 5 is instantiated for p <= 6 only");
+    }
     if (c.variant == 4) {
         if constexpr (D <= 8 && Q <= 8) return launch_tc<D, Q>(a, tc_tables(tab, D, Q), s);
         return set_error(PA_EINVAL, "apply variant 4 is instantiated for p <= 6 only");
@@ -50,6 +61,11 @@ int launch_batch_for(const BatchArgs<float> &b, const Tables<float> &tab, const 
 {
     if (c.variant == 0) return launch_flat_batch<float, D, Q>(b, tab, c, s);
     if (c.variant == 3) return launch_line_batch<float, D, Q, true, true>(b, tab, c, s);
+    if (c.variant == 6) return launch_plane_batch<float, D, Q, true>(b, tab, c, s);
+    if (c.variant == 5) {
+        if constexpr (D <= 7) return launch_plane_batch<float, D, Q, false>(b, tab, c, s);
+        return set_error(PA_EINVAL, "apply variant 5 is instantiated for p <= 6 only");
+    }
     if (c.variant == 4) {
         // batches of operators run the fused line variant
         ApplyLaunch l2;

@@ -17,7 +17,7 @@ template <int D, int Q>
 size_t smem_for(const ApplyLaunch &c)
 {
     if (c.variant == 0) return flat_smem_bytes<double, D, Q>(c.epb);
-    if (c.variant == 4) return 0;  // FP32 only
+    if (c.variant >= 4) return 0;  // FP32 only
     if (c.threads > 256) return 0;
     if (c.variant == 3 || line_ok<D>) return line_smem_bytes<double, D, Q>(c.epb);
     return 0;

@@ -57,12 +57,13 @@ __device__ __forceinline__ T sel3v(int k, T x0, T x1, T x2) { return k == 0 ? x0
 // the other two components and their diagonal entries; lane c = 0 adds the
 // divergence in component order and broadcasts it.  Each lane keeps J^-1
 // with its columns rotated to the order c, c + 1, c + 2 (mod 3).
-template <typename T, int D, int Q>
-__device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int64_t e0,
-                                                int ne_blk, int tid, int nt)
+template <typename T, int D, int Q, bool ROLLED = false>
+__device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
+                                                int64_t e0, int ne_blk, int tid, int nt)
 {
     using L = LineLayout<T, D, Q>;
     constexpr int CS = L::CS;
+    constexpr int kUnrollQz = ROLLED ? 1 : Q;  // as in z_columns
     constexpr unsigned kMask = 0x3fffffffu;  // lanes 0..29
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     const int c = lane / 10, slot = lane - 10 * c;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
         const bool act = o < total;
         const int oo = act ? o : base;  // a lane past the end works on a valid column and writes nothing
         const int el = oo / (Q * Q), col = oo - el * (Q * Q);
-        T *cpt = bufA + (size_t)el * L::A + col * CS + c * 3 * D;
+        T *cpt = bufA + (size_t)el * astride + col * CS + c * 3 * D;
         T in[3][D];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -96,14 +97,28 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int i = 0; i < D; ++i) acc[k][i] = T(0);
-#pragma unroll
+#pragma unroll(kUnrollQz)
         for (int qz = 0; qz < Q; ++qz) {
+            T bq[D], gq[D], bwq[D], gwq[D];
+            if constexpr (ROLLED)
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    bq[i] = tab.B[i * Q + qz];
+                    gq[i] = tab.G[i * Q + qz];
+                    bwq[i] = tab.Bw[i * Q + qz];
+                    gwq[i] = tab.Gw[i * Q + qz];
+                }
+            // unrolled, the tables stay constant-bank operands of the FMAs
+            auto tB = [&](int i) { if constexpr (ROLLED) return bq[i]; else return tab.B[i * Q + qz]; };
+            auto tG = [&](int i) { if constexpr (ROLLED) return gq[i]; else return tab.G[i * Q + qz]; };
+            auto tBw = [&](int i) { if constexpr (ROLLED) return bwq[i]; else return tab.Bw[i * Q + qz]; };
+            auto tGw = [&](int i) { if constexpr (ROLLED) return gwq[i]; else return tab.Gw[i * Q + qz]; };
             T g0 = T(0), g1 = T(0), g2 = T(0);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                g0 = fma(in[0][i], tab.B[i * Q + qz], g0);
-                g1 = fma(in[1][i], tab.B[i * Q + qz], g1);
-                g2 = fma(in[2][i], tab.G[i * Q + qz], g2);
+                g0 = fma(in[0][i], tB(i), g0);
+                g1 = fma(in[1][i], tB(i), g1);
+                g2 = fma(in[2][i], tG(i), g2);
             }
             // du[c][(c + r) mod 3]
             const T u0 = fma(R[0][0], g0, fma(R[1][0], g1, R[2][0] * g2));
@@ -122,7 +137,7 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
                 const T qv = fma(s0, R[m][0], fma(s1, R[m][1], s2 * R[m][2]));
 #pragma unroll
                 for (int i = 0; i < D; ++i)
-                    acc[m][i] = fma(qv, (m == 2 ? tab.Gw[i * Q + qz] : tab.Bw[i * Q + qz]), acc[m][i]);
+                    acc[m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[m][i]);
             }
         }
         if (act)
@@ -130,6 +145,104 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int i = 0; i < D; ++i) cpt[k * D + i] = acc[k][i];
+    }
+}
+
+// The fused Z stage with one thread per column (el, qx, qy): the column's
+// 9 x D inputs (channels [c][k], k = d/dxi, d/deta, interpolated) and 9 x D
+// accumulators in registers; Z sweep, pointwise stress of Eq. 7, Q
+// reconstruction and Z^T sweep, the result written back in place.  Columns
+// of element el start at bufA + el * astride, column col at col * CS.
+template <typename T, int D, int Q, bool ROLLED = false>
+__device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
+                                          int64_t e0, int ne_blk, int tid, int nt)
+{
+    constexpr int CS = LineLayout<T, D, Q>::CS;
+    // ROLLED: the qz loop is not unrolled (smaller code; the table columns of
+    // each qz are loaded once per iteration); same arithmetic either way
+    constexpr int kUnrollQz = ROLLED ? 1 : Q;
+    for (int o = tid; o < ne_blk * Q * Q; o += nt) {
+        int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
+        T *cp = bufA + (size_t)el * astride + col * CS;
+        T in[9][D];
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
+        const T *geo = a.geo + (e0 + el) * kGeoStride;
+        T Ji[9], cj[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
+        const T cl = geo[9], cm = geo[10], m2 = cm + cm;
+        // mu detJ J^-1: each shear stress is one 6-term dot with it
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
+        T acc[9][D];
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[ch][i] = T(0);
+#pragma unroll(kUnrollQz)
+        for (int qz = 0; qz < Q; ++qz) {
+            T bq[D], gq[D], bwq[D], gwq[D];
+            if constexpr (ROLLED)
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    bq[i] = tab.B[i * Q + qz];
+                    gq[i] = tab.G[i * Q + qz];
+                    bwq[i] = tab.Bw[i * Q + qz];
+                    gwq[i] = tab.Gw[i * Q + qz];
+                }
+            // unrolled, the tables stay constant-bank operands of the FMAs
+            auto tB = [&](int i) { if constexpr (ROLLED) return bq[i]; else return tab.B[i * Q + qz]; };
+            auto tG = [&](int i) { if constexpr (ROLLED) return gq[i]; else return tab.G[i * Q + qz]; };
+            auto tBw = [&](int i) { if constexpr (ROLLED) return bwq[i]; else return tab.Bw[i * Q + qz]; };
+            auto tGw = [&](int i) { if constexpr (ROLLED) return gwq[i]; else return tab.Gw[i * Q + qz]; };
+            T gr[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    g0 = fma(in[c * 3 + 0][i], tB(i), g0);
+                    g1 = fma(in[c * 3 + 1][i], tB(i), g1);
+                    g2 = fma(in[c * 3 + 2][i], tG(i), g2);
+                }
+                gr[c][0] = g0;
+                gr[c][1] = g1;
+                gr[c][2] = g2;
+            }
+            // Voigt stress (Eq. 7): the diagonal of grad u, then each shear
+            // stress mu detJ (du_ab + du_ba) as one 6-term dot
+            T dg[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dg[c] = fma(Ji[c], gr[c][0], fma(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
+            const T ld = cl * (dg[0] + dg[1] + dg[2]);
+            T s[3][3];
+            s[0][0] = fma(m2, dg[0], ld);
+            s[1][1] = fma(m2, dg[1], ld);
+            s[2][2] = fma(m2, dg[2], ld);
+            auto shear = [&](int ia, int ib) {
+                return fma(cj[ib], gr[ia][0], fma(cj[3 + ib], gr[ia][1], fma(cj[6 + ib], gr[ia][2],
+                       fma(cj[ia], gr[ib][0], fma(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
+            };
+            s[0][1] = s[1][0] = shear(0, 1);
+            s[0][2] = s[2][0] = shear(0, 2);
+            s[1][2] = s[2][1] = shear(1, 2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    T qv = fma(s[c][0], Ji[m * 3 + 0], fma(s[c][1], Ji[m * 3 + 1], s[c][2] * Ji[m * 3 + 2]));
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        acc[c * 3 + m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[c * 3 + m][i]);
+                }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) cp[ch * D + i] = acc[ch][i];
     }
 }
 
@@ -240,77 +353,8 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     __syncthreads();
 
     // ---- Z sweep + pointwise + Z^T sweep: column (el, qx, qy), in place
-    if constexpr (SPLIT) z_columns_split<T, D, Q>(a, tab, bufA, e0, ne_blk, tid, nt);
-    else
-    for (int o = tid; o < ne_blk * Q * Q; o += nt) {
-        int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
-        T *cp = bufA + (size_t)el * L::A + col * CS;
-        T in[9][D];
-#pragma unroll
-        for (int ch = 0; ch < 9; ++ch)
-#pragma unroll
-            for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
-        const T *geo = a.geo + (e0 + el) * kGeoStride;
-        T Ji[9], cj[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
-        const T cl = geo[9], cm = geo[10], m2 = cm + cm;
-        // mu detJ J^-1: each shear stress is one 6-term dot with it
-#pragma unroll
-        for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
-        T acc[9][D];
-#pragma unroll
-        for (int ch = 0; ch < 9; ++ch)
-#pragma unroll
-            for (int i = 0; i < D; ++i) acc[ch][i] = T(0);
-#pragma unroll
-        for (int qz = 0; qz < Q; ++qz) {
-            T gr[3][3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                T g0 = T(0), g1 = T(0), g2 = T(0);
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    g0 = fma(in[c * 3 + 0][i], tab.B[i * Q + qz], g0);
-                    g1 = fma(in[c * 3 + 1][i], tab.B[i * Q + qz], g1);
-                    g2 = fma(in[c * 3 + 2][i], tab.G[i * Q + qz], g2);
-                }
-                gr[c][0] = g0;
-                gr[c][1] = g1;
-                gr[c][2] = g2;
-            }
-            // Voigt stress (Eq. 7): the diagonal of grad u, then each shear
-            // stress mu detJ (du_ab + du_ba) as one 6-term dot
-            T dg[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dg[c] = fma(Ji[c], gr[c][0], fma(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
-            const T ld = cl * (dg[0] + dg[1] + dg[2]);
-            T s[3][3];
-            s[0][0] = fma(m2, dg[0], ld);
-            s[1][1] = fma(m2, dg[1], ld);
-            s[2][2] = fma(m2, dg[2], ld);
-            auto shear = [&](int ia, int ib) {
-                return fma(cj[ib], gr[ia][0], fma(cj[3 + ib], gr[ia][1], fma(cj[6 + ib], gr[ia][2],
-                       fma(cj[ia], gr[ib][0], fma(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
-            };
-            s[0][1] = s[1][0] = shear(0, 1);
-            s[0][2] = s[2][0] = shear(0, 2);
-            s[1][2] = s[2][1] = shear(1, 2);
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    T qv = fma(s[c][0], Ji[m * 3 + 0], fma(s[c][1], Ji[m * 3 + 1], s[c][2] * Ji[m * 3 + 2]));
-#pragma unroll
-                    for (int i = 0; i < D; ++i)
-                        acc[c * 3 + m][i] = fma(qv, (m == 2 ? tab.Gw[i * Q + qz] : tab.Bw[i * Q + qz]), acc[c * 3 + m][i]);
-                }
-        }
-#pragma unroll
-        for (int ch = 0; ch < 9; ++ch)
-#pragma unroll
-            for (int i = 0; i < D; ++i) cp[ch * D + i] = acc[ch][i];
-    }
+    if constexpr (SPLIT) z_columns_split<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
+    else z_columns<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
     __syncthreads();
 
     // ---- Y^T sweep: line (el, c, iz, qx) -> S3 [c][iz][iy][k*Q + qx]

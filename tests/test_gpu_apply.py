@@ -210,6 +210,66 @@ def test_apply_register_tiled_variant(pa, p, prec, variant):
     op.close()
 
 
+@pytest.mark.parametrize("variant", [5, 6])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_apply_plane_fused_variant(pa, p, variant):
+    """The plane-fused FP32 kernels (variant 5: X+Y and Y^T+X^T sweeps per
+    plane in registers, one thread per column in the fused Z stage; variant
+    6: three lanes per column) against the oracle with several CTA shapes
+    (ragged last CTA, partly idle warps), constrained; they sum in the order
+    of the line variants 2 and 3 (same column code), so their results are
+    bitwise those; the batched launch of variant 5/6 operators equals their
+    single applies."""
+    if variant == 5 and p > 6:
+        pytest.skip("variant 5 is instantiated for p <= 6")
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=330 + p, ny=ny, nz=nz)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    x = syn.uniform_vector(m.n_dofs(p), seed=17 + p)
+    op = pa.Operator(nx, ny, nz, m.affine, p, lam, mu, precision=pa.PA_FP32, ess_mask=ess)
+    xt = torch.tensor(x, dtype=op.dtype, device="cuda")
+    yo = oracle.apply(p, nx, ny, nz, m.affine, lam, mu, xt.double().cpu().numpy(), ess=ess)
+    pa.pa_op_set_launch(op.h, 2 if variant == 5 else 3, 1, 128)
+    y2 = op.apply(xt).clone()
+    ran = 0
+    for epb, th in [(1, 64), (5, 256), (3, 96), (2, 32), (16, 256)]:
+        try:
+            pa.pa_op_set_launch(op.h, variant, epb, th)
+        except pa.PAError as e:  # shape beyond the shared-memory limit for this degree
+            assert e.code == pa.PA_EINVAL
+            continue
+        y = op.apply(xt)
+        assert _relerr(y.double().cpu().numpy(), yo) <= TOL[1], (epb, th)
+        assert torch.equal(y, y2), (epb, th)
+        ran += 1
+    assert ran >= 3
+    with pytest.raises(pa.PAError):
+        pa.pa_op_set_launch(op.h, variant, 1, 512)  # at most 256 threads
+    # two operators of this degree in one batched launch of the variant
+    pa.pa_op_set_launch(op.h, variant, 3, 128)
+    op2 = pa.Operator(nx, ny, nz, m.affine, p, 2.0, 0.5, precision=pa.PA_FP32)
+    pa.pa_op_set_launch(op2.h, variant, 3, 128)
+    x2 = torch.tensor(syn.uniform_vector(op2.ndofs, seed=3), dtype=op2.dtype, device="cuda")
+    r1, r2 = op.apply(xt).clone(), op2.apply(x2).clone()
+    ys = [torch.full_like(xt, float("nan")), torch.full_like(x2, float("nan"))]
+    pa.pa_op_apply_batch([op.h, op2.h], [xt, x2], ys)
+    torch.cuda.synchronize()
+    assert torch.equal(ys[0], r1) and torch.equal(ys[1], r2)
+    op.close()
+    op2.close()
+
+
+def test_plane_variants_are_fp32_only(pa):
+    m = syn.box_mesh(2, 2, 2)
+    op = pa.Operator(2, 2, 2, m.affine, 2, 1.0, 1.0, precision=pa.PA_FP64)
+    for v in (5, 6):
+        with pytest.raises(pa.PAError) as ei:
+            pa.pa_op_set_launch(op.h, v, 2, 128)
+        assert ei.value.code == pa.PA_EINVAL
+    op.close()
+
+
 def test_autotune_keeps_parity(pa):
     p = 4
     m = syn.random_affine_cube(4, seed=9)
