@@ -106,13 +106,13 @@ def kernel_source_hash() -> str:
 # valid only for the kernel source and launch table with this hash.  The E-vector writes mostly stay in L2
 # and reach DRAM during the assembly kernel, so for p >= 4 the figure is
 # essentially the reads of x and of the geometry records.
-TRAFFIC_HASH = "9284aacec0bdd2a7"
+TRAFFIC_HASH = "6efc3f15735ea467"
 ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>",
                         3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)",
                         5: "pa_apply_plane_kernel<SPLIT=0>", 6: "pa_apply_plane_kernel<SPLIT=1>"}
 TRAFFIC_BYTES: dict = {
-    ("f64", 1): 249449344, ("f64", 2): 59693824, ("f64", 4): 26705920, ("f64", 6): 22366976, ("f64", 8): 22142208,
-    ("f32", 1): 96642688, ("f32", 2): 18397696, ("f32", 4): 13158144, ("f32", 6): 11214976, ("f32", 8): 11102720,
+    ("f64", 1): 251676416, ("f64", 2): 59448576, ("f64", 4): 26878976, ("f64", 6): 22385408, ("f64", 8): 22125312,
+    ("f32", 1): 98589440, ("f32", 2): 18400256, ("f32", 4): 13144576, ("f32", 6): 11214336, ("f32", 8): 11112448,
 }
 
 
