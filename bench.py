@@ -119,6 +119,12 @@ TRAFFIC_BYTES: dict = {
 # Coarse-level solve of the V-cycle: inexact, relative tolerance 1e-2 and at
 # most 10 iterations (the paper's coarse-solve setting, Sec. 3.2).
 COARSE_RTOL, COARSE_MAXIT = 1e-2, 10
+# Chebyshev-Jacobi smoother of the solve rows: degree 4 on [0.05, 1.2] of the
+# estimated lambda_max (the library's default interval), the fastest setting
+# of the degree / interval sweep (--gmg-sweep); the paper's setting, degree 2
+# (Sec. 5.2) on the interval [0.3, 1.2], is kept as one extra beam row
+CHEB_ORDER = 4
+PAPER_SMOOTHER = (2, 0.3, 1.2)
 
 
 class ClockSampler:
@@ -416,6 +422,9 @@ def run_solves(args, pa, torch):
              dict(key="beamh", name="beam 32x4x4 p=4 (4->2->1, then h-levels 16x2x2 and 8x1x1 at p=1) E=1 nu=0.3 f=(0,0,-1), "
                        "x=0 clamped", mesh=beam, p=4, levels=[4, 2, 1], h=2, nu=0.3, modes=None,
                   f0=(0.0, 0.0, -1.0), reps=args.solve_reps)]
+    cases.append(dict(key="beam_paper", name="beam 32x4x4 p=4 (4->2->1) as above, with the paper's smoother setting: "
+                           "Chebyshev degree 2 on [0.3, 1.2] lambda_max", mesh=beam, p=4, levels=[4, 2, 1], nu=0.3,
+                      modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps, smoother=PAPER_SMOOTHER))
     cases.append(dict(key="beam_c1", name="beam 32x4x4 p=4 (4->2->1) as above, coarse solve capped at one PCG "
                            "iteration (instead of the paper's 1e-2 / at most 10)", mesh=beam, p=4, levels=[4, 2, 1],
                       nu=0.3, modes=None, f0=(0.0, 0.0, -1.0), reps=args.solve_reps, coarse=(COARSE_RTOL, 1),
@@ -449,6 +458,7 @@ def run_solves(args, pa, torch):
         b = op.rhs(f0=c["f0"], modes=c["modes"], traction=c.get("traction"))
         h = c.get("h", 0)
         row = {"case": c["name"], "ndofs": op.ndofs, "levels": c["levels"], "h_levels": h, "rtol": 1e-10,
+               "smoother": list(c.get("smoother", (CHEB_ORDER, 0.05, 1.2))),
                "coarse_rtol_maxit": list(c.get("coarse", (COARSE_RTOL, COARSE_MAXIT)))}
         sols = {}
         for mode, key in ((pa.PA_SOLVE_FP64, "fp64"), (pa.PA_SOLVE_MIXED, "mixed_ir"), (pa.PA_SOLVE_MIXED_FCG, "mixed_fcg")):
@@ -457,7 +467,10 @@ def run_solves(args, pa, torch):
             if args.solve_modes and key not in args.solve_modes.split(","):
                 continue
             crtol, cmax = c.get("coarse", (COARSE_RTOL, COARSE_MAXIT))
-            s = pa.pa_solver_create_hp(op.h, c["levels"], h, 2, crtol, cmax, mode)
+            k, lo, hi = c.get("smoother", (CHEB_ORDER, 0.05, 1.2))
+            s = pa.pa_solver_create_hp(op.h, c["levels"], h, k, crtol, cmax, mode)
+            pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_LOWER, lo)
+            pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_UPPER, hi)
             if eager:
                 pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_GRAPHS, 0)
             x = torch.zeros_like(b)
@@ -473,7 +486,8 @@ def run_solves(args, pa, torch):
             row[key] = {"status": int(code), "solves_per_s": round(1.0 / statistics.median(times), 3),
                         "median_s": round(statistics.median(times), 5), "iterations": info.iterations,
                         "coarse_iterations": info.coarse_iterations,
-                        "true_rel_residual": float(f"{info.rel_residual:.3e}")}
+                        "true_rel_residual": float(f"{info.rel_residual:.3e}"),
+                        "tolerance_met": int(info.tolerance_met)}
             if mode == pa.PA_SOLVE_MIXED:
                 row[key]["refinements"] = info.refinements
             pa.pa_solver_destroy(s)
@@ -771,6 +785,98 @@ def run_serving(args, pa, torch):
                       "FP32 V-cycle (mixed precision), rtol 1e-10"}
 
 
+def _lanczos_extremes(pa, torch, op, ess, steps=80):
+    """Extreme eigenvalues of D^-1 A (through the symmetric D^-1/2 A D^-1/2)
+    from `steps` Lanczos steps with full reorthogonalisation, using the
+    operator's apply and diagonal (a check of the smoother's power-iteration
+    estimate; not part of any solve)."""
+    dis = op.diag().rsqrt()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    v = torch.rand(op.ndofs, dtype=torch.float64, device="cuda", generator=g) - 0.5
+    if ess is not None:
+        v[torch.tensor(ess, device="cuda").bool()] = 0.0
+    v /= v.norm()
+    basis, alpha, beta = [v], [], []
+    vprev, b = torch.zeros_like(v), 0.0
+    for _ in range(steps):
+        w = dis * op.apply(dis * v)
+        a = float(torch.dot(w, v))
+        alpha.append(a)
+        w = w - a * v - b * vprev
+        for u in basis:
+            w -= torch.dot(w, u) * u
+        b = float(w.norm())
+        if b < 1e-14:
+            break
+        beta.append(b)
+        vprev, v = v, w / b
+        basis.append(v)
+    n = len(alpha)
+    T = np.diag(alpha) + np.diag(beta[:n - 1], 1) + np.diag(beta[:n - 1], -1)
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])
+
+
+def run_gmg_sweep(args):
+    """Diagnosis of the GMG-PCG iteration counts (--gmg-sweep): for the beam
+    (32x4x4, p = 4, nu = 0.3) and the nu = 0.45 random-affine cubes (p = 6
+    and 8), the power-iteration lambda_max of every smoothed level beside an
+    80-step Lanczos estimate of the extreme eigenvalues of D^-1 A, and the
+    iterations and solve time for Chebyshev degrees k and target intervals
+    [lo, hi] * lambda_max."""
+    import torch
+
+    import paper_2601_08374_gb300 as pa
+    torch.cuda.set_device(0)
+    out = {"cases": []}
+    beam = syn.box_mesh(32, 4, 4, hi=(8.0, 1.0, 1.0))
+    cases = [("beam 32x4x4 p=4 nu=0.3", beam, 4, [4, 2, 1], 0.3, None, (0.0, 0.0, -1.0),
+              [pa.PA_SOLVE_FP64, pa.PA_SOLVE_MIXED_FCG])]
+    for p in (6, 8):
+        n = syn.mixed_n(p)
+        cases.append((f"cube {n}^3 p={p} nu=0.45 random affine", syn.random_affine_cube(n, seed=3000 + p), p,
+                      [6, 3, 1] if p == 6 else [8, 4, 2, 1], 0.45, syn.smooth_force_modes(seed=3100 + p),
+                      (0.0, 0.0, 0.0), [pa.PA_SOLVE_MIXED_FCG]))
+    ks = [int(v) for v in args.gmg_sweep_k.split(",")]
+    intervals = [tuple(float(t) for t in iv.split(":")) for iv in args.gmg_sweep_intervals.split(",")]
+    for name, m, p, lv, nu, modes, f0, solve_modes in cases:
+        lam, mu = syn.lame(1.0, nu)
+        ess = syn.clamp_mask(m, p)
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+        b = op.rhs(f0=f0, modes=modes)
+        row = {"case": name, "levels": lv, "lambda": [], "sweep": []}
+        s = pa.pa_solver_create(op.h, lv, 2, COARSE_RTOL, COARSE_MAXIT, pa.PA_SOLVE_FP64)
+        x = torch.zeros_like(b)
+        _, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 2000)
+        pa.pa_solver_destroy(s)
+        for li, pl in enumerate(lv[:-1]):
+            el = syn.clamp_mask(m, pl)
+            o2 = pa.Operator(m.nx, m.ny, m.nz, m.affine, pl, lam, mu, ess_mask=el)
+            lmin, lmax = _lanczos_extremes(pa, torch, o2, el)
+            o2.close()
+            row["lambda"].append({"p": pl, "power10": round(info.lambda_max[li], 4), "lanczos_max": round(lmax, 4),
+                                  "lanczos_min": float(f"{lmin:.4e}")})
+        for mode in solve_modes:
+            for k in ks:
+                s = pa.pa_solver_create(op.h, lv, k, COARSE_RTOL, COARSE_MAXIT, mode)
+                for lo, hi in intervals:
+                    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_LOWER, lo)
+                    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_UPPER, hi)
+                    pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)  # captures the graphs
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    code, info = pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)
+                    dt = time.perf_counter() - t0
+                    row["sweep"].append({"mode": {0: "fp64", 2: "mixed_fcg"}[mode], "k": k, "lo": lo, "hi": hi,
+                                         "iterations": info.iterations, "status": int(code), "s": round(dt, 4),
+                                         "rho": round(info.rel_residual ** (1.0 / max(info.iterations, 1)), 4)})
+                pa.pa_solver_destroy(s)
+        out["cases"].append(row)
+        op.close()
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def _oracle_sweep(ps, scale, per_p=None):
     import oracle
     lam, mu = syn.lame(1.0, 0.3)
@@ -864,6 +970,11 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--ps", default=",".join(map(str, SWEEP)))
+    ap.add_argument("--gmg-sweep", action="store_true",
+                    help="diagnose the GMG-PCG iteration counts (eigenvalue estimates, Chebyshev degree/interval sweep) "
+                         "instead of the benchmark")
+    ap.add_argument("--gmg-sweep-k", default="1,2,3,4,5,6")
+    ap.add_argument("--gmg-sweep-intervals", default="0.3:1.2,0.1:1.2,0.05:1.2,0.02:1.2,0.01:1.2,0.05:1.1,0.3:1.5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-solve", action="store_true", help="skip the oracle's beam solve in cpu_baseline")
     ap.add_argument("--no-autotune", action="store_true")
@@ -873,7 +984,7 @@ def main(argv=None):
     ap.add_argument("--clocks-dir", default="", help="directory for the raw nvidia-smi clock samples "
                     "(default: a temporary directory)")
     ap.add_argument("--solve-cases", default="", help="comma list of solve-case keys to run (default: all): "
-                    "beam, beam2mat, beamh, beam_c1, beam64, beam64h, cube6, cube8, cube6_c1")
+                    "beam, beam2mat, beamh, beam_paper, beam_c1, beam64, beam64h, cube6, cube8, cube6_c1")
     ap.add_argument("--solve-modes", default="", help="comma list of fp64, mixed_ir, mixed_fcg (default: each case's)")
     ap.add_argument("--solve-eager-maxit", type=int, default=0,
                     help="profiling aid: graphs off and this iteration cap for every solve (0: graphs, cap 1000)")
@@ -894,6 +1005,8 @@ def main(argv=None):
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.gmg_sweep:
+        return run_gmg_sweep(args)
     return run_ours(args)
 
 

@@ -48,7 +48,8 @@ enum pa_status {
     PA_ENOTCONV = 4,   /* solver reached its iteration cap                         */
     PA_EBREAKDOWN = 5, /* solver breakdown: p^T A p <= 0 or a NaN/Inf reduction    */
     PA_ETIMEOUT = 6,   /* a bounded device-side wait expired                       */
-    PA_EBUSY = 7       /* resource busy (e.g. server admission refused)            */
+    PA_EBUSY = 7,      /* resource busy (e.g. server admission refused)            */
+    PA_ECANCELED = 8   /* the request or solve was canceled (pa_server_cancel)    */
 };
 
 enum pa_precision { PA_FP64 = 0, PA_FP32 = 1 };
@@ -110,13 +111,20 @@ int pa_op_apply(pa_op *op, const void *x, void *y, void *stream);
  * rows).  Same argument rules as pa_op_apply. */
 int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream);
 
-/* y_k = A_k x_k for k < count in few launches: operators of equal degree and
- * precision are applied together, one launch of the element kernel over all
- * their elements (uneven sizes allowed) and one launch of the node
- * assembly over all their nodes, up to 24 operators per launch.  Each group
- * uses the launch shape of its first operator.  No counterpart in the
- * paper (it batches independent applies of Sec. 4.2-4.5).  An operator may
- * appear only once; x_k and y_k must not alias. */
+/* y_k = A_k x_k for k < count in few launches.  Operators of one precision
+ * whose launch shape the persistent multi-operator kernels reproduce (FP64:
+ * variant 0; FP32: variants 2 and 5 up to p = 6, variants 3 and 6 at any
+ * degree; isotropic material) are applied by one element launch and one
+ * assembly launch per 96 operators, whatever their degrees and sizes: a
+ * persistent grid whose CTAs walk the element tiles of all of them, each
+ * tile run by the body of its operator's degree.  Every result is bitwise
+ * that operator's own apply.  Other operators are grouped by (precision,
+ * degree), one launch pair per group of up to 24 (tensor-core shapes run as
+ * the register-tiled line variant there, so their bits differ from their
+ * own apply, within the FP32 tolerance); anisotropic ones are applied one
+ * by one.  No counterpart in the paper (it batches independent
+ * applies of Sec. 4.2-4.5).  An operator may appear only once; x_k and y_k
+ * must not alias. */
 int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream);
 
 /* Same computation with host buffers (no counterpart in the paper, whose
@@ -220,6 +228,14 @@ int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *t
  * of this operator since the last check (variant 4): PA_OK, or
  * PA_ETIMEOUT when a result was not valid.  Synchronous. */
 int pa_op_check(pa_op *op);
+
+/* Budget of the operator's bounded device waits (the tensor-core waits of
+ * variant 4), in seconds of SM clock, 0 < seconds <= 60 (default about 2).
+ * A wait that runs past it lets the MMAs in flight finish, marks the apply
+ * invalid (pa_op_check then returns PA_ETIMEOUT) and ends the kernel; the
+ * operator stays usable.  No counterpart in the paper: failure detection of
+ * this library. */
+int pa_op_set_wait_limit(pa_op *op, double seconds);
 
 /* Autotuner: times every admissible (variant, elements per CTA, threads)
  * with CUDA events on `stream`, applying the operator to the op's own
@@ -368,11 +384,37 @@ int pa_solver_destroy(pa_solver *s);
  *    (structured coarsening, Galerkin stencils, Chebyshev-Jacobi smoothing,
  *    dense solve of the last level) -- the h-levels under the p-levels of the
  *    paper's hierarchy (Sec. 3); 0: Jacobi-preconditioned coarse CG.
+ *  PA_SOLVER_OPT_CHEB_LOWER (default 0.05), PA_SOLVER_OPT_CHEB_UPPER
+ *    (default 1.2): the Chebyshev smoother (Sec. 3.1) targets the interval
+ *    [lower, upper] * lambda_max(D^-1 A) of each smoothed level, lambda_max
+ *    its power-iteration estimate; 0 < lower < upper < 100.  Takes effect
+ *    at the next solve.  (The upper factor covers the estimate's shortfall:
+ *    ten power iterations fall 8-17 % below lambda_max on the measured
+ *    problems, and an upper end below lambda_max makes the smoother amplify
+ *    the top modes.)
+ *  PA_SOLVER_OPT_POWER_ITERS (default 10, Sec. 3.1): power iterations of
+ *    the lambda_max estimates, 1..1000; setting it re-estimates every
+ *    smoothed level at once (synchronous).
+ *  PA_SOLVER_OPT_WAIT_LIMIT (seconds, default 2, at most 60): bound of every
+ *    grid-barrier wait of the persistent coarse kernel.  A wait that runs
+ *    past it ends the kernel and the solve returns PA_ETIMEOUT; the solver
+ *    stays usable.  (No counterpart in the paper: failure detection of this
+ *    library.)
+ *  PA_SOLVER_OPT_INJECT_INNER_FAILURE (test hook, default 0): k > 0 makes the
+ *    k-th inner solve of the next PA_SOLVE_MIXED solve report a breakdown
+ *    without running (fault injection on the host); the solve then returns
+ *    PA_EBREAKDOWN with info filled and x the last refined iterate.  One
+ *    shot: the option returns to 0 when it fires.
  */
 enum pa_solver_option {
     PA_SOLVER_OPT_GRAPHS = 1,
     PA_SOLVER_OPT_PERSISTENT_COARSE = 2,
-    PA_SOLVER_OPT_COARSE_HMG = 3
+    PA_SOLVER_OPT_COARSE_HMG = 3,
+    PA_SOLVER_OPT_CHEB_LOWER = 4,
+    PA_SOLVER_OPT_CHEB_UPPER = 5,
+    PA_SOLVER_OPT_POWER_ITERS = 6,
+    PA_SOLVER_OPT_WAIT_LIMIT = 7,
+    PA_SOLVER_OPT_INJECT_INNER_FAILURE = 8
 };
 int pa_solver_set_option(pa_solver *s, int option, double value);
 
@@ -397,13 +439,14 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
                      void *stream);
 
 /* Solve count independent systems A_k x_k = b_k together (flexible-CG modes
- * PA_SOLVE_FP64 and PA_SOLVE_MIXED_FCG only; all solvers with the same number
- * of levels, mode and Chebyshev order; each solver at most once).  The
- * solves advance in lockstep, one CG step per tick, and at every operator
- * apply of the step (Sec. 4.2-4.5 on each level of the V-cycle, Sec. 3) the
- * applies of all unfinished solves form one batched launch per (precision,
- * degree) instead of one launch each; a solve leaves the batch when it
- * converges or reaches maxit.  Every x_k, iteration count and residual is
+ * PA_SOLVE_FP64 and PA_SOLVE_MIXED_FCG only, any hierarchies; each solver at
+ * most once).  The solves advance in lockstep, one CG step per tick.  A step
+ * is split at its operator applies (Sec. 4.2-4.5 on each level of the
+ * V-cycle, Sec. 3) into phases; phase round j of a tick runs phase j of every
+ * solve that has one and then the applies that end them as one batched
+ * apply (pa_op_apply_batch: one persistent launch pair per precision for
+ * any mix of degrees); a solve leaves the batch when it converges or
+ * reaches maxit.  Every x_k, iteration count and residual is
  * bitwise that of pa_gmg_pcg_solve on the same solver.  b_k, x_k: device
  * double L-vectors (x_k in = initial guess, out = solution); infos: count
  * entries or NULL.  Waits for `stream`, returns when every x_k is written:
@@ -424,11 +467,11 @@ int pa_gmg_pcg_solve_batch(pa_solver *const *solvers, const double *const *b, do
  * CUDA stream of its own.  Then:
  *  - batch lane (flexible-CG modes PA_SOLVE_FP64 / PA_SOLVE_MIXED_FCG, at
  *    most PA_SERVER_OPT_BATCH_MAX_DOFS fine dofs): the request leaves its
- *    slot and joins the lockstep batch of its hierarchy (number of levels,
- *    mode), whose stepper thread advances every member one CG step per tick
- *    with the operator applies of all members batched into one launch per
- *    (precision, degree) (see pa_gmg_pcg_solve_batch); members join and
- *    leave between ticks (continuous batching);
+ *    slot and joins the lockstep batch of its solve mode -- any degree and
+ *    hierarchy depth -- whose stepper thread advances every member one CG
+ *    step per tick with the operator applies of all members batched into
+ *    one persistent launch pair per precision (see pa_gmg_pcg_solve_batch);
+ *    members join and leave between ticks (continuous batching);
  *  - otherwise the worker solves it with pa_gmg_pcg_solve on the solver's
  *    stream, overlapping with everything else on the GPU.
  * Finished requests release their memory and the next queued ones are
@@ -501,6 +544,13 @@ int pa_server_poll(pa_server *s, int64_t ticket, int *done);
  * solution if the request kept it; info and timing may be NULL. */
 int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, pa_solve_info *info,
                    pa_request_timing *timing);
+/* Cancels a request: a queued one completes at once with PA_ECANCELED
+ * (it held no memory); a running one ends with PA_ECANCELED at its next CG
+ * step (solved by a worker) or before the next lockstep tick (batch lane),
+ * and its memory is released; a finished one is left as it is.  The caller
+ * still collects the ticket with pa_server_wait.  PA_OK, or PA_EINVAL for an
+ * unknown ticket.  No counterpart in the paper (a serving control). */
+int pa_server_cancel(pa_server *s, int64_t ticket);
 int pa_server_stats(pa_server *s, pa_server_stats_t *out);
 /* Finishes queued and running requests, then stops the workers. */
 int pa_server_destroy(pa_server *s);

@@ -17,7 +17,7 @@ import numpy as np
 
 from .build import LIB as _LIB_PATH
 
-PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY = range(8)
+PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY, PA_ECANCELED = range(9)
 PA_FP64, PA_FP32 = 0, 1
 PA_SOLVE_FP64, PA_SOLVE_MIXED, PA_SOLVE_MIXED_FCG = 0, 1, 2
 
@@ -89,6 +89,7 @@ _sig("pa_op_rhs", [_vp, _dp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_set_material", [_vp, _dp])
 _sig("pa_op_set_anisotropic", [_vp, _dp])
 _sig("pa_op_check", [_vp])
+_sig("pa_op_set_wait_limit", [_vp, ctypes.c_double])
 _sig("pa_op_apply_stage", [_vp, ctypes.c_int, _vp, _vp, _vp])
 _sig("pa_op_traction", [_vp, ctypes.c_int, _dp, _vp, _vp])
 _sig("pa_op_assemble_p1", [_vp, _vp, _vp])
@@ -108,6 +109,7 @@ _sig("pa_server_poll", [_vp, ctypes.c_int64, _ip])
 _sig("pa_server_wait", [_vp, ctypes.c_int64, _dp, ctypes.c_int64, ctypes.POINTER(pa_solve_info),
                         ctypes.POINTER(pa_request_timing)])
 _sig("pa_server_stats", [_vp, ctypes.POINTER(pa_server_stats_t)])
+_sig("pa_server_cancel", [_vp, ctypes.c_int64])
 _sig("pa_server_destroy", [_vp])
 _sig("pa_server_set_option", [_vp, ctypes.c_int, ctypes.c_double])
 if hasattr(lib, "pa_solver_create"):
@@ -327,6 +329,11 @@ def pa_op_check(op):
     _check(lib.pa_op_check(op), "pa_op_check")
 
 
+def pa_op_set_wait_limit(op, seconds):
+    """Budget (s) of the operator's bounded device waits (tensor-core variant)."""
+    _check(lib.pa_op_set_wait_limit(op, float(seconds)), "pa_op_set_wait_limit")
+
+
 def pa_op_set_anisotropic(op, cvoigt):
     """Per-element symmetric 6x6 Voigt matrices [ne, 6, 6]; None restores the isotropic material."""
     if cvoigt is None:
@@ -375,7 +382,7 @@ def pa_op_profile_read(op):
     return te.value, ta.value, n.value
 
 
-def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=300, mode=PA_SOLVE_FP64):
+def pa_solver_create(op, p_levels, cheb_order=4, coarse_rtol=1e-4, coarse_maxit=300, mode=PA_SOLVE_FP64):
     h = _vp()
     lv = (ctypes.c_int * len(p_levels))(*p_levels)
     _check(lib.pa_solver_create(op, len(p_levels), lv, cheb_order, coarse_rtol, coarse_maxit, mode,
@@ -383,7 +390,7 @@ def pa_solver_create(op, p_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=
     return h
 
 
-def pa_solver_create_hp(op, p_levels, h_levels, cheb_order=2, coarse_rtol=1e-4, coarse_maxit=300,
+def pa_solver_create_hp(op, p_levels, h_levels, cheb_order=4, coarse_rtol=1e-4, coarse_maxit=300,
                         mode=PA_SOLVE_FP64):
     """p-levels on the operator's mesh, then `h_levels` p = 1 levels on meshes
     coarsened by two per direction (uniform refinement undone)."""
@@ -397,6 +404,11 @@ def pa_solver_create_hp(op, p_levels, h_levels, cheb_order=2, coarse_rtol=1e-4, 
 PA_SOLVER_OPT_GRAPHS = 1
 PA_SOLVER_OPT_PERSISTENT_COARSE = 2
 PA_SOLVER_OPT_COARSE_HMG = 3
+PA_SOLVER_OPT_CHEB_LOWER = 4
+PA_SOLVER_OPT_CHEB_UPPER = 5
+PA_SOLVER_OPT_POWER_ITERS = 6
+PA_SOLVER_OPT_WAIT_LIMIT = 7
+PA_SOLVER_OPT_INJECT_INNER_FAILURE = 8
 
 
 def pa_solver_set_option(h, option, value):
@@ -486,6 +498,11 @@ PA_SERVER_OPT_H_LEVELS = 4
 
 def pa_server_set_option(srv, option, value):
     _check(lib.pa_server_set_option(srv, option, float(value)), "pa_server_set_option")
+
+
+def pa_server_cancel(srv, ticket):
+    """Cancel a queued or running request (collect it with pa_server_wait)."""
+    _check(lib.pa_server_cancel(srv, ticket), "pa_server_cancel")
 
 
 def pa_server_stats(srv):

@@ -117,6 +117,7 @@ static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t
     a.g = op->g;
     a.cvoigt = static_cast<const T *>(op->d_cv);
     a.err = op->d_err;
+    a.wait_cycles = op->wait_cycles;
     const Tables<T> *tab;
     if constexpr (sizeof(T) == 8) tab = &op->tab64;
     else tab = &op->tab32;
@@ -459,10 +460,21 @@ int apply_batch_async(pa_op *const *ops, const void *const *xs, void *const *ys,
         if (o2.empty()) return PA_OK;
         return apply_batch_async(o2.data(), x2.data(), y2.data(), (int)o2.size(), s);
     }
-    // groups of equal (precision, degree), in first-appearance order
+    // operators the persistent multi launch reproduces bitwise: one launch
+    // pair per precision for any mix of degrees
+    std::vector<int> multi[2], rest;
+    for (int k = 0; k < count; ++k) {
+        if (multi_eligible(ops[k])) multi[ops[k]->precision == PA_FP64 ? 0 : 1].push_back(k);
+        else rest.push_back(k);
+    }
+    if (!multi[0].empty())
+        if (int rc = apply_multi_group<double>(ops, xs, ys, multi[0], s)) return rc;
+    if (!multi[1].empty())
+        if (int rc = apply_multi_group<float>(ops, xs, ys, multi[1], s)) return rc;
+    // the others: groups of equal (precision, degree), in first-appearance order
     std::vector<std::vector<int>> groups;
     std::vector<std::pair<int, int>> keys;
-    for (int k = 0; k < count; ++k) {
+    for (int k : rest) {
         std::pair<int, int> key{ops[k]->precision, ops[k]->p};
         size_t g = 0;
         while (g < keys.size() && keys[g] != key) ++g;
@@ -697,6 +709,17 @@ int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *t
     if (variant) *variant = op->launch.variant;
     if (elems_per_block) *elems_per_block = op->launch.epb;
     if (threads) *threads = op->launch.threads;
+    return PA_OK;
+}
+
+int pa_op_set_wait_limit(pa_op *op, double seconds)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_set_wait_limit: null op");
+    if (!(seconds > 0.0 && seconds <= 60.0)) return set_error(PA_EINVAL, "pa_op_set_wait_limit: seconds in (0, 60]");
+    int dev = 0, khz = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    PA_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    op->wait_cycles = std::max(1LL, (long long)(seconds * (double)khz * 1e3));
     return PA_OK;
 }
 

@@ -29,8 +29,9 @@
 // into TF32 hi / lo, to the rows of the next sweep's A operand (a transpose
 // through shared memory).  Operands are K-major without swizzle: core matrices of 8 rows x
 // 16 bytes, LBO 128 B along K, SBO (K / 4) * 128 B along M.  Every wait on
-// the tensor core is bounded; on timeout the kernel flags a.err, frees its
-// TMEM and returns.
+// the tensor core is bounded (the operator's wait budget, then a drain of
+// the MMAs in flight); on timeout the kernel flags a.err, frees its TMEM and
+// returns.
 #pragma once
 
 #include <cstdint>
@@ -235,12 +236,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) pa_apply_tc_kernel(ApplyArgs<fl
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar)));
         }
         uint32_t done = 0;
+        // the operator's wait budget (a.wait_cycles of SM clock)
+        const long long t0 = clock64();
+        while (!done && clock64() - t0 < a.wait_cycles)
+            asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+                         : "=r"(done) : "r"(saddr(mbar)), "r"(phase));
+        const bool late = !done;
+        // past the budget the sweep counts as failed, but the MMAs in flight
+        // must still finish before the TMEM they write is reused or freed:
+        // drain with the fixed bound
         for (int it = 0; it < (1 << 24) && !done; ++it)
             asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
                          : "=r"(done) : "r"(saddr(mbar)), "r"(phase));
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        return done != 0;
+        // one decision for the whole CTA (every thread leaves or stays)
+        return __syncthreads_or(late || !done) == 0;
     };
 
     for (int64_t b = blockIdx.x; b < nbatch && ok; b += gridDim.x) {

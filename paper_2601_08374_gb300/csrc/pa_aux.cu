@@ -171,6 +171,45 @@ __global__ void assemble_batch_kernel(AssembleBatch<T> b)
     }
 }
 
+// Node sums of operators of any degree (AssembleMulti): every node finds
+// its operator by bisection over the prefix sums and runs the node sum of
+// that operator's degree.
+template <typename T>
+__global__ void __launch_bounds__(256) assemble_multi_kernel(AssembleMulti<T> m)
+{
+    const int64_t total = m.node_start[m.count];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = m.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (m.node_start[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int k = lo;
+        const int gn = (int)(t - m.node_start[k]);
+        switch (m.g[k].p) {
+#define PA_ASM_MULTI(P) \
+    case P: assemble_node_p<T, P>(m.ye[k], m.y[k], m.x[k], m.ess[k], T(0), 0, m.g[k], gn); break;
+            PA_ASM_MULTI(1) PA_ASM_MULTI(2) PA_ASM_MULTI(3) PA_ASM_MULTI(4)
+            PA_ASM_MULTI(5) PA_ASM_MULTI(6) PA_ASM_MULTI(7) PA_ASM_MULTI(8)
+#undef PA_ASM_MULTI
+        default: break;
+        }
+    }
+}
+
+template <typename T>
+int launch_assemble_multi(const AssembleMulti<T> &b, cudaStream_t s)
+{
+    const int64_t nodes = b.node_start[b.count];
+    if (nodes <= 0) return PA_OK;
+    assemble_multi_kernel<T><<<grid_for(nodes, 256), 256, 0, s>>>(b);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+template int launch_assemble_multi<double>(const AssembleMulti<double> &, cudaStream_t);
+template int launch_assemble_multi<float>(const AssembleMulti<float> &, cudaStream_t);
+
 constexpr int64_t kNode32 = (int64_t)1 << 31;
 
 template <typename T>

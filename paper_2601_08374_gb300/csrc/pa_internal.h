@@ -1,6 +1,7 @@
 // Internal declarations of the PA elasticity library (not part of the ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -93,6 +94,7 @@ struct ApplyArgs {
     Grid g;
     const T *cvoigt = nullptr;   // anisotropic material: 6x6 Voigt matrices times detJ, upper triangle [ne][21]
     int *err = nullptr;          // device flag set by a kernel whose bounded wait on the tensor core ran out
+    long long wait_cycles = 4000000000LL;  // that wait's budget in SM clock cycles (about 2 s)
     T *qvec = nullptr;         // ablation stages only: quadrature values [ne][3][3][Q^3]
     const T *ctensor = nullptr;  // ablation stages only: elasticity tensor per element [ne][81]
 };
@@ -124,6 +126,29 @@ struct AssembleBatch {
 };
 template <typename T>
 int launch_assemble_batch(const AssembleBatch<T> &b, cudaStream_t s);
+
+// Operators of any degree in one persistent launch pair (pa_apply_multi.cu):
+// the node sums of up to kMaxMulti operators in one assembly launch.
+constexpr int kMaxMulti = 96;
+template <typename T>
+struct AssembleMulti {
+    int count;
+    int64_t node_start[kMaxMulti + 1];  // prefix sum of nodes per operator
+    const T *ye[kMaxMulti];
+    T *y[kMaxMulti];
+    const T *x[kMaxMulti];
+    const uint8_t *ess[kMaxMulti];
+    Grid g[kMaxMulti];
+};
+template <typename T>
+int launch_assemble_multi(const AssembleMulti<T> &b, cudaStream_t s);
+// Whether the multi launch reproduces the operator's own apply bitwise.
+bool multi_eligible(const pa_op *op);
+// y_k = A_k x_k for the operators idx of one precision (all multi-eligible):
+// one element launch and one assembly launch per kMaxMulti operators.
+template <typename T>
+int apply_multi_group(pa_op *const *ops, const void *const *xs, void *const *ys, const std::vector<int> &idx,
+                      cudaStream_t s);
 template <typename T>
 size_t apply_smem_bytes(int p, const ApplyLaunch &cfg);
 ApplyLaunch default_apply_launch(int p, int precision);
@@ -177,6 +202,12 @@ int lockstep_tick(Lockstep *L);
 int lockstep_active(const Lockstep *L);
 void lockstep_take_done(Lockstep *L, std::vector<LockstepDone> &out);
 int lockstep_key(const pa_solver *s);
+// Ends member `tag` between ticks with PA_ECANCELED (its LockstepDone is
+// queued like a finished member's).
+int lockstep_cancel(Lockstep *L, void *tag);
+// The solve of s ends with PA_ECANCELED at its next CG step once *flag != 0
+// (null: never).
+void solver_set_cancel(pa_solver *s, const std::atomic<int> *flag);
 
 }  // namespace pa
 
@@ -206,6 +237,7 @@ struct pa_op {
     std::vector<double> h_cv;      // per-element anisotropic 6x6 Voigt matrices [ne][36], empty if isotropic
     void *d_cv = nullptr;          // device copy: upper triangles times detJ [ne][21] in the op's precision
     int *d_err = nullptr;          // set when a tensor-core wait timed out (pa_op_check)
+    long long wait_cycles = 4000000000LL;  // budget of those waits (pa_op_set_wait_limit)
     // ablation stages (pa_op_apply_stage), allocated on first use:
     // Q values [ne][9][Q^3], elasticity tensors [ne][81], dense basis-gradient
     // tables [3][D^3][Q^3] and weighted transposed [3][Q^3][D^3]

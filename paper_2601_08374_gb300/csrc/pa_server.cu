@@ -18,6 +18,7 @@
 // arithmetic of single ones), so a request gives the same bits alone or in
 // any mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -36,6 +37,8 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+constexpr int kServerChebOrder = 4;  // Chebyshev degree of the served solves
+
 struct Ticket {
     int64_t id = 0;
     pa_request req{};
@@ -50,6 +53,7 @@ struct Ticket {
     double setup_s = 0.0, solve_s = 0.0;
     int batched = 0;
     std::vector<double> x;  // host copy of the solution when requested
+    std::atomic<int> cancel{0};  // pa_server_cancel of a running request
 };
 
 // Device resources of one request between setup and completion.
@@ -186,11 +190,14 @@ int setup_request(pa_server *srv, Ticket &t, Res &res)
         if ((rc = pa_op_setup(mesh, r.p, 0, lam, mu, PA_FP64, ess.empty() ? nullptr : ess.data(), &res.op))) break;
         pa_mesh_destroy(mesh);
         mesh = nullptr;
-        if ((rc = pa_solver_create_hp(res.op, (int)t.levels.size(), t.levels.data(), t.hlev, 2, 1e-2, 10, r.mode,
-                                      &res.sol)))
+        // Chebyshev degree 4 on [0.05, 1.2] lambda_max: the fastest setting of
+        // the measured degree / interval sweep on beams and cubes
+        if ((rc = pa_solver_create_hp(res.op, (int)t.levels.size(), t.levels.data(), t.hlev, kServerChebOrder, 1e-2, 10,
+                                      r.mode, &res.sol)))
             break;
         // concurrent solvers must not each hold a grid-wide barrier
         pa_solver_set_option(res.sol, PA_SOLVER_OPT_PERSISTENT_COARSE, 0.0);
+        pa::solver_set_cancel(res.sol, &t.cancel);
         const size_t n = (size_t)res.op->ndofs();
         if (cudaMalloc((void **)&res.b, n * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void **)&res.x, n * sizeof(double)) != cudaSuccess) {
@@ -214,6 +221,7 @@ void record_result(Ticket &t, Res &res, int status, const pa_solve_info &info, c
 {
     t.status = status;
     t.info = info;
+    if (status == PA_ECANCELED) t.info.status = PA_ECANCELED;
     if (status != PA_OK) t.error = err;
     if (t.req.keep_solution && res.x && status != PA_EINVAL) {
         const size_t n = (size_t)res.op->ndofs();
@@ -304,6 +312,10 @@ void stepper_main(pa_server *srv, Stepper *sp)
             if (rc) finish(job, rc, pa_solve_info{}, rc_create ? create_err : std::string(pa_last_error()));
             else active.push_back(job);
         }
+        // members canceled since the last tick leave before the next one
+        if (!rc_create)
+            for (BatchJob *job : active)
+                if (job->t->cancel.load()) pa::lockstep_cancel(L, job);
         int stepped = 0;
         if (!rc_create && pa::lockstep_active(L) > 0) {
             stepped = pa::lockstep_active(L);
@@ -390,7 +402,11 @@ void worker_main(pa_server *srv)
             srv->cv_work.notify_all();
             continue;
         }
-        if (rc == PA_OK) {
+        if (rc == PA_OK && t->cancel.load()) {
+            rc = pa::set_error(PA_ECANCELED, "server: request canceled during its setup");
+            t->solve_s = 0.0;
+            record_result(*t, res, rc, pa_solve_info{}, pa_last_error());
+        } else if (rc == PA_OK) {
             pa_solve_info info{};
             rc = pa_gmg_pcg_solve(res.sol, res.b, res.x, t->req.rtol, t->req.maxit, &info, res.st);
             t->solve_s = std::chrono::duration<double>(clk::now() - t_setup).count();
@@ -507,6 +523,34 @@ int pa_server_wait(pa_server *s, int64_t ticket, double *x_host, int64_t x_len, 
     }
     if (t->status != PA_OK) set_error(t->status, t->error);
     return t->status;
+}
+
+int pa_server_cancel(pa_server *s, int64_t ticket)
+{
+    if (!s) return set_error(PA_EINVAL, "pa_server_cancel: null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return set_error(PA_EINVAL, "pa_server_cancel: unknown ticket");
+    Ticket &t = *it->second;
+    if (t.state == 0) {
+        // still queued: it holds no memory and never starts
+        auto q = std::find(s->queue.begin(), s->queue.end(), it->second);
+        if (q != s->queue.end()) s->queue.erase(q);
+        t.state = 2;
+        t.status = PA_ECANCELED;
+        t.info.status = PA_ECANCELED;
+        t.error = "server: request canceled before admission";
+        t.t_start = t.t_end = clk::now();
+        ++s->completed;
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    } else if (t.state == 1) {
+        // running: its setup is skipped past, its solve ends at the next CG
+        // step (worker) or before the next tick (batch lane)
+        t.cancel.store(1);
+        s->cv_lane.notify_all();
+    }
+    return PA_OK;
 }
 
 int pa_server_stats(pa_server *s, pa_server_stats_t *out)

@@ -23,6 +23,7 @@
 // PA_SOLVE_MIXED_FCG is the FP64 flexible CG preconditioned by the FP32
 // V-cycle.  The coarse-level solve is FP64 in every mode.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -551,11 +552,11 @@ __global__ void k_cg_spmv_pq(Dev d, const double *__restrict__ vals, const doubl
 // four kernel launches.  Every CTA adds the per-CTA partial sums itself in
 // the same fixed order, so all CTAs take the same decisions and the result
 // is deterministic.  The barrier's spin is bounded by time; on expiry the
-// kernel raises F_CTIMEOUT and returns.
+// kernel raises F_CTIMEOUT and returns.  The bound is the solver's wait
+// budget (PA_SOLVER_OPT_WAIT_LIMIT, 2 s by default) in SM clock cycles.
 enum { F_CTIMEOUT = 3 };
-constexpr long long kBarrierLimitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
-__device__ inline bool grid_barrier(unsigned *bar, int *timeout_flag)
+__device__ inline bool grid_barrier(unsigned *bar, int *timeout_flag, long long limit_cycles)
 {
     __shared__ int ok;
     __syncthreads();
@@ -571,7 +572,7 @@ __device__ inline bool grid_barrier(unsigned *bar, int *timeout_flag)
         } else {
             const long long t0 = clock64();
             while (*gen == g0) {
-                if (clock64() - t0 > kBarrierLimitCycles || *(volatile int *)timeout_flag) {
+                if (clock64() - t0 > limit_cycles || *(volatile int *)timeout_flag) {
                     atomicExch(timeout_flag, 1);
                     ok = 0;
                     break;
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
                                                  double *__restrict__ r, double *__restrict__ p, double *__restrict__ q,
                                                  const double *__restrict__ dinv, const double *__restrict__ b,
                                                  const uint8_t *__restrict__ ess, Grid g, double tol2, int maxit,
-                                                 unsigned *bar, double *part)
+                                                 unsigned *bar, double *part, long long wait_cycles)
 {
     const int64_t n = 3 * g.Nn;
     double *pA = part, *pB = part + 3 * kRedBlocks, *pC = part + 6 * kRedBlocks;
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
         v2[1] += bi * bi;
     }
     publish<2>(pC, v2);
-    if (!grid_barrier(bar, tflag)) return;
+    if (!grid_barrier(bar, tflag, wait_cycles)) return;
     all_sum<2>(pC, t2);
     double rz = t2[0];
     const double bb = t2[1];
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
             v1[0] += p[row] * y;
         }
         publish<1>(pA, v1);
-        if (!grid_barrier(bar, tflag)) return;
+        if (!grid_barrier(bar, tflag, wait_cycles)) return;
         all_sum<1>(pA, t1);
         const double pq = t1[0];
         if (!(pq > 0.0) || !isfinite(pq)) break;
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
             v2[1] += ri * dinv[i] * ri;
         }
         publish<2>(pB, v2);
-        if (!grid_barrier(bar, tflag)) return;
+        if (!grid_barrier(bar, tflag, wait_cycles)) return;
         all_sum<2>(pB, t2);
         rr = t2[0];
         const double beta = t2[1] / rz;
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(256) k_cg_coop(Dev d, const double *__restrict
         ++it;
         if (rr <= tol2 * bb || !isfinite(rr)) break;
         GRID_STRIDE(i, n) p[i] = dinv[i] * r[i] + beta * p[i];
-        if (!grid_barrier(bar, tflag)) return;
+        if (!grid_barrier(bar, tflag, wait_cycles)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d.scal[C_RR] = rr;
@@ -1263,6 +1264,19 @@ struct pa_solver {
     double *xin = nullptr, *bin = nullptr;  // FP64 solve operates on these copies
     int mode = PA_SOLVE_FP64;
     int cheb_order = 2;
+    // Chebyshev target interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A) and
+    // the power iterations that estimate lambda_max
+    double cheb_lo = 0.05, cheb_hi = 1.2;
+    int power_its = 10;
+    // bound of the persistent coarse kernel's grid-barrier waits, in SM
+    // clock cycles (2 s at the device's clock by default)
+    long long wait_cycles = 4000000000LL;
+    int clock_khz = 2000000;  // SM clock of the device (its attribute, read at creation)
+    // test hook: the inner solve with this index (1-based) of the next
+    // iterative-refinement solve reports a breakdown (0: none)
+    int inject_inner_failure = 0;
+    // set by the owner (the server) to end the solve between CG steps
+    const std::atomic<int> *cancel = nullptr;
     double coarse_rtol = 1e-2;
     int coarse_maxit = 50;
     pa::Dev dev{};
@@ -1451,14 +1465,22 @@ double read_scalar(pa_solver *s, int slot, cudaStream_t st)
     return s->h_scal[slot];
 }
 
-// power iteration for lambda_max(D^-1 A) of level l (FP64), 10 steps from a
-// fixed pseudo-random start (Sec. 3.1)
+// Chebyshev centre and half-width of the interval [cheb_lo, cheb_hi] * lam
+void cheb_interval(const pa_solver *s, double lam, double *theta, double *delta)
+{
+    const double a = s->cheb_lo * lam, b = s->cheb_hi * lam;
+    *theta = 0.5 * (a + b);
+    *delta = 0.5 * (b - a);
+}
+
+// power iteration for lambda_max(D^-1 A) of level l (FP64), power_its (10 by
+// default, Sec. 3.1) steps from a fixed pseudo-random start
 int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
 {
     const int64_t n = L.n;
     k_random<<<blocks_for(n), 256, 0, st>>>(L.e, L.op->d_ess, n, 0x1234567ull + (uint64_t)L.p);
     double lam = 0.0;
-    for (int it = 0; it < 10; ++it) {
+    for (int it = 0; it < s->power_its; ++it) {
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, L.e, n, P_DEN);
         int rc = op_apply_async(L.op, L.e, L.t, false, st, nullptr);
         if (rc) return rc;
@@ -1476,10 +1498,7 @@ int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
     }
     PA_CUDA_TRY(cudaGetLastError());
     L.lmax = lam;
-    // Chebyshev interval [0.3, 1.2] * lambda_max
-    double a = 0.3 * lam, b = 1.2 * lam;
-    L.theta = 0.5 * (a + b);
-    L.delta = 0.5 * (b - a);
+    cheb_interval(s, lam, &L.theta, &L.delta);
     return PA_OK;
 }
 
@@ -1490,7 +1509,7 @@ int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
     const int64_t n = H.n;
     k_random<<<blocks_for(n), 256, 0, st>>>(H.e, H.ess, n, 0x5151ull + (uint64_t)n);
     double lam = 0.0;
-    for (int it = 0; it < 10; ++it) {
+    for (int it = 0; it < s->power_its; ++it) {
         k_norm2<double><<<red_blocks(n), kRedThreads, 0, st>>>(s->dev, H.e, n, P_DEN);
         k_stencil_apply<<<row3_blocks(n), 128, 0, st>>>(H.vals, H.e, H.t, H.g);
         k_cheb<double><<<blocks_for(n), 256, 0, st>>>(H.d, H.r, H.t, nullptr, H.dinv, 0.0, 1.0, 1, n);
@@ -1503,9 +1522,7 @@ int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
         k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.e, H.d, 1.0 / std::sqrt(num), n);
     }
     H.lmax = lam;
-    const double a = 0.3 * lam, b = 1.2 * lam;
-    H.theta = 0.5 * (a + b);
-    H.delta = 0.5 * (b - a);
+    cheb_interval(s, lam, &H.theta, &H.delta);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -1987,7 +2004,8 @@ int coarse_coop(pa_solver *s, cudaStream_t st)
     int maxit = s->coarse_maxit;
     unsigned *bar = s->bar;
     double *part = s->coop_part;
-    void *args[] = {&dv, &vals, &x, &r, &p, &q, &dinv, &b, &ess, &g, &tol2, &maxit, &bar, &part};
+    long long wait_cycles = s->wait_cycles;
+    void *args[] = {&dv, &vals, &x, &r, &p, &q, &dinv, &b, &ess, &g, &tol2, &maxit, &bar, &part, &wait_cycles};
     PA_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_cg_coop, dim3(s->coop_blocks), dim3(256), args, 0, st));
     return PA_OK;
 }
@@ -2267,6 +2285,10 @@ int fcg(pa_solver *s, const FcgVecs<T> &v, StepGraphs &sg, double tol2, double b
         return set_error(PA_EBREAKDOWN, "solver: non-finite value in the first preconditioned residual");
     }
     while (rr > tol2 * bb && it < maxit) {
+        if (s->cancel && s->cancel->load(std::memory_order_relaxed)) {
+            *iters = it;
+            return set_error(PA_ECANCELED, "solver: solve canceled");
+        }
         rc = step(false);
         if (rc) return rc;
         rr = s->h_scal[S_RR];
@@ -2508,7 +2530,6 @@ struct Lockstep {
     cudaEvent_t ev = nullptr;
     std::vector<LockMember> m;
     std::vector<LockstepDone> done;
-    size_t na = 0, nb = 0;  // phases per segment (equal for all members)
 };
 
 namespace {
@@ -2531,21 +2552,28 @@ void retire(Lockstep &L, LockMember &m, int rc_loop, bool converged)
 // applies between phases; the last phase is launched but not joined.
 int run_segment(Lockstep &L, bool second_half)
 {
-    const size_t nph = second_half ? L.nb : L.na;
+    // members may have different hierarchies, so different numbers of
+    // phases: phase round j runs phase j of every member that has one, then
+    // the applies that end those phases as one batched launch
+    auto seg = [&](LockMember &m) -> Segment & {
+        return second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
+    };
+    size_t nph = 0;
+    for (LockMember &m : L.m) nph = std::max(nph, seg(m).g.size());
     std::vector<pa_op *> ops;
     std::vector<const void *> xs;
     std::vector<void *> ys;
     for (size_t j = 0; j < nph; ++j) {
         for (LockMember &m : L.m) {
-            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
-            if (sg.g[j]) PA_CUDA_TRY(cudaGraphLaunch(sg.g[j], m.s->stream));
+            Segment &sg = seg(m);
+            if (j < sg.g.size() && sg.g[j]) PA_CUDA_TRY(cudaGraphLaunch(sg.g[j], m.s->stream));
         }
-        if (j + 1 == nph) break;
         ops.clear();
         xs.clear();
         ys.clear();
         for (LockMember &m : L.m) {
-            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
+            Segment &sg = seg(m);
+            if (j + 1 >= sg.g.size()) continue;  // its last phase (or none): no apply follows
             const ApplyRec &ap = sg.ap[j];
             if (!ap.op) continue;
             PA_CUDA_TRY(cudaEventRecord(m.ev, m.s->stream));
@@ -2559,8 +2587,8 @@ int run_segment(Lockstep &L, bool second_half)
         if (rc) return rc;
         PA_CUDA_TRY(cudaEventRecord(L.ev, L.st));
         for (LockMember &m : L.m) {
-            Segment &sg = second_half ? m.b[m.started ? 1 : 0] : m.a[m.started ? 1 : 0];
-            if (sg.ap[j].op) PA_CUDA_TRY(cudaStreamWaitEvent(m.s->stream, L.ev, 0));
+            Segment &sg = seg(m);
+            if (j + 1 < sg.g.size() && sg.ap[j].op) PA_CUDA_TRY(cudaStreamWaitEvent(m.s->stream, L.ev, 0));
         }
     }
     return PA_OK;
@@ -2627,21 +2655,31 @@ int lockstep_add(Lockstep *L, pa_solver *s, const double *b, double *x, double r
     rc = s->mode == PA_SOLVE_FP64 ? capture_member<double>(m) : capture_member<float>(m);
     if (!rc && cudaEventCreateWithFlags(&m.ev, cudaEventDisableTiming) != cudaSuccess)
         rc = cuda_error(cudaGetLastError(), "lockstep: cudaEventCreate");
-    if (!rc && !L->m.empty() && (m.a[0].g.size() != L->na || m.b[0].g.size() != L->nb))
-        rc = set_error(PA_EINVAL, "lockstep: solver hierarchy does not match the other members'");
     if (rc) {
         free_member(m);
         return rc;
-    }
-    if (L->m.empty()) {
-        L->na = m.a[0].g.size();
-        L->nb = m.b[0].g.size();
     }
     L->m.push_back(m);
     return PA_OK;
 }
 
-int lockstep_key(const pa_solver *s) { return (int)s->lv.size() * 16 + s->mode * 4 + s->cheb_order; }
+void solver_set_cancel(pa_solver *s, const std::atomic<int> *flag) { s->cancel = flag; }
+
+int lockstep_cancel(Lockstep *L, void *tag)
+{
+    for (size_t i = 0; i < L->m.size(); ++i) {
+        if (L->m[i].tag != tag) continue;
+        LockMember m = L->m[i];
+        L->m.erase(L->m.begin() + (std::ptrdiff_t)i);
+        retire(*L, m, set_error(PA_ECANCELED, "solver: solve canceled"), false);
+        return PA_OK;
+    }
+    return set_error(PA_EINVAL, "lockstep: no member with this tag");
+}
+
+// Members of any hierarchy step together; one lockstep per solve mode keeps
+// each lane's members of one precision mix.
+int lockstep_key(const pa_solver *s) { return s->mode; }
 
 int lockstep_tick(Lockstep *L)
 {
@@ -2874,6 +2912,9 @@ int pa_solver_create_hp(pa_op *fine, int nlev, const int *p_levels, int h_levels
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_coop, 256, 0) == cudaSuccess)
             s->coop_blocks = std::min(kCoopBlocks, per_sm * nsm);
+        int khz = 0;
+        if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) == cudaSuccess && khz > 0) s->clock_khz = khz;
+        s->wait_cycles = (long long)(2.0 * s->clock_khz * 1e3);
         cudaGetLastError();
     }
 
@@ -3016,6 +3057,63 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
         else s->use_hmg = value != 0.0;
         return PA_OK;
     }
+    case PA_SOLVER_OPT_CHEB_LOWER:
+    case PA_SOLVER_OPT_CHEB_UPPER:
+    case PA_SOLVER_OPT_POWER_ITERS: {
+        if (option == PA_SOLVER_OPT_POWER_ITERS) {
+            if (!(value >= 1.0 && value <= 1000.0)) return set_error(PA_EINVAL, "pa_solver_set_option: power iterations in 1..1000");
+        } else {
+            const double lo = option == PA_SOLVER_OPT_CHEB_LOWER ? value : s->cheb_lo;
+            const double hi = option == PA_SOLVER_OPT_CHEB_UPPER ? value : s->cheb_hi;
+            if (!(lo > 0.0) || !(hi > lo) || !(hi < 100.0))
+                return set_error(PA_EINVAL, "pa_solver_set_option: need 0 < lower < upper < 100 (fractions of lambda_max)");
+        }
+        // the step graphs hold the Chebyshev coefficients as kernel arguments
+        for (StepGraphs *g : {&s->g64, &s->g32, &s->gmx}) {
+            if (g->init) cudaGraphExecDestroy(g->init);
+            if (g->iter) cudaGraphExecDestroy(g->iter);
+            g->init = g->iter = nullptr;
+        }
+        if (option == PA_SOLVER_OPT_CHEB_LOWER) s->cheb_lo = value;
+        else if (option == PA_SOLVER_OPT_CHEB_UPPER) s->cheb_hi = value;
+        else s->power_its = (int)value;
+        cudaStream_t st = s->stream;
+        // smoothed levels are the ones with an estimate (the assembled p = 1
+        // level is solved, not smoothed; the last h-level is a dense solve)
+        for (Level &L : s->lv) {
+            if (!(L.lmax > 0.0)) continue;
+            if (option == PA_SOLVER_OPT_POWER_ITERS) {
+                if (int rc = estimate_lmax(s, L, st)) return rc;
+            } else {
+                cheb_interval(s, L.lmax, &L.theta, &L.delta);
+            }
+        }
+        for (HLevel &H : s->hl) {
+            if (!(H.lmax > 0.0)) continue;
+            if (option == PA_SOLVER_OPT_POWER_ITERS) {
+                if (int rc = h_power_lmax(s, H, st)) return rc;
+            } else {
+                cheb_interval(s, H.lmax, &H.theta, &H.delta);
+            }
+        }
+        PA_CUDA_TRY(cudaStreamSynchronize(st));
+        return PA_OK;
+    }
+    case PA_SOLVER_OPT_WAIT_LIMIT: {
+        if (!(value > 0.0 && value <= 60.0)) return set_error(PA_EINVAL, "pa_solver_set_option: wait limit in (0, 60] s");
+        // the limit is a kernel argument of the captured step graphs
+        for (StepGraphs *g : {&s->g64, &s->g32, &s->gmx}) {
+            if (g->init) cudaGraphExecDestroy(g->init);
+            if (g->iter) cudaGraphExecDestroy(g->iter);
+            g->init = g->iter = nullptr;
+        }
+        s->wait_cycles = std::max(1LL, (long long)(value * s->clock_khz * 1e3));
+        return PA_OK;
+    }
+    case PA_SOLVER_OPT_INJECT_INNER_FAILURE:
+        if (!(value >= 0.0 && value <= 1e6)) return set_error(PA_EINVAL, "pa_solver_set_option: inner-failure index >= 0");
+        s->inject_inner_failure = (int)value;
+        return PA_OK;
     default: return set_error(PA_EINVAL, "pa_solver_set_option: unknown option");
     }
 }
@@ -3087,6 +3185,13 @@ int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int 
             int it = 0;
             // inner solve: relative reduction 1e-4 or at most 50 iterations
             const int inner_cap = std::min(50, maxit - total_inner);
+            if (s->inject_inner_failure == refine + 1) {
+                // host-side fault injection (test hook, one shot): this inner
+                // solve reports a breakdown without running
+                s->inject_inner_failure = 0;
+                rc = set_error(PA_EBREAKDOWN, "solver: inner solve failure injected (PA_SOLVER_OPT_INJECT_INNER_FAILURE)");
+                break;
+            }
             rc = fcg<float>(s, v, s->g32, 1e-8, 1.0, inner_cap, &it, st);
             if (rc) break;
             inner_truncated = inner_cap < 50 && it == inner_cap;

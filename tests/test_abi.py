@@ -80,6 +80,12 @@ def test_argument_checks_before_any_device_call(pa):
     assert not out.value
     assert lib.pa_solver_create_hp(None, 3, lv, 1, 2, 1e-2, 10, 0, None) == pa.PA_EINVAL
     assert b"null" in lib.pa_last_error()
+    assert lib.pa_server_cancel(None, 1) == pa.PA_EINVAL
+    assert lib.pa_op_set_wait_limit(None, 1.0) == pa.PA_EINVAL
+    assert lib.pa_solver_set_option(None, pa.PA_SOLVER_OPT_WAIT_LIMIT, 1.0) == pa.PA_EINVAL
+    t = ctypes.c_double()
+    assert lib.pa_measure_fma_rate(7, ctypes.byref(t), None) == pa.PA_EINVAL
+    assert lib.pa_measure_fma_rate(0, None, None) == pa.PA_EINVAL
 
 
 def test_flop_model_reproduces_table6():

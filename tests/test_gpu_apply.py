@@ -637,3 +637,51 @@ def test_apply_largest_served_size_sampled(pa, prec):
     rows = np.concatenate([rng.choice(N, 2000, replace=False), [0, 1, 256, 257, N // 3, N - 1]])
     yo = oracle.apply_rows(p, n, n, n, m.affine, lam, mu, x, rows, ess=ess)
     assert np.max(np.abs(y[rows] - yo)) <= TOL[prec] * np.max(np.abs(yo))
+
+
+def test_multi_operator_launch_any_degrees(pa):
+    """The persistent multi-operator launch: operators of every degree
+    1..8, both precisions, uneven sizes (one element to a few hundred),
+    constrained or not, FP32 ones in the unsplit and split forms, plus
+    operators it does not hold (FP32 flat and tensor-core shapes, FP64 line
+    shapes) that take the per-degree path -- all in one batched call; every
+    result within the operator tolerance of the oracle and bitwise the
+    operator's own apply (except tensor-core shapes, which a batch runs as
+    the register-tiled line variant)."""
+    rng = np.random.default_rng(57)
+    ops, xs, refs, probs = [], [], [], []
+    k = 0
+    for p in range(1, 9):
+        for prec in (0, 1):
+            for launch in (None, "alt"):
+                dims = tuple(int(v) for v in rng.integers(1, 5, 3)) if (p + prec) % 3 else (1, 1, 1)
+                m = syn.random_affine_cube(dims[0], seed=1900 + k, ny=dims[1], nz=dims[2])
+                ess = syn.clamp_mask(m, p) if k % 2 else None
+                op = pa.Operator(*dims, m.affine, p, 1.3, 0.6, precision=prec, ess_mask=ess)
+                if launch == "alt":
+                    if prec == 1:
+                        v = [6, 3, 0, 4][k % 4]
+                        if v == 4 and p > 6:
+                            v = 3
+                        shape = (v, 128 // (p + 2) ** 2, 384) if v == 4 else (v, 2, 128)
+                    else:
+                        shape = (2, 1, 128) if p <= 4 else (0, 1, 128)
+                    pa.pa_op_set_launch(op.h, *shape)
+                x = torch.tensor(syn.uniform_vector(op.ndofs, seed=k), dtype=op.dtype, device="cuda")
+                ops.append(op)
+                xs.append(x)
+                refs.append(op.apply(x).clone())
+                probs.append((p, prec, m, ess))
+                k += 1
+    order = rng.permutation(len(ops))
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    pa.pa_op_apply_batch([ops[i].h for i in order], [xs[i] for i in order], [ys[i] for i in order])
+    torch.cuda.synchronize()
+    for i in range(len(ops)):
+        if pa.pa_op_get_launch(ops[i].h)[0] != 4:  # a batch runs tensor-core shapes as the line variant
+            assert torch.equal(ys[i], refs[i]), (i, probs[i][:2], pa.pa_op_get_launch(ops[i].h))
+        p, prec, m, ess = probs[i]
+        yo = oracle.apply(p, m.nx, m.ny, m.nz, m.affine, 1.3, 0.6, xs[i].double().cpu().numpy(), ess=ess)
+        assert _relerr(ys[i].double().cpu().numpy(), yo) <= TOL[prec], (i, p, prec)
+    for o in ops:
+        o.close()

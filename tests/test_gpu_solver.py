@@ -210,7 +210,10 @@ def test_lockstep_batch_equals_solo_solves(pa, mode):
         op.close()
 
 
-def test_lockstep_batch_rejects_mixed_hierarchies_and_refinement_mode(pa):
+def test_lockstep_batch_takes_mixed_hierarchies_and_rejects_refinement_mode(pa):
+    """Hierarchies of different depths share a lockstep (same results as
+    solo); iterative refinement, whose host decisions sit between inner
+    solves, is refused."""
     lam, mu = syn.lame(1.0, 0.3)
     m = _beam(4, 1, 1)
     ops, sols = [], []
@@ -220,10 +223,15 @@ def test_lockstep_batch_rejects_mixed_hierarchies_and_refinement_mode(pa):
         sols.append(pa.pa_solver_create(op.h, levels, 2, 1e-3, 300, mode))
     bs = [op.rhs(f0=(0.0, 0.0, -1.0)) for op in ops]
     xs = [torch.zeros_like(b) for b in bs]
-    for pair in ([0, 1], [0, 2]):
-        with pytest.raises(pa.PAError) as ei:
-            pa.pa_gmg_pcg_solve_batch([sols[i] for i in pair], [bs[i] for i in pair], [xs[i] for i in pair])
-        assert ei.value.code == pa.PA_EINVAL
+    code, infos = pa.pa_gmg_pcg_solve_batch([sols[0], sols[1]], [bs[0], bs[1]], [xs[0], xs[1]])
+    assert code == pa.PA_OK
+    for i in (0, 1):
+        x = torch.zeros_like(bs[i])
+        c, info = pa.pa_gmg_pcg_solve(sols[i], bs[i], x)
+        assert c == pa.PA_OK and torch.equal(x, xs[i]) and info.iterations == infos[i].iterations
+    with pytest.raises(pa.PAError) as ei:
+        pa.pa_gmg_pcg_solve_batch([sols[0], sols[2]], [bs[0], bs[2]], [xs[0], xs[2]])
+    assert ei.value.code == pa.PA_EINVAL
     for s in sols:
         pa.pa_solver_destroy(s)
     for op in ops:
@@ -515,3 +523,44 @@ def test_mixed_precision_cube_p8_at_full_size(pa):
     r = bh[rows] - oracle.apply_rows(p, n, n, n, m.affine, lam, mu, xh, rows, ess=ess)
     assert np.max(np.abs(r)) <= 1e-8 * np.max(np.abs(bh))
     op.close()
+
+
+def test_lockstep_members_of_any_hierarchy(pa):
+    """Solves of different degrees and hierarchy depths (2-1, 4-2-1, 6-3-1,
+    8-4-2-1, 4-2-1 with two h-levels) and both flexible-CG modes step in
+    one lockstep: phase rounds batch whatever applies are ready; every
+    iterate, count and residual is bitwise the solo solve's, and each
+    solution matches the oracle's direct solve."""
+    lam, mu = syn.lame(1.0, 0.3)
+    specs = [(_beam(4, 1, 1), 2, [2, 1], 0, 0), (_beam(8, 2, 2), 4, [4, 2, 1], 0, 2),
+             (syn.random_affine_cube(2, seed=81), 6, [6, 3, 1], 0, 0), (_beam(2, 1, 1), 8, [8, 4, 2, 1], 0, 2),
+             (_beam(16, 4, 4), 4, [4, 2, 1], 2, 0), (_beam(6, 2, 1), 4, [4, 2, 1], 0, 2)]
+    ops, sols, bs = [], [], []
+    for m, p, lv, h, mode in specs:
+        ess = syn.clamp_mask(m, p)
+        op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+        s = pa.pa_solver_create_hp(op.h, lv, h, 2, 1e-3, 300, mode)
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_PERSISTENT_COARSE, 0)
+        ops.append(op)
+        sols.append(s)
+        bs.append(op.rhs(f0=(0.0, 0.0, -1.0)))
+    solo = []
+    for s, b in zip(sols, bs):
+        x = torch.zeros_like(b)
+        code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 300)
+        assert code == pa.PA_OK
+        solo.append((info.iterations, info.rel_residual, x))
+    xs = [torch.zeros_like(b) for b in bs]
+    code, infos = pa.pa_gmg_pcg_solve_batch(sols, bs, xs, 1e-10, 300)
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    for k, (m, p, lv, h, mode) in enumerate(specs):
+        assert infos[k].iterations == solo[k][0] and infos[k].rel_residual == solo[k][1], k
+        assert torch.equal(xs[k], solo[k][2]), k
+        ess = syn.clamp_mask(m, p)
+        bo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+        xo, _ = oracle.solve_sparse(p, m.nx, m.ny, m.nz, m.affine, lam, mu, bo, ess)
+        assert np.linalg.norm(xs[k].cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo), k
+    for s in sols:
+        pa.pa_solver_destroy(s)
+    for op in ops:
+        op.close()
