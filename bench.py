@@ -721,33 +721,43 @@ def run_serving(args, pa, torch):
     small_on_noh, _, st_small_noh = burst(small, args.serve_slots, batch=1, h_levels=0)
     rate = args.serve_load * cap
     arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
-    srv = pa.pa_server_create(budget, args.serve_slots)
-    tickets = [None] * len(reqs)
-    start = time.perf_counter()
 
-    def submitter():
-        for i, r in enumerate(reqs):
-            delay = arrivals[i] - (time.perf_counter() - start)
-            if delay > 0:
-                time.sleep(delay)
-            tickets[i] = pa.pa_server_submit(srv, r)
+    def stream(batch):
+        """The Poisson stream through a fresh server (lane on or off)."""
+        srv = pa.pa_server_create(budget, args.serve_slots)
+        pa.pa_server_set_option(srv, pa.PA_SERVER_OPT_BATCH, batch)
+        tickets = [None] * len(reqs)
+        start = time.perf_counter()
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    lat, statuses, iters, solve_s, hlev = [], [], [], [], []
-    for i in range(len(reqs)):
-        while tickets[i] is None:
-            time.sleep(0.001)
-        code, info, tm, _ = pa.pa_server_wait(srv, tickets[i])
-        statuses.append(code)
-        lat.append(tm.latency_s)
-        iters.append(info.iterations)
-        solve_s.append(tm.solve_s)
-        hlev.append(tm.h_levels)
-    th.join()
-    wall = time.perf_counter() - start
-    st = pa.pa_server_stats(srv)
-    pa.pa_server_destroy(srv)
+        def submitter():
+            for i, r in enumerate(reqs):
+                delay = arrivals[i] - (time.perf_counter() - start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = pa.pa_server_submit(srv, r)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        res = {"lat": [], "status": [], "iters": [], "solve_s": [], "hlev": []}
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.001)
+            code, info, tm, _ = pa.pa_server_wait(srv, tickets[i])
+            res["status"].append(code)
+            res["lat"].append(tm.latency_s)
+            res["iters"].append(info.iterations)
+            res["solve_s"].append(tm.solve_s)
+            res["hlev"].append(tm.h_levels)
+        th.join()
+        res["wall"] = time.perf_counter() - start
+        res["stats"] = pa.pa_server_stats(srv)
+        pa.pa_server_destroy(srv)
+        return res
+
+    off = stream(0) if args.serve_lane_off else None
+    on = stream(1)
+    lat, statuses, iters, solve_s, hlev = on["lat"], on["status"], on["iters"], on["solve_s"], on["hlev"]
+    wall, st = on["wall"], on["stats"]
     lat = np.array(lat)
     return {"requests": len(reqs), "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
             "calibration_requests": ncal,
@@ -764,9 +774,16 @@ def run_serving(args, pa, torch):
             "requests_with_h_levels": int(sum(1 for h in hlev if h > 0)),
             "ok": int(sum(1 for c in statuses if c == pa.PA_OK)),
             "calibration_ok": [fp64_ok, cal_ok, noh_ok],
+            "p99_over_p50": round(float(np.percentile(lat, 99) / np.percentile(lat, 50)), 3),
             "batch_lane": {"batched": int(st.batched), "ticks": int(st.batch_ticks),
                            "mean_members_per_tick": round(st.batch_member_ticks / max(st.batch_ticks, 1), 2),
                            "max_members": int(st.batch_max_members)},
+            "lane_off": None if off is None else {
+                "solves_per_s": round(len(reqs) / off["wall"], 3),
+                "p50_latency_s": round(float(np.percentile(off["lat"], 50)), 4),
+                "p99_latency_s": round(float(np.percentile(off["lat"], 99)), 4),
+                "p99_over_p50": round(float(np.percentile(off["lat"], 99) / np.percentile(off["lat"], 50)), 3),
+                "ok": int(sum(1 for c in off["status"] if c == pa.PA_OK))},
             "small_burst": {"requests": len(small), "recipe": "p U{2,4,6,8}; cube n^3, n ~ U{3..8}; mixed precision",
                             "solves_per_s_lane_off": round(small_off, 3), "solves_per_s_lane_on": round(small_on, 3),
                             "lane_speedup": round(small_on / small_off, 3), "ok": [small_off_ok, small_on_ok],
@@ -996,6 +1013,7 @@ def main(argv=None):
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
     ap.add_argument("--serve-calibration", type=int, default=16)
     ap.add_argument("--serve-small", type=int, default=64, help="small-solve burst served with and without batching")
+    ap.add_argument("--serve-lane-off", type=int, default=1, help="also serve the stream with the batch lane off")
     ap.add_argument("--ablation-ps", default="2,4,8", help="degrees of the Table 8 stage ladder ('' skips it)")
     ap.add_argument("--ablation-reps", type=int, default=5)
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 operator sweep of the FP64 line")
