@@ -20,6 +20,10 @@
 #include "pa_apply_line.cuh"
 #include "pa_apply_plane.cuh"
 
+#ifndef PA_MULTI_MIN_BLOCKS_F32
+#define PA_MULTI_MIN_BLOCKS_F32 1
+#endif
+
 namespace pa {
 
 // 1D tables of every degree (q = p + 2), both precisions: filled once per
@@ -122,8 +126,15 @@ __device__ __forceinline__ void multi_tile(const ApplyArgs<T> &a, int epb, int64
     }
 }
 
+// Threads per CTA and the minimum CTAs per SM the register allocation must
+// allow (every degree's body shares one register count: the largest).
 template <typename T>
-__global__ void __launch_bounds__(256) pa_apply_multi_kernel(MultiArgs<T> m)
+constexpr int kMultiThreads = sizeof(T) == 8 ? 256 : 128;
+template <typename T>
+constexpr int kMultiMinBlocks = sizeof(T) == 8 ? 1 : PA_MULTI_MIN_BLOCKS_F32;
+
+template <typename T>
+__global__ void __launch_bounds__(kMultiThreads<T>, kMultiMinBlocks<T>) pa_apply_multi_kernel(MultiArgs<T> m)
 {
     const int64_t total = m.cta_start[m.count];
     for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
@@ -179,7 +190,7 @@ int apply_multi_group(pa_op *const *ops, const void *const *xs, void *const *ys,
                       cudaStream_t s)
 {
     if (int rc = ensure_tables()) return rc;
-    const int threads = sizeof(T) == 8 ? 256 : 128;
+    const int threads = kMultiThreads<T>;
     int dev = 0, nsm = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     PA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
