@@ -214,9 +214,16 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
  * registers) or 4 (FP32, p <= 6: the six 1D contractions on the tensor
  * cores, tcgen05.mma kind::tf32 with three TF32 products per contraction
  * for FP32 accuracy, accumulators in TMEM; one shape: 384 threads and
- * floor(128 / (p+2)^2) elements per CTA); elements per CTA; threads per CTA
- * (32..512, multiple of 32; variants 1-3 at most 256; in FP64 variants 1
- * and 2 only for p <= 4).
+ * floor(128 / (p+2)^2) elements per CTA), 5 (FP32, p <= 6: plane-fused --
+ * one thread per (element, component, z-plane) does the X and Y sweeps of
+ * its plane in registers, one thread per quadrature column the fused Z
+ * stage, one thread per plane the Y^T and X^T sweeps; two barriers per CTA
+ * pass), 6 (FP32: as 5 with the Z stage on three lanes per column) or 7
+ * (FP32: as 2 with the fused Z stage in two passes through shared memory,
+ * half the registers per thread); variants 2, 5, 7 give the same bits, as
+ * do 3 and 6; elements per CTA; threads per CTA (32..512, multiple of 32;
+ * variants 1-3 and 5-7 at most 256; in FP64 variants 1 and 2 only for
+ * p <= 4, variants 4-7 not at all).
  * pa_op_set_launch rejects shapes whose shared memory exceeds 227 KB.
  * pa_op_setup starts from a per-degree default shape; on a mesh with fewer
  * than 2 x 152 x (its elements per CTA) elements the elements per CTA drop

@@ -4,7 +4,8 @@
 // variant 3 = variant 2 with the fused Z stage split over three lanes per column,
 // variant 4 = the contractions on the tensor cores (tcgen05, three-pass TF32; p <= 6),
 // variant 5 = plane-fused sweeps (X+Y and Y^T+X^T per plane in registers, p <= 6),
-// variant 6 = variant 5 with the fused Z stage split over three lanes per column.
+// variant 6 = variant 5 with the fused Z stage split over three lanes per column,
+// variant 7 = variant 2 with the fused Z stage in two passes (half the registers).
 #include <cstring>
 
 #include "pa_apply.cuh"
@@ -33,6 +34,7 @@ size_t smem_for(const ApplyLaunch &c)
     // variant 5 keeps 18 D column values per thread: up to D = 7
     if (c.variant == 5) return D <= 7 ? plane_smem_bytes<float, D, Q>(c.epb) : 0;
     if (c.variant == 6) return plane_smem_bytes<float, D, Q>(c.epb);
+    if (c.variant == 7) return line_smem_bytes<float, D, Q, true>(c.epb);
     if (c.variant == 3 || line_ok<D>) return line_smem_bytes<float, D, Q>(c.epb);
     return 0;
 }
@@ -43,6 +45,7 @@ int launch_for(const ApplyArgs<float> &a, const Tables<float> &tab, const ApplyL
     if (c.variant == 0) return launch_flat<float, D, Q>(a, tab, c, s);
     if (c.variant == 3) return launch_line<float, D, Q, true, true>(a, tab, c, s);
     if (c.variant == 6) return launch_plane<float, D, Q, true>(a, tab, c, s);
+    if (c.variant == 7) return launch_line<float, D, Q, true, false, true>(a, tab, c, s);
     if (c.variant == 5) {
         if constexpr (D <= 7) return launch_plane<float, D, Q, false>(a, tab, c, s);
         return set_error(PA_EINVAL, "apply variant 5 is instantiated for p <= 6 only");
@@ -62,6 +65,7 @@ int launch_batch_for(const BatchArgs<float> &b, const Tables<float> &tab, const 
     if (c.variant == 0) return launch_flat_batch<float, D, Q>(b, tab, c, s);
     if (c.variant == 3) return launch_line_batch<float, D, Q, true, true>(b, tab, c, s);
     if (c.variant == 6) return launch_plane_batch<float, D, Q, true>(b, tab, c, s);
+    if (c.variant == 7) return launch_line_batch<float, D, Q, true, false, true>(b, tab, c, s);
     if (c.variant == 5) {
         if constexpr (D <= 7) return launch_plane_batch<float, D, Q, false>(b, tab, c, s);
         return set_error(PA_EINVAL, "apply variant 5 is instantiated for p <= 6 only");

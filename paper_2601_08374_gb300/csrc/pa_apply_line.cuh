@@ -27,17 +27,22 @@
 
 namespace pa {
 
-template <typename T, int D, int Q>
+// TWO: the fused Z stage runs in two passes (z_columns_2pass) whose
+// quadrature values [col][qz][9] (column stride QS, odd) share buffer B.
+template <typename T, int D, int Q, bool TWO = false>
 struct LineLayout {
     static constexpr int DP = D | 1;                      // odd pitch for ix / iy
     static constexpr int CS = (9 * D) | 1;                // odd column stride of S2
     static constexpr int BS = 2 * Q + 1;                  // odd row stride of S3
+    static constexpr int QS = (9 * Q) | 1;                // odd column stride of the quadrature values
     static constexpr int S0 = 3 * D * D * DP;
     static constexpr int S1 = 3 * D * 2 * Q * DP;
     static constexpr int S2 = Q * Q * CS;
     static constexpr int S3 = 3 * D * D * BS;
+    static constexpr int SQ = TWO ? Q * Q * QS : 0;
     static constexpr int A = S0 > S2 ? S0 : S2;
-    static constexpr int B = S1 > S3 ? S1 : S3;
+    static constexpr int B13 = S1 > S3 ? S1 : S3;
+    static constexpr int B = B13 > SQ ? B13 : SQ;
     static constexpr int per_elem = A + B;
     // bytes of the per-CTA element table (global base node of each element),
     // placed after the value buffers
@@ -246,14 +251,122 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
     }
 }
 
+// The fused Z stage in two passes per column, to halve the registers a
+// thread holds (9 D inputs, then 9 D accumulators, instead of both): pass 1
+// runs the Z sweep, the pointwise stress of Eq. 7 and the Q reconstruction
+// and stores the column's 9 quadrature values per point to qbuf; pass 2
+// runs the Z^T sweep from them.  Every accumulator receives the same terms
+// in the same order as in z_columns, so the results are bitwise the same.
+template <typename T, int D, int Q>
+__device__ __forceinline__ void z_columns_2pass(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
+                                                T *qbuf, int qstride, int64_t e0, int ne_blk, int tid, int nt)
+{
+    constexpr int CS = LineLayout<T, D, Q>::CS;
+    constexpr int QS = LineLayout<T, D, Q, true>::QS;
+    for (int o = tid; o < ne_blk * Q * Q; o += nt) {
+        const int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
+        T *cp = bufA + (size_t)el * astride + col * CS;
+        T *qp = qbuf + (size_t)el * qstride + col * QS;
+        {
+            T in[9][D];
+#pragma unroll
+            for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+                for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
+            const T *geo = a.geo + (e0 + el) * kGeoStride;
+            T Ji[9], cj[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
+            const T cl = geo[9], cm = geo[10], m2 = cm + cm;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
+            // both qz loops stay rolled, with the table columns of one qz
+            // loaded per iteration: unrolled, the compiler hoists every
+            // point's loads and the register saving is lost
+#pragma unroll 1
+            for (int qz = 0; qz < Q; ++qz) {
+                T bq[D], gq[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    bq[i] = tab.B[i * Q + qz];
+                    gq[i] = tab.G[i * Q + qz];
+                }
+                T gr[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        g0 = fma(in[c * 3 + 0][i], bq[i], g0);
+                        g1 = fma(in[c * 3 + 1][i], bq[i], g1);
+                        g2 = fma(in[c * 3 + 2][i], gq[i], g2);
+                    }
+                    gr[c][0] = g0;
+                    gr[c][1] = g1;
+                    gr[c][2] = g2;
+                }
+                T dg[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    dg[c] = fma(Ji[c], gr[c][0], fma(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
+                const T ld = cl * (dg[0] + dg[1] + dg[2]);
+                T sg[3][3];
+                sg[0][0] = fma(m2, dg[0], ld);
+                sg[1][1] = fma(m2, dg[1], ld);
+                sg[2][2] = fma(m2, dg[2], ld);
+                auto shear = [&](int ia, int ib) {
+                    return fma(cj[ib], gr[ia][0], fma(cj[3 + ib], gr[ia][1], fma(cj[6 + ib], gr[ia][2],
+                           fma(cj[ia], gr[ib][0], fma(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
+                };
+                sg[0][1] = sg[1][0] = shear(0, 1);
+                sg[0][2] = sg[2][0] = shear(0, 2);
+                sg[1][2] = sg[2][1] = shear(1, 2);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        qp[qz * 9 + c * 3 + m] =
+                            fma(sg[c][0], Ji[m * 3 + 0], fma(sg[c][1], Ji[m * 3 + 1], sg[c][2] * Ji[m * 3 + 2]));
+            }
+        }
+        T acc[9][D];
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[ch][i] = T(0);
+#pragma unroll 1
+        for (int qz = 0; qz < Q; ++qz) {
+            T bwq[D], gwq[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                bwq[i] = tab.Bw[i * Q + qz];
+                gwq[i] = tab.Gw[i * Q + qz];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const T qv = qp[qz * 9 + c * 3 + m];
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        acc[c * 3 + m][i] = fma(qv, (m == 2 ? gwq[i] : bwq[i]), acc[c * 3 + m][i]);
+                }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch)
+#pragma unroll
+            for (int i = 0; i < D; ++i) cp[ch * D + i] = acc[ch][i];
+    }
+}
+
 // FUSE: the gather is done by the X-sweep threads (one contiguous line of D
 // values each) and the X^T-sweep threads write their line of the E-vector
 // directly, instead of separate gather / store phases through shared memory.
 // SPLIT: the fused Z stage runs three lanes per column (z_columns_split).
-template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false, bool TWO = false>
 __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
-    using L = LineLayout<T, D, Q>;
+    using L = LineLayout<T, D, Q, TWO>;
     constexpr int D3 = D * D * D, DP = L::DP, CS = L::CS, BS = L::BS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *bufA = reinterpret_cast<T *>(smem_raw);
@@ -354,6 +467,7 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
 
     // ---- Z sweep + pointwise + Z^T sweep: column (el, qx, qy), in place
     if constexpr (SPLIT) z_columns_split<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
+    else if constexpr (TWO) z_columns_2pass<T, D, Q>(a, tab, bufA, L::A, bufB, L::B, e0, ne_blk, tid, nt);
     else z_columns<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
     __syncthreads();
 
@@ -422,34 +536,34 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     }
 }
 
-template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false, bool TWO = false>
 __global__ void __launch_bounds__(256) pa_apply_line_kernel(ApplyArgs<T> a, Tables<T> tab, int epb)
 {
-    line_body<T, D, Q, FUSE, SPLIT>(a, tab, epb, blockIdx.x);
+    line_body<T, D, Q, FUSE, SPLIT, TWO>(a, tab, epb, blockIdx.x);
 }
 
 // Several operators of the same degree and precision in one launch: CTA b
 // belongs to the operator k with cta_start[k] <= b < cta_start[k + 1].
-template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false, bool TWO = false>
 __global__ void __launch_bounds__(256) pa_apply_line_batch_kernel(BatchArgs<T> bt, Tables<T> tab, int epb)
 {
     int k = 0;
     while (k + 1 < bt.count && (int64_t)blockIdx.x >= bt.cta_start[k + 1]) ++k;
-    line_body<T, D, Q, FUSE, SPLIT>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
+    line_body<T, D, Q, FUSE, SPLIT, TWO>(bt.args[k], tab, epb, (int64_t)blockIdx.x - bt.cta_start[k]);
 }
 
-template <typename T, int D, int Q>
+template <typename T, int D, int Q, bool TWO = false>
 size_t line_smem_bytes(int epb)
 {
-    return LineLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
+    return LineLayout<T, D, Q, TWO>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
 }
 
-template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false, bool TWO = false>
 int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
-    size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_line_kernel<T, D, Q, FUSE, SPLIT>;
+    size_t smem = line_smem_bytes<T, D, Q, TWO>(cfg.epb);
+    auto kern = pa_apply_line_kernel<T, D, Q, FUSE, SPLIT, TWO>;
     static bool smem_set = false;
     if (!smem_set) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -462,12 +576,12 @@ int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
     return PA_OK;
 }
 
-template <typename T, int D, int Q, bool FUSE, bool SPLIT = false>
+template <typename T, int D, int Q, bool FUSE, bool SPLIT = false, bool TWO = false>
 int launch_line_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLaunch &cfg, cudaStream_t s)
 {
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
-    const size_t smem = line_smem_bytes<T, D, Q>(cfg.epb);
-    auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE, SPLIT>;
+    const size_t smem = line_smem_bytes<T, D, Q, TWO>(cfg.epb);
+    auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE, SPLIT, TWO>;
     static bool smem_set = false;
     if (!smem_set) {
         PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

@@ -182,7 +182,7 @@ bool multi_eligible(const pa_op *op)
     const int v = op->launch.variant;
     if (op->precision == PA_FP64) return v == 0;
     if (v == 3 || v == 6) return true;
-    return (v == 2 || v == 5) && op->p <= 6;
+    return (v == 2 || v == 5 || v == 7) && op->p <= 6;
 }
 
 template <typename T>

@@ -1,6 +1,8 @@
 // Element-to-node assembly, the closed-form PA diagonal and the load vector.
 #include <cstdint>
 
+#include <algorithm>
+
 #include "pa_internal.h"
 
 namespace pa {
@@ -81,47 +83,108 @@ __device__ __forceinline__ void assemble_node(const T *__restrict__ ye, T *__res
 // (grids of fewer than 2^31 nodes): the divisions by p and by the grid
 // extents are the costly part of a node's work.  Same additions in the same
 // order as assemble_node.
+// Elements of one axis that hold grid coordinate gi (degree P, ne elements
+// along the axis), with the node's local index in each: one owner inside an
+// element, two on an element boundary (the lower element first).  Both
+// entries are written at fixed indices, so the arrays stay in registers.
+template <int P>
+__device__ __forceinline__ int axis_owners_p(int gi, int ne, int e[2], int li[2])
+{
+    const int k = gi / P, r = gi - k * P;
+    if (r == 0) {
+        const bool lo = k >= 1, hi = k < ne;
+        e[0] = lo ? k - 1 : k;
+        li[0] = lo ? P : 0;
+        e[1] = k;
+        li[1] = 0;
+        return (int)lo + (int)hi;
+    }
+    e[0] = e[1] = k;
+    li[0] = li[1] = r;
+    return 1;
+}
+
+// Sum of the (at most 8) E-vector entries of global node (gx, gy, gz) given
+// its owners along each axis: z owners outermost, then y, then x, each in
+// increasing element order.  Fixed-length loops guarded by the counts.
 template <typename T, int P>
-__device__ __forceinline__ void assemble_node_p(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
-                                                const uint8_t *__restrict__ ess, T ess_value, int accumulate,
-                                                const Grid &g, int gn)
+__device__ __forceinline__ void node_sum_p(const T *__restrict__ ye, const Grid &g, const int ex[2], const int ix[2],
+                                           int cx, const int ey[2], const int iy[2], int cy, const int ez[2],
+                                           const int iz[2], int cz, T acc[3])
 {
     constexpr int D = P + 1, D3 = D * D * D;
-    const int t = gn / g.Mx;
-    const int gi[3] = {gn - t * g.Mx, t % g.My, t / g.My};
-    const int ne[3] = {g.nx, g.ny, g.nz};
-    int e[3][2], li[3][2], cnt[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int k = gi[a] / P, r = gi[a] - k * P;
-        cnt[a] = 0;
-        if (r == 0) {
-            if (k - 1 >= 0) { e[a][cnt[a]] = k - 1; li[a][cnt[a]] = P; ++cnt[a]; }
-            if (k < ne[a]) { e[a][cnt[a]] = k; li[a][cnt[a]] = 0; ++cnt[a]; }
-        } else {
-            e[a][0] = k;
-            li[a][0] = r;
-            cnt[a] = 1;
-        }
-    }
     T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-    for (int c = 0; c < cnt[2]; ++c)
-        for (int b = 0; b < cnt[1]; ++b)
-            for (int a = 0; a < cnt[0]; ++a) {
-                const int el = e[0][a] + g.nx * (e[1][b] + g.ny * e[2][c]);
-                const int loc = li[0][a] + D * (li[1][b] + D * li[2][c]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (c >= cz || b >= cy || a >= cx) continue;
+                const int el = ex[a] + g.nx * (ey[b] + g.ny * ez[c]);
+                const int loc = ix[a] + D * (iy[b] + D * iz[c]);
                 const T *base = ye + (int64_t)el * (3 * D3) + loc;
                 acc0 += base[0];
                 acc1 += base[D3];
                 acc2 += base[2 * D3];
             }
-    T acc[3] = {acc0, acc1, acc2};
+    acc[0] = acc0;
+    acc[1] = acc1;
+    acc[2] = acc2;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void assemble_node_p(const T *__restrict__ ye, T *__restrict__ y, const T *__restrict__ xin,
+                                                const uint8_t *__restrict__ ess, T ess_value, int accumulate,
+                                                const Grid &g, int gn)
+{
+    const int t = gn / g.Mx;
+    int ex[2], ix[2], ey[2], iy[2], ez[2], iz[2];
+    const int cx = axis_owners_p<P>(gn - t * g.Mx, g.nx, ex, ix);
+    const int cy = axis_owners_p<P>(t % g.My, g.ny, ey, iy);
+    const int cz = axis_owners_p<P>(t / g.My, g.nz, ez, iz);
+    T acc[3];
+    node_sum_p<T, P>(ye, g, ex, ix, cx, ey, iy, cy, ez, iz, cz, acc);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int64_t k = c * g.Nn + gn;
         T v = acc[c];
         if (ess && ess[k]) v = xin ? xin[k] : ess_value;
         y[k] = accumulate ? y[k] + v : v;
+    }
+}
+
+// The node sum organised by node rows: a CTA takes whole rows (gy, gz) of
+// the grid, so the y and z owners are the same for all its threads and only
+// every P-th node along x (an element boundary) has a second owner; no
+// division by a grid extent per node.  Same additions in the same order as
+// assemble_node_p.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) assemble_rows_kernel(const T *__restrict__ ye, T *__restrict__ y,
+                                                            const T *__restrict__ xin, const uint8_t *__restrict__ ess,
+                                                            T ess_value, int accumulate, Grid g,
+                                                            const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    const int64_t rows = (int64_t)g.My * g.Mz;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        int ey[2], iy[2], ez[2], iz[2];
+        const int cy = axis_owners_p<P>((int)(row % g.My), g.ny, ey, iy);
+        const int cz = axis_owners_p<P>((int)(row / g.My), g.nz, ez, iz);
+        for (int gx = threadIdx.x; gx < g.Mx; gx += blockDim.x) {
+            int ex[2], ix[2];
+            const int cx = axis_owners_p<P>(gx, g.nx, ex, ix);
+            T acc[3];
+            node_sum_p<T, P>(ye, g, ex, ix, cx, ey, iy, cy, ez, iz, cz, acc);
+            const int64_t gn = gx + (int64_t)g.Mx * row;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t k = c * g.Nn + gn;
+                T v = acc[c];
+                if (ess && ess[k]) v = xin ? xin[k] : ess_value;
+                y[k] = accumulate ? y[k] + v : v;
+            }
+        }
     }
 }
 
@@ -248,10 +311,18 @@ int launch_assemble(const T *ye, T *y, const T *xin, const uint8_t *ess, T ess_v
     const unsigned nb = grid_for(g.Nn, th);
     const int acc = accumulate ? 1 : 0;
     if (g.Nn < kNode32) {
+        // rows of Mx nodes: one CTA per row at a time, its width Mx rounded up to a warp
+        const int64_t rows = (int64_t)g.My * g.Mz;
+        const int rth = (int)std::min<int64_t>(256, ((int64_t)g.Mx + 31) / 32 * 32);
+        const unsigned rb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, (int64_t)152 * 16));
+        // p = 1: every node is an element boundary along x and the rows
+        // gain nothing (measured 46 vs 43 us at 100^3 nodes); the per-node
+        // form stays there
         switch (g.p) {
+        case 1: assemble_kernel_p<T, 1><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip); break;
 #define PA_ASM(P) \
-    case P: assemble_kernel_p<T, P><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip); break;
-            PA_ASM(1) PA_ASM(2) PA_ASM(3) PA_ASM(4) PA_ASM(5) PA_ASM(6) PA_ASM(7) PA_ASM(8)
+    case P: assemble_rows_kernel<T, P><<<rb, rth, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip); break;
+            PA_ASM(2) PA_ASM(3) PA_ASM(4) PA_ASM(5) PA_ASM(6) PA_ASM(7) PA_ASM(8)
 #undef PA_ASM
         default: assemble_kernel<T><<<nb, th, 0, s>>>(ye, y, xin, ess, ess_value, acc, g, skip);
         }

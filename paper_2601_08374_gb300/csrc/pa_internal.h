@@ -74,12 +74,13 @@ struct Grid {
 int make_grid(int nx, int ny, int nz, int p, Grid &g, const char *who);
 
 // --------------------------------------------------------- apply launch --
-constexpr int kMaxVariant = 6;
+constexpr int kMaxVariant = 7;
 struct ApplyLaunch {
     int variant = 0;  // 0: flattened smem sweeps, 1: register-tiled lines, 2: lines + fused gather/store,
                       // 3: as 2 with the Z stage split over three lanes per column,
                       // 4: tensor-core contractions (FP32, p <= 6),
-                      // 5: plane-fused sweeps (FP32, p <= 6), 6: as 5 with the Z stage split
+                      // 5: plane-fused sweeps (FP32, p <= 6), 6: as 5 with the Z stage split,
+                      // 7: as 2 with the Z stage in two passes (FP32)
     int epb = 1;      // elements per CTA
     int threads = 256;
 };

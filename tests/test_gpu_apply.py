@@ -210,6 +210,41 @@ def test_apply_register_tiled_variant(pa, p, prec, variant):
     op.close()
 
 
+@pytest.mark.parametrize("p", range(1, 9))
+def test_apply_two_pass_column_variant(pa, p):
+    """Variant 7 (FP32 line kernel whose fused Z stage runs in two passes
+    through shared memory) against the oracle with several CTA shapes,
+    constrained, and bitwise against variant 2 (the same terms in the same
+    order); in a batched launch it equals its single applies."""
+    nx, ny, nz = MESH_DIMS[p]
+    m = syn.random_affine_cube(nx, seed=360 + p, ny=ny, nz=nz)
+    lam, mu = syn.lame(1.0, 0.3)
+    ess = syn.clamp_mask(m, p)
+    op = pa.Operator(nx, ny, nz, m.affine, p, lam, mu, precision=pa.PA_FP32, ess_mask=ess)
+    xt = torch.tensor(syn.uniform_vector(op.ndofs, seed=27 + p), dtype=op.dtype, device="cuda")
+    yo = oracle.apply(p, nx, ny, nz, m.affine, lam, mu, xt.double().cpu().numpy(), ess=ess)
+    pa.pa_op_set_launch(op.h, 2, 1, 128)
+    y2 = op.apply(xt).clone()
+    ran = 0
+    for epb, th in [(1, 64), (3, 96), (2, 128), (5, 256)]:
+        try:
+            pa.pa_op_set_launch(op.h, 7, epb, th)
+        except pa.PAError as e:
+            assert e.code == pa.PA_EINVAL
+            continue
+        y = op.apply(xt)
+        assert _relerr(y.double().cpu().numpy(), yo) <= TOL[1], (epb, th)
+        assert torch.equal(y, y2), (epb, th)
+        ran += 1
+    assert ran >= 2
+    pa.pa_op_set_launch(op.h, 7, 1, 128)
+    ys = torch.full_like(xt, float("nan"))
+    pa.pa_op_apply_batch([op.h], [xt], [ys])
+    torch.cuda.synchronize()
+    assert torch.equal(ys, y2)
+    op.close()
+
+
 @pytest.mark.parametrize("variant", [5, 6])
 @pytest.mark.parametrize("p", range(1, 9))
 def test_apply_plane_fused_variant(pa, p, variant):
@@ -263,7 +298,7 @@ def test_apply_plane_fused_variant(pa, p, variant):
 def test_plane_variants_are_fp32_only(pa):
     m = syn.box_mesh(2, 2, 2)
     op = pa.Operator(2, 2, 2, m.affine, 2, 1.0, 1.0, precision=pa.PA_FP64)
-    for v in (5, 6):
+    for v in (5, 6, 7):
         with pytest.raises(pa.PAError) as ei:
             pa.pa_op_set_launch(op.h, v, 2, 128)
         assert ei.value.code == pa.PA_EINVAL
