@@ -467,12 +467,13 @@ def test_beam_config3_solution_against_oracle_solve(pa, beam_config3_oracle, mod
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_p8_cube_hierarchy_against_oracle_solve(pa, mode):
-    """The p = 8 hierarchy of the mixed-precision configuration (8 -> 4 ->
-    2 -> 1, nu = 0.45, random affine maps, smooth sine-mode force, x = 0
-    clamped) on a 2^3 cube the host can factor (14,739 dofs): every mode
-    within 1e-8 of the oracle's direct solve."""
-    p, n = 8, 2
+@pytest.mark.parametrize("p", [6, 8])
+def test_p8_cube_hierarchy_against_oracle_solve(pa, mode, p):
+    """The hierarchies of the mixed-precision configuration (6 -> 3 -> 1
+    and 8 -> 4 -> 2 -> 1, nu = 0.45, random affine maps, smooth sine-mode
+    force, x = 0 clamped) on a 2^3 cube the host can factor (6,591 and
+    14,739 dofs): every mode within 1e-8 of the oracle's direct solve."""
+    n = 2
     m = syn.random_affine_cube(n, seed=3000 + p)
     lam, mu = syn.lame(1.0, 0.45)
     ess = syn.clamp_mask(m, p)
@@ -484,13 +485,13 @@ def test_p8_cube_hierarchy_against_oracle_solve(pa, mode):
     b = op.rhs(modes=modes)
     assert np.max(np.abs(b.cpu().numpy() - bo)) <= 1e-12 * np.max(np.abs(bo))
     x = torch.zeros_like(b)
-    s = pa.pa_solver_create(op.h, [8, 4, 2, 1], 2, 1e-2, 10, mode)
+    s = pa.pa_solver_create(op.h, [8, 4, 2, 1] if p == 8 else [6, 3, 1], 2, 1e-2, 10, mode)
     code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
     pa.pa_solver_destroy(s)
     op.close()
     assert code == pa.PA_OK, pa.lib.pa_last_error()
     err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
-    assert err <= 1e-8, (mode, err)
+    assert err <= 1e-8, (mode, p, err)
 
 
 def test_mixed_precision_cube_p8_at_full_size(pa):
