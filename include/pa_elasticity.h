@@ -231,9 +231,11 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);
 
-/* Reports (and clears) a timeout of a bounded tensor-core wait in an apply
- * of this operator since the last check (variant 4): PA_OK, or
- * PA_ETIMEOUT when a result was not valid.  Synchronous. */
+/* Reports (and clears) the operator's device status since the last check:
+ * PA_OK; PA_ETIMEOUT when a bounded tensor-core wait of an apply timed out
+ * (variant 4; that result is not valid); PA_EINVAL when, in the
+ * bounds-checking build of the library (build.py --bounds), a kernel met an
+ * index outside its array and skipped the access.  Synchronous. */
 int pa_op_check(pa_op *op);
 
 /* Budget of the operator's bounded device waits (the tensor-core waits of

@@ -21,6 +21,9 @@ PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, 
 PA_FP64, PA_FP32 = 0, 1
 PA_SOLVE_FP64, PA_SOLVE_MIXED, PA_SOLVE_MIXED_FCG = 0, 1, 2
 
+# PA_ELASTICITY_LIB selects another build of the same library (the tests'
+# bounds-checking build); the default is the in-tree product build
+_LIB_PATH = os.environ.get("PA_ELASTICITY_LIB", _LIB_PATH)
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: build it with `python paper_2601_08374_gb300/build.py`")
 

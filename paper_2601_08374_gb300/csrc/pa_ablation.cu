@@ -120,12 +120,8 @@ int stage_elements(pa_op *op, int stage, const ApplyArgs<double> &a, cudaStream_
         dense_fwd_kernel<D, Q><<<(unsigned)ne, kDenseThreads, 0, s>>>(a, dphi);
         PA_CUDA_TRY(cudaGetLastError());
         const size_t smem = sizeof(double) * 9 * Q3;
-        static bool smem_set = false;
-        if (!smem_set) {
-            PA_CUDA_TRY(cudaFuncSetAttribute(dense_bwd_kernel<D, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024));
-            smem_set = true;
-        }
+        static bool smem_set[kMaxAttrDevices] = {};
+        if (int rc = max_smem_once(dense_bwd_kernel<D, Q>, smem_set)) return rc;
         (void)D3;
         dense_bwd_kernel<D, Q><<<(unsigned)ne, kDenseThreads, smem, s>>>(a, dphiw);
         PA_CUDA_TRY(cudaGetLastError());

@@ -369,6 +369,7 @@ int pa_op_setup(const pa_mesh *mesh, int p, int q, double lambda, double mu, int
         pa_op_destroy(op);
         return rc;
     }
+    g.flags = op->d_err;  // status flags the kernels may set (bounds build)
     if ((err = cudaMemcpy(op->d_affine, mesh->affine.data(), sizeof(double) * 12 * (size_t)g.ne,
                           cudaMemcpyHostToDevice)) != cudaSuccess) {
         pa_op_destroy(op);
@@ -631,7 +632,9 @@ int pa_op_check(pa_op *op)
     PA_CUDA_TRY(cudaMemcpy(&flag, op->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!flag) return PA_OK;
     PA_CUDA_TRY(cudaMemset(op->d_err, 0, sizeof(int)));
-    return set_error(PA_ETIMEOUT, "pa_op_check: a tensor-core wait of an apply timed out (its result is not valid)");
+    if (flag & 1)
+        return set_error(PA_ETIMEOUT, "pa_op_check: a tensor-core wait of an apply timed out (its result is not valid)");
+    return set_error(PA_EINVAL, "pa_op_check: an index outside its array was met (bounds-checking build)");
 }
 
 int pa_op_set_anisotropic(pa_op *op, const double *cvoigt)
@@ -725,6 +728,7 @@ int pa_op_set_wait_limit(pa_op *op, double seconds)
 
 int pa_op_autotune(pa_op *op, void *stream)
 {
+    NvtxRange nvtx("pa_op_autotune");
     if (!op) return set_error(PA_EINVAL, "pa_op_autotune: null op");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)op->ndofs() * op->elem;

@@ -114,8 +114,9 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
             int c = r / D3, a3 = r - c * D3;
             int iz = a3 / (D * D), iy = (a3 / D) % D, ix = a3 % D;
             int64_t k = c * Nn + gbase[el] + ix + Mx * iy + MxMy * iz;
-            T v = a.x[k];
-            if (a.ess && a.ess[k]) v = T(0);
+            const bool in = PA_INB(a.g, k, 3 * Nn);
+            T v = in ? a.x[k] : T(0);
+            if (in && a.ess && a.ess[k]) v = T(0);
             bufA[(size_t)el * L::bufA + r] = v;
         }
     }
@@ -408,7 +409,7 @@ __device__ __forceinline__ void flat_body(const ApplyArgs<T> &a, const Tables<T>
                 acc[1] = fma(in[1][off1 + qx], sBw[ixs[1] * Q + qx], acc[1]);
             }
             for (int u = 0; u < 2; ++u)
-                if (oo[u] < total) a.ye[e0 * 3 * D3 + oo[u]] = acc[u];
+                if (oo[u] < total && PA_INB(a.g, e0 * 3 * D3 + oo[u], a.g.ne * 3 * D3)) a.ye[e0 * 3 * D3 + oo[u]] = acc[u];
         }
     }
 }
@@ -454,11 +455,8 @@ int launch_flat(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
 {
     size_t smem = flat_smem_bytes<T, D, Q>(cfg.epb);
     auto kern = a.cvoigt ? pa_apply_flat_aniso_kernel<T, D, Q> : pa_apply_flat_kernel<T, D, Q>;
-    static bool smem_set[2] = {false, false};
-    if (!smem_set[a.cvoigt ? 1 : 0]) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set[a.cvoigt ? 1 : 0] = true;
-    }
+    static bool smem_set[2][kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set[a.cvoigt ? 1 : 0])) return rc;
     int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(a, tab, cfg.epb);
@@ -471,11 +469,8 @@ int launch_flat_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLa
 {
     const size_t smem = flat_smem_bytes<T, D, Q>(cfg.epb);
     auto kern = pa_apply_flat_batch_kernel<T, D, Q>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set)) return rc;
     const int64_t nblk = b.cta_start[b.count];
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(b, tab, cfg.epb);

@@ -397,8 +397,9 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
         int el = o / (3 * D3), r = o - el * 3 * D3;
         int ix = r % D, iy = (r / D) % D, iz = (r / (D * D)) % D, c = r / D3;
         int64_t k = c * Nn + gbase[el] + ix + Mx * iy + MxMy * iz;
-        T v = a.x[k];
-        if (a.ess && a.ess[k]) v = T(0);
+        const bool in = PA_INB(a.g, k, 3 * Nn);
+        T v = in ? a.x[k] : T(0);
+        if (in && a.ess && a.ess[k]) v = T(0);
         bufA[(size_t)el * L::A + ((c * D + iz) * D + iy) * DP + ix] = v;
     }
     if (!FUSE) __syncthreads();
@@ -412,8 +413,9 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
             const int64_t k0 = c * Nn + gbase[el] + Mx * iy + MxMy * iz;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                T v = a.x[k0 + i];
-                if (a.ess && a.ess[k0 + i]) v = T(0);
+                const bool in = PA_INB(a.g, k0 + i, 3 * Nn);
+                T v = in ? a.x[k0 + i] : T(0);
+                if (in && a.ess && a.ess[k0 + i]) v = T(0);
                 xv[i] = v;
             }
         } else {
@@ -513,6 +515,10 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
         }
         T *out = FUSE ? a.ye + (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D
                       : bufA + (size_t)el * L::A + ((c * D + iz) * D + iy) * DP;
+        // (a line of D entries: its first and last index checked)
+        if (FUSE && !(PA_INB(a.g, (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D, a.g.ne * 3 * D3) &&
+                      PA_INB(a.g, (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D + D - 1, a.g.ne * 3 * D3)))
+            continue;
 #pragma unroll
         for (int ix = 0; ix < D; ++ix) {
             T y = T(0);
@@ -532,7 +538,7 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     for (int o = tid; o < ne_blk * 3 * D3; o += nt) {
         int el = o / (3 * D3), r = o - el * 3 * D3;
         int ix = r % D, rest = r / D;  // rest = (c*D + iz)*D + iy
-        ye[o] = bufA[(size_t)el * L::A + rest * DP + ix];
+        if (PA_INB(a.g, e0 * 3 * D3 + o, a.g.ne * 3 * D3)) ye[o] = bufA[(size_t)el * L::A + rest * DP + ix];
     }
 }
 
@@ -564,11 +570,8 @@ int launch_line(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch &
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
     size_t smem = line_smem_bytes<T, D, Q, TWO>(cfg.epb);
     auto kern = pa_apply_line_kernel<T, D, Q, FUSE, SPLIT, TWO>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set)) return rc;
     int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(a, tab, cfg.epb);
@@ -582,11 +585,8 @@ int launch_line_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyLa
     if (cfg.threads > 256) return set_error(PA_EINVAL, "line kernel: at most 256 threads per CTA");
     const size_t smem = line_smem_bytes<T, D, Q, TWO>(cfg.epb);
     auto kern = pa_apply_line_batch_kernel<T, D, Q, FUSE, SPLIT, TWO>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set)) return rc;
     const int64_t nblk = b.cta_start[b.count];
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(b, tab, cfg.epb);

@@ -194,13 +194,8 @@ int apply_multi_group(pa_op *const *ops, const void *const *xs, void *const *ys,
     int dev = 0, nsm = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     PA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    static bool smem_set[2] = {false, false};
-    const int pi = sizeof(T) == 8 ? 0 : 1;
-    if (!smem_set[pi]) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(pa_apply_multi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
-        smem_set[pi] = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(pa_apply_multi_kernel<T>, smem_set)) return rc;
     for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxMulti) {
         const size_t m = std::min(idx.size() - c0, (size_t)kMaxMulti);
         MultiArgs<T> ma{};

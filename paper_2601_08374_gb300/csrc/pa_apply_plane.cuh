@@ -66,8 +66,9 @@ __device__ __forceinline__ void plane_forward(const ApplyArgs<T> &a, const Table
 #pragma unroll
         for (int ix = 0; ix < D; ++ix) {
             const int64_t k = k0 + Mx * iy + ix;
-            T v = a.x[k];
-            if (a.ess && a.ess[k]) v = T(0);
+            const bool in = PA_INB(a.g, k, 3 * a.g.Nn);
+            T v = in ? a.x[k] : T(0);
+            if (in && a.ess && a.ess[k]) v = T(0);
             xv[iy][ix] = v;
         }
     // the table columns of one qx are loaded once per iteration (the loop
@@ -201,8 +202,9 @@ __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T
     for (int o = tid; o < ne_blk * 3 * D; o += nt) {
         const int el = o / (3 * D), r = o - el * 3 * D;
         const int c = r / D, iz = r - c * D;
-        plane_backward<T, D, Q>(tab, buf + (size_t)el * L::A + c * 3 * D + iz,
-                                a.ye + (e0 + el) * 3 * D3 + (c * D + iz) * D * D);
+        const int64_t ob = (e0 + el) * 3 * D3 + (c * D + iz) * D * D;  // a plane of D^2 entries
+        if (!(PA_INB(a.g, ob, a.g.ne * 3 * D3) && PA_INB(a.g, ob + D * D - 1, a.g.ne * 3 * D3))) continue;
+        plane_backward<T, D, Q>(tab, buf + (size_t)el * L::A + c * 3 * D + iz, a.ye + ob);
     }
 }
 
@@ -228,11 +230,8 @@ int launch_plane(const ApplyArgs<T> &a, const Tables<T> &tab, const ApplyLaunch 
     if (cfg.threads > 256) return set_error(PA_EINVAL, "plane kernel: at most 256 threads per CTA");
     const size_t smem = plane_smem_bytes<T, D, Q>(cfg.epb);
     auto kern = pa_apply_plane_kernel<T, D, Q, SPLIT>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set)) return rc;
     const int64_t nblk = (a.g.ne + cfg.epb - 1) / cfg.epb;
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(a, tab, cfg.epb);
@@ -246,11 +245,8 @@ int launch_plane_batch(const BatchArgs<T> &b, const Tables<T> &tab, const ApplyL
     if (cfg.threads > 256) return set_error(PA_EINVAL, "plane kernel: at most 256 threads per CTA");
     const size_t smem = plane_smem_bytes<T, D, Q>(cfg.epb);
     auto kern = pa_apply_plane_batch_kernel<T, D, Q, SPLIT>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set)) return rc;
     const int64_t nblk = b.cta_start[b.count];
     if (nblk <= 0) return PA_OK;
     kern<<<(unsigned)nblk, cfg.threads, smem, s>>>(b, tab, cfg.epb);

@@ -270,8 +270,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) pa_apply_tc_kernel(ApplyArgs<fl
 #pragma unroll
             for (int ix = 0; ix < D; ++ix) {
                 const int64_t k = c * Nn + base + ix;
-                float xv = a.x[k];
-                if (a.ess && a.ess[k]) xv = 0.f;
+                const bool in = PA_INB(a.g, k, 3 * Nn);
+                float xv = in ? a.x[k] : 0.f;
+                if (in && a.ess && a.ess[k]) xv = 0.f;
                 put(Ahi, Alo, row, 8 * c + ix, xv);
             }
         }
@@ -393,14 +394,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) pa_apply_tc_kernel(ApplyArgs<fl
             const int c = part;
             ld16(lane_base + 16 * c, v);
             ld_wait();
-            if (act) {
-                float *out = a.ye + ((e0 + el) * 3 + c) * D3 + (iz * D + iy) * D;
+            const int64_t ob = ((e0 + el) * 3 + c) * D3 + (iz * D + iy) * D;
+            if (act && PA_INB(a.g, ob, g.ne * 3 * D3) && PA_INB(a.g, ob + D - 1, g.ne * 3 * D3)) {
+                float *out = a.ye + ob;
 #pragma unroll
                 for (int ix = 0; ix < D; ++ix) out[ix] = v[ix];
             }
         }
     }
-    if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
+    if (!ok && tid == 0 && a.err) atomicOr(a.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -422,11 +424,8 @@ int launch_tc(const ApplyArgs<float> &a, const TcTables &tt, cudaStream_t s)
     const int64_t nbatch = (a.g.ne + E - 1) / E;
     if (nbatch <= 0) return PA_OK;
     auto kern = pa_apply_tc_kernel<D, Q>;
-    static bool smem_set = false;
-    if (!smem_set) {
-        PA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
-        smem_set = true;
-    }
+    static bool smem_set[kMaxAttrDevices] = {};
+    if (int rc = max_smem_once(kern, smem_set, (int)tc_smem_bytes())) return rc;
     const int64_t grid = nbatch < 2 * 152 ? nbatch : 2 * 152;
     kern<<<(unsigned)grid, kTcThreads, tc_smem_bytes(), s>>>(a, tt, nbatch);
     PA_CUDA_TRY(cudaGetLastError());

@@ -123,6 +123,9 @@ __device__ __forceinline__ void node_sum_p(const T *__restrict__ ye, const Grid 
                 if (c >= cz || b >= cy || a >= cx) continue;
                 const int el = ex[a] + g.nx * (ey[b] + g.ny * ez[c]);
                 const int loc = ix[a] + D * (iy[b] + D * iz[c]);
+                if (!(PA_INB(g, (int64_t)el * (3 * D3) + loc, g.ne * 3 * D3) &&
+                      PA_INB(g, (int64_t)el * (3 * D3) + loc + 2 * D3, g.ne * 3 * D3)))
+                    continue;
                 const T *base = ye + (int64_t)el * (3 * D3) + loc;
                 acc0 += base[0];
                 acc1 += base[D3];

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "pa_elasticity.h"
 
@@ -19,7 +20,36 @@ constexpr int kMaxQ = kMaxP + 2;
 // ---------------------------------------------------------------- errors --
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
+
+// A kernel's dynamic shared-memory limit raised once per device (the
+// attribute belongs to the device the call is made on): done[] is the
+// caller's per-kernel record, indexed by device.
+constexpr int kMaxAttrDevices = 64;
+template <typename K>
+inline int max_smem_once(K kern, bool (&done)[kMaxAttrDevices], int bytes = 227 * 1024)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxAttrDevices) return set_error(PA_EINVAL, "device index out of range");
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+        done[dev] = true;
+    }
+    return PA_OK;
+}
+
 void clear_error();
+
+// NVTX range for tools that record them (Nsight Systems and the like); the
+// NVTX v3 header is header-only and costs a branch when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define PA_CUDA_TRY(call)                                       \
     do {                                                        \
@@ -64,7 +94,25 @@ struct Grid {
     int nx, ny, nz, p;
     int Mx, My, Mz;
     int64_t ne, Nn;
+    int *flags = nullptr;  // the operator's device status flags (bit 1: an index out of bounds, bounds build)
 };
+
+// Bounds-checking build (PA_BOUNDS_CHECK, `build.py --bounds`): every gather
+// of x and every E-vector load or store checks its index against the
+// array's length; an index outside it sets bit 1 of the grid's status flags
+// (read by pa_op_check) and the access is skipped instead of made.  In the
+// product build the check is the constant true and compiles away.
+#ifdef PA_BOUNDS_CHECK
+__device__ __forceinline__ bool pa_in_bounds(const Grid &g, int64_t i, int64_t n)
+{
+    if (i >= 0 && i < n) return true;
+    if (g.flags) atomicOr(g.flags, 2);
+    return false;
+}
+#define PA_INB(g, i, n) ::pa::pa_in_bounds((g), (int64_t)(i), (int64_t)(n))
+#else
+#define PA_INB(g, i, n) true
+#endif
 
 // Fills g for an nx*ny*nz mesh of degree p after checking every size the
 // kernels index with: dimensions >= 1, at most 2^31 elements, node counts

@@ -290,6 +290,7 @@ int lockstep_key(const pa_solver *s) { return s->mode; }
 
 int lockstep_tick(Lockstep *L)
 {
+    NvtxRange nvtx("lockstep_tick");
     if (L->m.empty()) return PA_OK;
     int rc = run_segment(*L, false);
     if (rc) return rc;

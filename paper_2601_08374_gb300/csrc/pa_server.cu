@@ -167,6 +167,7 @@ void release(Res &r)
 // vector b and x = 0 (all ready on the device when it returns PA_OK).
 int setup_request(pa_server *srv, Ticket &t, Res &res)
 {
+    pa::NvtxRange nvtx("server: request setup");
     const pa_request &r = t.req;
     pa_mesh *mesh = nullptr;
     int rc = PA_OK;

@@ -835,6 +835,7 @@ int pa_op_restrict(const pa_op *coarse, const pa_op *fine, const double *rf, dou
 int pa_gmg_pcg_solve(pa_solver *s, const double *b, double *x, double rtol, int maxit, pa_solve_info *info,
                      void *stream)
 {
+    NvtxRange nvtx("pa_gmg_pcg_solve");
     if (!s || !b || !x) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: null argument");
     if (!(rtol > 0.0) || maxit < 0) return set_error(PA_EINVAL, "pa_gmg_pcg_solve: bad tolerance or cap");
     // the caller's stream first finishes producing b and x; the solve runs on

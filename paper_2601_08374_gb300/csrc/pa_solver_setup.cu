@@ -454,6 +454,7 @@ int pa_solver_create(pa_op *fine, int nlev, const int *p_levels, int cheb_order,
 int pa_solver_create_hp(pa_op *fine, int nlev, const int *p_levels, int h_levels, int cheb_order, double coarse_rtol,
                         int coarse_maxit, int mode, pa_solver **out)
 {
+    NvtxRange nvtx("pa_solver_create");
     if (!out) return set_error(PA_EINVAL, "pa_solver_create: null output");
     *out = nullptr;
     if (!fine || !p_levels || nlev < 1 || nlev > 8) return set_error(PA_EINVAL, "pa_solver_create: bad levels");

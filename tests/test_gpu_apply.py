@@ -314,7 +314,7 @@ def test_autotune_keeps_parity(pa):
     for prec in (0, 1):
         op = pa.Operator(4, 4, 4, m.affine, p, lam, mu, precision=prec)
         cfg = pa.pa_op_autotune(op.h)
-        assert cfg[0] in (0, 1, 2, 3) and cfg[1] >= 1 and cfg[2] % 32 == 0
+        assert cfg[0] in range(8) and cfg[1] >= 1 and cfg[2] % 32 == 0  # any admissible variant 0-7
         y = op.apply(torch.tensor(x, dtype=op.dtype, device="cuda")).double().cpu().numpy()
         assert _relerr(y, yo) <= TOL[prec]
         op.close()
