@@ -86,33 +86,44 @@ def workload(p: int, scale: float = 1.0):
     return n, mesh, x
 
 
-def kernel_source_hash() -> str:
-    """Hash of the element kernels' source and of the default launch table
-    (the shapes the sweep runs), so stored ncu traffic goes stale with them."""
+# Sources of each precision's element kernels (default launch shapes)
+KERNEL_SOURCES = {"f64": ("pa_apply.cuh", "pa_apply_f64.cu"),
+                  "f32": ("pa_apply_line.cuh", "pa_apply_plane.cuh", "pa_apply_f32.cu")}
+
+
+def kernel_source_hash(dtype_name: str) -> str:
+    """Hash of one precision's element-kernel sources and of its rows of the
+    default launch table (the shapes the sweep runs), so stored ncu traffic
+    goes stale with them."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_08374_gb300", "csrc")
-    for f in ("pa_apply.cuh", "pa_apply_line.cuh", "pa_apply_plane.cuh", "pa_apply_f64.cu", "pa_apply_f32.cu"):
+    for f in KERNEL_SOURCES[dtype_name]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "pa_api.cu"), "rb") as fh:
-        api = fh.read()
-    i = api.index(b"ApplyLaunch default_apply_launch(")
-    h.update(api[i:api.index(b"\n}\n", i)])
+        api = fh.read().decode()
+    i = api.index("ApplyLaunch default_apply_launch(")
+    tag = dtype_name[1:]  # "64" / "32"
+    for line in api[i:api.index("\n}\n", i)].splitlines():
+        if line.strip().startswith("static const int") and f"{tag}[" in line:
+            h.update(line.strip().encode())
     return h.hexdigest()[:16]
 
 
 # ncu DRAM bytes (read + write) per launch of the element kernel, keyed by
 # (precision, p): one-kernel captures of the sweep's element launches,
-# valid only for the kernel source and launch table with this hash.  The E-vector writes mostly stay in L2
-# and reach DRAM during the assembly kernel, so for p >= 4 the figure is
-# essentially the reads of x and of the geometry records.
-TRAFFIC_HASH = "6efc3f15735ea467"
+# valid only while that precision's kernel sources and launch-table rows
+# hash to the stored value.  The E-vector writes mostly stay in L2 and reach
+# DRAM during the assembly kernel, so for p >= 4 the figure is essentially
+# the reads of x and of the geometry records.
+TRAFFIC_HASH = {"f64": "5a9bbf390dd7b49b", "f32": ""}
 ELEMENT_KERNEL_NAMES = {0: "pa_apply_flat_kernel", 1: "pa_apply_line_kernel<FUSE=0>", 2: "pa_apply_line_kernel<FUSE=1>",
                         3: "pa_apply_line_kernel<FUSE=1,SPLIT=1>", 4: "pa_apply_tc_kernel (tcgen05 kind::tf32)",
-                        5: "pa_apply_plane_kernel<SPLIT=0>", 6: "pa_apply_plane_kernel<SPLIT=1>"}
+                        5: "pa_apply_plane_kernel<SPLIT=0>", 6: "pa_apply_plane_kernel<SPLIT=1>",
+                        7: "pa_apply_line_kernel<FUSE=1,TWO=1>"}
 TRAFFIC_BYTES: dict = {
-    ("f64", 1): 251676416, ("f64", 2): 59448576, ("f64", 4): 26878976, ("f64", 6): 22385408, ("f64", 8): 22125312,
-    ("f32", 1): 98589440, ("f32", 2): 18400256, ("f32", 4): 13144576, ("f32", 6): 11214336, ("f32", 8): 11112448,
+    ("f64", 1): 251751168, ("f64", 2): 59483392, ("f64", 4): 26786304, ("f64", 6): 22378496, ("f64", 8): 22188544,
+    ("f32", 1): 98374912, ("f32", 2): 18398464, ("f32", 4): 13144576, ("f32", 6): 11213824, ("f32", 8): 11154944,
 }
 
 
@@ -334,7 +345,7 @@ def run_ours(args):
     el_ms = sum(c["elem_ms"] for c in cases)
     achieved = fl_total / (el_ms * 1e-3) / 1e12
     traffic = None
-    if TRAFFIC_HASH and TRAFFIC_HASH == kernel_source_hash():
+    if TRAFFIC_HASH.get(dtype_name) == kernel_source_hash(dtype_name):
         tb = [TRAFFIC_BYTES.get((dtype_name, c["p"])) for c in cases]
         if all(t is not None for t in tb):
             traffic = int(sum(tb) / len(tb))
@@ -610,6 +621,7 @@ def run_fp32_sweep(args, pa, torch, sms, mhz):
     ms = e0.elapsed_time(e1)
     peak = derived_peak_tflops("f32", sms, mhz)
     fma_measured = pa.pa_measure_fma_rate(pa.PA_FP32, stream)
+    fma2_measured = pa.pa_measure_fma_rate(pa.PA_FMA_FP32X2, stream)
     per_p, fl_tot, el_tot = [], 0.0, 0.0
     for c in cases:
         te, ta, na = pa.pa_op_profile_read(c["op"].h)
@@ -624,6 +636,7 @@ def run_fp32_sweep(args, pa, torch, sms, mhz):
             "dtype": "f32", "element_kernel_tflops_alg": round(fl_tot / (el_tot * 1e-3) / 1e12, 3),
             "frac_of_derived_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / peak, 4),
             "derived_fp32_peak_tflops": round(peak, 3), "measured_fp32_fma_peak_tflops": round(fma_measured, 3),
+            "measured_fp32_paired_fma_peak_tflops": round(fma2_measured, 3),
             "frac_of_measured_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / fma_measured, 4), "per_p": per_p}
 
 

@@ -265,11 +265,15 @@ int pa_op_profile_read(pa_op *op, double *element_ms, double *assemble_ms, int64
 /* Measured multiply-add rate of the CUDA cores in TFLOP/s (2 flops per
  * FMA) for PA_FP64 or PA_FP32 arithmetic: the ceiling of the element
  * kernels, which are bound by those units (Sec. 4: the operator's flops are
- * FMAs of the sum-factorised contractions).  Runs a probe kernel of
- * independent FMA chains over every SM on `stream` (best of five timed
- * launches after one warm-up), allocates and frees a small output buffer,
- * synchronises.  No counterpart in the paper, which takes its CPUs' peaks
- * from a benchmark tool. */
+ * FMAs of the sum-factorised contractions).  precision = PA_FMA_FP32X2
+ * measures FP32 on paired FMA instructions (two FP32 FMAs per instruction,
+ * the form the FP32 element kernels use where they can), the same FMA work
+ * in half the instructions.  Runs a probe kernel of independent FMA chains
+ * over every SM on `stream` (best of five timed launches after one
+ * warm-up), allocates and frees a small output buffer, synchronises.
+ * PA_EINVAL for another precision.  No counterpart in the paper, which takes
+ * its CPUs' peaks from a benchmark tool. */
+#define PA_FMA_FP32X2 2
 int pa_measure_fma_rate(int precision, double *tflops, void *stream);
 
 /* p-transfer between two operators on the same mesh with degrees

@@ -19,6 +19,7 @@ from .build import LIB as _LIB_PATH
 
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY, PA_ECANCELED = range(9)
 PA_FP64, PA_FP32 = 0, 1
+PA_FMA_FP32X2 = 2  # pa_measure_fma_rate: FP32 on paired FMA instructions
 PA_SOLVE_FP64, PA_SOLVE_MIXED, PA_SOLVE_MIXED_FCG = 0, 1, 2
 
 # PA_ELASTICITY_LIB selects another build of the same library (the tests'
@@ -353,7 +354,8 @@ def pa_op_traction(op, face, t, F, stream=None):
 
 
 def pa_measure_fma_rate(precision, stream=None):
-    """Measured FMA rate of the CUDA cores (TFLOP/s) for PA_FP64 / PA_FP32."""
+    """Measured FMA rate of the CUDA cores (TFLOP/s) for PA_FP64 / PA_FP32,
+    or FP32 on paired FMA instructions (PA_FMA_FP32X2)."""
     t = ctypes.c_double()
     _check(lib.pa_measure_fma_rate(precision, ctypes.byref(t), _stream_ptr(stream)), "pa_measure_fma_rate")
     return t.value

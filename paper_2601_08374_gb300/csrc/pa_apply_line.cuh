@@ -19,9 +19,20 @@
 //   S3  Y^T-sweep out       [c][iz][iy][k*Q+qx]  (row stride BS = 2Q+1)
 // Buffer A holds S0 then S2 then the output staging; buffer B holds S1
 // then S3.  The E-vector leaves through a coalesced copy of the staging.
+//
+// FP32 runs on paired FMA instructions (__ffma2_rn: two fmaf in one
+// instruction, the same FMA work in half the issue slots) wherever two sums
+// share an operand and their other operands load as pairs: the forward X
+// and Y sweeps two quadrature outputs at a time (even Q), the transposed
+// sweeps and the Z^T sweep two node outputs at a time, with the weights from
+// the transposed tables BwT, GwT.  Each sum keeps its terms and their order,
+// so the results are bitwise those of the scalar form.  Measured against the
+// scalar form: p = 6 0.0608 -> 0.0540 ms, p = 8 0.0715 -> 0.0658 ms per
+// launch on the ~3M-dof sweep meshes.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pa_internal.h"
 
@@ -69,6 +80,10 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
     using L = LineLayout<T, D, Q>;
     constexpr int CS = L::CS;
     constexpr int kUnrollQz = ROLLED ? 1 : Q;  // as in z_columns
+    // FP32: Z^T on node pairs from the transposed tables, as in z_columns
+    constexpr bool PT = sizeof(T) == 4;
+    constexpr int NA = PT ? (D + 1) / 2 : D;
+    using AccT = std::conditional_t<PT, float2, T>;
     constexpr unsigned kMask = 0x3fffffffu;  // lanes 0..29
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     const int c = lane / 10, slot = lane - 10 * c;
@@ -97,11 +112,14 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
             R[n][2] = sel3v(cp, j0, j1, j2);
         }
         const T cl = geo[9], cm = geo[10], m2 = cm + cm;
-        T acc[3][D];
+        AccT acc[3][NA];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int i = 0; i < D; ++i) acc[k][i] = T(0);
+            for (int i = 0; i < NA; ++i) {
+                if constexpr (PT) acc[k][i] = make_float2(0.f, 0.f);
+                else acc[k][i] = T(0);
+            }
 #pragma unroll(kUnrollQz)
         for (int qz = 0; qz < Q; ++qz) {
             T bq[D], gq[D], bwq[D], gwq[D];
@@ -140,16 +158,31 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const T qv = fma(s0, R[m][0], fma(s1, R[m][1], s2 * R[m][2]));
+                if constexpr (PT) {
+                    const float2 qd = make_float2(qv, qv);
+                    const float *wt = (m == 2 ? tab.GwT : tab.BwT) + qz * kTStride;
 #pragma unroll
-                for (int i = 0; i < D; ++i)
-                    acc[m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[m][i]);
+                    for (int j = 0; j < NA; ++j)
+                        acc[m][j] = __ffma2_rn(qd, make_float2(wt[2 * j], wt[2 * j + 1]), acc[m][j]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        acc[m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[m][i]);
+                }
             }
         }
         if (act)
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int i = 0; i < D; ++i) cpt[k * D + i] = acc[k][i];
+                for (int j = 0; j < NA; ++j) {
+                    if constexpr (PT) {
+                        cpt[k * D + 2 * j] = acc[k][j].x;
+                        if (2 * j + 1 < D) cpt[k * D + 2 * j + 1] = acc[k][j].y;
+                    } else {
+                        cpt[k * D + j] = acc[k][j];
+                    }
+                }
     }
 }
 
@@ -166,6 +199,13 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
     // ROLLED: the qz loop is not unrolled (smaller code; the table columns of
     // each qz are loaded once per iteration); same arithmetic either way
     constexpr int kUnrollQz = ROLLED ? 1 : Q;
+    // FP32: the Z^T sweep accumulates nodes i, i + 1 of a channel on one
+    // paired FMA (__ffma2_rn, two fmaf per instruction) with the weight pair
+    // from the transposed tables; for an odd D the last pair's second lane
+    // runs on a zero weight and is not stored.  Same terms, same order.
+    constexpr bool PT = sizeof(T) == 4;
+    constexpr int NA = PT ? (D + 1) / 2 : D;
+    using AccT = std::conditional_t<PT, float2, T>;
     for (int o = tid; o < ne_blk * Q * Q; o += nt) {
         int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
         T *cp = bufA + (size_t)el * astride + col * CS;
@@ -182,11 +222,14 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
         // mu detJ J^-1: each shear stress is one 6-term dot with it
 #pragma unroll
         for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
-        T acc[9][D];
+        AccT acc[9][NA];
 #pragma unroll
         for (int ch = 0; ch < 9; ++ch)
 #pragma unroll
-            for (int i = 0; i < D; ++i) acc[ch][i] = T(0);
+            for (int i = 0; i < NA; ++i) {
+                if constexpr (PT) acc[ch][i] = make_float2(0.f, 0.f);
+                else acc[ch][i] = T(0);
+            }
 #pragma unroll(kUnrollQz)
         for (int qz = 0; qz < Q; ++qz) {
             T bq[D], gq[D], bwq[D], gwq[D];
@@ -239,15 +282,165 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
                     T qv = fma(s[c][0], Ji[m * 3 + 0], fma(s[c][1], Ji[m * 3 + 1], s[c][2] * Ji[m * 3 + 2]));
+                    if constexpr (PT) {
+                        const float2 qd = make_float2(qv, qv);
+                        const float *wt = (m == 2 ? tab.GwT : tab.BwT) + qz * kTStride;
 #pragma unroll
-                    for (int i = 0; i < D; ++i)
-                        acc[c * 3 + m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[c * 3 + m][i]);
+                        for (int j = 0; j < NA; ++j)
+                            acc[c * 3 + m][j] = __ffma2_rn(qd, make_float2(wt[2 * j], wt[2 * j + 1]), acc[c * 3 + m][j]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < D; ++i)
+                            acc[c * 3 + m][i] = fma(qv, (m == 2 ? tGw(i) : tBw(i)), acc[c * 3 + m][i]);
+                    }
                 }
         }
 #pragma unroll
         for (int ch = 0; ch < 9; ++ch)
 #pragma unroll
-            for (int i = 0; i < D; ++i) cp[ch * D + i] = acc[ch][i];
+            for (int j = 0; j < NA; ++j) {
+                if constexpr (PT) {
+                    cp[ch * D + 2 * j] = acc[ch][j].x;
+                    if (2 * j + 1 < D) cp[ch * D + 2 * j + 1] = acc[ch][j].y;
+                } else {
+                    cp[ch * D + j] = acc[ch][j];
+                }
+            }
+    }
+}
+
+// FP32 form of z_columns on paired FMAs (__ffma2_rn: two independent FP32
+// FMAs in one instruction, each rounded as one fmaf).  The channels d/dxi
+// and d/deta of a component share their Z-sweep weight, and the Q
+// reconstructions m = 0, 1 of a component share their Z^T weight, so those
+// accumulators advance two at a time; the third channels of components 0
+// and 1 pair up the same way, that of component 2 stays scalar.  Every
+// accumulator receives the same terms in the same order as in z_columns, so
+// the results are bitwise z_columns'.  The paired FMA runs at the scalar
+// FMA's rate (measured: 80.4 against 78.6 TFLOP/s over the whole GPU); it
+// saves issue slots, not pipe cycles.  The plane kernel (p <= 4) uses this
+// form (measured 5-7 % faster); the line kernels keep z_columns, where the
+// paired registers cost occupancy (p = 6: 164 -> 182 registers, 16 %
+// slower).
+template <int D, int Q, bool ROLLED = false>
+__device__ __forceinline__ void z_columns_f2(const ApplyArgs<float> &a, const Tables<float> &tab, float *bufA,
+                                             int astride, int64_t e0, int ne_blk, int tid, int nt)
+{
+    constexpr int CS = LineLayout<float, D, Q>::CS;
+    constexpr int kUnrollQz = ROLLED ? 1 : Q;
+    for (int o = tid; o < ne_blk * Q * Q; o += nt) {
+        int el = o / (Q * Q), col = o - el * Q * Q;  // col = qy*Q + qx
+        float *cp = bufA + (size_t)el * astride + col * CS;
+        // channel pairs: (c, 0) with (c, 1) for each c; (0, 2) with (1, 2);
+        // (2, 2) alone
+        float2 in01[3][D], in2p[D];
+        float in22[D];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < D; ++i) in01[c][i] = make_float2(cp[(3 * c) * D + i], cp[(3 * c + 1) * D + i]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            in2p[i] = make_float2(cp[2 * D + i], cp[5 * D + i]);
+            in22[i] = cp[8 * D + i];
+        }
+        const float *geo = a.geo + (e0 + el) * kGeoStride;
+        float Ji[9], cj[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
+        const float cl = geo[9], cm = geo[10], m2 = cm + cm;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cj[i] = cm * Ji[i];
+        float2 acc01[3][D], acc2p[D];
+        float acc22[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc01[c][i] = make_float2(0.f, 0.f);
+            acc2p[i] = make_float2(0.f, 0.f);
+            acc22[i] = 0.f;
+        }
+#pragma unroll(kUnrollQz)
+        for (int qz = 0; qz < Q; ++qz) {
+            float bq[D], gq[D], bwq[D], gwq[D];
+            if constexpr (ROLLED)
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    bq[i] = tab.B[i * Q + qz];
+                    gq[i] = tab.G[i * Q + qz];
+                    bwq[i] = tab.Bw[i * Q + qz];
+                    gwq[i] = tab.Gw[i * Q + qz];
+                }
+            auto tB = [&](int i) { if constexpr (ROLLED) return bq[i]; else return tab.B[i * Q + qz]; };
+            auto tG = [&](int i) { if constexpr (ROLLED) return gq[i]; else return tab.G[i * Q + qz]; };
+            auto tBw = [&](int i) { if constexpr (ROLLED) return bwq[i]; else return tab.Bw[i * Q + qz]; };
+            auto tGw = [&](int i) { if constexpr (ROLLED) return gwq[i]; else return tab.Gw[i * Q + qz]; };
+            float2 g01[3], g2p = make_float2(0.f, 0.f);
+            float g22 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g01[c] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float b = tB(i), g = tG(i);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g01[c] = __ffma2_rn(in01[c][i], make_float2(b, b), g01[c]);
+                g2p = __ffma2_rn(in2p[i], make_float2(g, g), g2p);
+                g22 = fmaf(in22[i], g, g22);
+            }
+            float gr[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gr[c][0] = g01[c].x;
+                gr[c][1] = g01[c].y;
+            }
+            gr[0][2] = g2p.x;
+            gr[1][2] = g2p.y;
+            gr[2][2] = g22;
+            // Voigt stress (Eq. 7), as in z_columns
+            float dg[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                dg[c] = fmaf(Ji[c], gr[c][0], fmaf(Ji[3 + c], gr[c][1], Ji[6 + c] * gr[c][2]));
+            const float ld = cl * (dg[0] + dg[1] + dg[2]);
+            float s[3][3];
+            s[0][0] = fmaf(m2, dg[0], ld);
+            s[1][1] = fmaf(m2, dg[1], ld);
+            s[2][2] = fmaf(m2, dg[2], ld);
+            auto shear = [&](int ia, int ib) {
+                return fmaf(cj[ib], gr[ia][0], fmaf(cj[3 + ib], gr[ia][1], fmaf(cj[6 + ib], gr[ia][2],
+                       fmaf(cj[ia], gr[ib][0], fmaf(cj[3 + ia], gr[ib][1], cj[6 + ia] * gr[ib][2])))));
+            };
+            s[0][1] = s[1][0] = shear(0, 1);
+            s[0][2] = s[2][0] = shear(0, 2);
+            s[1][2] = s[2][1] = shear(1, 2);
+            float qv[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    qv[c][m] = fmaf(s[c][0], Ji[m * 3 + 0], fmaf(s[c][1], Ji[m * 3 + 1], s[c][2] * Ji[m * 3 + 2]));
+            const float2 q2 = make_float2(qv[0][2], qv[1][2]);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const float bw = tBw(i), gw = tGw(i);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    acc01[c][i] = __ffma2_rn(make_float2(qv[c][0], qv[c][1]), make_float2(bw, bw), acc01[c][i]);
+                acc2p[i] = __ffma2_rn(q2, make_float2(gw, gw), acc2p[i]);
+                acc22[i] = fmaf(qv[2][2], gw, acc22[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cp[(3 * c) * D + i] = acc01[c][i].x;
+                cp[(3 * c + 1) * D + i] = acc01[c][i].y;
+            }
+            cp[2 * D + i] = acc2p[i].x;
+            cp[5 * D + i] = acc2p[i].y;
+            cp[8 * D + i] = acc22[i];
+        }
     }
 }
 
@@ -368,6 +561,12 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
 {
     using L = LineLayout<T, D, Q, TWO>;
     constexpr int D3 = D * D * D, DP = L::DP, CS = L::CS, BS = L::BS;
+    // FP32, even Q: the forward X and Y sweeps produce two quadrature
+    // outputs per paired FMA (__ffma2_rn, two fmaf per instruction)
+    constexpr bool kPairQ = sizeof(T) == 4 && Q % 2 == 0;
+    // FP32: the transposed Y and X sweeps produce two node outputs per paired
+    // FMA, with weight pairs from the transposed tables
+    constexpr bool kPairT = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *bufA = reinterpret_cast<T *>(smem_raw);
     T *bufB = bufA + (size_t)epb * L::A;
@@ -424,16 +623,37 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
             for (int i = 0; i < D; ++i) xv[i] = in[i];
         }
         T *out = bufB + (size_t)el * L::B + (c * D + iz) * 2 * Q * DP + iy;
+        if constexpr (kPairQ) {
+            // outputs q, q + 1 on paired FMAs (table pairs adjacent and
+            // 8-byte aligned for an even Q); same sums, same order
+            float2 xd[D];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            T u = T(0), v = T(0);
+            for (int i = 0; i < D; ++i) xd[i] = make_float2(xv[i], xv[i]);
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                u = fma(xv[i], tab.B[i * Q + q], u);
-                v = fma(xv[i], tab.G[i * Q + q], v);
+            for (int q = 0; q < Q; q += 2) {
+                float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    u = __ffma2_rn(xd[i], make_float2(tab.B[i * Q + q], tab.B[i * Q + q + 1]), u);
+                    v = __ffma2_rn(xd[i], make_float2(tab.G[i * Q + q], tab.G[i * Q + q + 1]), v);
+                }
+                out[(0 * Q + q) * DP] = u.x;
+                out[(0 * Q + q + 1) * DP] = u.y;
+                out[(1 * Q + q) * DP] = v.x;
+                out[(1 * Q + q + 1) * DP] = v.y;
             }
-            out[(0 * Q + q) * DP] = u;
-            out[(1 * Q + q) * DP] = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                T u = T(0), v = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    u = fma(xv[i], tab.B[i * Q + q], u);
+                    v = fma(xv[i], tab.G[i * Q + q], v);
+                }
+                out[(0 * Q + q) * DP] = u;
+                out[(1 * Q + q) * DP] = v;
+            }
         }
     }
     __syncthreads();
@@ -450,19 +670,47 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
             vv[i] = in[Q * DP + i];
         }
         T *out = bufA + (size_t)el * L::A + qx * CS + (c * 3) * D + iz;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            T d0 = T(0), d1 = T(0), d2 = T(0);
+        if constexpr (kPairQ) {
+            float2 ud[D], vd[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                d0 = fma(vv[i], tab.B[i * Q + q], d0);  // d/dxi
-                d1 = fma(uv[i], tab.G[i * Q + q], d1);  // d/deta
-                d2 = fma(uv[i], tab.B[i * Q + q], d2);  // interpolated, G follows along z
+                ud[i] = make_float2(uv[i], uv[i]);
+                vd[i] = make_float2(vv[i], vv[i]);
             }
-            T *o2 = out + q * Q * CS;
-            o2[0 * D] = d0;
-            o2[1 * D] = d1;
-            o2[2 * D] = d2;
+#pragma unroll
+            for (int q = 0; q < Q; q += 2) {
+                float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f), d2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float2 b2 = make_float2(tab.B[i * Q + q], tab.B[i * Q + q + 1]);
+                    d0 = __ffma2_rn(vd[i], b2, d0);                                                  // d/dxi
+                    d1 = __ffma2_rn(ud[i], make_float2(tab.G[i * Q + q], tab.G[i * Q + q + 1]), d1);  // d/deta
+                    d2 = __ffma2_rn(ud[i], b2, d2);                                                  // interpolated
+                }
+                T *o2 = out + q * Q * CS;
+                o2[0 * D] = d0.x;
+                o2[1 * D] = d1.x;
+                o2[2 * D] = d2.x;
+                o2 += Q * CS;
+                o2[0 * D] = d0.y;
+                o2[1 * D] = d1.y;
+                o2[2 * D] = d2.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                T d0 = T(0), d1 = T(0), d2 = T(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    d0 = fma(vv[i], tab.B[i * Q + q], d0);  // d/dxi
+                    d1 = fma(uv[i], tab.G[i * Q + q], d1);  // d/deta
+                    d2 = fma(uv[i], tab.B[i * Q + q], d2);  // interpolated, G follows along z
+                }
+                T *o2 = out + q * Q * CS;
+                o2[0 * D] = d0;
+                o2[1 * D] = d1;
+                o2[2 * D] = d2;
+            }
         }
     }
     __syncthreads();
@@ -487,17 +735,46 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
             t2[q] = col[2 * D];
         }
         T *out = bufB + (size_t)el * L::B + ((c * D + iz) * D) * BS + qx;
-#pragma unroll
-        for (int iy = 0; iy < D; ++iy) {
-            T u0 = T(0), u12 = T(0);
+        if constexpr (kPairT) {
+            // outputs iy, iy + 1 on paired FMAs, weight pairs from the
+            // transposed tables (an odd D's last second lane unused)
+            float2 t0d[Q], t1d[Q], t2d[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                u0 = fma(t0[q], tab.Bw[iy * Q + q], u0);
-                u12 = fma(t1[q], tab.Gw[iy * Q + q], u12);
-                u12 = fma(t2[q], tab.Bw[iy * Q + q], u12);
+                t0d[q] = make_float2(t0[q], t0[q]);
+                t1d[q] = make_float2(t1[q], t1[q]);
+                t2d[q] = make_float2(t2[q], t2[q]);
             }
-            out[iy * BS] = u0;
-            out[iy * BS + Q] = u12;
+#pragma unroll
+            for (int iy = 0; iy < D; iy += 2) {
+                float2 u0 = make_float2(0.f, 0.f), u12 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float2 bw = make_float2(tab.BwT[q * kTStride + iy], tab.BwT[q * kTStride + iy + 1]);
+                    u0 = __ffma2_rn(t0d[q], bw, u0);
+                    u12 = __ffma2_rn(t1d[q], make_float2(tab.GwT[q * kTStride + iy], tab.GwT[q * kTStride + iy + 1]), u12);
+                    u12 = __ffma2_rn(t2d[q], bw, u12);
+                }
+                out[iy * BS] = u0.x;
+                out[iy * BS + Q] = u12.x;
+                if (iy + 1 < D) {
+                    out[(iy + 1) * BS] = u0.y;
+                    out[(iy + 1) * BS + Q] = u12.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int iy = 0; iy < D; ++iy) {
+                T u0 = T(0), u12 = T(0);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    u0 = fma(t0[q], tab.Bw[iy * Q + q], u0);
+                    u12 = fma(t1[q], tab.Gw[iy * Q + q], u12);
+                    u12 = fma(t2[q], tab.Bw[iy * Q + q], u12);
+                }
+                out[iy * BS] = u0;
+                out[iy * BS + Q] = u12;
+            }
         }
     }
     __syncthreads();
@@ -519,15 +796,35 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
         if (FUSE && !(PA_INB(a.g, (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D, a.g.ne * 3 * D3) &&
                       PA_INB(a.g, (e0 + el) * 3 * D3 + ((c * D + iz) * D + iy) * D + D - 1, a.g.ne * 3 * D3)))
             continue;
-#pragma unroll
-        for (int ix = 0; ix < D; ++ix) {
-            T y = T(0);
+        if constexpr (kPairT) {
+            float2 u0d[Q], u12d[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                y = fma(u0[q], tab.Gw[ix * Q + q], y);
-                y = fma(u12[q], tab.Bw[ix * Q + q], y);
+                u0d[q] = make_float2(u0[q], u0[q]);
+                u12d[q] = make_float2(u12[q], u12[q]);
             }
-            out[ix] = y;
+#pragma unroll
+            for (int ix = 0; ix < D; ix += 2) {
+                float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    y = __ffma2_rn(u0d[q], make_float2(tab.GwT[q * kTStride + ix], tab.GwT[q * kTStride + ix + 1]), y);
+                    y = __ffma2_rn(u12d[q], make_float2(tab.BwT[q * kTStride + ix], tab.BwT[q * kTStride + ix + 1]), y);
+                }
+                out[ix] = y.x;
+                if (ix + 1 < D) out[ix + 1] = y.y;
+            }
+        } else {
+#pragma unroll
+            for (int ix = 0; ix < D; ++ix) {
+                T y = T(0);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    y = fma(u0[q], tab.Gw[ix * Q + q], y);
+                    y = fma(u12[q], tab.Bw[ix * Q + q], y);
+                }
+                out[ix] = y;
+            }
         }
     }
     if (FUSE) return;

@@ -196,17 +196,23 @@ int apply_multi_group(pa_op *const *ops, const void *const *xs, void *const *ys,
     PA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     static bool smem_set[kMaxAttrDevices] = {};
     if (int rc = max_smem_once(pa_apply_multi_kernel<T>, smem_set)) return rc;
-    for (size_t c0 = 0; c0 < idx.size(); c0 += kMaxMulti) {
-        const size_t m = std::min(idx.size() - c0, (size_t)kMaxMulti);
+    // the operators of one degree next to each other in the tile list, the
+    // highest degree first: the CTAs walk the list in step, so at any time
+    // they run the bodies of one or two degrees (whose code then stays in
+    // the instruction cache), and the longest tiles start first
+    std::vector<int> order(idx);
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return ops[u]->p > ops[v]->p; });
+    for (size_t c0 = 0; c0 < order.size(); c0 += kMaxMulti) {
+        const size_t m = std::min(order.size() - c0, (size_t)kMaxMulti);
         MultiArgs<T> ma{};
         AssembleMulti<T> mb{};
         ma.count = mb.count = (int)m;
         ma.cta_start[0] = mb.node_start[0] = 0;
         size_t smem = 0;
         for (size_t j = 0; j < m; ++j) {
-            pa_op *op = ops[idx[c0 + j]];
+            pa_op *op = ops[order[c0 + j]];
             MultiOp<T> &o = ma.op[j];
-            o.x = static_cast<const T *>(xs[idx[c0 + j]]);
+            o.x = static_cast<const T *>(xs[order[c0 + j]]);
             o.ye = static_cast<T *>(op->d_ye);
             o.geo = static_cast<const T *>(op->d_geo);
             o.ess = op->d_ess;
@@ -220,7 +226,7 @@ int apply_multi_group(pa_op *const *ops, const void *const *xs, void *const *ys,
             smem = std::max(smem, multi_tile_smem<T>(op->p, o.epb, o.split != 0));
             ma.cta_start[j + 1] = ma.cta_start[j] + (op->g.ne + o.epb - 1) / o.epb;
             mb.ye[j] = o.ye;
-            mb.y[j] = static_cast<T *>(ys[idx[c0 + j]]);
+            mb.y[j] = static_cast<T *>(ys[order[c0 + j]]);
             mb.x[j] = o.x;
             mb.ess[j] = op->d_ess;
             mb.g[j] = op->g;

@@ -17,8 +17,10 @@
 //            plane's D x D outputs, which it writes to the E-vector.
 //
 // Two barriers per CTA pass instead of six; each shared word written feeds
-// D or Q FMAs of the next stage.  The sums run in the same order as in the
-// line variants, so the results are bitwise theirs.
+// D or Q FMAs of the next stage.  In FP32, stages A and B run on paired FMAs
+// (__ffma2_rn: two fmaf per instruction, half the issue slots for the same
+// FMA work).  The sums run in the same order as in the line variants, so
+// the results are bitwise theirs.
 #pragma once
 
 #include <cstdint>
@@ -160,6 +162,106 @@ __device__ __forceinline__ void plane_backward(const Tables<T> &tab, const T *co
         for (int ix = 0; ix < D; ++ix) out[iy * D + ix] = acc[iy][ix];
 }
 
+// FP32 stage A on paired FMAs (__ffma2_rn, two fmaf in one instruction):
+// the X sweep runs two rows iy of the plane at a time (the last row of an
+// odd D alone), the Y sweep two quadrature rows qy at a time (the last of
+// an odd Q alone).  Same terms in the same order per sum as plane_forward:
+// bitwise its results (measured 2-3 % faster at p = 2, 4; paired forms of
+// stage C, over outputs ix or over rows iy with the transposed tables,
+// measured within 1 % of the scalar stage and are not used).
+template <int D, int Q>
+__device__ __forceinline__ void plane_forward_f2(const ApplyArgs<float> &a, const Tables<float> &tab,
+                                                 float *colbase, int64_t k0, int64_t Mx)
+{
+    constexpr int CS = PlaneLayout<float, D, Q>::CS;
+    constexpr int H = D / 2, HQ = Q / 2;
+    float2 xp[H][D];  // rows 2h and 2h + 1
+    float xl[D];      // row D - 1 of an odd D
+#pragma unroll
+    for (int iy = 0; iy < D; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < D; ++ix) {
+            const int64_t k = k0 + Mx * iy + ix;
+            const bool in = PA_INB(a.g, k, 3 * a.g.Nn);
+            float v = in ? a.x[k] : 0.f;
+            if (in && a.ess && a.ess[k]) v = 0.f;
+            if (iy < 2 * H) {
+                if (iy & 1) xp[iy >> 1][ix].y = v;
+                else xp[iy >> 1][ix].x = v;
+            } else {
+                xl[ix] = v;
+            }
+        }
+#pragma unroll(PlaneLayout<float, D, Q>::kUnroll)
+    for (int qx = 0; qx < Q; ++qx) {
+        float bq[D], gq[D];
+#pragma unroll
+        for (int ix = 0; ix < D; ++ix) {
+            bq[ix] = tab.B[ix * Q + qx];
+            gq[ix] = tab.G[ix * Q + qx];
+        }
+        float u[D], v[D];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            float2 su = make_float2(0.f, 0.f), sv = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int ix = 0; ix < D; ++ix) {
+                su = __ffma2_rn(xp[h][ix], make_float2(bq[ix], bq[ix]), su);
+                sv = __ffma2_rn(xp[h][ix], make_float2(gq[ix], gq[ix]), sv);
+            }
+            u[2 * h] = su.x;
+            u[2 * h + 1] = su.y;
+            v[2 * h] = sv.x;
+            v[2 * h + 1] = sv.y;
+        }
+        if constexpr (D & 1) {
+            float su = 0.f, sv = 0.f;
+#pragma unroll
+            for (int ix = 0; ix < D; ++ix) {
+                su = fmaf(xl[ix], bq[ix], su);
+                sv = fmaf(xl[ix], gq[ix], sv);
+            }
+            u[D - 1] = su;
+            v[D - 1] = sv;
+        }
+#pragma unroll
+        for (int j = 0; j < HQ; ++j) {
+            const int qy = 2 * j;
+            float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f), d2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int iy = 0; iy < D; ++iy) {
+                const float2 b2 = make_float2(tab.B[iy * Q + qy], tab.B[iy * Q + qy + 1]);
+                const float2 g2 = make_float2(tab.G[iy * Q + qy], tab.G[iy * Q + qy + 1]);
+                d0 = __ffma2_rn(make_float2(v[iy], v[iy]), b2, d0);  // d/dxi
+                d1 = __ffma2_rn(make_float2(u[iy], u[iy]), g2, d1);  // d/deta
+                d2 = __ffma2_rn(make_float2(u[iy], u[iy]), b2, d2);  // interpolated
+            }
+            float *o = colbase + (qy * Q + qx) * CS;
+            o[0 * D] = d0.x;
+            o[1 * D] = d1.x;
+            o[2 * D] = d2.x;
+            o += Q * CS;
+            o[0 * D] = d0.y;
+            o[1 * D] = d1.y;
+            o[2 * D] = d2.y;
+        }
+        if constexpr (Q & 1) {
+            constexpr int qy = Q - 1;
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+            for (int iy = 0; iy < D; ++iy) {
+                d0 = fmaf(v[iy], tab.B[iy * Q + qy], d0);
+                d1 = fmaf(u[iy], tab.G[iy * Q + qy], d1);
+                d2 = fmaf(u[iy], tab.B[iy * Q + qy], d2);
+            }
+            float *o = colbase + (qy * Q + qx) * CS;
+            o[0 * D] = d0;
+            o[1 * D] = d1;
+            o[2 * D] = d2;
+        }
+    }
+}
+
 template <typename T, int D, int Q, bool SPLIT>
 __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T> &tab, int epb, int64_t blk)
 {
@@ -189,12 +291,15 @@ __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T
     for (int o = tid; o < ne_blk * 3 * D; o += nt) {
         const int el = o / (3 * D), r = o - el * 3 * D;
         const int c = r / D, iz = r - c * D;
-        plane_forward<T, D, Q>(a, tab, buf + (size_t)el * L::A + c * 3 * D + iz, c * Nn + gbase[el] + MxMy * iz, Mx);
+        T *cb = buf + (size_t)el * L::A + c * 3 * D + iz;
+        if constexpr (sizeof(T) == 4) plane_forward_f2<D, Q>(a, tab, cb, c * Nn + gbase[el] + MxMy * iz, Mx);
+        else plane_forward<T, D, Q>(a, tab, cb, c * Nn + gbase[el] + MxMy * iz, Mx);
     }
     __syncthreads();
 
     // stage B: Z sweep, pointwise stress, Z^T sweep per column, in place
     if constexpr (SPLIT) z_columns_split<T, D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
+    else if constexpr (sizeof(T) == 4) z_columns_f2<D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
     else z_columns<T, D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
     __syncthreads();
 

@@ -151,6 +151,7 @@ void fill_tables(const Basis1D &b, Tables<T> &t)
         t.Bw[i] = T(b.Bw[i]);
         t.Gw[i] = T(b.Gw[i]);
     }
+    transpose_tables(t, b.D, b.Q);
 }
 template void fill_tables<double>(const Basis1D &, Tables<double> &);
 template void fill_tables<float>(const Basis1D &, Tables<float> &);

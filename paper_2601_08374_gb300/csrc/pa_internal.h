@@ -74,17 +74,41 @@ struct Basis1D {
     void build(int p, int q);
 };
 
+// Even row stride of the transposed tables.
+constexpr int kTStride = (kMaxD + 1) & ~1;
+
 // Kernel-parameter tables (passed by value; constant-bank operands).
 template <typename T>
 struct Tables {
-    T B[kMaxD * kMaxQ];
-    T G[kMaxD * kMaxQ];
-    T Bw[kMaxD * kMaxQ];
-    T Gw[kMaxD * kMaxQ];
+    // 16-byte aligned: adjacent entries of an even index load as one pair
+    alignas(16) T B[kMaxD * kMaxQ];
+    alignas(16) T G[kMaxD * kMaxQ];
+    alignas(16) T Bw[kMaxD * kMaxQ];
+    alignas(16) T Gw[kMaxD * kMaxQ];
+    // FP32 only: Bw and Gw transposed, [q * kTStride + i], zero past i = p,
+    // so that the weights of nodes i, i + 1 (i even) at one point q load as
+    // one aligned pair
+    alignas(16) T BwT[sizeof(T) == 4 ? kMaxQ * kTStride : 1];
+    alignas(16) T GwT[sizeof(T) == 4 ? kMaxQ * kTStride : 1];
 };
 
 template <typename T>
 void fill_tables(const Basis1D &b, Tables<T> &t);
+
+// Fill the transposed tables BwT, GwT (FP32) from Bw, Gw of degree D - 1;
+// every table builder ends with this.
+template <typename T>
+inline void transpose_tables(Tables<T> &t, int D, int Q)
+{
+    constexpr int nT = (int)(sizeof(t.BwT) / sizeof(T));
+    for (int k = 0; k < nT; ++k) t.BwT[k] = t.GwT[k] = T(0);
+    if (nT < kMaxQ * kTStride) return;
+    for (int i = 0; i < D; ++i)
+        for (int q = 0; q < Q; ++q) {
+            t.BwT[q * kTStride + i] = t.Bw[i * Q + q];
+            t.GwT[q * kTStride + i] = t.Gw[i * Q + q];
+        }
+}
 
 // Geometry record per element (12 values of the op's precision):
 // J^-1 row-major (9), lambda*detJ, mu*detJ, detJ.

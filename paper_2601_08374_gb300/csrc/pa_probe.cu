@@ -35,7 +35,28 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(T *out, int it
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-template <typename T>
+// The same FMA work on paired instructions (__ffma2_rn): kChains / 2
+// chains of float2 per thread.
+__global__ void __launch_bounds__(kProbeThreads) fma2_probe_kernel(float *out, int iters, float b, float c)
+{
+    float2 a[kChains / 2];
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k)
+        a[k] = make_float2(float(threadIdx.x + 2 * k) * 1e-3f, float(threadIdx.x + 2 * k + 1) * 1e-3f);
+    const float2 bb = make_float2(b, b), cc = make_float2(c, c);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < kChains / 2; ++k) a[k] = __ffma2_rn(a[k], bb, cc);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) s += a[k].x + a[k].y;
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T, bool PAIRED = false>
 int measure(double *tflops, cudaStream_t s)
 {
     int dev = 0, sms = 0;
@@ -55,7 +76,8 @@ int measure(double *tflops, cudaStream_t s)
     } else {
         for (int rep = 0; rep < 6 && rc == PA_OK; ++rep) {
             cudaEventRecord(e0, s);
-            fma_probe_kernel<T><<<blocks, kProbeThreads, 0, s>>>(out, iters, T(0.999), T(1e-4));
+            if constexpr (PAIRED) fma2_probe_kernel<<<blocks, kProbeThreads, 0, s>>>(out, iters, 0.999f, 1e-4f);
+            else fma_probe_kernel<T><<<blocks, kProbeThreads, 0, s>>>(out, iters, T(0.999), T(1e-4));
             cudaEventRecord(e1, s);
             cudaError_t e = cudaEventSynchronize(e1);
             if (e != cudaSuccess) {
@@ -84,7 +106,9 @@ using namespace pa;
 extern "C" int pa_measure_fma_rate(int precision, double *tflops, void *stream)
 {
     if (!tflops) return set_error(PA_EINVAL, "pa_measure_fma_rate: null output");
-    if (precision != PA_FP64 && precision != PA_FP32) return set_error(PA_EINVAL, "pa_measure_fma_rate: bad precision");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return precision == PA_FP64 ? measure<double>(tflops, s) : measure<float>(tflops, s);
+    if (precision == PA_FP64) return measure<double>(tflops, s);
+    if (precision == PA_FP32) return measure<float>(tflops, s);
+    if (precision == PA_FMA_FP32X2) return measure<float, true>(tflops, s);
+    return set_error(PA_EINVAL, "pa_measure_fma_rate: bad precision");
 }

@@ -95,6 +95,7 @@ void stack_tables(int p, Tables<T> &t)
             t.Bw[i * Q + k] = (T)(B[i * Q + k] * qw[k]);
             t.Gw[i * Q + k] = (T)(G[i * Q + k] * qw[k]);
         }
+    transpose_tables(t, D, Q);
 }
 
 template <typename T>
