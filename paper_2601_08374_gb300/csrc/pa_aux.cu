@@ -168,24 +168,39 @@ __global__ void __launch_bounds__(256) assemble_rows_kernel(const T *__restrict_
                                                             T ess_value, int accumulate, Grid g,
                                                             const int *__restrict__ skip)
 {
+    // R rows per pass (rows row0 + r * gridDim.x): their loads are issued
+    // before any of their stores, so a thread keeps R node sums in flight.
+    // Measured against one row per pass: p = 2, 4 5 % faster with two rows
+    // (FP64 and FP32), p = 6, 8 within +-4 % and four rows slower everywhere
+    constexpr int R = P <= 4 ? 2 : 1;
     if (skip && *skip) return;
     const int64_t rows = (int64_t)g.My * g.Mz;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        int ey[2], iy[2], ez[2], iz[2];
-        const int cy = axis_owners_p<P>((int)(row % g.My), g.ny, ey, iy);
-        const int cz = axis_owners_p<P>((int)(row / g.My), g.nz, ez, iz);
+    for (int64_t row0 = blockIdx.x; row0 < rows; row0 += (int64_t)R * gridDim.x) {
         for (int gx = threadIdx.x; gx < g.Mx; gx += blockDim.x) {
             int ex[2], ix[2];
             const int cx = axis_owners_p<P>(gx, g.nx, ex, ix);
-            T acc[3];
-            node_sum_p<T, P>(ye, g, ex, ix, cx, ey, iy, cy, ez, iz, cz, acc);
-            const int64_t gn = gx + (int64_t)g.Mx * row;
+            T acc[R][3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int64_t k = c * g.Nn + gn;
-                T v = acc[c];
-                if (ess && ess[k]) v = xin ? xin[k] : ess_value;
-                y[k] = accumulate ? y[k] + v : v;
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = row0 + (int64_t)r * gridDim.x;
+                if (row >= rows) break;
+                int ey[2], iy[2], ez[2], iz[2];
+                const int cy = axis_owners_p<P>((int)(row % g.My), g.ny, ey, iy);
+                const int cz = axis_owners_p<P>((int)(row / g.My), g.nz, ez, iz);
+                node_sum_p<T, P>(ye, g, ex, ix, cx, ey, iy, cy, ez, iz, cz, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = row0 + (int64_t)r * gridDim.x;
+                if (row >= rows) break;
+                const int64_t gn = gx + (int64_t)g.Mx * row;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int64_t k = c * g.Nn + gn;
+                    T v = acc[r][c];
+                    if (ess && ess[k]) v = xin ? xin[k] : ess_value;
+                    y[k] = accumulate ? y[k] + v : v;
+                }
             }
         }
     }
