@@ -588,6 +588,29 @@ def serving_requests(pa, count, seed):
     return out
 
 
+def ua_geometry_timing(pa, torch, c, stream, reps=20):
+    """Element-kernel time of one FP32 plane-kernel operator with the stored
+    geometry records and with UA geometry (J only, J^-1 and detJ recomputed
+    in the kernel), measured the same way: warm-up, then `reps` back-to-back
+    applies of the same x / y with per-launch CUDA events."""
+    op = c["op"]
+    out = {"p": c["p"], "launch": list(pa.pa_op_get_launch(op.h)),
+           "geometry_bytes_stored": int(c["ne"] * 12 * 4), "geometry_bytes_ua": int(c["ne"] * 9 * 4)}
+    for mode, key in ((pa.PA_GEOMETRY_STORED, "element_ms_stored"), (pa.PA_GEOMETRY_UA, "element_ms_ua")):
+        pa.pa_op_set_geometry_mode(op.h, mode)
+        for _ in range(3):
+            pa.pa_op_apply(op.h, c["x"], c["y"], stream)
+        pa.pa_op_profile(op.h, True)
+        for _ in range(reps):
+            pa.pa_op_apply(op.h, c["x"], c["y"], stream)
+        te, _, na = pa.pa_op_profile_read(op.h)
+        pa.pa_op_profile(op.h, False)
+        out[key] = round(te / max(na, 1), 5)
+    pa.pa_op_set_geometry_mode(op.h, pa.PA_GEOMETRY_STORED)
+    out["ua_over_stored"] = round(out["element_ms_ua"] / out["element_ms_stored"], 4)
+    return out
+
+
 def run_fp32_sweep(args, pa, torch, sms, mhz):
     """The same operator sweep in FP32 (the apply of the mixed-precision
     solves): GDoF/s per p and over the sweep, with the element kernel's
@@ -623,9 +646,12 @@ def run_fp32_sweep(args, pa, torch, sms, mhz):
     fma_measured = pa.pa_measure_fma_rate(pa.PA_FP32, stream)
     fma2_measured = pa.pa_measure_fma_rate(pa.PA_FMA_FP32X2, stream)
     per_p, fl_tot, el_tot = [], 0.0, 0.0
+    ua = []
     for c in cases:
         te, ta, na = pa.pa_op_profile_read(c["op"].h)
         pa.pa_op_profile(c["op"].h, False)
+        if c["p"] <= 2 and c["launch"][0] == 5:
+            ua.append(ua_geometry_timing(pa, torch, c, stream))
         fl = flops_per_element(c["p"]) * c["ne"]
         fl_tot += fl * na
         el_tot += te
@@ -637,7 +663,8 @@ def run_fp32_sweep(args, pa, torch, sms, mhz):
             "frac_of_derived_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / peak, 4),
             "derived_fp32_peak_tflops": round(peak, 3), "measured_fp32_fma_peak_tflops": round(fma_measured, 3),
             "measured_fp32_paired_fma_peak_tflops": round(fma2_measured, 3),
-            "frac_of_measured_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / fma_measured, 4), "per_p": per_p}
+            "frac_of_measured_fp32_peak": round(fl_tot / (el_tot * 1e-3) / 1e12 / fma_measured, 4), "per_p": per_p,
+            "ua_geometry": ua}
 
 
 def run_ablation(args, pa, torch):

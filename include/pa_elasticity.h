@@ -229,6 +229,26 @@ int pa_op_apply_stage(pa_op *op, int stage, const void *x, void *y, void *stream
  * than 2 x 152 x (its elements per CTA) elements the elements per CTA drop
  * to max(1, n_e / 304), so that every SM gets two CTAs where it can. */
 int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads);
+
+/* Geometry data of the element kernel.  PA_GEOMETRY_STORED (the default):
+ * the stored per-element record of the PA data D (J^-1, lambda detJ,
+ * mu detJ, detJ; 12 values).  PA_GEOMETRY_UA: the unassembled evaluation
+ * the paper contrasts with PA (Sec. 2, the operator chain: UA recomputes D
+ * in every application): only the 9 entries of each element's J are kept
+ * ([n_e][9] in the operator's precision, uploaded from the maps given at
+ * mesh creation, owned by the operator), and the plane kernel recomputes
+ * J^-1, detJ and the material factors per element at the start of each CTA
+ * pass.  UA is available for FP32 operators with p <= 6 and the constant
+ * isotropic material; it runs in variant 5 (setting UA moves the launch
+ * shape to variant 5; pa_op_set_launch then rejects other variants), and
+ * pa_op_set_material with a per-element material or pa_op_set_anisotropic
+ * return PA_EINVAL while it is set.  Batched applies take UA operators one
+ * by one.  The diagonal and the solver levels keep the stored records.
+ * Synchronous (one host-to-device copy).  PA_EINVAL for another mode or an
+ * operator that does not qualify. */
+#define PA_GEOMETRY_STORED 0
+#define PA_GEOMETRY_UA 1
+int pa_op_set_geometry_mode(pa_op *op, int mode);
 int pa_op_get_launch(const pa_op *op, int *variant, int *elems_per_block, int *threads);
 
 /* Reports (and clears) the operator's device status since the last check:

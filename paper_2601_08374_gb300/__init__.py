@@ -20,6 +20,7 @@ from .build import LIB as _LIB_PATH
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ENOTCONV, PA_EBREAKDOWN, PA_ETIMEOUT, PA_EBUSY, PA_ECANCELED = range(9)
 PA_FP64, PA_FP32 = 0, 1
 PA_FMA_FP32X2 = 2  # pa_measure_fma_rate: FP32 on paired FMA instructions
+PA_GEOMETRY_STORED, PA_GEOMETRY_UA = 0, 1
 PA_SOLVE_FP64, PA_SOLVE_MIXED, PA_SOLVE_MIXED_FCG = 0, 1, 2
 
 # PA_ELASTICITY_LIB selects another build of the same library (the tests'
@@ -103,6 +104,7 @@ _sig("pa_apply_noalloc", [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int
                           ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("pa_measure_fma_rate", [ctypes.c_int, _dp, _vp])
 _sig("pa_op_set_launch", [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int])
+_sig("pa_op_set_geometry_mode", [_vp, ctypes.c_int])
 _sig("pa_op_get_launch", [_vp, _ip, _ip, _ip])
 _sig("pa_op_autotune", [_vp, _vp])
 _sig("pa_op_profile", [_vp, ctypes.c_int])
@@ -363,6 +365,12 @@ def pa_measure_fma_rate(precision, stream=None):
 
 def pa_op_set_launch(op, variant, elems_per_block, threads):
     _check(lib.pa_op_set_launch(op, variant, elems_per_block, threads), "pa_op_set_launch")
+
+
+def pa_op_set_geometry_mode(op, mode):
+    """PA_GEOMETRY_STORED (stored per-element records) or PA_GEOMETRY_UA
+    (J only; J^-1 and detJ recomputed in the FP32 plane kernel)."""
+    _check(lib.pa_op_set_geometry_mode(op, mode), "pa_op_set_geometry_mode")
 
 
 def pa_op_get_launch(op):

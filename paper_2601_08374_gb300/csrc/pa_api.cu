@@ -118,6 +118,12 @@ static int apply_impl(pa_op *op, const T *x, T *y, bool accumulate, cudaStream_t
     a.cvoigt = static_cast<const T *>(op->d_cv);
     a.err = op->d_err;
     a.wait_cycles = op->wait_cycles;
+    if (op->geometry_mode == PA_GEOMETRY_UA) {
+        a.geo = static_cast<const T *>(op->d_ua);
+        a.ua = 1;
+        a.ua_lambda = (T)op->lambda;
+        a.ua_mu = (T)op->mu;
+    }
     const Tables<T> *tab;
     if constexpr (sizeof(T) == 8) tab = &op->tab64;
     else tab = &op->tab32;
@@ -308,6 +314,7 @@ int pa_op_destroy(pa_op *op)
     cudaFree(op->d_yh);
     for (void *q : op->d_abl) cudaFree(q);
     cudaFree(op->d_cv);
+    cudaFree(op->d_ua);
     cudaFree(op->d_err);
     delete op;
     return PA_OK;
@@ -440,16 +447,18 @@ namespace pa {
 
 int apply_batch_async(pa_op *const *ops, const void *const *xs, void *const *ys, int count, cudaStream_t s)
 {
-    // anisotropic operators are applied one by one (the batched kernels take
-    // the isotropic material)
-    bool any_aniso = false;
-    for (int k = 0; k < count; ++k) any_aniso = any_aniso || ops[k]->d_cv;
-    if (any_aniso) {
+    // anisotropic operators and operators with UA geometry are applied one
+    // by one (the batched kernels take the isotropic material and the stored
+    // geometry records)
+    auto single = [](const pa_op *op) { return op->d_cv != nullptr || op->geometry_mode == PA_GEOMETRY_UA; };
+    bool any_single = false;
+    for (int k = 0; k < count; ++k) any_single = any_single || single(ops[k]);
+    if (any_single) {
         std::vector<pa_op *> o2;
         std::vector<const void *> x2;
         std::vector<void *> y2;
         for (int k = 0; k < count; ++k) {
-            if (ops[k]->d_cv) {
+            if (single(ops[k])) {
                 int rc = op_apply_async(ops[k], xs[k], ys[k], false, s, nullptr);
                 if (rc) return rc;
             } else {
@@ -615,6 +624,8 @@ int pa_op_set_material(pa_op *op, const double *lambda_mu)
         op->h_mat.clear();
         return upload_geometry(op);
     }
+    if (op->geometry_mode == PA_GEOMETRY_UA)
+        return set_error(PA_EINVAL, "pa_op_set_material: UA geometry takes the operator's constant material");
     for (int64_t k = 0; k < 2 * ne; ++k)
         if (!std::isfinite(lambda_mu[k])) return set_error(PA_EINVAL, "pa_op_set_material: non-finite material");
     try {
@@ -647,6 +658,8 @@ int pa_op_set_anisotropic(pa_op *op, const double *cvoigt)
         op->d_cv = nullptr;
         return PA_OK;
     }
+    if (op->geometry_mode == PA_GEOMETRY_UA)
+        return set_error(PA_EINVAL, "pa_op_set_anisotropic: UA geometry takes the isotropic material");
     for (int64_t e = 0; e < ne; ++e)
         for (int i = 0; i < 6; ++i)
             for (int j = 0; j < 6; ++j) {
@@ -696,6 +709,8 @@ int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads)
     if (!op) return set_error(PA_EINVAL, "pa_op_set_launch: null op");
     if (variant < 0 || variant > kMaxVariant || elems_per_block < 1 || threads < 32 || threads > 512 || threads % 32)
         return set_error(PA_EINVAL, "pa_op_set_launch: bad shape");
+    if (op->geometry_mode == PA_GEOMETRY_UA && variant != 5)
+        return set_error(PA_EINVAL, "pa_op_set_launch: UA geometry runs in the plane kernel (variant 5)");
     ApplyLaunch c;
     c.variant = variant;
     c.epb = elems_per_block;
@@ -703,6 +718,55 @@ int pa_op_set_launch(pa_op *op, int variant, int elems_per_block, int threads)
     size_t smem = op->precision == PA_FP64 ? apply_smem_bytes<double>(op->p, c) : apply_smem_bytes<float>(op->p, c);
     if (smem == 0 || smem > 227 * 1024) return set_error(PA_EINVAL, "pa_op_set_launch: shared memory too large");
     op->launch = c;
+    return PA_OK;
+}
+
+int pa_op_set_geometry_mode(pa_op *op, int mode)
+{
+    if (!op) return set_error(PA_EINVAL, "pa_op_set_geometry_mode: null op");
+    if (mode == PA_GEOMETRY_STORED) {
+        cudaFree(op->d_ua);
+        op->d_ua = nullptr;
+        op->geometry_mode = PA_GEOMETRY_STORED;
+        return PA_OK;
+    }
+    if (mode != PA_GEOMETRY_UA) return set_error(PA_EINVAL, "pa_op_set_geometry_mode: unknown mode");
+    if (op->precision != PA_FP32 || op->p > 6)
+        return set_error(PA_EINVAL, "pa_op_set_geometry_mode: UA geometry runs in the FP32 plane kernel (p <= 6)");
+    if (!op->h_mat.empty() || op->d_cv)
+        return set_error(PA_EINVAL, "pa_op_set_geometry_mode: UA geometry takes the constant isotropic material");
+    if (op->geometry_mode == PA_GEOMETRY_UA) return PA_OK;
+    const int64_t ne = op->g.ne;
+    std::vector<float> J;
+    try {
+        J.resize((size_t)ne * kUaStride);
+    } catch (...) {
+        return set_error(PA_ENOMEM, "pa_op_set_geometry_mode: host allocation");
+    }
+    for (int64_t e = 0; e < ne; ++e)
+        for (int k = 0; k < kUaStride; ++k) J[(size_t)e * kUaStride + k] = (float)op->h_affine[12 * e + k];
+    void *d = nullptr;
+    if (cudaMalloc(&d, J.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PA_ENOMEM, "pa_op_set_geometry_mode: device allocation");
+    }
+    const cudaError_t e = cudaMemcpy(d, J.data(), J.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_error(e, "pa_op_set_geometry_mode: upload");
+    }
+    op->d_ua = d;
+    op->geometry_mode = PA_GEOMETRY_UA;
+    if (op->launch.variant != 5) {
+        // the plane kernel's shape: the default for p <= 4, one element per CTA above
+        ApplyLaunch c = default_apply_launch(op->p, PA_FP32);
+        if (c.variant != 5) {
+            c.variant = 5;
+            c.epb = 1;
+            c.threads = 128;
+        }
+        op->launch = c;
+    }
     return PA_OK;
 }
 

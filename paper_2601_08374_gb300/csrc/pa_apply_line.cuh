@@ -74,8 +74,8 @@ __device__ __forceinline__ T sel3v(int k, T x0, T x1, T x2) { return k == 0 ? x0
 // divergence in component order and broadcasts it.  Each lane keeps J^-1
 // with its columns rotated to the order c, c + 1, c + 2 (mod 3).
 template <typename T, int D, int Q, bool ROLLED = false>
-__device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
-                                                int64_t e0, int ne_blk, int tid, int nt)
+__device__ __forceinline__ void z_columns_split(const T *geo0, const Tables<T> &tab, T *bufA, int astride, int ne_blk,
+                                                int tid, int nt)
 {
     using L = LineLayout<T, D, Q>;
     constexpr int CS = L::CS;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int i = 0; i < D; ++i) in[k][i] = cpt[k * D + i];
-        const T *geo = a.geo + (e0 + el) * kGeoStride;
+        const T *geo = geo0 + (size_t)el * kGeoStride;
         T R[3][3];  // R[n][r] = Ji[n][(c + r) mod 3]
 #pragma unroll
         for (int n = 0; n < 3; ++n) {
@@ -190,10 +190,11 @@ __device__ __forceinline__ void z_columns_split(const ApplyArgs<T> &a, const Tab
 // 9 x D inputs (channels [c][k], k = d/dxi, d/deta, interpolated) and 9 x D
 // accumulators in registers; Z sweep, pointwise stress of Eq. 7, Q
 // reconstruction and Z^T sweep, the result written back in place.  Columns
-// of element el start at bufA + el * astride, column col at col * CS.
+// of element el start at bufA + el * astride, column col at col * CS; its
+// geometry record at geo0 + el * kGeoStride.
 template <typename T, int D, int Q, bool ROLLED = false>
-__device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
-                                          int64_t e0, int ne_blk, int tid, int nt)
+__device__ __forceinline__ void z_columns(const T *geo0, const Tables<T> &tab, T *bufA, int astride, int ne_blk,
+                                          int tid, int nt)
 {
     constexpr int CS = LineLayout<T, D, Q>::CS;
     // ROLLED: the qz loop is not unrolled (smaller code; the table columns of
@@ -214,7 +215,7 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
         for (int ch = 0; ch < 9; ++ch)
 #pragma unroll
             for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
-        const T *geo = a.geo + (e0 + el) * kGeoStride;
+        const T *geo = geo0 + (size_t)el * kGeoStride;
         T Ji[9], cj[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
@@ -323,8 +324,8 @@ __device__ __forceinline__ void z_columns(const ApplyArgs<T> &a, const Tables<T>
 // paired registers cost occupancy (p = 6: 164 -> 182 registers, 16 %
 // slower).
 template <int D, int Q, bool ROLLED = false>
-__device__ __forceinline__ void z_columns_f2(const ApplyArgs<float> &a, const Tables<float> &tab, float *bufA,
-                                             int astride, int64_t e0, int ne_blk, int tid, int nt)
+__device__ __forceinline__ void z_columns_f2(const float *geo0, const Tables<float> &tab, float *bufA, int astride,
+                                             int ne_blk, int tid, int nt)
 {
     constexpr int CS = LineLayout<float, D, Q>::CS;
     constexpr int kUnrollQz = ROLLED ? 1 : Q;
@@ -344,7 +345,7 @@ __device__ __forceinline__ void z_columns_f2(const ApplyArgs<float> &a, const Ta
             in2p[i] = make_float2(cp[2 * D + i], cp[5 * D + i]);
             in22[i] = cp[8 * D + i];
         }
-        const float *geo = a.geo + (e0 + el) * kGeoStride;
+        const float *geo = geo0 + (size_t)el * kGeoStride;
         float Ji[9], cj[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
@@ -451,8 +452,8 @@ __device__ __forceinline__ void z_columns_f2(const ApplyArgs<float> &a, const Ta
 // runs the Z^T sweep from them.  Every accumulator receives the same terms
 // in the same order as in z_columns, so the results are bitwise the same.
 template <typename T, int D, int Q>
-__device__ __forceinline__ void z_columns_2pass(const ApplyArgs<T> &a, const Tables<T> &tab, T *bufA, int astride,
-                                                T *qbuf, int qstride, int64_t e0, int ne_blk, int tid, int nt)
+__device__ __forceinline__ void z_columns_2pass(const T *geo0, const Tables<T> &tab, T *bufA, int astride, T *qbuf,
+                                                int qstride, int ne_blk, int tid, int nt)
 {
     constexpr int CS = LineLayout<T, D, Q>::CS;
     constexpr int QS = LineLayout<T, D, Q, true>::QS;
@@ -466,7 +467,7 @@ __device__ __forceinline__ void z_columns_2pass(const ApplyArgs<T> &a, const Tab
             for (int ch = 0; ch < 9; ++ch)
 #pragma unroll
                 for (int i = 0; i < D; ++i) in[ch][i] = cp[ch * D + i];
-            const T *geo = a.geo + (e0 + el) * kGeoStride;
+            const T *geo = geo0 + (size_t)el * kGeoStride;
             T Ji[9], cj[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) Ji[i] = geo[i];
@@ -716,9 +717,10 @@ __device__ __forceinline__ void line_body(const ApplyArgs<T> &a, const Tables<T>
     __syncthreads();
 
     // ---- Z sweep + pointwise + Z^T sweep: column (el, qx, qy), in place
-    if constexpr (SPLIT) z_columns_split<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
-    else if constexpr (TWO) z_columns_2pass<T, D, Q>(a, tab, bufA, L::A, bufB, L::B, e0, ne_blk, tid, nt);
-    else z_columns<T, D, Q>(a, tab, bufA, L::A, e0, ne_blk, tid, nt);
+    const T *geo0 = a.geo + e0 * kGeoStride;  // the tile's geometry records
+    if constexpr (SPLIT) z_columns_split<T, D, Q>(geo0, tab, bufA, L::A, ne_blk, tid, nt);
+    else if constexpr (TWO) z_columns_2pass<T, D, Q>(geo0, tab, bufA, L::A, bufB, L::B, ne_blk, tid, nt);
+    else z_columns<T, D, Q>(geo0, tab, bufA, L::A, ne_blk, tid, nt);
     __syncthreads();
 
     // ---- Y^T sweep: line (el, c, iz, qx) -> S3 [c][iz][iy][k*Q + qx]

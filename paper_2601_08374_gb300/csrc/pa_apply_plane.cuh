@@ -47,10 +47,36 @@ struct PlaneLayout {
     __host__ __device__ static size_t table_offset(int epb) { return (((size_t)epb * A * sizeof(T)) + 15) & ~(size_t)15; }
 };
 
+// Shared memory of a CTA: the column buffers, the elements' base nodes and
+// (geometry recomputed in the kernel) the tile's geometry records.
 template <typename T, int D, int Q>
 size_t plane_smem_bytes(int epb)
 {
-    return PlaneLayout<T, D, Q>::table_offset(epb) + sizeof(int64_t) * (size_t)epb;
+    return PlaneLayout<T, D, Q>::table_offset(epb) + (sizeof(int64_t) + kGeoStride * sizeof(T)) * (size_t)epb;
+}
+
+// The geometry record of an element (J^-1 row-major, lambda detJ, mu detJ,
+// detJ; the PA data of Sec. 4.4 for an affine element) from the 9 entries
+// of its map's J, recomputed in the element kernel: the unassembled (UA)
+// evaluation of the data D that the paper contrasts with PA (Sec. 2).
+template <typename T>
+__device__ __forceinline__ void ua_record(const T *__restrict__ J, T lambda, T mu, T *rec)
+{
+    const T c0 = J[4] * J[8] - J[5] * J[7], c1 = J[5] * J[6] - J[3] * J[8], c2 = J[3] * J[7] - J[4] * J[6];
+    const T det = J[0] * c0 + J[1] * c1 + J[2] * c2;
+    const T id = T(1) / det;
+    rec[0] = c0 * id;
+    rec[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+    rec[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+    rec[3] = c1 * id;
+    rec[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+    rec[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+    rec[6] = c2 * id;
+    rec[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+    rec[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+    rec[9] = lambda * det;
+    rec[10] = mu * det;
+    rec[11] = det;
 }
 
 // Stage A for plane (el, c, iz): x-plane [iy][ix] in registers, then per qx
@@ -279,13 +305,21 @@ __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T
     const int64_t Nn = a.g.Nn;
     const int64_t Mx = a.g.Mx, MxMy = (int64_t)a.g.Mx * a.g.My;
     int64_t *gbase = reinterpret_cast<int64_t *>(smem_raw + L::table_offset(epb));
+    T *geo_s = reinterpret_cast<T *>(gbase + epb);  // the tile's geometry records
     for (int el = tid; el < ne_blk; el += nt) {
         const int64_t e = e0 + el;
         const int64_t t = e / a.g.nx;
         const int ex = (int)(e - t * a.g.nx), ey = (int)(t % a.g.ny), ez = (int)(t / a.g.ny);
         gbase[el] = (int64_t)ex * p + Mx * ((int64_t)ey * p) + MxMy * ((int64_t)ez * p);
+        if (a.ua) ua_record(a.geo + e * kUaStride, a.ua_lambda, a.ua_mu, geo_s + (size_t)el * kGeoStride);
     }
+    // stored records: one coalesced copy of the tile's records to shared
+    // memory, which the column threads read (measured at p = 1: 5.5 % less
+    // element time than each column thread loading its element's record)
+    if (!a.ua)
+        for (int k = tid; k < ne_blk * kGeoStride; k += nt) geo_s[k] = a.geo[e0 * kGeoStride + k];
     __syncthreads();
+    const T *geo0 = geo_s;  // the tile's geometry records
 
     // stage A: plane (el, c, iz) -> columns [qy][qx][c][k][iz]
     for (int o = tid; o < ne_blk * 3 * D; o += nt) {
@@ -298,9 +332,9 @@ __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T
     __syncthreads();
 
     // stage B: Z sweep, pointwise stress, Z^T sweep per column, in place
-    if constexpr (SPLIT) z_columns_split<T, D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
-    else if constexpr (sizeof(T) == 4) z_columns_f2<D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
-    else z_columns<T, D, Q, L::ROLL>(a, tab, buf, L::A, e0, ne_blk, tid, nt);
+    if constexpr (SPLIT) z_columns_split<T, D, Q, L::ROLL>(geo0, tab, buf, L::A, ne_blk, tid, nt);
+    else if constexpr (sizeof(T) == 4) z_columns_f2<D, Q, L::ROLL>(geo0, tab, buf, L::A, ne_blk, tid, nt);
+    else z_columns<T, D, Q, L::ROLL>(geo0, tab, buf, L::A, ne_blk, tid, nt);
     __syncthreads();
 
     // stage C: plane (el, c, iz) -> E-vector [e][c][iz][iy][ix]

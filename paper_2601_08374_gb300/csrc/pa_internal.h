@@ -113,6 +113,8 @@ inline void transpose_tables(Tables<T> &t, int D, int Q)
 // Geometry record per element (12 values of the op's precision):
 // J^-1 row-major (9), lambda*detJ, mu*detJ, detJ.
 constexpr int kGeoStride = 12;
+// UA geometry: J row-major per element.
+constexpr int kUaStride = 9;
 
 struct Grid {
     int nx, ny, nz, p;
@@ -170,6 +172,11 @@ struct ApplyArgs {
     long long wait_cycles = 4000000000LL;  // that wait's budget in SM clock cycles (about 2 s)
     T *qvec = nullptr;         // ablation stages only: quadrature values [ne][3][3][Q^3]
     const T *ctensor = nullptr;  // ablation stages only: elasticity tensor per element [ne][81]
+    // UA geometry (plane kernel): geo holds the 9 entries of each element's J
+    // [ne][kUaStride]; the records are recomputed in the kernel with the
+    // constant material (ua_lambda, ua_mu)
+    int ua = 0;
+    T ua_lambda = T(0), ua_mu = T(0);
 };
 
 template <typename T>
@@ -309,6 +316,8 @@ struct pa_op {
     std::vector<double> h_mat;     // per-element (lambda_e, mu_e), empty for the constant material
     std::vector<double> h_cv;      // per-element anisotropic 6x6 Voigt matrices [ne][36], empty if isotropic
     void *d_cv = nullptr;          // device copy: upper triangles times detJ [ne][21] in the op's precision
+    int geometry_mode = 0;         // PA_GEOMETRY_STORED or PA_GEOMETRY_UA
+    void *d_ua = nullptr;          // UA geometry: J per element [ne][9] in the op's precision
     int *d_err = nullptr;          // set when a tensor-core wait timed out (pa_op_check)
     long long wait_cycles = 4000000000LL;  // budget of those waits (pa_op_set_wait_limit)
     // ablation stages (pa_op_apply_stage), allocated on first use:

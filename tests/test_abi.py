@@ -86,6 +86,7 @@ def test_argument_checks_before_any_device_call(pa):
     t = ctypes.c_double()
     assert lib.pa_measure_fma_rate(7, ctypes.byref(t), None) == pa.PA_EINVAL
     assert lib.pa_measure_fma_rate(0, None, None) == pa.PA_EINVAL
+    assert lib.pa_op_set_geometry_mode(None, pa.PA_GEOMETRY_UA) == pa.PA_EINVAL
 
 
 def test_flop_model_reproduces_table6():
