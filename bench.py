@@ -884,7 +884,8 @@ def run_gmg_sweep(args):
     and 8), the power-iteration lambda_max of every smoothed level beside an
     80-step Lanczos estimate of the extreme eigenvalues of D^-1 A, and the
     iterations and solve time for Chebyshev degrees k and target intervals
-    [lo, hi] * lambda_max."""
+    [lo, hi] * lambda_max, for the first-kind Chebyshev smoother and the
+    fourth-kind one (upper end only)."""
     import torch
 
     import paper_2601_08374_gb300 as pa
@@ -900,6 +901,8 @@ def run_gmg_sweep(args):
                       (0.0, 0.0, 0.0), [pa.PA_SOLVE_MIXED_FCG]))
     ks = [int(v) for v in args.gmg_sweep_k.split(",")]
     intervals = [tuple(float(t) for t in iv.split(":")) for iv in args.gmg_sweep_intervals.split(",")]
+    kinds = [int(v) for v in args.gmg_sweep_kinds.split(",")]
+    lo_min = min(lo for lo, _ in intervals)
     for name, m, p, lv, nu, modes, f0, solve_modes in cases:
         lam, mu = syn.lame(1.0, nu)
         ess = syn.clamp_mask(m, p)
@@ -920,17 +923,22 @@ def run_gmg_sweep(args):
         for mode in solve_modes:
             for k in ks:
                 s = pa.pa_solver_create(op.h, lv, k, COARSE_RTOL, COARSE_MAXIT, mode)
-                for lo, hi in intervals:
-                    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_LOWER, lo)
-                    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_UPPER, hi)
-                    pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)  # captures the graphs
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    code, info = pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)
-                    dt = time.perf_counter() - t0
-                    row["sweep"].append({"mode": {0: "fp64", 2: "mixed_fcg"}[mode], "k": k, "lo": lo, "hi": hi,
-                                         "iterations": info.iterations, "status": int(code), "s": round(dt, 4),
-                                         "rho": round(info.rel_residual ** (1.0 / max(info.iterations, 1)), 4)})
+                for kind in kinds:
+                    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_KIND, kind)
+                    # the fourth kind has no lower end: one row per upper end
+                    ivs = intervals if kind == 1 else [(lo_min, hi) for hi in sorted({hi for _, hi in intervals})]
+                    for lo, hi in ivs:
+                        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_LOWER, lo)
+                        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_UPPER, hi)
+                        pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)  # captures the graphs
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        code, info = pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 2000)
+                        dt = time.perf_counter() - t0
+                        row["sweep"].append({"mode": {0: "fp64", 2: "mixed_fcg"}[mode], "kind": kind, "k": k,
+                                             "lo": lo if kind == 1 else 0.0, "hi": hi,
+                                             "iterations": info.iterations, "status": int(code), "s": round(dt, 4),
+                                             "rho": round(info.rel_residual ** (1.0 / max(info.iterations, 1)), 4)})
                 pa.pa_solver_destroy(s)
         out["cases"].append(row)
         op.close()
@@ -1035,6 +1043,8 @@ def main(argv=None):
                     help="diagnose the GMG-PCG iteration counts (eigenvalue estimates, Chebyshev degree/interval sweep) "
                          "instead of the benchmark")
     ap.add_argument("--gmg-sweep-k", default="1,2,3,4,5,6")
+    ap.add_argument("--gmg-sweep-kinds", default="1,4", help="Chebyshev kinds of the sweep (1: first kind on "
+                    "[lo, hi] * lambda_max, 4: fourth kind on [0, hi * lambda_max])")
     ap.add_argument("--gmg-sweep-intervals", default="0.3:1.2,0.1:1.2,0.05:1.2,0.02:1.2,0.01:1.2,0.05:1.1,0.3:1.5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-solve", action="store_true", help="skip the oracle's beam solve in cpu_baseline")

@@ -121,8 +121,8 @@ int pa_op_apply_add(pa_op *op, const void *x, void *y, void *stream);
  * that operator's own apply.  Other operators are grouped by (precision,
  * degree), one launch pair per group of up to 24 (tensor-core shapes run as
  * the register-tiled line variant there, so their bits differ from their
- * own apply, within the FP32 tolerance); anisotropic ones are applied one
- * by one.  No counterpart in the paper (it batches independent
+ * own apply, within the FP32 tolerance); anisotropic ones and ones with UA
+ * geometry are applied one by one.  No counterpart in the paper (it batches independent
  * applies of Sec. 4.2-4.5).  An operator may appear only once; x_k and y_k
  * must not alias. */
 int pa_op_apply_batch(pa_op *const *ops, const void *const *xs, void *const *ys, int count, void *stream);
@@ -425,6 +425,13 @@ int pa_solver_destroy(pa_solver *s);
  *    ten power iterations fall 8-17 % below lambda_max on the measured
  *    problems, and an upper end below lambda_max makes the smoother amplify
  *    the top modes.)
+ *  PA_SOLVER_OPT_CHEB_KIND (default 1): 1 -- the first-kind Chebyshev
+ *    iteration on [lower, upper] * lambda_max (the paper's smoother, Sec.
+ *    3.1); 4 -- the fourth-kind Chebyshev smoother on [0, upper *
+ *    lambda_max] (Lottes 2023; no lower bound: after k steps the residual
+ *    polynomial is W_k(1 - 2 lambda / (upper lambda_max)) / (2k + 1)).
+ *    Same steps and kernels, other coefficients.  Takes effect at the next
+ *    solve.  (Not in the paper: a smoother of this library.)
  *  PA_SOLVER_OPT_POWER_ITERS (default 10, Sec. 3.1): power iterations of
  *    the lambda_max estimates, 1..1000; setting it re-estimates every
  *    smoothed level at once (synchronous).
@@ -447,7 +454,8 @@ enum pa_solver_option {
     PA_SOLVER_OPT_CHEB_UPPER = 5,
     PA_SOLVER_OPT_POWER_ITERS = 6,
     PA_SOLVER_OPT_WAIT_LIMIT = 7,
-    PA_SOLVER_OPT_INJECT_INNER_FAILURE = 8
+    PA_SOLVER_OPT_INJECT_INNER_FAILURE = 8,
+    PA_SOLVER_OPT_CHEB_KIND = 9
 };
 int pa_solver_set_option(pa_solver *s, int option, double value);
 

@@ -422,6 +422,7 @@ PA_SOLVER_OPT_CHEB_UPPER = 5
 PA_SOLVER_OPT_POWER_ITERS = 6
 PA_SOLVER_OPT_WAIT_LIMIT = 7
 PA_SOLVER_OPT_INJECT_INNER_FAILURE = 8
+PA_SOLVER_OPT_CHEB_KIND = 9
 
 
 def pa_solver_set_option(h, option, value):

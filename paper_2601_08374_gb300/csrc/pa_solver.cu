@@ -33,7 +33,7 @@ FirstStep h_first_step(const HLevel &H)
     f.e = H.e;
     f.d = H.d;
     f.dinv = H.dinv;
-    f.cr = 1.0 / H.theta;
+    f.cr = H.cheb.cr[0];
     return f;
 }
 
@@ -51,20 +51,9 @@ FirstStep coarse_first_step(pa_solver *s) { return s->hl.size() > 1 ? h_first_st
 double *h_smooth(pa_solver *s, HLevel &H, double *e, bool from_zero, cudaStream_t st)
 {
     const int64_t n = H.n;
-    const double sigma = H.theta / H.delta;
-    double rho_prev = 1.0 / sigma;
     double *cur = e;
     for (int k = 0; k < s->cheb_order; ++k) {
-        double cd, cr;
-        if (k == 0) {
-            cd = 0.0;
-            cr = 1.0 / H.theta;
-        } else {
-            const double rho = 1.0 / (2.0 * sigma - rho_prev);
-            cd = rho * rho_prev;
-            cr = 2.0 * rho / H.delta;
-            rho_prev = rho;
-        }
+        const double cd = H.cheb.cd[k], cr = H.cheb.cr[k];
         if (k == 0 && from_zero) {
             continue;  // taken by the producer of H.r
         } else {
@@ -192,8 +181,6 @@ int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
     const int64_t n = L.n;
     T *e = LV<T>::e(L), *dv = LV<T>::d(L), *r = LV<T>::r(L), *t = LV<T>::t(L), *dinv = LV<T>::dinv(L);
     pa_op *op = LV<T>::op(L);
-    const double sigma = L.theta / L.delta;
-    double rho_prev = 1.0 / sigma;
     for (int k = 0; k < s->cheb_order; ++k) {
         const T *tt = nullptr;
         if (!(k == 0 && from_zero)) {
@@ -201,16 +188,7 @@ int smooth(pa_solver *s, Level &L, bool from_zero, cudaStream_t st)
             if (rc) return rc;
             tt = t;
         }
-        double cd, cr;
-        if (k == 0) {
-            cd = 0.0;
-            cr = 1.0 / L.theta;
-        } else {
-            double rho = 1.0 / (2.0 * sigma - rho_prev);
-            cd = rho * rho_prev;
-            cr = 2.0 * rho / L.delta;
-            rho_prev = rho;
-        }
+        const double cd = L.cheb.cd[k], cr = L.cheb.cr[k];
         if (emit(s))
             k_cheb<T><<<blocks_for(n), 256, 0, st>>>(e, dv, r, tt, dinv, cd, cr, (k == 0 && from_zero) ? 1 : 0, n);
     }

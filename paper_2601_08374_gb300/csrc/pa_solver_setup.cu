@@ -170,12 +170,44 @@ double read_scalar(pa_solver *s, int slot, cudaStream_t st)
     return s->h_scal[slot];
 }
 
-// Chebyshev centre and half-width of the interval [cheb_lo, cheb_hi] * lam
-void cheb_interval(const pa_solver *s, double lam, double *theta, double *delta)
+// Chebyshev centre and half-width of the interval [cheb_lo, cheb_hi] * lam,
+// and the coefficients of the smoothing steps (d = cd d + cr Dinv (r - A e),
+// e += d):
+//   kind 1: the first-kind Chebyshev iteration on [a, b] (three-term
+//     recurrence of Saad, Iterative Methods for Sparse Linear Systems,
+//     Sec. 12.3): cr_0 = 1/theta, then rho_k = 1 / (2 sigma - rho_(k-1)),
+//     cd_k = rho_k rho_(k-1), cr_k = 2 rho_k / delta, sigma = theta / delta;
+//   kind 4: the fourth-kind Chebyshev smoother on [0, b] (Lottes, Optimal
+//     polynomial smoothers for multigrid V-cycles, 2023): cr_0 = 4 / (3 b),
+//     cd_k = (2k - 1) / (2k + 3), cr_k = (8k + 4) / ((2k + 3) b); after m
+//     steps the residual polynomial is W_m(1 - 2 lambda / b) / (2m + 1), W_m
+//     the fourth-kind Chebyshev polynomial, which needs no lower bound.
+void cheb_interval(const pa_solver *s, double lam, double *theta, double *delta, ChebCoef *c)
 {
     const double a = s->cheb_lo * lam, b = s->cheb_hi * lam;
     *theta = 0.5 * (a + b);
     *delta = 0.5 * (b - a);
+    *c = ChebCoef{};
+    if (s->cheb_kind == 4) {
+        for (int k = 0; k < s->cheb_order && k < kMaxCheb; ++k) {
+            c->cd[k] = k == 0 ? 0.0 : (2.0 * k - 1.0) / (2.0 * k + 3.0);
+            c->cr[k] = k == 0 ? 4.0 / (3.0 * b) : (8.0 * k + 4.0) / ((2.0 * k + 3.0) * b);
+        }
+        return;
+    }
+    const double sigma = *theta / *delta;
+    double rho_prev = 1.0 / sigma;
+    for (int k = 0; k < s->cheb_order && k < kMaxCheb; ++k) {
+        if (k == 0) {
+            c->cd[k] = 0.0;
+            c->cr[k] = 1.0 / *theta;
+        } else {
+            const double rho = 1.0 / (2.0 * sigma - rho_prev);
+            c->cd[k] = rho * rho_prev;
+            c->cr[k] = 2.0 * rho / *delta;
+            rho_prev = rho;
+        }
+    }
 }
 
 // power iteration for lambda_max(D^-1 A) of level l (FP64), power_its (10 by
@@ -203,7 +235,7 @@ int estimate_lmax(pa_solver *s, Level &L, cudaStream_t st)
     }
     PA_CUDA_TRY(cudaGetLastError());
     L.lmax = lam;
-    cheb_interval(s, lam, &L.theta, &L.delta);
+    cheb_interval(s, lam, &L.theta, &L.delta, &L.cheb);
     return PA_OK;
 }
 
@@ -227,7 +259,7 @@ int h_power_lmax(pa_solver *s, HLevel &H, cudaStream_t st)
         k_scale_copy<double, double><<<blocks_for(n), 256, 0, st>>>(H.e, H.d, 1.0 / std::sqrt(num), n);
     }
     H.lmax = lam;
-    cheb_interval(s, lam, &H.theta, &H.delta);
+    cheb_interval(s, lam, &H.theta, &H.delta, &H.cheb);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
 }
@@ -654,8 +686,11 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
     }
     case PA_SOLVER_OPT_CHEB_LOWER:
     case PA_SOLVER_OPT_CHEB_UPPER:
+    case PA_SOLVER_OPT_CHEB_KIND:
     case PA_SOLVER_OPT_POWER_ITERS: {
-        if (option == PA_SOLVER_OPT_POWER_ITERS) {
+        if (option == PA_SOLVER_OPT_CHEB_KIND) {
+            if (value != 1.0 && value != 4.0) return set_error(PA_EINVAL, "pa_solver_set_option: Chebyshev kind 1 or 4");
+        } else if (option == PA_SOLVER_OPT_POWER_ITERS) {
             if (!(value >= 1.0 && value <= 1000.0)) return set_error(PA_EINVAL, "pa_solver_set_option: power iterations in 1..1000");
         } else {
             const double lo = option == PA_SOLVER_OPT_CHEB_LOWER ? value : s->cheb_lo;
@@ -671,6 +706,7 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
         }
         if (option == PA_SOLVER_OPT_CHEB_LOWER) s->cheb_lo = value;
         else if (option == PA_SOLVER_OPT_CHEB_UPPER) s->cheb_hi = value;
+        else if (option == PA_SOLVER_OPT_CHEB_KIND) s->cheb_kind = (int)value;
         else s->power_its = (int)value;
         cudaStream_t st = s->stream;
         // smoothed levels are the ones with an estimate (the assembled p = 1
@@ -680,7 +716,7 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
             if (option == PA_SOLVER_OPT_POWER_ITERS) {
                 if (int rc = estimate_lmax(s, L, st)) return rc;
             } else {
-                cheb_interval(s, L.lmax, &L.theta, &L.delta);
+                cheb_interval(s, L.lmax, &L.theta, &L.delta, &L.cheb);
             }
         }
         for (HLevel &H : s->hl) {
@@ -688,7 +724,7 @@ int pa_solver_set_option(pa_solver *s, int option, double value)
             if (option == PA_SOLVER_OPT_POWER_ITERS) {
                 if (int rc = h_power_lmax(s, H, st)) return rc;
             } else {
-                cheb_interval(s, H.lmax, &H.theta, &H.delta);
+                cheb_interval(s, H.lmax, &H.theta, &H.delta, &H.cheb);
             }
         }
         PA_CUDA_TRY(cudaStreamSynchronize(st));

@@ -40,6 +40,13 @@ struct XferTab {
     double L[kMaxD * kMaxD];
 };
 
+// Coefficients of the cheb_order smoothing steps of a level: step k sets
+// d = cd[k] d + cr[k] Dinv (r - A e), then e += d (cd[0] = 0).
+constexpr int kMaxCheb = 8;
+struct ChebCoef {
+    double cd[kMaxCheb] = {}, cr[kMaxCheb] = {};
+};
+
 // ---------------------------------------------------------------- levels --
 struct Level {
     int p = 0;
@@ -58,6 +65,7 @@ struct Level {
     bool hdown = false;  // the next level is this mesh coarsened once (p = 1 both), not a lower degree
     double lmax = 0.0;
     double theta = 0.0, delta = 0.0;
+    ChebCoef cheb{};  // smoothing-step coefficients
     // coarse CG vectors
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr;
     double *stencil = nullptr;  // assembled p = 1 coarse matrix (81 planes of n), or null
@@ -74,6 +82,7 @@ struct HLevel {
     double *e2 = nullptr;       // second iterate buffer of the fused smoothing steps
     double *xa = nullptr, *xb = nullptr;  // transfer temporaries (size of this level)
     double theta = 0.0, delta = 0.0, lmax = 0.0;
+    ChebCoef cheb{};            // smoothing-step coefficients
     double *Ainv = nullptr;     // dense inverse on the coarsest level
 };
 
@@ -102,6 +111,7 @@ struct pa_solver {
     // Chebyshev target interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A) and
     // the power iterations that estimate lambda_max
     double cheb_lo = 0.05, cheb_hi = 1.2;
+    int cheb_kind = 1;  // 1: first-kind Chebyshev on the interval, 4: fourth kind on [0, cheb_hi]
     int power_its = 10;
     // bound of the persistent coarse kernel's grid-barrier waits, in SM
     // clock cycles (2 s at the device's clock by default)

@@ -565,3 +565,63 @@ def test_lockstep_members_of_any_hierarchy(pa):
         pa.pa_solver_destroy(s)
     for op in ops:
         op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("h_levels", [0, 1])
+def test_fourth_kind_chebyshev_against_oracle_solve(pa, mode, h_levels):
+    """The fourth-kind Chebyshev smoother (PA_SOLVER_OPT_CHEB_KIND = 4, on
+    the p-levels and the h-levels alike) on the beam and on the p = 6
+    nu = 0.45 cube of the mixed configuration at a size the host can factor:
+    every mode within 1e-8 of the oracle's direct solve, in no more outer
+    iterations than a fixed bound; switching back to the first kind gives
+    the first kind's iteration count again."""
+    lam, mu = syn.lame(1.0, 0.3)
+    m = _beam(16, 2, 2)
+    p = 4
+    ess = syn.clamp_mask(m, p)
+    bo = oracle.load(p, m.nx, m.ny, m.nz, m.affine, f0=(0.0, 0.0, -1.0), ess=ess)
+    xo, res = oracle.solve_sparse(p, m.nx, m.ny, m.nz, m.affine, lam, mu, bo, ess)
+    assert res <= 1e-9  # the beam's FP64 floor (measured 2.1e-10)
+    op = pa.Operator(m.nx, m.ny, m.nz, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(f0=(0.0, 0.0, -1.0))
+    s = pa.pa_solver_create_hp(op.h, [4, 2, 1], h_levels, 4, 1e-2, 10, mode)
+    x = torch.zeros_like(b)
+    code1, info1 = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 500)
+    assert code1 == pa.PA_OK
+    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_KIND, 4)
+    code, info = pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 500)
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, (mode, h_levels, err)
+    assert info.iterations <= 40
+    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_KIND, 1)
+    code, info_back = pa.pa_gmg_pcg_solve(s, b, x.zero_(), 1e-10, 500)
+    assert code == pa.PA_OK and info_back.iterations == info1.iterations
+    with pytest.raises(pa.PAError):
+        pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_KIND, 2)
+    pa.pa_solver_destroy(s)
+    op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_fourth_kind_chebyshev_cube_p6(pa, mode):
+    p, n = 6, 2
+    m = syn.random_affine_cube(n, seed=3000 + p)
+    lam, mu = syn.lame(1.0, 0.45)
+    ess = syn.clamp_mask(m, p)
+    modes = syn.smooth_force_modes(seed=3100 + p)
+    bo = oracle.load(p, n, n, n, m.affine, modes=modes, ess=ess)
+    xo, res = oracle.solve_sparse(p, n, n, n, m.affine, lam, mu, bo, ess)
+    assert res <= 1e-12
+    op = pa.Operator(n, n, n, m.affine, p, lam, mu, ess_mask=ess)
+    b = op.rhs(modes=modes)
+    s = pa.pa_solver_create(op.h, [6, 3, 1], 4, 1e-2, 10, mode)
+    pa.pa_solver_set_option(s, pa.PA_SOLVER_OPT_CHEB_KIND, 4)
+    x = torch.zeros_like(b)
+    code, info = pa.pa_gmg_pcg_solve(s, b, x, 1e-10, 1000)
+    pa.pa_solver_destroy(s)
+    op.close()
+    assert code == pa.PA_OK, pa.lib.pa_last_error()
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    assert err <= 1e-8, (mode, err)
