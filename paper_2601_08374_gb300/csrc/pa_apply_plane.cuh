@@ -322,8 +322,20 @@ __device__ __forceinline__ void plane_body(const ApplyArgs<T> &a, const Tables<T
     const T *geo0 = geo_s;  // the tile's geometry records
 
     // stage A: plane (el, c, iz) -> columns [qy][qx][c][k][iz]
+    // from p = 2 on the element index varies fastest across the threads, so
+    // that neighbouring lanes gather neighbouring nodes of x (measured: p = 3
+    // 3-5 %, p = 2, 4 1-2 % faster than the plane index fastest); at p = 1
+    // with 32 elements per CTA that order puts two lanes on one shared-memory
+    // bank in the column stores, and the plane index stays fastest
     for (int o = tid; o < ne_blk * 3 * D; o += nt) {
-        const int el = o / (3 * D), r = o - el * 3 * D;
+        int el, r;
+        if constexpr (D >= 3) {
+            r = o / ne_blk;
+            el = o - r * ne_blk;
+        } else {
+            el = o / (3 * D);
+            r = o - el * 3 * D;
+        }
         const int c = r / D, iz = r - c * D;
         T *cb = buf + (size_t)el * L::A + c * 3 * D + iz;
         if constexpr (sizeof(T) == 4) plane_forward_f2<D, Q>(a, tab, cb, c * Nn + gbase[el] + MxMy * iz, Mx);
