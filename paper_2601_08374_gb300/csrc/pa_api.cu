@@ -87,8 +87,8 @@ int upload_geometry(pa_op *op)
 ApplyLaunch default_apply_launch(int p, int precision)
 {
     static const int v64[kMaxP + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    static const int epb64[kMaxP + 1] = {0, 32, 6, 6, 4, 2, 1, 1, 1};
-    static const int thr64[kMaxP + 1] = {0, 384, 128, 256, 256, 256, 128, 256, 512};
+    static const int epb64[kMaxP + 1] = {0, 32, 12, 6, 4, 2, 1, 1, 1};
+    static const int thr64[kMaxP + 1] = {0, 384, 256, 256, 256, 256, 256, 256, 512};
     static const int v32[kMaxP + 1] = {0, 5, 5, 5, 5, 2, 2, 2, 3};
     static const int epb32[kMaxP + 1] = {0, 32, 16, 8, 8, 2, 2, 1, 1};
     static const int thr32[kMaxP + 1] = {0, 96, 96, 96, 96, 128, 128, 96, 96};
